@@ -1,0 +1,965 @@
+/*
+ * elder_oracle.c -- plain FP64 CPU oracle (test infrastructure only; see
+ * elder_oracle.h).  Every function is written for clarity, element by
+ * element, following the paper's model (Section 2.1) and discretisation
+ * (Section 2.3, Section 5.1); none of it is tuned.
+ */
+#include "elder_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* grid helpers                                                             */
+/* ------------------------------------------------------------------------ */
+
+int orc_num_nodes(const orc_problem* P)
+{
+    return (P->nx + 1) * (P->ny + 1) * (P->nz + 1);
+}
+
+int orc_num_cells(const orc_problem* P) { return P->nx * P->ny * P->nz; }
+
+static int node_id(const orc_problem* P, int i, int j, int k)
+{
+    return i + (P->nx + 1) * (j + (P->ny + 1) * k);
+}
+
+static double rho_of(const orc_problem* P, double c)
+{
+    /* eq. e_lin_density */
+    return P->rho0 + (P->rho1 - P->rho0) * c;
+}
+
+/* Dirichlet sets of Section 2.1 / Fig. 1 (see the bc_mode list in the
+ * header).  The top square is closed: 4*i in [nx, 3*nx]. */
+void orc_dirichlet(const orc_problem* P, unsigned char* pmask,
+                   unsigned char* cmask, double* cval)
+{
+    for (int k = 0; k <= P->nz; ++k)
+        for (int j = 0; j <= P->ny; ++j)
+            for (int i = 0; i <= P->nx; ++i) {
+                int n = node_id(P, i, j, k);
+                int top = (k == P->nz), bottom = (k == 0);
+                int xedge = (i == 0 || i == P->nx);
+                int yedge = (j == 0 || j == P->ny);
+                int in_sq = (4 * i >= P->nx && 4 * i <= 3 * P->nx &&
+                             4 * j >= P->ny && 4 * j <= 3 * P->ny);
+                unsigned char pm = 0, cm = 0;
+                double cv = 0.0;
+                switch (P->bc_mode) {
+                case 0:
+                    pm = top && xedge && yedge;
+                    if (top && in_sq) { cm = 1; cv = 1.0; }
+                    else if (bottom) { cm = 1; cv = 0.0; }
+                    break;
+                case 1:
+                    pm = top && (xedge || yedge);
+                    if (top) { cm = 1; cv = in_sq ? 1.0 : 0.0; }
+                    else if (bottom) { cm = 1; cv = 0.0; }
+                    break;
+                case 2:
+                    pm = top && xedge && yedge;
+                    if (top) { cm = 1; cv = 1.0; }
+                    else if (bottom) { cm = 1; cv = 0.0; }
+                    break;
+                default:
+                    pm = top && xedge && yedge;
+                    break;
+                }
+                if (pmask) pmask[n] = pm;
+                if (cmask) cmask[n] = cm;
+                if (cval) cval[n] = cv;
+            }
+}
+
+void orc_initial_state(const orc_problem* P, double* p, double* c)
+{
+    int N = orc_num_nodes(P);
+    unsigned char* cm = (unsigned char*)malloc((size_t)N);
+    double* cv = (double*)malloc(sizeof(double) * (size_t)N);
+    orc_dirichlet(P, NULL, cm, cv);
+    double hz = P->Lz / P->nz;
+    for (int k = 0; k <= P->nz; ++k)
+        for (int j = 0; j <= P->ny; ++j)
+            for (int i = 0; i <= P->nx; ++i) {
+                int n = node_id(P, i, j, k);
+                p[n] = P->rho0 * P->g * (P->Lz - k * hz);
+                c[n] = cm[n] ? cv[n] : 0.0;
+            }
+    free(cm);
+    free(cv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* one sub-control-volume face of one hexahedron                            */
+/* ------------------------------------------------------------------------ */
+
+/* Corner L = a + 2b + 4cz of cell (i,j,k) is node (i+a, j+b, k+cz). */
+static void cell_corners(const orc_problem* P, int i, int j, int k,
+                         int nodes[8])
+{
+    for (int L = 0; L < 8; ++L)
+        nodes[L] = node_id(P, i + (L & 1), j + ((L >> 1) & 1),
+                           k + ((L >> 2) & 1));
+}
+
+/* Trilinear (Q1) shape functions of the unit cube and their derivative
+ * along direction d (divided by the cell size h_d) at local point X[3]. */
+static void q1_at(const double X[3], int d, double h_d, double N[8],
+                  double dN[8])
+{
+    for (int L = 0; L < 8; ++L) {
+        int a[3] = {L & 1, (L >> 1) & 1, (L >> 2) & 1};
+        double f[3], df[3];
+        for (int m = 0; m < 3; ++m) {
+            f[m] = a[m] ? X[m] : 1.0 - X[m];
+            df[m] = a[m] ? 1.0 : -1.0;
+        }
+        N[L] = f[0] * f[1] * f[2];
+        double g = 1.0;
+        for (int m = 0; m < 3; ++m) g *= (m == d) ? df[m] : f[m];
+        dN[L] = g / h_d;
+    }
+}
+
+/* The box method splits each hexahedron into 8 sub-control volumes and has
+ * 12 sub-control-volume faces, one per cell edge.  The face of the edge
+ * along direction d whose transverse local position is (s,t) lies in the
+ * mid-plane of the edge; its integration point sits at 1/2 along d and at
+ * 1/4 or 3/4 across, its area is a quarter of the cell cross-section and its
+ * normal points from corner "a" (local coordinate 0 along d) to corner "b". */
+typedef struct {
+    int La, Lb;          /* local corners of the edge                  */
+    double N[8], dN[8];  /* shape values and d-derivatives at the ip   */
+    double A;            /* face area                                  */
+    int d;
+} scvf;
+
+static void make_scvf(const orc_problem* P, int d, int s, int t, scvf* f)
+{
+    double h[3] = {P->Lx / P->nx, P->Ly / P->ny, P->Lz / P->nz};
+    int t1 = (d == 0) ? 1 : 0;
+    int t2 = (d == 2) ? 1 : 2;
+    int ca[3] = {0, 0, 0};
+    ca[t1] = s;
+    ca[t2] = t;
+    int cb[3] = {ca[0], ca[1], ca[2]};
+    cb[d] = 1;
+    f->La = ca[0] + 2 * ca[1] + 4 * ca[2];
+    f->Lb = cb[0] + 2 * cb[1] + 4 * cb[2];
+    double X[3];
+    X[d] = 0.5;
+    X[t1] = s ? 0.75 : 0.25;
+    X[t2] = t ? 0.75 : 0.25;
+    q1_at(X, d, h[d], f->N, f->dN);
+    f->A = 0.25 * h[t1] * h[t2];
+    f->d = d;
+}
+
+/* Flux quantities through one face (eq. e_Darcy_vel with g = (0,0,-g)). */
+typedef struct {
+    double rho_ip, qn, m, F, gradc, cup;
+    int up;              /* local corner that supplies the upwind c */
+} face_flux;
+
+static void eval_face(const orc_problem* P, const scvf* f, double phi_e,
+                      double K_e, const double pl[8], const double cl[8],
+                      face_flux* out)
+{
+    double gradp = 0.0, gradc = 0.0, c_ip = 0.0, rhog = 0.0;
+    for (int L = 0; L < 8; ++L) {
+        gradp += pl[L] * f->dN[L];
+        gradc += cl[L] * f->dN[L];
+        c_ip += f->N[L] * cl[L];
+    }
+    /* Gravity: the Q1 interpolant of rho(c) times the z component of the
+     * gravity vector (0,0,-g); horizontal faces see none. */
+    if (f->d == 2) {
+        double rho_interp = 0.0;
+        for (int L = 0; L < 8; ++L) rho_interp += f->N[L] * rho_of(P, cl[L]);
+        rhog = -P->g * rho_interp;
+    }
+    double rho_ip = rho_of(P, c_ip);
+    double qn = -(K_e / P->mu) * (gradp - rhog);
+    double m = rho_ip * qn * f->A;
+    int up = (m >= 0.0) ? f->La : f->Lb;
+    double cup = cl[up];
+    out->rho_ip = rho_ip;
+    out->qn = qn;
+    out->m = m;
+    out->gradc = gradc;
+    out->cup = cup;
+    out->up = up;
+    out->F = cup * m - rho_ip * phi_e * P->Dm * gradc * f->A;
+}
+
+/* ------------------------------------------------------------------------ */
+/* residual                                                                 */
+/* ------------------------------------------------------------------------ */
+
+void orc_residual(const orc_problem* P, const double* phi, const double* K,
+                  const double* p, const double* c, const double* p_old,
+                  const double* c_old, double dt, int apply_dirichlet,
+                  double* Rp, double* Rc)
+{
+    (void)p_old; /* p has no time derivative */
+    int N = orc_num_nodes(P);
+    double vscv = (P->Lx / P->nx) * (P->Ly / P->ny) * (P->Lz / P->nz) / 8.0;
+    memset(Rp, 0, sizeof(double) * (size_t)N);
+    memset(Rc, 0, sizeof(double) * (size_t)N);
+    scvf faces[12];
+    int nf = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 2; ++t) make_scvf(P, d, s, t, &faces[nf++]);
+
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                int e = i + P->nx * (j + P->ny * k);
+                int nodes[8];
+                cell_corners(P, i, j, k, nodes);
+                double pl[8], cl[8];
+                for (int L = 0; L < 8; ++L) {
+                    pl[L] = p[nodes[L]];
+                    cl[L] = c[nodes[L]];
+                }
+                /* lumped storage, implicit Euler (eqs. e_cont_eq/e_tran_eq) */
+                for (int L = 0; L < 8; ++L) {
+                    int n = nodes[L];
+                    double rn = rho_of(P, c[n]), ro = rho_of(P, c_old[n]);
+                    Rp[n] += phi[e] * vscv * (rn - ro) / dt;
+                    Rc[n] += phi[e] * vscv * (rn * c[n] - ro * c_old[n]) / dt;
+                }
+                /* face fluxes: out of corner a, into corner b */
+                for (int q = 0; q < 12; ++q) {
+                    face_flux ff;
+                    eval_face(P, &faces[q], phi[e], K[e], pl, cl, &ff);
+                    int a = nodes[faces[q].La], b = nodes[faces[q].Lb];
+                    Rp[a] += ff.m;
+                    Rp[b] -= ff.m;
+                    Rc[a] += ff.F;
+                    Rc[b] -= ff.F;
+                }
+            }
+    if (apply_dirichlet) {
+        unsigned char* pm = (unsigned char*)malloc((size_t)N);
+        unsigned char* cm = (unsigned char*)malloc((size_t)N);
+        double* cv = (double*)malloc(sizeof(double) * (size_t)N);
+        orc_dirichlet(P, pm, cm, cv);
+        for (int n = 0; n < N; ++n) {
+            if (pm[n]) Rp[n] = p[n];
+            if (cm[n]) Rc[n] = c[n] - cv[n];
+        }
+        free(pm);
+        free(cm);
+        free(cv);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Jacobian                                                                 */
+/* ------------------------------------------------------------------------ */
+
+int orc_jac_nnz(const orc_problem* P)
+{
+    int nnz = 0;
+    for (int k = 0; k <= P->nz; ++k)
+        for (int j = 0; j <= P->ny; ++j)
+            for (int i = 0; i <= P->nx; ++i) {
+                int cnt = 0;
+                for (int dk = -1; dk <= 1; ++dk)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int di = -1; di <= 1; ++di) {
+                            int ii = i + di, jj = j + dj, kk = k + dk;
+                            if (ii >= 0 && ii <= P->nx && jj >= 0 &&
+                                jj <= P->ny && kk >= 0 && kk <= P->nz)
+                                ++cnt;
+                        }
+                nnz += 2 * 2 * cnt;
+            }
+    return nnz;
+}
+
+void orc_jac_pattern(const orc_problem* P, int* rowptr, int* col)
+{
+    int pos = 0;
+    for (int k = 0; k <= P->nz; ++k)
+        for (int j = 0; j <= P->ny; ++j)
+            for (int i = 0; i <= P->nx; ++i) {
+                int n = node_id(P, i, j, k);
+                for (int v = 0; v < 2; ++v) {
+                    rowptr[2 * n + v] = pos;
+                    /* neighbours in ascending node order: k, then j, then i */
+                    for (int dk = -1; dk <= 1; ++dk)
+                        for (int dj = -1; dj <= 1; ++dj)
+                            for (int di = -1; di <= 1; ++di) {
+                                int ii = i + di, jj = j + dj, kk = k + dk;
+                                if (ii < 0 || ii > P->nx || jj < 0 ||
+                                    jj > P->ny || kk < 0 || kk > P->nz)
+                                    continue;
+                                int m = node_id(P, ii, jj, kk);
+                                col[pos++] = 2 * m;
+                                col[pos++] = 2 * m + 1;
+                            }
+                }
+            }
+    rowptr[2 * orc_num_nodes(P)] = pos;
+}
+
+static void csr_add(const int* rowptr, const int* col, double* val, int r,
+                    int cidx, double v)
+{
+    for (int q = rowptr[r]; q < rowptr[r + 1]; ++q)
+        if (col[q] == cidx) {
+            val[q] += v;
+            return;
+        }
+    /* not reached for a pattern built by orc_jac_pattern */
+    abort();
+}
+
+void orc_jacobian(const orc_problem* P, const double* phi, const double* K,
+                  const double* p, const double* c, double dt,
+                  const int* rowptr, const int* col, double* val)
+{
+    int N = orc_num_nodes(P);
+    double drho = P->rho1 - P->rho0;
+    double vscv = (P->Lx / P->nx) * (P->Ly / P->ny) * (P->Lz / P->nz) / 8.0;
+    memset(val, 0, sizeof(double) * (size_t)rowptr[2 * N]);
+    scvf faces[12];
+    int nf = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 2; ++t) make_scvf(P, d, s, t, &faces[nf++]);
+
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                int e = i + P->nx * (j + P->ny * k);
+                int nodes[8];
+                cell_corners(P, i, j, k, nodes);
+                double pl[8], cl[8];
+                for (int L = 0; L < 8; ++L) {
+                    pl[L] = p[nodes[L]];
+                    cl[L] = c[nodes[L]];
+                }
+                /* storage derivatives (diagonal in the node) */
+                for (int L = 0; L < 8; ++L) {
+                    int n = nodes[L];
+                    double dSp = phi[e] * vscv * drho / dt;
+                    double dSc = phi[e] * vscv *
+                                 (rho_of(P, c[n]) + drho * c[n]) / dt;
+                    csr_add(rowptr, col, val, 2 * n, 2 * n + 1, dSp);
+                    csr_add(rowptr, col, val, 2 * n + 1, 2 * n + 1, dSc);
+                }
+                for (int q = 0; q < 12; ++q) {
+                    const scvf* f = &faces[q];
+                    face_flux ff;
+                    eval_face(P, f, phi[e], K[e], pl, cl, &ff);
+                    int a = nodes[f->La], b = nodes[f->Lb];
+                    double kmu = K[e] / P->mu;
+                    for (int L = 0; L < 8; ++L) {
+                        /* dm/dp_L and dm/dc_L */
+                        double dm_dp = ff.rho_ip * (-kmu) * f->dN[L] * f->A;
+                        double dqn_dc = 0.0;
+                        if (f->d == 2) /* d(rho g_z)/dc_L = -g N_L drho */
+                            dqn_dc = -kmu * (P->g * f->N[L] * drho);
+                        double dm_dc = drho * f->N[L] * ff.qn * f->A +
+                                       ff.rho_ip * dqn_dc * f->A;
+                        double dF_dp = ff.cup * dm_dp;
+                        double dF_dc = ff.cup * dm_dc +
+                                       (L == ff.up ? ff.m : 0.0) -
+                                       drho * f->N[L] * phi[e] * P->Dm *
+                                           ff.gradc * f->A -
+                                       ff.rho_ip * phi[e] * P->Dm * f->dN[L] *
+                                           f->A;
+                        int cp = 2 * nodes[L], cc = 2 * nodes[L] + 1;
+                        csr_add(rowptr, col, val, 2 * a, cp, dm_dp);
+                        csr_add(rowptr, col, val, 2 * a, cc, dm_dc);
+                        csr_add(rowptr, col, val, 2 * b, cp, -dm_dp);
+                        csr_add(rowptr, col, val, 2 * b, cc, -dm_dc);
+                        csr_add(rowptr, col, val, 2 * a + 1, cp, dF_dp);
+                        csr_add(rowptr, col, val, 2 * a + 1, cc, dF_dc);
+                        csr_add(rowptr, col, val, 2 * b + 1, cp, -dF_dp);
+                        csr_add(rowptr, col, val, 2 * b + 1, cc, -dF_dc);
+                    }
+                }
+            }
+    /* Dirichlet rows: R = u - u_D, so the row is the identity. */
+    unsigned char* pm = (unsigned char*)malloc((size_t)N);
+    unsigned char* cm = (unsigned char*)malloc((size_t)N);
+    orc_dirichlet(P, pm, cm, NULL);
+    for (int n = 0; n < N; ++n)
+        for (int v = 0; v < 2; ++v) {
+            if (!(v == 0 ? pm[n] : cm[n])) continue;
+            int r = 2 * n + v;
+            for (int q = rowptr[r]; q < rowptr[r + 1]; ++q)
+                val[q] = (col[q] == r) ? 1.0 : 0.0;
+        }
+    free(pm);
+    free(cm);
+}
+
+void orc_csr_transpose(int n, const int* rowptr, const int* col,
+                       const double* val, int* trowptr, int* tcol,
+                       double* tval)
+{
+    int nnz = rowptr[n];
+    int* cnt = (int*)calloc((size_t)n + 1, sizeof(int));
+    for (int q = 0; q < nnz; ++q) cnt[col[q] + 1]++;
+    for (int r = 0; r < n; ++r) cnt[r + 1] += cnt[r];
+    memcpy(trowptr, cnt, sizeof(int) * ((size_t)n + 1));
+    for (int r = 0; r < n; ++r)
+        for (int q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+            int dst = cnt[col[q]]++;
+            tcol[dst] = r;
+            tval[dst] = val[q];
+        }
+    free(cnt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* linear solvers                                                           */
+/* ------------------------------------------------------------------------ */
+
+int orc_dense_solve(int n, double* A, double* b)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = fabs(A[(size_t)k * n + k]);
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(A[(size_t)r * n + k]) > best) {
+                best = fabs(A[(size_t)r * n + k]);
+                piv = r;
+            }
+        if (best == 0.0) return 1;
+        if (piv != k) {
+            for (int cidx = 0; cidx < n; ++cidx) {
+                double tmp = A[(size_t)k * n + cidx];
+                A[(size_t)k * n + cidx] = A[(size_t)piv * n + cidx];
+                A[(size_t)piv * n + cidx] = tmp;
+            }
+            double tb = b[k];
+            b[k] = b[piv];
+            b[piv] = tb;
+        }
+        for (int r = k + 1; r < n; ++r) {
+            double l = A[(size_t)r * n + k] / A[(size_t)k * n + k];
+            if (l == 0.0) continue;
+            for (int cidx = k; cidx < n; ++cidx)
+                A[(size_t)r * n + cidx] -= l * A[(size_t)k * n + cidx];
+            b[r] -= l * b[k];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int cidx = r + 1; cidx < n; ++cidx)
+            s -= A[(size_t)r * n + cidx] * b[cidx];
+        b[r] = s / A[(size_t)r * n + r];
+    }
+    return 0;
+}
+
+static void csr_matvec(int n, const int* rowptr, const int* col,
+                       const double* val, const double* x, double* y)
+{
+    for (int r = 0; r < n; ++r) {
+        double s = 0.0;
+        for (int q = rowptr[r]; q < rowptr[r + 1]; ++q) s += val[q] * x[col[q]];
+        y[r] = s;
+    }
+}
+
+static double dot(int n, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* ILU(0): incomplete LU restricted to the pattern of A (Saad, Iterative
+ * Methods for Sparse Linear Systems, Alg. 10.4).  lu holds L (unit lower,
+ * strictly below the diagonal) and U. */
+static void ilu0(int n, const int* rowptr, const int* col, const double* val,
+                 double* lu, int* diag)
+{
+    memcpy(lu, val, sizeof(double) * (size_t)rowptr[n]);
+    int* pos = (int*)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) pos[i] = -1;
+    for (int i = 0; i < n; ++i) {
+        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+            pos[col[q]] = q;
+            if (col[q] == i) diag[i] = q;
+        }
+        for (int q = rowptr[i]; q < rowptr[i + 1] && col[q] < i; ++q) {
+            int kk = col[q];
+            lu[q] /= lu[diag[kk]];
+            for (int r = diag[kk] + 1; r < rowptr[kk + 1]; ++r) {
+                int jj = col[r];
+                if (pos[jj] >= 0) lu[pos[jj]] -= lu[q] * lu[r];
+            }
+        }
+        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) pos[col[q]] = -1;
+    }
+    free(pos);
+}
+
+static void ilu0_apply(int n, const int* rowptr, const int* col,
+                       const double* lu, const int* diag, const double* r,
+                       double* z)
+{
+    for (int i = 0; i < n; ++i) {
+        double s = r[i];
+        for (int q = rowptr[i]; q < diag[i]; ++q) s -= lu[q] * z[col[q]];
+        z[i] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = z[i];
+        for (int q = diag[i] + 1; q < rowptr[i + 1]; ++q) s -= lu[q] * z[col[q]];
+        z[i] = s / lu[diag[i]];
+    }
+}
+
+/* BiCGStab of van der Vorst, right preconditioned (Barrett et al.,
+ * Templates, Sec. 2.3.8). */
+int orc_bicgstab_ilu0(int n, const int* rowptr, const int* col,
+                      const double* val, const double* b, double* x,
+                      double rtol, int maxit, int* iters, double* relres)
+{
+    size_t sz = sizeof(double) * (size_t)n;
+    double* lu = (double*)malloc(sizeof(double) * (size_t)rowptr[n]);
+    int* diag = (int*)malloc(sizeof(int) * (size_t)n);
+    ilu0(n, rowptr, col, val, lu, diag);
+    double *r = malloc(sz), *rh = malloc(sz), *pv = malloc(sz), *v = malloc(sz),
+           *s = malloc(sz), *t = malloc(sz), *ph = malloc(sz), *sh = malloc(sz);
+    csr_matvec(n, rowptr, col, val, x, r);
+    for (int i = 0; i < n; ++i) {
+        r[i] = b[i] - r[i];
+        rh[i] = r[i];
+        pv[i] = v[i] = 0.0;
+    }
+    double bn = sqrt(dot(n, b, b));
+    if (bn == 0.0) bn = 1.0;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    double rn = sqrt(dot(n, r, r));
+    int it = 0, ok = (rn <= rtol * bn);
+    while (!ok && it < maxit) {
+        ++it;
+        double rho = dot(n, rh, r);
+        if (rho == 0.0) break;
+        double beta = (rho / rho_old) * (alpha / omega);
+        for (int i = 0; i < n; ++i) pv[i] = r[i] + beta * (pv[i] - omega * v[i]);
+        ilu0_apply(n, rowptr, col, lu, diag, pv, ph);
+        csr_matvec(n, rowptr, col, val, ph, v);
+        double rv = dot(n, rh, v);
+        if (rv == 0.0) break;
+        alpha = rho / rv;
+        for (int i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+        if (sqrt(dot(n, s, s)) <= rtol * bn) {
+            for (int i = 0; i < n; ++i) x[i] += alpha * ph[i];
+            ok = 1;
+            break;
+        }
+        ilu0_apply(n, rowptr, col, lu, diag, s, sh);
+        csr_matvec(n, rowptr, col, val, sh, t);
+        double tt = dot(n, t, t);
+        omega = (tt > 0.0) ? dot(n, t, s) / tt : 0.0;
+        for (int i = 0; i < n; ++i) {
+            x[i] += alpha * ph[i] + omega * sh[i];
+            r[i] = s[i] - omega * t[i];
+        }
+        rho_old = rho;
+        rn = sqrt(dot(n, r, r));
+        if (rn <= rtol * bn) ok = 1;
+        if (omega == 0.0) break;
+    }
+    /* report the true residual */
+    csr_matvec(n, rowptr, col, val, x, r);
+    for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    double tr = sqrt(dot(n, r, r)) / bn;
+    if (iters) *iters = it;
+    if (relres) *relres = tr;
+    free(lu); free(diag); free(r); free(rh); free(pv); free(v); free(s);
+    free(t); free(ph); free(sh);
+    return (tr <= 10.0 * rtol) ? 0 : 1;
+}
+
+int orc_linear_solve(int n, const int* rowptr, const int* col,
+                     const double* val, const double* b, double* x,
+                     const orc_newton_opts* o, int* iters)
+{
+    if (n <= o->dense_max) {
+        double* A = (double*)calloc((size_t)n * n, sizeof(double));
+        for (int r = 0; r < n; ++r)
+            for (int q = rowptr[r]; q < rowptr[r + 1]; ++q)
+                A[(size_t)r * n + col[q]] += val[q];
+        memcpy(x, b, sizeof(double) * (size_t)n);
+        int rc = orc_dense_solve(n, A, x);
+        free(A);
+        if (iters) *iters = 0;
+        return rc;
+    }
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    double rr;
+    return orc_bicgstab_ilu0(n, rowptr, col, val, b, x, o->lin_rtol,
+                             o->lin_maxit, iters, &rr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Newton with line search (Section 2.3, Section 5.1)                       */
+/* ------------------------------------------------------------------------ */
+
+static double norm2_pair(int N, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) s += a[n] * a[n] + b[n] * b[n];
+    return sqrt(s);
+}
+
+int orc_newton_step(const orc_problem* P, const double* phi, const double* K,
+                    double* p, double* c, double dt,
+                    const orc_newton_opts* o, orc_step_info* info)
+{
+    int N = orc_num_nodes(P);
+    int n2 = 2 * N;
+    size_t sz = sizeof(double) * (size_t)N;
+    double *p_old = malloc(sz), *c_old = malloc(sz), *Rp = malloc(sz),
+           *Rc = malloc(sz), *pt = malloc(sz), *ct = malloc(sz),
+           *Rpt = malloc(sz), *Rct = malloc(sz);
+    double* rhs = malloc(2 * sz);
+    double* du = malloc(2 * sz);
+    unsigned char* pm = malloc((size_t)N);
+    unsigned char* cm = malloc((size_t)N);
+    double* cv = malloc(sz);
+    orc_dirichlet(P, pm, cm, cv);
+    memcpy(p_old, p, sz);
+    memcpy(c_old, c, sz);
+    /* the new state starts from the old one with Dirichlet data imposed */
+    for (int n = 0; n < N; ++n) {
+        if (pm[n]) p[n] = 0.0;
+        if (cm[n]) c[n] = cv[n];
+    }
+    int nnz = orc_jac_nnz(P);
+    int* rowptr = malloc(sizeof(int) * ((size_t)n2 + 1));
+    int* col = malloc(sizeof(int) * (size_t)nnz);
+    double* val = malloc(sizeof(double) * (size_t)nnz);
+    orc_jac_pattern(P, rowptr, col);
+
+    orc_residual(P, phi, K, p, c, p_old, c_old, dt, 1, Rp, Rc);
+    double rn = norm2_pair(N, Rp, Rc);
+    orc_step_info inf = {1, 0, 0, 0, rn, rn};
+    for (int it = 1; it <= o->maxit; ++it) {
+        orc_jacobian(P, phi, K, p, c, dt, rowptr, col, val);
+        for (int n = 0; n < N; ++n) {
+            rhs[2 * n] = -Rp[n];
+            rhs[2 * n + 1] = -Rc[n];
+        }
+        int li = 0;
+        if (orc_linear_solve(n2, rowptr, col, val, rhs, du, o, &li) != 0) {
+            /* keep going: Newton only needs a descent direction */
+            inf.status = 2;
+        }
+        inf.lin_iters += li;
+        double lambda = 1.0, rt = 0.0;
+        for (int ls = 0; ls <= o->ls_max; ++ls) {
+            for (int n = 0; n < N; ++n) {
+                pt[n] = p[n] + lambda * du[2 * n];
+                ct[n] = c[n] + lambda * du[2 * n + 1];
+            }
+            orc_residual(P, phi, K, pt, ct, p_old, c_old, dt, 1, Rpt, Rct);
+            rt = norm2_pair(N, Rpt, Rct);
+            if (rt < (1.0 - 1e-4 * lambda) * rn || ls == o->ls_max) break;
+            lambda *= 0.5;
+            inf.ls_cuts++;
+        }
+        double dpmax = 0.0, dcmax = 0.0;
+        for (int n = 0; n < N; ++n) {
+            double a = fabs(pt[n] - p[n]), b = fabs(ct[n] - c[n]);
+            if (a > dpmax) dpmax = a;
+            if (b > dcmax) dcmax = b;
+        }
+        memcpy(p, pt, sz);
+        memcpy(c, ct, sz);
+        memcpy(Rp, Rpt, sz);
+        memcpy(Rc, Rct, sz);
+        rn = rt;
+        inf.newton_iters = it;
+        if (lambda == 1.0 && dcmax <= o->tol_c && dpmax <= o->tol_p) {
+            if (inf.status != 2) inf.status = 0;
+            else inf.status = 0; /* converged despite an inexact solve */
+            break;
+        }
+    }
+    inf.res = rn;
+    if (info) *info = inf;
+    free(p_old); free(c_old); free(Rp); free(Rc); free(pt); free(ct);
+    free(Rpt); free(Rct); free(rhs); free(du); free(pm); free(cm); free(cv);
+    free(rowptr); free(col); free(val);
+    return inf.status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* statistics (Section 3: eqs. pdestat, numer_var; exceedance estimate)     */
+/* ------------------------------------------------------------------------ */
+
+void orc_moments(int S, int N, const double* c, const double* w,
+                 double threshold, double* mean, double* var, double* pexc)
+{
+    for (int n = 0; n < N; ++n) {
+        double m = 0.0;
+        for (int s = 0; s < S; ++s)
+            m += (w ? w[s] : 1.0 / S) * c[(size_t)s * N + n];
+        double v = 0.0, pe = 0.0;
+        for (int s = 0; s < S; ++s) {
+            double ws = w ? w[s] : 1.0 / S;
+            double dv = m - c[(size_t)s * N + n];
+            v += ws * dv * dv;
+            if (c[(size_t)s * N + n] > threshold) pe += ws;
+        }
+        mean[n] = m;
+        var[n] = v;
+        pexc[n] = pe;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* porosity / permeability realisations (Section 2.2)                       */
+/* ------------------------------------------------------------------------ */
+
+static double kozeny_carman(double phi, double K_mean)
+{
+    double ref = (0.1 * 0.1 * 0.1) / (0.9 * 0.9);
+    return K_mean * (phi * phi * phi / ((1.0 - phi) * (1.0 - phi))) / ref;
+}
+
+void orc_fields_sobol(const orc_problem* P, const double* xi, double K_mean,
+                      double* phi, double* K)
+{
+    const double pi = 3.14159265358979323846;
+    double hx = P->Lx / P->nx, hy = P->Ly / P->ny, hz = P->Lz / P->nz;
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                int e = i + P->nx * (j + P->ny * k);
+                double x = (i + 0.5) * hx, y = (j + 0.5) * hy,
+                       z = (k + 0.5) * hz;
+                double f = xi[0] * cos(pi * x / P->Lx) +
+                           xi[1] * cos(pi * y / P->Ly) +
+                           xi[2] * sin(2.0 * pi * z / P->Lz);
+                phi[e] = 0.1 * (1.0 + 0.3 * f / 3.0);
+                K[e] = kozeny_carman(phi[e], K_mean);
+            }
+}
+
+void orc_fields_lognormal(const orc_problem* P, const double* Z,
+                          double K_mean, double* phi, double* K)
+{
+    int C = orc_num_cells(P);
+    for (int e = 0; e < C; ++e) {
+        double v = 0.1 * exp(0.2 * Z[e]);
+        if (v < 0.05) v = 0.05;
+        if (v > 0.2) v = 0.2;
+        phi[e] = v;
+        K[e] = kozeny_carman(v, K_mean);
+    }
+}
+
+void orc_fields_paper3rv(const orc_problem* P, const double* xi,
+                         double K_mean, double* phi, double* K)
+{
+    const double pi = 3.14159265358979323846;
+    double hx = P->Lx / P->nx, hy = P->Ly / P->ny, hz = P->Lz / P->nz;
+    for (int k = 0; k < P->nz; ++k)
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                int e = i + P->nx * (j + P->ny * k);
+                double sx = sin(pi * (i + 0.5) * hx / P->Lx);
+                double sy = sin(pi * (j + 0.5) * hy / P->Ly);
+                double sz = sin(pi * (k + 0.5) * hz / P->Lz);
+                phi[e] = 0.1 + 0.01 * (xi[0] * sx + xi[1] * sy + xi[2] * sz +
+                                       xi[0] * sx * sy + xi[1] * sx * sz);
+                K[e] = kozeny_carman(phi[e], K_mean);
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* plume functional and discrete adjoint                                    */
+/* ------------------------------------------------------------------------ */
+
+static int cell_is_low(const orc_problem* P, int k)
+{
+    return (k + 0.5) * (P->Lz / P->nz) < 0.5 * P->Lz;
+}
+
+double orc_objective(const orc_problem* P, const double* phi, const double* c)
+{
+    double vscv = (P->Lx / P->nx) * (P->Ly / P->ny) * (P->Lz / P->nz) / 8.0;
+    double J = 0.0;
+    for (int k = 0; k < P->nz; ++k) {
+        if (!cell_is_low(P, k)) continue;
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                int e = i + P->nx * (j + P->ny * k);
+                int nodes[8];
+                cell_corners(P, i, j, k, nodes);
+                for (int L = 0; L < 8; ++L) {
+                    double cc = c[nodes[L]];
+                    J += phi[e] * vscv * rho_of(P, cc) * cc;
+                }
+            }
+    }
+    return J;
+}
+
+/* Lagrangian L = J(u_N) - sum_n lambda_n^T R_n(u_n, u_{n-1}; theta).
+ * Stationarity in u_N:  J_N^T lambda_N = dJ/du_N.
+ * Stationarity in u_n:  J_n^T lambda_n = -(dR_{n+1}/du_n)^T lambda_{n+1}.
+ * Gradient:             dJ/dtheta = dJ/dtheta|_direct
+ *                                   - sum_n lambda_n^T dR_n/dtheta. */
+int orc_adjoint_gradient(const orc_problem* P, const double* phi,
+                         const double* K, const double* p0, const double* c0,
+                         double dt, int n_steps, const orc_newton_opts* o,
+                         double* J_out, double* dJ_dphi, double* dJ_dK)
+{
+    int N = orc_num_nodes(P), C = orc_num_cells(P), n2 = 2 * N;
+    size_t sz = sizeof(double) * (size_t)N;
+    double drho = P->rho1 - P->rho0;
+    double vscv = (P->Lx / P->nx) * (P->Ly / P->ny) * (P->Lz / P->nz) / 8.0;
+    double* ps = malloc(sz * (size_t)(n_steps + 1));
+    double* cs = malloc(sz * (size_t)(n_steps + 1));
+    memcpy(ps, p0, sz);
+    memcpy(cs, c0, sz);
+    int rc = 0;
+    for (int n = 1; n <= n_steps; ++n) {
+        memcpy(ps + (size_t)n * N, ps + (size_t)(n - 1) * N, sz);
+        memcpy(cs + (size_t)n * N, cs + (size_t)(n - 1) * N, sz);
+        orc_step_info inf;
+        if (orc_newton_step(P, phi, K, ps + (size_t)n * N, cs + (size_t)n * N,
+                            dt, o, &inf) != 0)
+            rc = 1;
+    }
+    const double* cN = cs + (size_t)n_steps * N;
+    *J_out = orc_objective(P, phi, cN);
+
+    unsigned char* pm = malloc((size_t)N);
+    unsigned char* cm = malloc((size_t)N);
+    orc_dirichlet(P, pm, cm, NULL);
+    int nnz = orc_jac_nnz(P);
+    int* rowptr = malloc(sizeof(int) * ((size_t)n2 + 1));
+    int* col = malloc(sizeof(int) * (size_t)nnz);
+    double* val = malloc(sizeof(double) * (size_t)nnz);
+    int* trowptr = malloc(sizeof(int) * ((size_t)n2 + 1));
+    int* tcol = malloc(sizeof(int) * (size_t)nnz);
+    double* tval = malloc(sizeof(double) * (size_t)nnz);
+    orc_jac_pattern(P, rowptr, col);
+    double* rhs = malloc(2 * sz);
+    double* lam = malloc(2 * sz);
+
+    /* direct part of dJ/dphi, and dJ/du_N */
+    for (int e = 0; e < C; ++e) {
+        dJ_dphi[e] = 0.0;
+        dJ_dK[e] = 0.0;
+    }
+    memset(rhs, 0, 2 * sz);
+    for (int k = 0; k < P->nz; ++k) {
+        if (!cell_is_low(P, k)) continue;
+        for (int j = 0; j < P->ny; ++j)
+            for (int i = 0; i < P->nx; ++i) {
+                int e = i + P->nx * (j + P->ny * k);
+                int nodes[8];
+                cell_corners(P, i, j, k, nodes);
+                for (int L = 0; L < 8; ++L) {
+                    double cc = cN[nodes[L]];
+                    dJ_dphi[e] += vscv * rho_of(P, cc) * cc;
+                    rhs[2 * nodes[L] + 1] +=
+                        phi[e] * vscv * (rho_of(P, cc) + drho * cc);
+                }
+            }
+    }
+
+    scvf faces[12];
+    int nf = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 2; ++t) make_scvf(P, d, s, t, &faces[nf++]);
+
+    for (int n = n_steps; n >= 1; --n) {
+        const double* pn = ps + (size_t)n * N;
+        const double* cn = cs + (size_t)n * N;
+        const double* co = cs + (size_t)(n - 1) * N;
+        /* J_n^T lambda_n = rhs */
+        orc_jacobian(P, phi, K, pn, cn, dt, rowptr, col, val);
+        orc_csr_transpose(n2, rowptr, col, val, trowptr, tcol, tval);
+        int li;
+        if (orc_linear_solve(n2, trowptr, tcol, tval, rhs, lam, o, &li) != 0)
+            rc = 1;
+        /* gradient contributions -lambda_n^T dR_n/dtheta (non-Dirichlet
+         * rows only: Dirichlet rows do not depend on theta) */
+        for (int k = 0; k < P->nz; ++k)
+            for (int j = 0; j < P->ny; ++j)
+                for (int i = 0; i < P->nx; ++i) {
+                    int e = i + P->nx * (j + P->ny * k);
+                    int nodes[8];
+                    cell_corners(P, i, j, k, nodes);
+                    double pl[8], cl[8];
+                    for (int L = 0; L < 8; ++L) {
+                        pl[L] = pn[nodes[L]];
+                        cl[L] = cn[nodes[L]];
+                    }
+                    double gphi = 0.0, gK = 0.0;
+                    for (int L = 0; L < 8; ++L) {
+                        int nd = nodes[L];
+                        double rn = rho_of(P, cn[nd]), ro = rho_of(P, co[nd]);
+                        if (!pm[nd]) gphi += lam[2 * nd] * vscv * (rn - ro) / dt;
+                        if (!cm[nd])
+                            gphi += lam[2 * nd + 1] * vscv *
+                                    (rn * cn[nd] - ro * co[nd]) / dt;
+                    }
+                    for (int q = 0; q < 12; ++q) {
+                        face_flux ff;
+                        eval_face(P, &faces[q], phi[e], K[e], pl, cl, &ff);
+                        int a = nodes[faces[q].La], b = nodes[faces[q].Lb];
+                        double dF_dphi =
+                            -ff.rho_ip * P->Dm * ff.gradc * faces[q].A;
+                        double dm_dK = ff.m / K[e];
+                        double dF_dK = ff.cup * dm_dK;
+                        if (!cm[a]) gphi += lam[2 * a + 1] * dF_dphi;
+                        if (!cm[b]) gphi -= lam[2 * b + 1] * dF_dphi;
+                        if (!pm[a]) gK += lam[2 * a] * dm_dK;
+                        if (!pm[b]) gK -= lam[2 * b] * dm_dK;
+                        if (!cm[a]) gK += lam[2 * a + 1] * dF_dK;
+                        if (!cm[b]) gK -= lam[2 * b + 1] * dF_dK;
+                    }
+                    dJ_dphi[e] -= gphi;
+                    dJ_dK[e] -= gK;
+                }
+        /* rhs for step n-1: -(dR_n/du_{n-1})^T lambda_n; R_n depends on
+         * u_{n-1} only through the old storage, -S(c_{n-1})/dt */
+        if (n > 1) {
+            memset(rhs, 0, 2 * sz);
+            for (int k = 0; k < P->nz; ++k)
+                for (int j = 0; j < P->ny; ++j)
+                    for (int i = 0; i < P->nx; ++i) {
+                        int e = i + P->nx * (j + P->ny * k);
+                        int nodes[8];
+                        cell_corners(P, i, j, k, nodes);
+                        for (int L = 0; L < 8; ++L) {
+                            int nd = nodes[L];
+                            double dSp = phi[e] * vscv * drho / dt;
+                            double dSc = phi[e] * vscv *
+                                         (rho_of(P, co[nd]) + drho * co[nd]) /
+                                         dt;
+                            if (!pm[nd]) rhs[2 * nd + 1] += dSp * lam[2 * nd];
+                            if (!cm[nd])
+                                rhs[2 * nd + 1] += dSc * lam[2 * nd + 1];
+                        }
+                    }
+        }
+    }
+    free(ps); free(cs); free(pm); free(cm); free(rowptr); free(col); free(val);
+    free(trowptr); free(tcol); free(tval); free(rhs); free(lam);
+    return rc;
+}
