@@ -1,0 +1,201 @@
+/*
+ * elder.h -- C ABI of the GB300 implicit time step for the stochastic 3D
+ * Elder-like density-driven flow problem (Litvinenko, Logashenko, Tempone,
+ * Wittum, Keyes, arXiv:1906.01632).
+ *
+ * Model (Section 2.1): fluid mass conservation (eq. e_cont_eq), salt
+ * transport (eq. e_tran_eq), Darcy law q = -(K/mu)(grad p - rho(c) g) with
+ * g = (0,0,-g) (eq. e_Darcy_vel), scalar permeability (eq. e_scalar_perm),
+ * linear density rho(c) = rho0 + (rho1-rho0) c (eq. e_lin_density), constant
+ * viscosity, molecular diffusion phi*Dm (eq. e_mol_diff).
+ * Discretisation and solver (Section 2.3, Section 5.1): vertex-centred finite
+ * volumes on a structured hexahedral box, implicit Euler, Newton with line
+ * search, BiCGStab preconditioned by a geometric-multigrid V-cycle whose
+ * coarse matrices are the Jacobians of the discretised system on each grid.
+ *
+ * Conventions shared by every entry point
+ * --------------------------------------
+ *  - Grid: nodes (i,j,k), 0<=i<=nx, 0<=j<=ny, 0<=k<=nz, at x = i*Lx/nx,
+ *    y = j*Ly/ny, z = k*Lz/nz; z points up (the top is z = Lz).
+ *    N = (nx+1)(ny+1)(nz+1) nodes, C = nx*ny*nz cells.
+ *  - Node arrays are [S][N] with n = i + (nx+1)*(j + (ny+1)*k) (x fastest);
+ *    cell arrays are [S][C] with e = i + nx*(j + ny*k).
+ *  - Pairs of unknowns/residual rows are interleaved [S][N][2] = (p, c).
+ *  - All array arguments are DEVICE pointers owned by the caller unless a
+ *    comment says "host"; the library never frees them.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered; entry points that return per-sample status synchronise
+ *    the stream before returning.
+ *  - Every function returns an elder_status code; none throws.  After a
+ *    failure, elder_last_error() describes it.  A context may be used by one
+ *    host thread at a time.
+ */
+#ifndef ELDER_H
+#define ELDER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ELDER_OK = 0,
+    ELDER_EINVAL = 1,    /* bad argument or unsupported grid              */
+    ELDER_ENOMEM = 2,    /* device allocation failed                      */
+    ELDER_ECUDA = 3,     /* a CUDA call failed                            */
+    ELDER_ENOTCONV = 4,  /* at least one sample failed: see its status    */
+    ELDER_ETIMEOUT = 5   /* a bounded device wait gave up                 */
+} elder_status;
+
+/* per-sample status of elder_step / elder_solve */
+enum {
+    ELDER_SAMPLE_OK = 0,
+    ELDER_SAMPLE_NEWTON_MAXIT = 1,  /* Newton iteration cap reached        */
+    ELDER_SAMPLE_KRYLOV_MAXIT = 2,  /* BiCGStab cap reached (elder_solve)  */
+    ELDER_SAMPLE_BREAKDOWN = 3,     /* BiCGStab breakdown (rho or omega 0) */
+    ELDER_SAMPLE_NONFINITE = 4      /* NaN/Inf in a residual norm          */
+};
+
+enum { ELDER_FP64 = 0, ELDER_MIXED = 1 };
+
+/* Boundary-condition sets (Section 2.1 and the caption of Fig. 1):
+ *  0 benchmark: c=1 on the closed top square [Lx/4,3Lx/4]x[Ly/4,3Ly/4],
+ *    c=0 on the bottom, p=0 at the four top corners; no-flow elsewhere;
+ *  1 paper variant: c=1 on the top square, c=0 on the rest of the top and
+ *    on the bottom, p=0 on the four top edges;
+ *  2 diffusion column test: c=1 on the whole top, c=0 on the bottom,
+ *    p=0 at the four top corners;
+ *  3 no c Dirichlet data, p=0 at the four top corners. */
+typedef struct {
+    int nx, ny, nz;           /* cells; for modes 0/1 nx, ny multiples of 4 */
+    double Lx, Ly, Lz;        /* box size [m]                               */
+    double rho0, rho1;        /* densities of water and brine [kg/m^3]      */
+    double mu;                /* viscosity [Pa s]                           */
+    double g;                 /* gravity [m/s^2], acting along -z           */
+    double Dm;                /* molecular diffusion [m^2/s]                */
+    int bc_mode;              /* see above                                  */
+    int precision;            /* ELDER_FP64 or ELDER_MIXED                  */
+    int max_samples;          /* largest S any call will pass               */
+    /* Newton with line search (Section 2.3) */
+    int newton_maxit;         /* iteration cap                              */
+    double newton_tol_c;      /* converged: max|dc| <= tol_c ...            */
+    double newton_tol_p;      /* ... and max|dp| <= tol_p at a full step    */
+    int ls_max;               /* step halvings before a step is forced      */
+    /* BiCGStab (Section 5.1) */
+    double lin_rtol;          /* relative residual target per Newton solve  */
+    int lin_maxit;            /* iteration cap                              */
+    /* geometric multigrid V-cycle (Section 5.1) */
+    int mg_levels;            /* 0 = coarsen as far as the grid allows      */
+    int nu1, nu2;             /* pre/post smoothing sweeps                  */
+    double omega;             /* damping of the block-Jacobi smoother       */
+    int coarse_K_harmonic;    /* 0 arithmetic, 1 harmonic mean of K         */
+    int use_graphs;           /* capture the Krylov iteration in CUDA graphs*/
+} elder_config;
+
+/* Per-sample statistics of one elder_step call (host struct). */
+typedef struct {
+    int32_t status;           /* ELDER_SAMPLE_*                             */
+    int32_t newton_iters;
+    int32_t krylov_iters;     /* summed over the Newton iterations          */
+    int32_t ls_cuts;          /* step halvings                              */
+    double res0;              /* ||R(u^n)||_2 with Dirichlet data imposed   */
+    double res;               /* ||R(u^{n+1})||_2                           */
+} elder_stats;
+
+typedef struct elder_ctx elder_ctx;
+
+/* Fills *cfg with the benchmark problem of Table 1 (Dm = 3.565e-6, see the
+ * design notes on the printed 0.565e-6) on an nx*ny*nz grid and default
+ * solver settings.  Returns ELDER_EINVAL for a NULL cfg. */
+int elder_config_default(elder_config* cfg, int nx, int ny, int nz);
+
+/* Creates a context: validates the grid, builds the multigrid hierarchy and
+ * allocates all device workspace for up to cfg->max_samples samples on the
+ * current device.  *out receives the handle (NULL on failure). */
+int elder_create(const elder_config* cfg, elder_ctx** out);
+
+/* Frees the context and its device workspace (NULL is accepted). */
+int elder_destroy(elder_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last failed elder_create
+ * when ctx is NULL); never NULL. */
+const char* elder_last_error(const elder_ctx* ctx);
+
+/* Number of nodes N and cells C of the context's grid (host outputs). */
+int elder_sizes(const elder_ctx* ctx, int64_t* N, int64_t* C, int* levels);
+
+/* Sample preprocessing (Section 2.2, eq. e_perm_Kozeny_Carman): per-cell
+ * porosity and permeability for S samples.
+ *  kind 0: params = xi [S][3] in [-1,1]^3, phi = 0.1*(1 + 0.3*(xi1 cos(pi
+ *          x/Lx) + xi2 cos(pi y/Ly) + xi3 sin(2 pi z/Lz))/3) at cell centres;
+ *  kind 1: params = Z [S][C] standard normals, phi = clip(0.1 exp(0.2 Z),
+ *          0.05, 0.2);
+ *  kind 2: params = xi [S][3], the paper's field eq. poro-paral3RVS.
+ * K = K_mean * [phi^3/(1-phi)^2] / [0.1^3/0.9^2] (Kozeny-Carman normalised so
+ * that K(0.1) = K_mean).  phi, K: [S][C] device outputs. */
+int elder_fields(elder_ctx* ctx, int S, int kind, const double* params,
+                 double K_mean, double* phi, double* K, void* stream);
+
+/* Residual R(u; u_old) of the implicit Euler step (eqs. e_cont_eq,
+ * e_tran_eq, box-method fluxes), FP64, for S samples.  R: [S][N][2] device
+ * output; Dirichlet rows hold u - u_D.  Used by the parity tests. */
+int elder_residual(elder_ctx* ctx, int S, const double* phi, const double* K,
+                   const double* p, const double* c, const double* p_old,
+                   const double* c_old, double dt, double* R, void* stream);
+
+/* Jacobian dR/du at (p, c) on the finest grid in the library's storage:
+ * J[S][27][N][4], slot s = (dx+1) + 3(dy+1) + 9(dz+1) for the neighbour at
+ * offset (dx,dy,dz), block (row p|c, col p|c) = {pp, pc, cp, cc}; entries
+ * of neighbours outside the grid are 0; Dirichlet rows are identity rows.
+ * FP64 output regardless of precision (Section 5.1: "assembled as the
+ * Jacobians of the discretized nonlinear systems"). */
+int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
+                   const double* p, const double* c, double dt, double* J,
+                   void* stream);
+
+/* One implicit Euler step for S samples (Sections 2.3 and 5.1): Newton with
+ * line search on the FP64 residual, each Newton system solved by
+ * multigrid-preconditioned BiCGStab (FP64, or FP32 multigrid and Krylov
+ * storage with FP64 inner products in ELDER_MIXED).
+ *  phi, K: [S][C] inputs.  p, c: [S][N] in: u^n, out: u^{n+1}.
+ *  dt: time step [s].  status, stats: HOST arrays of S entries (stats may
+ *  be NULL), written after the stream is synchronised.  A failed sample
+ *  keeps u^n.  Returns ELDER_ENOTCONV when any sample failed. */
+int elder_step(elder_ctx* ctx, int S, const double* phi, const double* K,
+               double* p, double* c, double dt, int32_t* status,
+               elder_stats* stats, void* stream);
+
+/* Linearises at (p, c) and solves J x = rhs (transpose=0) or J^T x = rhs
+ * (transpose=1) with the multigrid-preconditioned BiCGStab of elder_step,
+ * to the relative residual rtol.  rhs, x: [S][N][2] device; x is output
+ * only.  status: HOST [S].  The FP64 solver is used for rtol < 1e-6. */
+int elder_solve(elder_ctx* ctx, int S, const double* phi, const double* K,
+                const double* p, const double* c, double dt, int transpose,
+                const double* rhs, double* x, double rtol, int32_t* status,
+                void* stream);
+
+/* Sample statistics over S fields c[S][N] (Section 3, eqs. pdestat and
+ * numer_var, and the exceedance estimate of Section 3.3):
+ * mean = sum_i w_i c_i, var = sum_i w_i (mean - c_i)^2,
+ * p_exceed = sum_i w_i [c_i > threshold].  w: [S] device weights or NULL for
+ * 1/S.  mean, var, p_exceed: [N] device outputs. */
+int elder_moments(elder_ctx* ctx, int S, const double* c, const double* w,
+                  double threshold, double* mean, double* var,
+                  double* p_exceed, void* stream);
+
+/* Discrete adjoint of n_steps implicit Euler steps of one sample from
+ * (p0, c0): objective J = salt mass sum_e phi_e |scv| rho(c) c over the
+ * cells whose centre lies below Lz/2 at the final time, and its gradients
+ * with respect to per-cell phi and K (independent inputs).  Forward states
+ * are kept every ckpt_every steps and recomputed in the reverse sweep.
+ *  J_out: HOST double.  dJ_dphi, dJ_dK: [C] device outputs. */
+int elder_grad(elder_ctx* ctx, int n_steps, const double* phi,
+               const double* K, const double* p0, const double* c0, double dt,
+               int ckpt_every, double* J_out, double* dJ_dphi, double* dJ_dK,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELDER_H */

@@ -1,0 +1,843 @@
+// assembly.cu -- FV residual and Jacobian of the implicit Elder step and the
+// per-level pieces of the multigrid hierarchy.
+//
+// Box method (Section 2.3): each hexahedron is split into 8 sub-control
+// volumes (one per corner, |scv| = hx*hy*hz/8) and 12 sub-control-volume
+// faces (one per edge).  The face of an edge along direction d lies in the
+// edge's mid-plane; its integration point sits at 1/2 along d and at 1/4 or
+// 3/4 across, on the edge's side, and its area is a quarter of the cell's
+// cross-section.  At that point the trilinear interpolant gives
+//   grad p . e_d = sum_edges w (p_B - p_A)/h_d,   w = (9,3,3,1)/16,
+//   c_ip = sum_edges w (c_A + c_B)/2,
+// and the fluxes (eqs. e_cont_eq, e_tran_eq, e_Darcy_vel, g = (0,0,-g)):
+//   m = rho(c_ip) q.n A,  q.n = -(K/mu)(grad p . e_d + [d=z] g rho(c_ip)),
+//   F = c_up m - rho(c_ip) phi Dm (grad c . e_d) A,  c_up = m>=0 ? c_A : c_B.
+// Storage is lumped: sum_{e ni i} phi_e |scv| (rho(c_i)(c_i) - old)/dt.
+//
+// Every node kernel gathers the contributions of the up to 8 cells around
+// its node (one thread per node, no atomics, deterministic).
+#include "kernels.h"
+
+namespace elder {
+
+__device__ __forceinline__ bool sample_on(const int* mask, int stride, int s)
+{
+    return mask == nullptr || mask[(size_t)s * stride] != 0;
+}
+
+// Local corner L = lx + 2 ly + 4 lz of the edge of direction D with
+// transverse local position (u, v), at end 0 (A) or 1 (B).
+__host__ __device__ constexpr int corner_of(int D, int u, int v, int end)
+{
+    return D == 0 ? (end + 2 * u + 4 * v)
+                  : (D == 1 ? (u + 2 * end + 4 * v) : (u + 2 * v + 4 * end));
+}
+
+// ---------------------------------------------------------------------------
+// residual (FP64)
+// ---------------------------------------------------------------------------
+
+template <int D, int S_, int T_>
+__device__ __forceinline__ void flux_face(const double (&p8)[8],
+                                          const double (&c8)[8], double phi_e,
+                                          double kmu, const Phys& ph,
+                                          double invh, double area, double& m,
+                                          double& F)
+{
+    double gp = 0.0, gc = 0.0, ci = 0.0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const double w = (u == S_ ? 0.75 : 0.25) * (v == T_ ? 0.75 : 0.25);
+            const int A = corner_of(D, u, v, 0), B = corner_of(D, u, v, 1);
+            gp = fma(w, p8[B] - p8[A], gp);
+            gc = fma(w, c8[B] - c8[A], gc);
+            ci = fma(w, c8[A] + c8[B], ci);
+        }
+    gp *= invh;
+    gc *= invh;
+    ci *= 0.5;
+    const double rho = fma(ph.drho, ci, ph.rho0);
+    const double G = (D == 2) ? fma(ph.g, rho, gp) : gp;
+    m = rho * (-kmu * G) * area;
+    const double cup =
+        (m >= 0.0) ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
+    F = cup * m - rho * phi_e * ph.Dm * gc * area;
+}
+
+struct CellGeom {
+    double ih[3];    // 1/h_d
+    double area[3];  // face areas of the three directions
+};
+
+template <int OX, int OY, int OZ>
+__device__ __forceinline__ void residual_cell(
+    const Grid& G, const Phys& ph, const CellGeom& cg, int i, int j, int k,
+    const double* __restrict__ phi, const double* __restrict__ K,
+    const double* __restrict__ p, const double* __restrict__ c, double& Rp,
+    double& Rc, double& phis)
+{
+    const int ci = i + OX, cj = j + OY, ck = k + OZ;
+    if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz)
+        return;
+    const int e = ci + G.nx * (cj + G.ny * ck);
+    const double phi_e = __ldg(phi + e);
+    const double kmu = __ldg(K + e) / ph.mu;
+    phis += phi_e;
+    const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
+    const int base = ci + sy * cj + sz * ck;
+    double p8[8], c8[8];
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
+        p8[L] = __ldg(p + base + off);
+        c8[L] = __ldg(c + base + off);
+    }
+    constexpr int lx = -OX, ly = -OY, lz = -OZ;  // this node's local corner
+    double m, F;
+    flux_face<0, ly, lz>(p8, c8, phi_e, kmu, ph, cg.ih[0], cg.area[0], m, F);
+    if (lx == 0) { Rp += m; Rc += F; } else { Rp -= m; Rc -= F; }
+    flux_face<1, lx, lz>(p8, c8, phi_e, kmu, ph, cg.ih[1], cg.area[1], m, F);
+    if (ly == 0) { Rp += m; Rc += F; } else { Rp -= m; Rc -= F; }
+    flux_face<2, lx, ly>(p8, c8, phi_e, kmu, ph, cg.ih[2], cg.area[2], m, F);
+    if (lz == 0) { Rp += m; Rc += F; } else { Rp -= m; Rc -= F; }
+}
+
+__host__ __device__ inline CellGeom make_geom(const Grid& G)
+{
+    CellGeom cg;
+    cg.ih[0] = 1.0 / G.hx;
+    cg.ih[1] = 1.0 / G.hy;
+    cg.ih[2] = 1.0 / G.hz;
+    cg.area[0] = 0.25 * G.hy * G.hz;
+    cg.area[1] = 0.25 * G.hx * G.hz;
+    cg.area[2] = 0.25 * G.hx * G.hy;
+    return cg;
+}
+
+__global__ void __launch_bounds__(kBS)
+    k_residual(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
+               const double* __restrict__ cval, const double* __restrict__ phi,
+               const double* __restrict__ K, const double* __restrict__ p,
+               const double* __restrict__ c, const double* __restrict__ p_old,
+               const double* __restrict__ c_old, V2<double>* __restrict__ R,
+               double* __restrict__ partial, const int* mask, int mstride)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
+    phi += oc; K += oc; p += on; c += on; p_old += on; c_old += on; R += on;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (n < G.N) {
+        int i, j, k;
+        node_ijk(G, n, i, j, k);
+        double Rp = 0.0, Rc = 0.0, phis = 0.0;
+        residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        const double vscv = 0.125 * G.hx * G.hy * G.hz;
+        const double cn = c[n], co = c_old[n];
+        const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
+        Rp += phis * vscv * (rn - ro) / ph.dt;
+        Rc += phis * vscv * (rn * cn - ro * co) / ph.dt;
+        const uint8_t b = bc[n];
+        if (b & BC_P) Rp = p[n];
+        if (b & BC_C) Rc = cn - cval[n];
+        R[n] = V2<double>{Rp, Rc};
+        sq = Rp * Rp + Rc * Rc;
+    }
+    if (partial) {
+        const double t = block_sum(sq, red);
+        if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
+                     const double* cval, const double* phi, const double* K,
+                     const double* p, const double* c, const double* p_old,
+                     const double* c_old, V2<double>* R, double* partial,
+                     const int* mask, int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_residual<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), bc, cval, phi, K, p,
+                                     c, p_old, c_old, R, partial, mask, mstride);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian (T = double: FP64 path; T = float: FP32 copy for mixed precision)
+// ---------------------------------------------------------------------------
+//
+// For one face (rows of this node, sign sig = +1 when the node is end A):
+//   dm/dp_B = alpha w, dm/dp_A = -alpha w,   alpha = -rho (K/mu) A / h
+//   dm/dc_X = beta w (both ends),           beta = (drho/2) A (q - [z] rho (K/mu) g)
+//   dF/dp_X = c_up dm/dp_X
+//   dF/dc_B = (c_up beta - gam - del) w + [B up] m
+//   dF/dc_A = (c_up beta - gam + del) w + [A up] m
+//       gam = (drho/2) phi Dm A (grad c . e_d),  del = rho phi Dm A / h.
+// Pressures enter through p' = p - rho0 g (Lz - z) (same differences up to
+// the constant rho0 g h_z on vertical edges), so that the FP32 copy keeps the
+// Darcy driving force without cancelling against the hydrostatic part.
+
+template <class T> struct PhysT {
+    T rho0, drho, g, Dm;
+};
+
+template <class T, int D, int S_, int T_, int OX, int OY, int OZ>
+__device__ __forceinline__ void jac_face(const T (&p8)[8], const T (&c8)[8],
+                                         T phi_e, T kmu, const PhysT<T>& ph,
+                                         T invh, T area, T (&acc)[27][4])
+{
+    constexpr int lnode = (D == 0) ? -OX : (D == 1 ? -OY : -OZ);
+    const T sig = (lnode == 0) ? T(1) : T(-1);
+    T gp = 0, gc = 0, ci = 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const T w = T((u == S_ ? 0.75 : 0.25) * (v == T_ ? 0.75 : 0.25));
+            const int A = corner_of(D, u, v, 0), B = corner_of(D, u, v, 1);
+            gp += w * (p8[B] - p8[A]);
+            gc += w * (c8[B] - c8[A]);
+            ci += w * (c8[A] + c8[B]);
+        }
+    gp *= invh;
+    gc *= invh;
+    ci *= T(0.5);
+    const T rho = ph.rho0 + ph.drho * ci;
+    const T Gd = (D == 2) ? gp + ph.g * ph.drho * ci : gp;
+    const T q = -kmu * Gd;
+    const T m = rho * q * area;
+    const T alpha = -rho * kmu * area * invh;
+    const T beta = T(0.5) * ph.drho * area * (q - (D == 2 ? rho * kmu * ph.g : T(0)));
+    constexpr int cA = corner_of(D, S_, T_, 0), cB = corner_of(D, S_, T_, 1);
+    const bool upA = (m >= T(0));
+    const T cup = upA ? c8[cA] : c8[cB];
+    const T gam = T(0.5) * ph.drho * phi_e * ph.Dm * area * gc;
+    const T del = rho * phi_e * ph.Dm * area * invh;
+    const T sa = sig * alpha, sb = sig * beta, sca = sig * cup * alpha;
+    const T scc = sig * (cup * beta - gam), sd = sig * del;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const T w = T((u == S_ ? 0.75 : 0.25) * (v == T_ ? 0.75 : 0.25));
+            constexpr int dummy = 0;
+            (void)dummy;
+            const int A = corner_of(D, u, v, 0), B = corner_of(D, u, v, 1);
+            const int sA = slot27(OX + (A & 1), OY + ((A >> 1) & 1), OZ + (A >> 2));
+            const int sB = slot27(OX + (B & 1), OY + ((B >> 1) & 1), OZ + (B >> 2));
+            acc[sB][0] += w * sa;
+            acc[sA][0] -= w * sa;
+            acc[sB][1] += w * sb;
+            acc[sA][1] += w * sb;
+            acc[sB][2] += w * sca;
+            acc[sA][2] -= w * sca;
+            acc[sB][3] += w * (scc - sd);
+            acc[sA][3] += w * (scc + sd);
+        }
+    constexpr int slA = slot27(OX + (cA & 1), OY + ((cA >> 1) & 1), OZ + (cA >> 2));
+    constexpr int slB = slot27(OX + (cB & 1), OY + ((cB >> 1) & 1), OZ + (cB >> 2));
+    acc[slA][3] += upA ? sig * m : T(0);
+    acc[slB][3] += upA ? T(0) : sig * m;
+}
+
+template <class T, int OX, int OY, int OZ>
+__device__ __forceinline__ void jac_cell(const Grid& G, const Phys& ph,
+                                         const PhysT<T>& pt,
+                                         const CellGeom& cg, int i, int j,
+                                         int k, const double* __restrict__ phi,
+                                         const double* __restrict__ K,
+                                         const double* __restrict__ p,
+                                         const double* __restrict__ c,
+                                         T (&acc)[27][4], double& phis)
+{
+    const int ci = i + OX, cj = j + OY, ck = k + OZ;
+    if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz)
+        return;
+    const int e = ci + G.nx * (cj + G.ny * ck);
+    const double phid = __ldg(phi + e);
+    phis += phid;
+    const T phi_e = T(phid);
+    const T kmu = T(__ldg(K + e) / ph.mu);
+    const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
+    const int base = ci + sy * cj + sz * ck;
+    const double rg = ph.rho0 * ph.g;
+    T p8[8], c8[8];
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
+        const double z = (ck + (L >> 2)) * G.hz;
+        p8[L] = T(fma(rg, z - G.Lz, __ldg(p + base + off)));
+        c8[L] = T(__ldg(c + base + off));
+    }
+    constexpr int lx = -OX, ly = -OY, lz = -OZ;
+    jac_face<T, 0, ly, lz, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[0]), T(cg.area[0]), acc);
+    jac_face<T, 1, lx, lz, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[1]), T(cg.area[1]), acc);
+    jac_face<T, 2, lx, ly, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[2]), T(cg.area[2]), acc);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128)
+    k_jacobian(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
+               const double* __restrict__ phi, const double* __restrict__ K,
+               const double* __restrict__ p, const double* __restrict__ c,
+               B4<T>* __restrict__ J, const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
+    phi += oc; K += oc; p += on; c += on;
+    J += (size_t)s * 27 * G.N;
+    PhysT<T> pt{T(ph.rho0), T(ph.drho), T(ph.g), T(ph.Dm)};
+    int i, j, k;
+    node_ijk(G, n, i, j, k);
+    T acc[27][4];
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[q][r] = T(0);
+    double phis = 0.0;
+    jac_cell<T, -1, -1, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, 0, -1, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, -1, 0, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, 0, 0, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, -1, -1, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, 0, -1, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, -1, 0, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    jac_cell<T, 0, 0, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    // lumped storage: d/dc of rho(c) and rho(c) c
+    const double vdt = phis * 0.125 * G.hx * G.hy * G.hz / ph.dt;
+    const double cn = c[n];
+    acc[13][1] += T(vdt * ph.drho);
+    acc[13][3] += T(vdt * (ph.rho0 + 2.0 * ph.drho * cn));
+    const uint8_t b = bc[n];
+    if (b & BC_P) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) { acc[q][0] = T(0); acc[q][1] = T(0); }
+        acc[13][0] = T(1);
+    }
+    if (b & BC_C) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) { acc[q][2] = T(0); acc[q][3] = T(0); }
+        acc[13][3] = T(1);
+    }
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+        J[(size_t)q * G.N + n] = B4<T>{acc[q][0], acc[q][1], acc[q][2], acc[q][3]};
+}
+
+template <class T>
+void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
+                     const double* phi, const double* K, const double* p,
+                     const double* c, B4<T>* J, const int* mask, int mstride,
+                     int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N, 128), S);
+    k_jacobian<T><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c,
+                                         J, mask, mstride);
+}
+template void launch_jacobian<double>(const Grid&, const Phys&, const uint8_t*,
+                                      const double*, const double*,
+                                      const double*, const double*,
+                                      B4<double>*, const int*, int, int,
+                                      cudaStream_t);
+template void launch_jacobian<float>(const Grid&, const Phys&, const uint8_t*,
+                                     const double*, const double*,
+                                     const double*, const double*, B4<float>*,
+                                     const int*, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// hierarchy: state injection, cell averaging, block-diagonal inverse
+// ---------------------------------------------------------------------------
+
+__global__ void k_inject(Grid Gf, Grid Gc, const double* __restrict__ pf,
+                         const double* __restrict__ cf, double* __restrict__ pc,
+                         double* __restrict__ cc, const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Gc.N) return;
+    int I, J, K;
+    node_ijk(Gc, n, I, J, K);
+    const int f = node_id(Gf, 2 * I, 2 * J, 2 * K);
+    pc[(size_t)s * Gc.N + n] = pf[(size_t)s * Gf.N + f];
+    cc[(size_t)s * Gc.N + n] = cf[(size_t)s * Gf.N + f];
+}
+
+void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
+                   const double* cf, double* pc, double* cc, const int* mask,
+                   int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(Gc.N), S);
+    k_inject<<<grid, kBS, 0, st>>>(Gf, Gc, pf, cf, pc, cc, mask, mstride);
+}
+
+__global__ void k_average_cells(Grid Gf, Grid Gc, const double* __restrict__ phif,
+                                const double* __restrict__ Kf,
+                                double* __restrict__ phic,
+                                double* __restrict__ Kc, int harmonic)
+{
+    const int s = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Gc.C) return;
+    const int I = e % Gc.nx, J = (e / Gc.nx) % Gc.ny, K = e / (Gc.nx * Gc.ny);
+    double sp = 0.0, sk = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        const int f = (2 * I + (q & 1)) +
+                      Gf.nx * ((2 * J + ((q >> 1) & 1)) + Gf.ny * (2 * K + (q >> 2)));
+        sp += phif[(size_t)s * Gf.C + f];
+        const double kv = Kf[(size_t)s * Gf.C + f];
+        sk += harmonic ? 1.0 / kv : kv;
+    }
+    phic[(size_t)s * Gc.C + e] = 0.125 * sp;
+    Kc[(size_t)s * Gc.C + e] = harmonic ? 8.0 / sk : 0.125 * sk;
+}
+
+void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
+                          const double* Kf, double* phic, double* Kc,
+                          int harmonic, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(Gc.C), S);
+    k_average_cells<<<grid, kBS, 0, st>>>(Gf, Gc, phif, Kf, phic, Kc, harmonic);
+}
+
+// Inverse of the 2x2 diagonal block of the interior operator: rows and
+// columns of Dirichlet components are replaced by the identity.
+template <class T>
+__global__ void k_block_diag_inverse(Grid G, const uint8_t* __restrict__ bc,
+                                     const B4<T>* __restrict__ J,
+                                     B4<T>* __restrict__ Dinv, const int* mask,
+                                     int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const B4<T> d = J[((size_t)s * 27 + 13) * G.N + n];
+    double a = d.pp, b = d.pc, c = d.cp, e = d.cc;
+    const uint8_t m = bc[n];
+    if (m & BC_P) { a = 1.0; b = 0.0; c = 0.0; }
+    if (m & BC_C) { e = 1.0; b = 0.0; c = 0.0; }
+    const double det = a * e - b * c;
+    const double id = 1.0 / det;
+    Dinv[(size_t)s * G.N + n] = B4<T>{T(e * id), T(-b * id), T(-c * id), T(a * id)};
+}
+
+template <class T>
+void launch_block_diag_inverse(const Grid& G, const uint8_t* bc,
+                               const B4<T>* J, B4<T>* Dinv, const int* mask,
+                               int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_block_diag_inverse<T><<<grid, kBS, 0, st>>>(G, bc, J, Dinv, mask, mstride);
+}
+template void launch_block_diag_inverse<double>(const Grid&, const uint8_t*,
+                                                const B4<double>*, B4<double>*,
+                                                const int*, int, int,
+                                                cudaStream_t);
+template void launch_block_diag_inverse<float>(const Grid&, const uint8_t*,
+                                               const B4<float>*, B4<float>*,
+                                               const int*, int, int,
+                                               cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// coarsest level: dense inverse of the interior operator (Gauss-Jordan with
+// partial pivoting, FP64), one block per sample.  work: [S][n][2n].
+// ---------------------------------------------------------------------------
+
+template <class T>
+__global__ void k_coarse_build(Grid G, const uint8_t* __restrict__ bc,
+                               const B4<T>* __restrict__ J, double* __restrict__ W,
+                               const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= G.N) return;
+    const int n2 = 2 * G.N;
+    double* row0 = W + (size_t)s * n2 * 2 * n2 + (size_t)(2 * node) * 2 * n2;
+    double* row1 = row0 + 2 * n2;
+    for (int q = 0; q < 2 * n2; ++q) { row0[q] = 0.0; row1[q] = 0.0; }
+    int i, j, k;
+    node_ijk(G, node, i, j, k);
+    const uint8_t mr = bc[node];
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int ii = i + dx, jj = j + dy, kk = k + dz;
+                if (ii < 0 || ii > G.nx || jj < 0 || jj > G.ny || kk < 0 || kk > G.nz)
+                    continue;
+                const int m = node_id(G, ii, jj, kk);
+                const uint8_t mc = bc[m];
+                const B4<T> B = J[((size_t)s * 27 + slot27(dx, dy, dz)) * G.N + node];
+                if (!(mr & BC_P)) {
+                    if (!(mc & BC_P)) row0[2 * m] = B.pp;
+                    if (!(mc & BC_C)) row0[2 * m + 1] = B.pc;
+                }
+                if (!(mr & BC_C)) {
+                    if (!(mc & BC_P)) row1[2 * m] = B.cp;
+                    if (!(mc & BC_C)) row1[2 * m + 1] = B.cc;
+                }
+            }
+    if (mr & BC_P) row0[2 * node] = 1.0;
+    if (mr & BC_C) row1[2 * node + 1] = 1.0;
+    row0[n2 + 2 * node] = 1.0;
+    row1[n2 + 2 * node + 1] = 1.0;
+}
+
+__global__ void k_gauss_jordan(int n, double* __restrict__ W,
+                               double* __restrict__ Ainv, const int* mask,
+                               int mstride)
+{
+    extern __shared__ double sh[];  // n factors + reduction scratch
+    __shared__ double rv[32];
+    __shared__ int ri[32];
+    const int s = blockIdx.x;
+    if (!sample_on(mask, mstride, s)) return;
+    const int w2 = 2 * n;
+    double* A = W + (size_t)s * n * w2;
+    double* f = sh;
+    for (int k = 0; k < n; ++k) {
+        // pivot: argmax |A[r][k]| over r >= k
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+            const double a = fabs(A[(size_t)r * w2 + k]);
+            if (a > best) { best = a; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+                if (rv[q] > rv[0] || (rv[q] == rv[0] && ri[q] < ri[0])) { rv[0] = rv[q]; ri[0] = ri[q]; }
+        }
+        __syncthreads();
+        const int piv = ri[0];
+        __syncthreads();
+        if (piv != k)
+            for (int q = threadIdx.x; q < w2; q += blockDim.x) {
+                const double t = A[(size_t)k * w2 + q];
+                A[(size_t)k * w2 + q] = A[(size_t)piv * w2 + q];
+                A[(size_t)piv * w2 + q] = t;
+            }
+        __syncthreads();
+        const double inv = 1.0 / A[(size_t)k * w2 + k];
+        __syncthreads();
+        for (int q = threadIdx.x; q < w2; q += blockDim.x) A[(size_t)k * w2 + q] *= inv;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) f[r] = A[(size_t)r * w2 + k];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n * w2; idx += blockDim.x) {
+            const int r = idx / w2, q = idx - r * w2;
+            if (r == k || q < k) continue;
+            A[(size_t)r * w2 + q] -= f[r] * A[(size_t)k * w2 + q];
+        }
+        __syncthreads();
+    }
+    double* out = Ainv + (size_t)s * n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int r = idx / n, q = idx - r * n;
+        out[idx] = A[(size_t)r * w2 + n + q];
+    }
+}
+
+template <class T>
+void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<T>* J,
+                           double* work, double* Ainv, const int* mask,
+                           int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N, 64), S);
+    k_coarse_build<T><<<grid, 64, 0, st>>>(G, bc, J, work, mask, mstride);
+    const int n = 2 * G.N;
+    k_gauss_jordan<<<S, 256, sizeof(double) * n, st>>>(n, work, Ainv, mask, mstride);
+}
+template void launch_coarse_inverse<double>(const Grid&, const uint8_t*,
+                                            const B4<double>*, double*,
+                                            double*, const int*, int, int,
+                                            cudaStream_t);
+template void launch_coarse_inverse<float>(const Grid&, const uint8_t*,
+                                           const B4<float>*, double*, double*,
+                                           const int*, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Dirichlet data and sample fields
+// ---------------------------------------------------------------------------
+
+__global__ void k_impose_dirichlet(Grid G, const uint8_t* __restrict__ bc,
+                                   const double* __restrict__ cval, double* p,
+                                   double* c)
+{
+    const int s = blockIdx.y;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const uint8_t b = bc[n];
+    if (b & BC_P) p[(size_t)s * G.N + n] = 0.0;
+    if (b & BC_C) c[(size_t)s * G.N + n] = cval[n];
+}
+
+void launch_impose_dirichlet(const Grid& G, const uint8_t* bc,
+                             const double* cval, double* p, double* c, int S,
+                             cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_impose_dirichlet<<<grid, kBS, 0, st>>>(G, bc, cval, p, c);
+}
+
+// Section 2.2: porosity realisations and Kozeny-Carman permeability
+// (eq. e_perm_Kozeny_Carman, normalised so that K(0.1) = K_mean).
+__global__ void k_fields(Grid G, int kind, const double* __restrict__ params,
+                         double K_mean, double* __restrict__ phi,
+                         double* __restrict__ K)
+{
+    const int s = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G.C) return;
+    const int i = e % G.nx, j = (e / G.nx) % G.ny, k = e / (G.nx * G.ny);
+    const double Lx = G.nx * G.hx, Ly = G.ny * G.hy, Lz = G.nz * G.hz;
+    const double x = (i + 0.5) * G.hx, y = (j + 0.5) * G.hy, z = (k + 0.5) * G.hz;
+    const double pi = 3.14159265358979323846;
+    double ph;
+    if (kind == 1) {
+        ph = 0.1 * exp(0.2 * params[(size_t)s * G.C + e]);
+        ph = fmin(fmax(ph, 0.05), 0.2);
+    } else {
+        const double* xi = params + (size_t)s * 3;
+        if (kind == 0) {
+            const double f = xi[0] * cos(pi * x / Lx) + xi[1] * cos(pi * y / Ly) +
+                             xi[2] * sin(2.0 * pi * z / Lz);
+            ph = 0.1 * (1.0 + 0.3 * f / 3.0);
+        } else {
+            const double sx = sin(pi * x / Lx), sy = sin(pi * y / Ly), sz = sin(pi * z / Lz);
+            ph = 0.1 + 0.01 * (xi[0] * sx + xi[1] * sy + xi[2] * sz + xi[0] * sx * sy +
+                               xi[1] * sx * sz);
+        }
+    }
+    const double ref = (0.1 * 0.1 * 0.1) / (0.9 * 0.9);
+    phi[(size_t)s * G.C + e] = ph;
+    K[(size_t)s * G.C + e] = K_mean * (ph * ph * ph / ((1.0 - ph) * (1.0 - ph))) / ref;
+}
+
+void launch_fields(const Grid& G, int kind, const double* params,
+                   double K_mean, double* phi, double* K, int S,
+                   cudaStream_t st)
+{
+    dim3 grid(nblocks(G.C), S);
+    k_fields<<<grid, kBS, 0, st>>>(G, kind, params, K_mean, phi, K);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint pieces (one sample)
+// ---------------------------------------------------------------------------
+//
+// Objective: salt mass in the cells whose centre lies below Lz/2,
+// J = sum_e sum_corners phi_e |scv| rho(c_L) c_L.
+
+__global__ void k_objective_cells(Grid G, Phys ph, const double* __restrict__ phi,
+                                  const double* __restrict__ c,
+                                  double* __restrict__ partial,
+                                  double* __restrict__ dJdphi)
+{
+    __shared__ double red[32];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double Jl = 0.0;
+    if (e < G.C) {
+        const int i = e % G.nx, j = (e / G.nx) % G.ny, k = e / (G.nx * G.ny);
+        const double vscv = 0.125 * G.hx * G.hy * G.hz;
+        double sm = 0.0;
+        if ((k + 0.5) * G.hz < 0.5 * G.Lz) {
+            for (int L = 0; L < 8; ++L) {
+                const double cc = c[node_id(G, i + (L & 1), j + ((L >> 1) & 1), k + (L >> 2))];
+                sm += vscv * fma(ph.drho, cc, ph.rho0) * cc;
+            }
+        }
+        dJdphi[e] = sm;
+        Jl = phi[e] * sm;
+    }
+    const double t = block_sum(Jl, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void k_objective_nodes(Grid G, Phys ph, const double* __restrict__ phi,
+                                  const double* __restrict__ c,
+                                  V2<double>* __restrict__ dJdu)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    int i, j, k;
+    node_ijk(G, n, i, j, k);
+    const double vscv = 0.125 * G.hx * G.hy * G.hz;
+    double phis = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        const int ci = i - (q & 1), cj = j - ((q >> 1) & 1), ck = k - (q >> 2);
+        if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
+        if (!((ck + 0.5) * G.hz < 0.5 * G.Lz)) continue;
+        phis += phi[ci + G.nx * (cj + G.ny * ck)];
+    }
+    const double cc = c[n];
+    dJdu[n] = V2<double>{0.0, phis * vscv * (ph.rho0 + 2.0 * ph.drho * cc)};
+}
+
+void launch_objective(const Grid& G, const Phys& ph, const double* phi,
+                      const double* c, double* partial, double* dJdphi,
+                      V2<double>* dJdu, cudaStream_t st)
+{
+    k_objective_cells<<<nblocks(G.C), kBS, 0, st>>>(G, ph, phi, c, partial, dJdphi);
+    k_objective_nodes<<<nblocks(G.N), kBS, 0, st>>>(G, ph, phi, c, dJdu);
+}
+
+// -lambda_n^T dR_n/dtheta per cell: R_n depends on phi_e through the storage
+// of the cell's 8 sub-control volumes and the diffusive part of the 12 face
+// fluxes, on K_e through the Darcy mass flux m (and c_up m).  Dirichlet rows
+// do not depend on theta.
+template <int D, int S_, int T_>
+__device__ __forceinline__ void adj_face(const double (&p8)[8],
+                                         const double (&c8)[8],
+                                         const double (&lp)[8],
+                                         const double (&lc)[8], double phi_e,
+                                         double K_e, const Phys& ph,
+                                         double invh, double area,
+                                         double& gphi, double& gK)
+{
+    double gp = 0.0, gc = 0.0, ci = 0.0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const double w = (u == S_ ? 0.75 : 0.25) * (v == T_ ? 0.75 : 0.25);
+            const int A = corner_of(D, u, v, 0), B = corner_of(D, u, v, 1);
+            gp = fma(w, p8[B] - p8[A], gp);
+            gc = fma(w, c8[B] - c8[A], gc);
+            ci = fma(w, c8[A] + c8[B], ci);
+        }
+    gp *= invh;
+    gc *= invh;
+    ci *= 0.5;
+    const double rho = fma(ph.drho, ci, ph.rho0);
+    const double G = (D == 2) ? fma(ph.g, rho, gp) : gp;
+    const double m = rho * (-(K_e / ph.mu) * G) * area;
+    constexpr int a = corner_of(D, S_, T_, 0), b = corner_of(D, S_, T_, 1);
+    const double cup = (m >= 0.0) ? c8[a] : c8[b];
+    const double dF_dphi = -rho * ph.Dm * gc * area;
+    const double dm_dK = m / K_e;
+    gphi += (lc[a] - lc[b]) * dF_dphi;
+    gK += (lp[a] - lp[b]) * dm_dK + (lc[a] - lc[b]) * cup * dm_dK;
+}
+
+__global__ void k_adjoint_theta(Grid G, Phys ph, CellGeom cg,
+                                const uint8_t* __restrict__ bc,
+                                const double* __restrict__ phi,
+                                const double* __restrict__ K,
+                                const double* __restrict__ p,
+                                const double* __restrict__ c,
+                                const double* __restrict__ c_old,
+                                const V2<double>* __restrict__ lam,
+                                double* __restrict__ dJdphi,
+                                double* __restrict__ dJdK)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G.C) return;
+    const int i = e % G.nx, j = (e / G.nx) % G.ny, k = e / (G.nx * G.ny);
+    const double phi_e = phi[e], K_e = K[e];
+    const double vdt = 0.125 * G.hx * G.hy * G.hz / ph.dt;
+    double p8[8], c8[8], lp[8], lc[8];
+    double gphi = 0.0, gK = 0.0;
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const int nd = node_id(G, i + (L & 1), j + ((L >> 1) & 1), k + (L >> 2));
+        p8[L] = p[nd];
+        c8[L] = c[nd];
+        const uint8_t b = bc[nd];
+        const V2<double> l = lam[nd];
+        lp[L] = (b & BC_P) ? 0.0 : l.p;   // Dirichlet rows carry no theta
+        lc[L] = (b & BC_C) ? 0.0 : l.c;
+        const double co = c_old[nd];
+        const double rn = fma(ph.drho, c8[L], ph.rho0), ro = fma(ph.drho, co, ph.rho0);
+        gphi += lp[L] * vdt * (rn - ro) + lc[L] * vdt * (rn * c8[L] - ro * co);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (s == 0 && t == 0) {
+                adj_face<0, 0, 0>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[0], cg.area[0], gphi, gK);
+                adj_face<1, 0, 0>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[1], cg.area[1], gphi, gK);
+                adj_face<2, 0, 0>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[2], cg.area[2], gphi, gK);
+            } else if (s == 0 && t == 1) {
+                adj_face<0, 0, 1>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[0], cg.area[0], gphi, gK);
+                adj_face<1, 0, 1>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[1], cg.area[1], gphi, gK);
+                adj_face<2, 0, 1>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[2], cg.area[2], gphi, gK);
+            } else if (s == 1 && t == 0) {
+                adj_face<0, 1, 0>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[0], cg.area[0], gphi, gK);
+                adj_face<1, 1, 0>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[1], cg.area[1], gphi, gK);
+                adj_face<2, 1, 0>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[2], cg.area[2], gphi, gK);
+            } else {
+                adj_face<0, 1, 1>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[0], cg.area[0], gphi, gK);
+                adj_face<1, 1, 1>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[1], cg.area[1], gphi, gK);
+                adj_face<2, 1, 1>(p8, c8, lp, lc, phi_e, K_e, ph, cg.ih[2], cg.area[2], gphi, gK);
+            }
+        }
+    dJdphi[e] -= gphi;
+    dJdK[e] -= gK;
+}
+
+void launch_adjoint_theta(const Grid& G, const Phys& ph, const uint8_t* bc,
+                          const double* phi, const double* K, const double* p,
+                          const double* c, const double* c_old,
+                          const V2<double>* lam, double* dJdphi, double* dJdK,
+                          cudaStream_t st)
+{
+    k_adjoint_theta<<<nblocks(G.C), kBS, 0, st>>>(G, ph, make_geom(G), bc, phi, K,
+                                                  p, c, c_old, lam, dJdphi, dJdK);
+}
+
+// rhs of step n-1: -(dR_n/du_{n-1})^T lambda_n.  R_n depends on u_{n-1} only
+// through the old storage -S(c_{n-1})/dt, which is diagonal in the node.
+__global__ void k_adjoint_prev_rhs(Grid G, Phys ph, const uint8_t* __restrict__ bc,
+                                   const double* __restrict__ phi,
+                                   const double* __restrict__ c_old,
+                                   const V2<double>* __restrict__ lam,
+                                   V2<double>* __restrict__ rhs)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    int i, j, k;
+    node_ijk(G, n, i, j, k);
+    double phis = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        const int ci = i - (q & 1), cj = j - ((q >> 1) & 1), ck = k - (q >> 2);
+        if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
+        phis += phi[ci + G.nx * (cj + G.ny * ck)];
+    }
+    const double vdt = phis * 0.125 * G.hx * G.hy * G.hz / ph.dt;
+    const uint8_t b = bc[n];
+    const V2<double> l = lam[n];
+    double r = 0.0;
+    if (!(b & BC_P)) r += vdt * ph.drho * l.p;
+    if (!(b & BC_C)) r += vdt * (ph.rho0 + 2.0 * ph.drho * c_old[n]) * l.c;
+    rhs[n] = V2<double>{0.0, r};
+}
+
+void launch_adjoint_prev_rhs(const Grid& G, const Phys& ph, const uint8_t* bc,
+                             const double* phi, const double* c_old,
+                             const V2<double>* lam, V2<double>* rhs,
+                             cudaStream_t st)
+{
+    k_adjoint_prev_rhs<<<nblocks(G.N), kBS, 0, st>>>(G, ph, bc, phi, c_old, lam, rhs);
+}
+
+}  // namespace elder

@@ -1,0 +1,102 @@
+// common.cuh -- device-side definitions shared by the Elder step kernels.
+//
+// Grid, physical constants, Dirichlet bits and small vector types.  The
+// discretisation is the vertex-centred box method of Section 2.3 on a
+// structured hexahedral box; node n = i + (nx+1)*(j + (ny+1)*k), cell
+// e = i + nx*(j + ny*k).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace elder {
+
+struct Grid {
+    int nx, ny, nz;   // cells per direction
+    int N, C;         // nodes, cells
+    double hx, hy, hz;
+    double Lz;
+};
+
+// Constants of Table 1 / eq. e_lin_density and the time step.
+struct Phys {
+    double rho0, drho;   // rho(c) = rho0 + drho * c
+    double mu, g, Dm;    // viscosity, gravity (along -z), molecular diffusion
+    double dt;           // time step [s]
+};
+
+// Per-sample status codes (values of the C ABI's ELDER_SAMPLE_*).
+constexpr int ELDER_SAMPLE_NEWTON_MAXIT_ = 1;
+constexpr int ELDER_SAMPLE_KRYLOV_MAXIT_ = 2;
+constexpr int ELDER_SAMPLE_BREAKDOWN_ = 3;
+constexpr int ELDER_SAMPLE_NONFINITE_ = 4;
+
+// Dirichlet bits per node (the same on every sample).
+enum : uint8_t { BC_P = 1, BC_C = 2 };
+
+// Column slot of the neighbour at offset (dx,dy,dz) in a 27-point row.
+__host__ __device__ constexpr int slot27(int dx, int dy, int dz)
+{
+    return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+}
+
+template <class T> struct alignas(2 * sizeof(T)) V2 { T p, c; };
+// 2x2 Jacobian block: rows (p-eq, c-eq) x cols (p, c).
+template <class T> struct alignas(4 * sizeof(T)) B4 { T pp, pc, cp, cc; };
+
+__host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
+{
+    return i + (G.nx + 1) * (j + (G.ny + 1) * k);
+}
+
+__device__ __forceinline__ void node_ijk(const Grid& G, int n, int& i, int& j,
+                                         int& k)
+{
+    int nx1 = G.nx + 1, ny1 = G.ny + 1;
+    k = n / (nx1 * ny1);
+    int r = n - k * nx1 * ny1;
+    j = r / nx1;
+    i = r - j * nx1;
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32,
+// at most 1024); every thread receives the result.
+__device__ __forceinline__ double block_sum(double v, double* smem32)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem32[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double t = (threadIdx.x < nw) ? smem32[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) smem32[0] = t;
+    __syncthreads();
+    double r = smem32[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* smem32)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem32[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double t = (threadIdx.x < nw) ? smem32[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1)
+            t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) smem32[0] = t;
+    __syncthreads();
+    double r = smem32[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace elder

@@ -1,0 +1,963 @@
+// elder_api.cu -- context, multigrid hierarchy, Newton / BiCGStab drivers and
+// the C ABI declared in include/elder.h.
+//
+// One implicit Euler step (Sections 2.3 and 5.1) for a batch of S samples:
+//   Newton on the FP64 residual, with a line search;
+//   each Newton system J d = -R solved by BiCGStab, right-preconditioned by
+//   one geometric-multigrid V-cycle whose level matrices are the Jacobians
+//   re-assembled on each grid (injected state, cell-averaged phi and K);
+//   damped 2x2-block-Jacobi smoothing, full weighting / trilinear transfers,
+//   dense inverse on the coarsest grid.
+// Batching: every kernel covers all samples (grid.y); converged or failed
+// samples are masked out by per-sample flags that live on the device.  The
+// host only polls those flags (a few bytes) between Newton and Krylov
+// iterations.  With use_graphs the body of one BiCGStab iteration (two
+// V-cycles, two stencil products, vector updates, scalar recurrences) is
+// captured once per (S, transpose) and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/elder.h"
+#include "kernels.h"
+
+using namespace elder;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+constexpr int KSTRIDE = sizeof(KScal) / sizeof(int);
+constexpr int NSTRIDE = sizeof(NScal) / sizeof(int);
+constexpr int MAX_COARSE_UNKNOWNS = 1200;
+
+struct Fail {
+    int code;
+    std::string msg;
+};
+
+#define CK(call)                                                              \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess)                                                \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? ELDER_ENOMEM          \
+                                                       : ELDER_ECUDA,         \
+                       std::string(#call) + ": " + cudaGetErrorString(e_)};   \
+    } while (0)
+
+#define CKL() CK(cudaGetLastError())
+
+template <class X> X* dalloc(size_t n)
+{
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    CK(cudaMalloc(&p, n * sizeof(X)));
+    return static_cast<X*>(p);
+}
+
+struct DevFree {
+    std::vector<void*> ptrs;
+    void add(void* p) { ptrs.push_back(p); }
+    ~DevFree()
+    {
+        for (void* p : ptrs) cudaFree(p);
+    }
+};
+
+// Dirichlet sets (Section 2.1 and the caption of Fig. 1); see elder.h.
+void dirichlet_host(const elder_config& cf, const Grid& G, std::vector<uint8_t>& bc,
+                    std::vector<double>& cval)
+{
+    bc.assign(G.N, 0);
+    cval.assign(G.N, 0.0);
+    for (int k = 0; k <= G.nz; ++k)
+        for (int j = 0; j <= G.ny; ++j)
+            for (int i = 0; i <= G.nx; ++i) {
+                const int n = node_id(G, i, j, k);
+                const bool top = (k == G.nz), bottom = (k == 0);
+                const bool xe = (i == 0 || i == G.nx), ye = (j == 0 || j == G.ny);
+                const bool sq = (4 * i >= G.nx && 4 * i <= 3 * G.nx && 4 * j >= G.ny &&
+                                 4 * j <= 3 * G.ny);
+                uint8_t b = 0;
+                double cv = 0.0;
+                switch (cf.bc_mode) {
+                case 0:
+                    if (top && xe && ye) b |= BC_P;
+                    if (top && sq) { b |= BC_C; cv = 1.0; }
+                    else if (bottom) b |= BC_C;
+                    break;
+                case 1:
+                    if (top && (xe || ye)) b |= BC_P;
+                    if (top) { b |= BC_C; cv = sq ? 1.0 : 0.0; }
+                    else if (bottom) b |= BC_C;
+                    break;
+                case 2:
+                    if (top && xe && ye) b |= BC_P;
+                    if (top) { b |= BC_C; cv = 1.0; }
+                    else if (bottom) b |= BC_C;
+                    break;
+                default:
+                    if (top && xe && ye) b |= BC_P;
+                    break;
+                }
+                bc[n] = b;
+                cval[n] = cv;
+            }
+}
+
+Grid make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz)
+{
+    Grid G;
+    G.nx = nx;
+    G.ny = ny;
+    G.nz = nz;
+    G.N = (nx + 1) * (ny + 1) * (nz + 1);
+    G.C = nx * ny * nz;
+    G.hx = Lx / nx;
+    G.hy = Ly / ny;
+    G.hz = Lz / nz;
+    G.Lz = Lz;
+    return G;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// solver state for one precision
+// ---------------------------------------------------------------------------
+
+struct SolverBase {
+    virtual ~SolverBase() {}
+};
+
+template <class T> struct Solver : SolverBase {
+    int S = 0;
+    std::vector<B4<T>*> J, Dinv;
+    std::vector<V2<T>*> mb, mx, mx2, mr;  // multigrid vectors per level
+    V2<T> *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr,
+          *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr;
+    double *Ainv = nullptr, *work = nullptr;
+    DevFree mem;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (S, trans)
+    ~Solver()
+    {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    }
+};
+
+struct elder_ctx {
+    elder_config cfg;
+    int device = 0;
+    std::string err = "no error";
+    std::vector<Grid> grids;
+    std::vector<uint8_t*> bc;          // per level [N]
+    double* cval = nullptr;            // level 0 [N]
+    std::vector<double*> phi, K, pl, cl;  // levels >= 1: [S][C], [S][N]
+    double *p_old = nullptr, *c_old = nullptr, *pt = nullptr, *ct = nullptr;
+    V2<double> *R = nullptr, *Rt = nullptr, *tmp2 = nullptr;
+    double* partial = nullptr;         // [S][2][nblk0]
+    double* partial2 = nullptr;
+    NScal* ns = nullptr;
+    KScal* ks = nullptr;
+    NScal* h_ns = nullptr;             // pinned
+    KScal* h_ks = nullptr;             // pinned
+    double* h_scalar = nullptr;        // pinned
+    DevFree mem;
+    std::unique_ptr<Solver<double>> s64;
+    std::unique_ptr<Solver<float>> s32;
+    int nblk0 = 0;
+    ~elder_ctx()
+    {
+        s64.reset();
+        s32.reset();
+        if (h_ns) cudaFreeHost(h_ns);
+        if (h_ks) cudaFreeHost(h_ks);
+        if (h_scalar) cudaFreeHost(h_scalar);
+    }
+};
+
+namespace {
+
+Phys make_phys(const elder_config& c, double dt)
+{
+    return Phys{c.rho0, c.rho1 - c.rho0, c.mu, c.g, c.Dm, dt};
+}
+
+template <class T> Solver<T>& solver(elder_ctx* ctx);
+template <> Solver<double>& solver<double>(elder_ctx* ctx)
+{
+    if (!ctx->s64) ctx->s64.reset(new Solver<double>());
+    return *ctx->s64;
+}
+template <> Solver<float>& solver<float>(elder_ctx* ctx)
+{
+    if (!ctx->s32) ctx->s32.reset(new Solver<float>());
+    return *ctx->s32;
+}
+
+template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv)
+{
+    if (sv.S) return;
+    // the coarsest level is solved by a dense inverse: bound its size
+    if (2 * ctx->grids.back().N > MAX_COARSE_UNKNOWNS) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "coarsest grid %dx%dx%d has %d unknowns (> %d): the grid does not "
+                      "coarsen far enough for the multigrid solver",
+                      ctx->grids.back().nx, ctx->grids.back().ny, ctx->grids.back().nz,
+                      2 * ctx->grids.back().N, MAX_COARSE_UNKNOWNS);
+        throw Fail{ELDER_EINVAL, buf};
+    }
+    const int S = ctx->cfg.max_samples;
+    const int L = (int)ctx->grids.size();
+    for (int l = 0; l < L; ++l) {
+        const Grid& G = ctx->grids[l];
+        const size_t nN = (size_t)S * G.N;
+        sv.J.push_back(dalloc<B4<T>>(nN * 27));
+        sv.mem.add(sv.J.back());
+        sv.Dinv.push_back(dalloc<B4<T>>(nN));
+        sv.mem.add(sv.Dinv.back());
+        for (auto* vec : {&sv.mb, &sv.mx, &sv.mx2, &sv.mr}) {
+            vec->push_back(dalloc<V2<T>>(nN));
+            sv.mem.add(vec->back());
+        }
+    }
+    const size_t n0 = (size_t)S * ctx->grids[0].N;
+    for (V2<T>** q : {&sv.x, &sv.r, &sv.rh, &sv.p, &sv.v, &sv.s, &sv.t, &sv.ph, &sv.sh, &sv.b}) {
+        *q = dalloc<V2<T>>(n0);
+        sv.mem.add(*q);
+    }
+    const int nc = 2 * ctx->grids.back().N;
+    sv.Ainv = dalloc<double>((size_t)S * nc * nc);
+    sv.mem.add(sv.Ainv);
+    sv.work = dalloc<double>((size_t)S * nc * 2 * nc);
+    sv.mem.add(sv.work);
+    sv.S = S;
+}
+
+// Re-discretised Jacobians on every level (Section 5.1): level 0 at the
+// current iterate, coarser levels at the injected state with the averaged
+// coefficients; then the block-diagonal inverses and the coarse inverse.
+template <class T>
+void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
+              const double* K0, const double* p0, const double* c0,
+              const Phys& ph, const int* mask, int mstride, cudaStream_t st)
+{
+    const int L = (int)ctx->grids.size();
+    for (int l = 0; l < L; ++l) {
+        const Grid& G = ctx->grids[l];
+        const double* phi = l == 0 ? phi0 : ctx->phi[l];
+        const double* K = l == 0 ? K0 : ctx->K[l];
+        const double* p = l == 0 ? p0 : ctx->pl[l];
+        const double* c = l == 0 ? c0 : ctx->cl[l];
+        if (l > 0) {
+            const double* pf = l == 1 ? p0 : ctx->pl[l - 1];
+            const double* cf = l == 1 ? c0 : ctx->cl[l - 1];
+            launch_inject(ctx->grids[l - 1], G, pf, cf, ctx->pl[l], ctx->cl[l], mask,
+                          mstride, S, st);
+        }
+        launch_jacobian<T>(G, ph, ctx->bc[l], phi, K, p, c, sv.J[l], mask, mstride, S, st);
+        launch_block_diag_inverse<T>(G, ctx->bc[l], sv.J[l], sv.Dinv[l], mask, mstride, S, st);
+    }
+    launch_coarse_inverse<T>(ctx->grids.back(), ctx->bc.back(), sv.J.back(), sv.work,
+                             sv.Ainv, mask, mstride, S, st);
+    CKL();
+}
+
+void average_coefficients(elder_ctx* ctx, int S, const double* phi0,
+                          const double* K0, cudaStream_t st)
+{
+    for (size_t l = 1; l < ctx->grids.size(); ++l) {
+        const double* pf = l == 1 ? phi0 : ctx->phi[l - 1];
+        const double* kf = l == 1 ? K0 : ctx->K[l - 1];
+        launch_average_cells(ctx->grids[l - 1], ctx->grids[l], pf, kf, ctx->phi[l],
+                             ctx->K[l], ctx->cfg.coarse_K_harmonic, S, st);
+    }
+    CKL();
+}
+
+// One V-cycle: out = M b on level l (masked by the Krylov flags).
+template <class T>
+void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
+            int trans, int S, cudaStream_t st)
+{
+    const int L = (int)ctx->grids.size();
+    const Grid& G = ctx->grids[l];
+    const int* mask = &ctx->ks[0].active;
+    if (l == L - 1) {
+        launch_coarse_apply<T>(G, sv.Ainv, b, out, trans, mask, KSTRIDE, S, st);
+        return;
+    }
+    const elder_config& cf = ctx->cfg;
+    const int nu1 = std::max(1, cf.nu1), nu2 = std::max(0, cf.nu2);
+    const int sweeps = nu1 + nu2;
+    V2<T>* bufA = out;
+    V2<T>* bufB = sv.mx2[l];
+    // choose the first buffer so that the last sweep lands in `out`
+    V2<T>* cur = ((sweeps - 1) % 2 == 0) ? bufA : bufB;
+    V2<T>* oth = (cur == bufA) ? bufB : bufA;
+    launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, nullptr, cur, cf.omega, trans,
+                     mask, KSTRIDE, S, st);
+    for (int q = 1; q < nu1; ++q) {
+        launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
+                         mask, KSTRIDE, S, st);
+        std::swap(cur, oth);
+    }
+    launch_mg_residual<T>(G, sv.J[l], ctx->bc[l], b, cur, sv.mr[l], trans, mask, KSTRIDE, S,
+                          st);
+    launch_restrict<T>(G, ctx->grids[l + 1], ctx->bc[l + 1], sv.mr[l], sv.mb[l + 1], mask,
+                       KSTRIDE, S, st);
+    vcycle<T>(ctx, sv, l + 1, sv.mb[l + 1], sv.mx[l + 1], trans, S, st);
+    launch_prolong_add<T>(G, ctx->grids[l + 1], ctx->bc[l], sv.mx[l + 1], cur, mask, KSTRIDE,
+                          S, st);
+    for (int q = 0; q < nu2; ++q) {
+        launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
+                         mask, KSTRIDE, S, st);
+        std::swap(cur, oth);
+    }
+    if (cur != out) CK(cudaMemcpyAsync(out, cur, sizeof(V2<T>) * (size_t)S * G.N,
+                                       cudaMemcpyDeviceToDevice, st));
+}
+
+template <class T>
+void bicg_iteration(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
+                    int S, cudaStream_t st)
+{
+    const Grid& G = ctx->grids[0];
+    const int nb = ctx->nblk0;
+    KScal* ks = ctx->ks;
+    const int* mask = &ks[0].active;
+    launch_bicg_p<T>(G, sv.r, sv.v, sv.p, ks, S, st);
+    vcycle<T>(ctx, sv, 0, sv.p, sv.ph, trans, S, st);
+    launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.ph, sv.v, trans, 1, sv.rh, ctx->partial, mask,
+                   KSTRIDE, S, st);
+    launch_bicg_finalize(1, ctx->partial, nb, ks, rtol, maxit, S, st);
+    launch_bicg_s<T>(G, sv.r, sv.v, sv.s, nullptr, ks, S, st);
+    vcycle<T>(ctx, sv, 0, sv.s, sv.sh, trans, S, st);
+    launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.sh, sv.t, trans, 2, sv.s, ctx->partial, mask,
+                   KSTRIDE, S, st);
+    launch_bicg_finalize(2, ctx->partial, nb, ks, rtol, maxit, S, st);
+    launch_bicg_xr<T>(G, sv.ph, sv.sh, sv.s, sv.t, sv.rh, sv.x, sv.r, ctx->partial, ks, S, st);
+    launch_bicg_finalize(3, ctx->partial, nb, ks, rtol, maxit, S, st);
+}
+
+__global__ void k_arm_krylov(KScal* ks, const NScal* ns, int S)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    ks[s].active = ns ? ns[s].active : 1;
+    ks[s].iters = 0;
+    ks[s].status = 0;
+}
+
+bool any_krylov_active(elder_ctx* ctx, int S, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(ctx->h_ks, ctx->ks, sizeof(KScal) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int s = 0; s < S; ++s)
+        if (ctx->h_ks[s].active) return true;
+    return false;
+}
+
+// Solve A x = b (or A^T x = b) on the interior system for the samples whose
+// Newton flag is set (all samples when ns == nullptr).  b and the result
+// live in sv.b and sv.x.
+template <class T>
+void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
+              const NScal* ns, int S, cudaStream_t st)
+{
+    const Grid& G = ctx->grids[0];
+    k_arm_krylov<<<nblocks(S, 128), 128, 0, st>>>(ctx->ks, ns, S);
+    launch_bicg_init<T>(G, ctx->bc[0], sv.b, sv.x, sv.r, sv.rh, sv.p, sv.v, ctx->partial,
+                        ctx->ks, S, st);
+    launch_bicg_finalize(0, ctx->partial, ctx->nblk0, ctx->ks, rtol, maxit, S, st);
+    CKL();
+    const bool graphs = ctx->cfg.use_graphs != 0;
+    cudaGraphExec_t exec = nullptr;
+    if (graphs) {
+        auto key = std::make_pair(S, trans);
+        auto it = sv.graphs.find(key);
+        if (it == sv.graphs.end()) {
+            cudaStream_t cs;
+            CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            bicg_iteration<T>(ctx, sv, trans, rtol, maxit, S, cs);
+            CK(cudaStreamEndCapture(cs, &g));
+            CK(cudaGraphInstantiate(&exec, g, 0));
+            CK(cudaGraphDestroy(g));
+            CK(cudaStreamDestroy(cs));
+            sv.graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+    }
+    // The captured finalize kernels bake in rtol and maxit; graphs are keyed
+    // on (S, trans) only, so they are used only with the configured values.
+    const bool use_exec = graphs && rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit;
+    const int poll = 2;
+    for (int it = 0; it < maxit; ++it) {
+        if (it % poll == 0 && !any_krylov_active(ctx, S, st)) break;
+        if (use_exec) CK(cudaGraphLaunch(exec, st));
+        else bicg_iteration<T>(ctx, sv, trans, rtol, maxit, S, st);
+        CKL();
+    }
+}
+
+template <class T>
+int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
+              double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st)
+{
+    Solver<T>& sv = solver<T>(ctx);
+    solver_alloc<T>(ctx, sv);
+    const elder_config& cf = ctx->cfg;
+    const Grid& G = ctx->grids[0];
+    const Phys ph = make_phys(cf, dt);
+    const size_t nN = (size_t)S * G.N;
+    const int nb = ctx->nblk0;
+    NScal* ns = ctx->ns;
+    const int* nmask = &ns[0].active;
+    const int* lsmask = &ns[0].ls_active;
+
+    CK(cudaMemcpyAsync(ctx->p_old, p, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->c_old, c, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    launch_impose_dirichlet(G, ctx->bc[0], ctx->cval, p, c, S, st);
+    average_coefficients(ctx, S, phi, K, st);
+    for (int s = 0; s < S; ++s) {
+        NScal z;
+        std::memset(&z, 0, sizeof(z));
+        z.active = 1;
+        z.ls_active = 1;
+        z.lambda = 1.0;
+        ctx->h_ns[s] = z;
+    }
+    CK(cudaMemcpyAsync(ns, ctx->h_ns, sizeof(NScal) * S, cudaMemcpyHostToDevice, st));
+    launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, p, c, ctx->p_old, ctx->c_old, ctx->R,
+                    ctx->partial, nullptr, 0, S, st);
+    launch_norm_finalize(ctx->partial, nb, ns, 0, S, st);
+    CKL();
+
+    for (int it = 0; it < cf.newton_maxit; ++it) {
+        CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int s = 0; s < S; ++s) any = any || ctx->h_ns[s].active;
+        if (!any) break;
+        assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, st);
+        launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
+        bicgstab<T>(ctx, sv, 0, cf.lin_rtol, cf.lin_maxit, ns, S, st);
+        for (int ls = 0; ls <= cf.ls_max; ++ls) {
+            launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
+            launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
+                            ctx->c_old, ctx->Rt, ctx->partial, lsmask, NSTRIDE, S, st);
+            launch_norm_finalize(ctx->partial, nb, ns, 1, S, st);
+            launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, cf.ls_max, S, st);
+            CKL();
+            CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bool searching = false;
+            for (int s = 0; s < S; ++s) searching = searching || ctx->h_ns[s].ls_active;
+            if (!searching) break;
+        }
+        launch_newton_accept(G, p, c, ctx->pt, ctx->ct, ctx->R, ctx->Rt, ns, S, st);
+        launch_newton_check(ns, ctx->ks, cf.newton_tol_p, cf.newton_tol_c, cf.newton_maxit, S,
+                            st);
+        CKL();
+    }
+    // samples still active here ran out of Newton iterations
+    CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool changed = false;
+    for (int s = 0; s < S; ++s)
+        if (ctx->h_ns[s].active) {
+            ctx->h_ns[s].active = 0;
+            ctx->h_ns[s].status = ELDER_SAMPLE_NEWTON_MAXIT;
+            changed = true;
+        }
+    if (changed)
+        CK(cudaMemcpyAsync(ns, ctx->h_ns, sizeof(NScal) * S, cudaMemcpyHostToDevice, st));
+    launch_newton_restore_failed(G, p, c, ctx->p_old, ctx->c_old, ns, S, st);
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    int rc = ELDER_OK;
+    for (int s = 0; s < S; ++s) {
+        const NScal& k = ctx->h_ns[s];
+        if (status) status[s] = k.status;
+        if (stats) {
+            stats[s].status = k.status;
+            stats[s].newton_iters = k.iters;
+            stats[s].krylov_iters = k.kiters;
+            stats[s].ls_cuts = k.ls_cuts;
+            stats[s].res0 = k.res0;
+            stats[s].res = k.rn;
+        }
+        if (k.status != 0) rc = ELDER_ENOTCONV;
+    }
+    return rc;
+}
+
+template <class T>
+int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const double* p,
+               const double* c, double dt, int trans, const double* rhs, double* x,
+               double rtol, int32_t* status, cudaStream_t st)
+{
+    Solver<T>& sv = solver<T>(ctx);
+    solver_alloc<T>(ctx, sv);
+    const Grid& G = ctx->grids[0];
+    const Phys ph = make_phys(ctx->cfg, dt);
+    const size_t nN = (size_t)S * G.N;
+    average_coefficients(ctx, S, phi, K, st);
+    assemble<T>(ctx, sv, S, phi, K, p, c, ph, nullptr, 0, st);
+    const V2<double>* rhs2 = reinterpret_cast<const V2<double>*>(rhs);
+    V2<double>* x2 = reinterpret_cast<V2<double>*>(x);
+    // rhs in solver precision
+    V2<T>* bT = sv.b;
+    if (std::is_same<T, double>::value)
+        CK(cudaMemcpyAsync(bT, rhs, sizeof(double) * 2 * nN, cudaMemcpyDeviceToDevice, st));
+    else
+        launch_convert<double, T>(rhs2, bT, nN, st);
+    // Dirichlet rows of J are identity rows (R = u - u_D).
+    // forward:   x_D = rhs_D, interior rhs_I - J_ID x_D
+    // transpose: interior J_II^T y_I = rhs_I, then y_D = rhs_D - J_ID^T y_I
+    if (!trans) {
+        launch_axpy_mask<T>(G, ctx->bc[0], bT, sv.mr[0], 1.0, 0, S, st);  // mr = b on D
+        launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.mr[0], sv.mx2[0], 0, 0, nullptr, nullptr,
+                       nullptr, 0, S, st);                                 // J x_D (interior)
+        launch_axpy_mask<T>(G, ctx->bc[0], sv.mx2[0], bT, -1.0, 2, S, st);
+    }
+    bicgstab<T>(ctx, sv, trans, rtol, ctx->cfg.lin_maxit, nullptr, S, st);
+    if (!trans) {
+        launch_axpy_mask<T>(G, ctx->bc[0], sv.mr[0], sv.x, 1.0, 1, S, st);
+    } else {
+        // (A^T y_I) on Dirichlet rows, unmasked
+        launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.x, sv.mx2[0], 1, 3, nullptr, nullptr,
+                       nullptr, 0, S, st);
+        // x_D = rhs_D - (A^T y_I)_D : rebuild rhs in mr then combine
+        if (std::is_same<T, double>::value)
+            CK(cudaMemcpyAsync(sv.mr[0], rhs, sizeof(double) * 2 * nN,
+                               cudaMemcpyDeviceToDevice, st));
+        else
+            launch_convert<double, T>(rhs2, sv.mr[0], nN, st);
+        launch_axpy_mask<T>(G, ctx->bc[0], sv.mx2[0], sv.mr[0], -1.0, 1, S, st);
+        launch_axpy_mask<T>(G, ctx->bc[0], sv.mr[0], sv.x, 1.0, 1, S, st);
+    }
+    if (std::is_same<T, double>::value)
+        CK(cudaMemcpyAsync(x, sv.x, sizeof(double) * 2 * nN, cudaMemcpyDeviceToDevice, st));
+    else
+        launch_convert<T, double>(sv.x, x2, nN, st);
+    CKL();
+    CK(cudaMemcpyAsync(ctx->h_ks, ctx->ks, sizeof(KScal) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int rc = ELDER_OK;
+    for (int s = 0; s < S; ++s) {
+        int stt = ctx->h_ks[s].status;
+        if (stt == 0 && ctx->h_ks[s].active) stt = ELDER_SAMPLE_KRYLOV_MAXIT;
+        if (status) status[s] = stt;
+        if (stt != 0) rc = ELDER_ENOTCONV;
+    }
+    return rc;
+}
+
+int set_error(elder_ctx* ctx, const Fail& f)
+{
+    if (ctx) ctx->err = f.msg;
+    else g_create_error = f.msg;
+    return f.code;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
+{
+    if (!cfg) return ELDER_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = nx;
+    cfg->ny = ny;
+    cfg->nz = nz;
+    cfg->Lx = 600.0;
+    cfg->Ly = 600.0;
+    cfg->Lz = 150.0;
+    cfg->rho0 = 1000.0;
+    cfg->rho1 = 1200.0;
+    cfg->mu = 1e-3;
+    cfg->g = 9.81;
+    cfg->Dm = 3.565e-6;
+    cfg->bc_mode = 0;
+    cfg->precision = ELDER_FP64;
+    cfg->max_samples = 1;
+    cfg->newton_maxit = 25;
+    cfg->newton_tol_c = 1e-11;
+    cfg->newton_tol_p = 1e-11 * 1000.0 * 9.81 * 150.0;
+    cfg->ls_max = 6;
+    cfg->lin_rtol = 1e-4;
+    cfg->lin_maxit = 200;
+    cfg->mg_levels = 0;
+    cfg->nu1 = 2;
+    cfg->nu2 = 2;
+    cfg->omega = 0.7;
+    cfg->coarse_K_harmonic = 0;
+    cfg->use_graphs = 1;
+    return ELDER_OK;
+}
+
+const char* elder_last_error(const elder_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int elder_create(const elder_config* cfg, elder_ctx** out)
+{
+    if (!out) return ELDER_EINVAL;
+    *out = nullptr;
+    if (!cfg) {
+        g_create_error = "cfg is NULL";
+        return ELDER_EINVAL;
+    }
+    const elder_config& c = *cfg;
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.max_samples < 1 || !(c.Lx > 0) ||
+        !(c.Ly > 0) || !(c.Lz > 0) || !(c.mu > 0) || c.bc_mode < 0 || c.bc_mode > 3 ||
+        (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
+        c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0) {
+        g_create_error = "invalid elder_config";
+        return ELDER_EINVAL;
+    }
+    if ((c.bc_mode == 0 || c.bc_mode == 1) && (c.nx % 4 || c.ny % 4)) {
+        g_create_error = "bc_mode 0/1 need nx and ny divisible by 4 (square edges on nodes)";
+        return ELDER_EINVAL;
+    }
+    std::unique_ptr<elder_ctx> ctx(new elder_ctx());
+    ctx->cfg = c;
+    try {
+        CK(cudaGetDevice(&ctx->device));
+        // hierarchy: halve while all three counts are even (and the top square
+        // stays node-aligned in modes 0/1)
+        Grid G = make_grid(c.nx, c.ny, c.nz, c.Lx, c.Ly, c.Lz);
+        ctx->grids.push_back(G);
+        while (c.mg_levels == 0 || (int)ctx->grids.size() < c.mg_levels) {
+            const Grid& Gf = ctx->grids.back();
+            if (Gf.nx % 2 || Gf.ny % 2 || Gf.nz % 2) break;
+            if ((c.bc_mode == 0 || c.bc_mode == 1) && ((Gf.nx / 2) % 4 || (Gf.ny / 2) % 4))
+                break;
+            ctx->grids.push_back(make_grid(Gf.nx / 2, Gf.ny / 2, Gf.nz / 2, c.Lx, c.Ly, c.Lz));
+        }
+        const int S = c.max_samples;
+        const int L = (int)ctx->grids.size();
+        ctx->phi.assign(L, nullptr);
+        ctx->K.assign(L, nullptr);
+        ctx->pl.assign(L, nullptr);
+        ctx->cl.assign(L, nullptr);
+        for (int l = 0; l < L; ++l) {
+            const Grid& Gl = ctx->grids[l];
+            std::vector<uint8_t> bc;
+            std::vector<double> cv;
+            dirichlet_host(c, Gl, bc, cv);
+            uint8_t* dbc = dalloc<uint8_t>(Gl.N);
+            ctx->mem.add(dbc);
+            CK(cudaMemcpy(dbc, bc.data(), Gl.N, cudaMemcpyHostToDevice));
+            ctx->bc.push_back(dbc);
+            if (l == 0) {
+                ctx->cval = dalloc<double>(Gl.N);
+                ctx->mem.add(ctx->cval);
+                CK(cudaMemcpy(ctx->cval, cv.data(), sizeof(double) * Gl.N,
+                              cudaMemcpyHostToDevice));
+            } else {
+                ctx->phi[l] = dalloc<double>((size_t)S * Gl.C);
+                ctx->K[l] = dalloc<double>((size_t)S * Gl.C);
+                ctx->pl[l] = dalloc<double>((size_t)S * Gl.N);
+                ctx->cl[l] = dalloc<double>((size_t)S * Gl.N);
+                for (void* q : {(void*)ctx->phi[l], (void*)ctx->K[l], (void*)ctx->pl[l],
+                                (void*)ctx->cl[l]})
+                    ctx->mem.add(q);
+            }
+        }
+        const size_t nN = (size_t)S * G.N;
+        ctx->nblk0 = nblocks(G.N);
+        for (double** q : {&ctx->p_old, &ctx->c_old, &ctx->pt, &ctx->ct}) {
+            *q = dalloc<double>(nN);
+            ctx->mem.add(*q);
+        }
+        for (V2<double>** q : {&ctx->R, &ctx->Rt, &ctx->tmp2}) {
+            *q = dalloc<V2<double>>(nN);
+            ctx->mem.add(*q);
+        }
+        ctx->partial = dalloc<double>((size_t)S * 2 * ctx->nblk0);
+        ctx->partial2 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
+        ctx->ns = dalloc<NScal>(S);
+        ctx->ks = dalloc<KScal>(S);
+        for (void* q : {(void*)ctx->partial, (void*)ctx->partial2, (void*)ctx->ns,
+                        (void*)ctx->ks})
+            ctx->mem.add(q);
+        CK(cudaMemset(ctx->ks, 0, sizeof(KScal) * S));
+        CK(cudaMemset(ctx->ns, 0, sizeof(NScal) * S));
+        CK(cudaMallocHost((void**)&ctx->h_ns, sizeof(NScal) * S));
+        CK(cudaMallocHost((void**)&ctx->h_ks, sizeof(KScal) * S));
+        CK(cudaMallocHost((void**)&ctx->h_scalar, sizeof(double) * 64));
+        // solver workspace up front when the grid supports the solver (grids
+        // that do not still serve the residual, Jacobian and moment calls)
+        if (2 * ctx->grids.back().N <= MAX_COARSE_UNKNOWNS) {
+            if (c.precision == ELDER_MIXED)
+                solver_alloc<float>(ctx.get(), solver<float>(ctx.get()));
+            else
+                solver_alloc<double>(ctx.get(), solver<double>(ctx.get()));
+        }
+        CK(cudaDeviceSynchronize());
+    } catch (const Fail& f) {
+        g_create_error = f.msg;
+        return f.code;
+    }
+    *out = ctx.release();
+    return ELDER_OK;
+}
+
+int elder_destroy(elder_ctx* ctx)
+{
+    delete ctx;
+    return ELDER_OK;
+}
+
+int elder_sizes(const elder_ctx* ctx, int64_t* N, int64_t* C, int* levels)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (N) *N = ctx->grids[0].N;
+    if (C) *C = ctx->grids[0].C;
+    if (levels) *levels = (int)ctx->grids.size();
+    return ELDER_OK;
+}
+
+static bool bad_S(elder_ctx* ctx, int S)
+{
+    if (S < 1 || S > ctx->cfg.max_samples) {
+        ctx->err = "S out of range [1, max_samples]";
+        return true;
+    }
+    return false;
+}
+
+int elder_fields(elder_ctx* ctx, int S, int kind, const double* params, double K_mean,
+                 double* phi, double* K, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (S < 1 || kind < 0 || kind > 2 || !params || !phi || !K) {
+        ctx->err = "elder_fields: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        launch_fields(ctx->grids[0], kind, params, K_mean, phi, K, S, (cudaStream_t)stream);
+        CKL();
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    return ELDER_OK;
+}
+
+int elder_residual(elder_ctx* ctx, int S, const double* phi, const double* K,
+                   const double* p, const double* c, const double* p_old,
+                   const double* c_old, double dt, double* R, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !p_old || !c_old || !R || !(dt > 0)) {
+        ctx->err = "elder_residual: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        launch_residual(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], ctx->cval, phi, K,
+                        p, c, p_old, c_old, reinterpret_cast<V2<double>*>(R), nullptr, nullptr,
+                        0, S, (cudaStream_t)stream);
+        CKL();
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    return ELDER_OK;
+}
+
+int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
+                   const double* p, const double* c, double dt, double* J, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !J || !(dt > 0)) {
+        ctx->err = "elder_jacobian: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        launch_jacobian<double>(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], phi, K, p,
+                                c, reinterpret_cast<B4<double>*>(J), nullptr, 0, S,
+                                (cudaStream_t)stream);
+        CKL();
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    return ELDER_OK;
+}
+
+int elder_step(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
+               double* c, double dt, int32_t* status, elder_stats* stats, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !(dt > 0)) {
+        ctx->err = "elder_step: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        if (ctx->cfg.precision == ELDER_MIXED)
+            return step_impl<float>(ctx, S, phi, K, p, c, dt, status, stats,
+                                    (cudaStream_t)stream);
+        return step_impl<double>(ctx, S, phi, K, p, c, dt, status, stats,
+                                 (cudaStream_t)stream);
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+}
+
+int elder_solve(elder_ctx* ctx, int S, const double* phi, const double* K, const double* p,
+                const double* c, double dt, int transpose, const double* rhs, double* x,
+                double rtol, int32_t* status, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !rhs || !x || !(dt > 0) || !(rtol > 0)) {
+        ctx->err = "elder_solve: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        if (ctx->cfg.precision == ELDER_MIXED && rtol >= 1e-6)
+            return solve_impl<float>(ctx, S, phi, K, p, c, dt, transpose, rhs, x, rtol, status,
+                                     (cudaStream_t)stream);
+        return solve_impl<double>(ctx, S, phi, K, p, c, dt, transpose, rhs, x, rtol, status,
+                                  (cudaStream_t)stream);
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+}
+
+int elder_moments(elder_ctx* ctx, int S, const double* c, const double* w, double threshold,
+                  double* mean, double* var, double* p_exceed, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (S < 1 || !c || !mean || !var || !p_exceed) {
+        ctx->err = "elder_moments: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        launch_moments(ctx->grids[0].N, S, c, w, threshold, mean, var, p_exceed,
+                       (cudaStream_t)stream);
+        CKL();
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    return ELDER_OK;
+}
+
+int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
+               const double* p0, const double* c0, double dt, int ckpt_every, double* J_out,
+               double* dJ_dphi, double* dJ_dK, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (n_steps < 1 || ckpt_every < 1 || !phi || !K || !p0 || !c0 || !J_out || !dJ_dphi ||
+        !dJ_dK || !(dt > 0)) {
+        ctx->err = "elder_grad: bad argument";
+        return ELDER_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const Grid& G = ctx->grids[0];
+    const Phys ph = make_phys(ctx->cfg, dt);
+    const size_t N = G.N;
+    try {
+        Solver<double>& sv = solver<double>(ctx);
+        solver_alloc<double>(ctx, sv);
+        DevFree local;
+        const int nck = (n_steps + ckpt_every - 1) / ckpt_every + 1;
+        double* ck = dalloc<double>(2 * N * nck);  // checkpoints (p, c) every k steps
+        local.add(ck);
+        double* seg = dalloc<double>(2 * N * (ckpt_every + 1));  // recomputed segment
+        local.add(seg);
+        V2<double>* rhs = dalloc<V2<double>>(N);
+        local.add(rhs);
+        double* pj = dalloc<double>(ctx->nblk0 + nblocks(G.C) + 1);
+        local.add(pj);
+        double* dsum = pj + ctx->nblk0 + nblocks(G.C);
+        double* cur = dalloc<double>(2 * N);
+        local.add(cur);
+        int32_t stat = 0;
+        auto fwd_step = [&](double* pc) -> int {
+            const int rc = (ctx->cfg.precision == ELDER_MIXED)
+                               ? step_impl<float>(ctx, 1, phi, K, pc, pc + N, dt, &stat,
+                                                  nullptr, st)
+                               : step_impl<double>(ctx, 1, phi, K, pc, pc + N, dt, &stat,
+                                                   nullptr, st);
+            return rc;
+        };
+        // forward sweep with checkpoints
+        CK(cudaMemcpyAsync(cur, p0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(cur + N, c0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ck, cur, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, st));
+        int rc_all = ELDER_OK;
+        for (int n = 1; n <= n_steps; ++n) {
+            if (fwd_step(cur) != ELDER_OK) rc_all = ELDER_ENOTCONV;
+            if (n % ckpt_every == 0)
+                CK(cudaMemcpyAsync(ck + 2 * N * (n / ckpt_every), cur, sizeof(double) * 2 * N,
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+        // objective, dJ/dphi (direct part) and dJ/du_N
+        CK(cudaMemsetAsync(dJ_dK, 0, sizeof(double) * G.C, st));
+        launch_objective(G, ph, phi, cur + N, pj, dJ_dphi, rhs, st);
+        launch_sum_partials(pj, nblocks(G.C), dsum, 1, st);
+        CKL();
+        CK(cudaMemcpyAsync(ctx->h_scalar, dsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *J_out = ctx->h_scalar[0];
+        // reverse sweep, segment by segment
+        const int last_seg = (n_steps - 1) / ckpt_every;
+        for (int sg = last_seg; sg >= 0; --sg) {
+            const int k0 = sg * ckpt_every;
+            const int k1 = std::min(n_steps, k0 + ckpt_every);
+            CK(cudaMemcpyAsync(seg, ck + 2 * N * sg, sizeof(double) * 2 * N,
+                               cudaMemcpyDeviceToDevice, st));
+            for (int n = k0 + 1; n <= k1; ++n) {
+                double* dst = seg + 2 * N * (n - k0);
+                CK(cudaMemcpyAsync(dst, seg + 2 * N * (n - k0 - 1), sizeof(double) * 2 * N,
+                                   cudaMemcpyDeviceToDevice, st));
+                if (fwd_step(dst) != ELDER_OK) rc_all = ELDER_ENOTCONV;
+            }
+            for (int n = k1; n >= k0 + 1; --n) {
+                const double* un = seg + 2 * N * (n - k0);
+                const double* uo = seg + 2 * N * (n - k0 - 1);
+                // J_n^T lambda_n = rhs (interior part; the Dirichlet rows of R_n
+                // neither depend on theta nor on u_{n-1}, so lambda_D is not needed)
+                average_coefficients(ctx, 1, phi, K, st);
+                assemble<double>(ctx, sv, 1, phi, K, un, un + N, ph, nullptr, 0, st);
+                CK(cudaMemcpyAsync(sv.b, rhs, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice,
+                                   st));
+                bicgstab<double>(ctx, sv, 1, 1e-12, std::max(ctx->cfg.lin_maxit, 400), nullptr,
+                                 1, st);
+                launch_adjoint_theta(G, ph, ctx->bc[0], phi, K, un, un + N, uo + N, sv.x,
+                                     dJ_dphi, dJ_dK, st);
+                if (n > 1)
+                    launch_adjoint_prev_rhs(G, ph, ctx->bc[0], phi, uo + N, sv.x, rhs, st);
+                CKL();
+            }
+        }
+        CK(cudaStreamSynchronize(st));
+        return rc_all;
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// kernels.h -- host-side launch wrappers of the Elder step kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace elder {
+
+// Per-sample Krylov scalars (BiCGStab of van der Vorst, Templates 2.3.8).
+struct KScal {
+    double rho, rho_old, alpha, omega;
+    double bn2, rn2;
+    int active, iters, status, pad;
+};
+
+// Per-sample Newton state (Section 2.3: Newton with line search).
+struct NScal {
+    double rn, rt, lambda;       // ||R(u)||, ||R(u_trial)||, step length
+    double res0;
+    double dmax_p, dmax_c;       // max |lambda * delta| of the last step
+    int active;                  // still iterating
+    int ls_active;               // line search still running
+    int accepted;                // trial accepted in this Newton iteration
+    int iters, ls_cuts, kiters, ls_count, status;
+};
+
+constexpr int kBS = 256;  // threads per block of the node kernels
+
+inline int nblocks(int n, int bs = kBS) { return (n + bs - 1) / bs; }
+
+// ---- assembly.cu ---------------------------------------------------------
+void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
+                     const double* cval, const double* phi, const double* K,
+                     const double* p, const double* c, const double* p_old,
+                     const double* c_old, V2<double>* R, double* partial,
+                     const int* mask, int mask_stride, int S,
+                     cudaStream_t st);
+template <class T>
+void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
+                     const double* phi, const double* K, const double* p,
+                     const double* c, B4<T>* J, const int* mask,
+                     int mask_stride, int S, cudaStream_t st);
+void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
+                   const double* cf, double* pc, double* cc, const int* mask,
+                   int mask_stride, int S, cudaStream_t st);
+void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
+                          const double* Kf, double* phic, double* Kc,
+                          int harmonic, int S, cudaStream_t st);
+template <class T>
+void launch_block_diag_inverse(const Grid& G, const uint8_t* bc,
+                               const B4<T>* J, B4<T>* Dinv, const int* mask,
+                               int mask_stride, int S, cudaStream_t st);
+template <class T>
+void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<T>* J,
+                           double* work, double* Ainv, const int* mask,
+                           int mask_stride, int S, cudaStream_t st);
+void launch_impose_dirichlet(const Grid& G, const uint8_t* bc,
+                             const double* cval, double* p, double* c, int S,
+                             cudaStream_t st);
+void launch_fields(const Grid& G, int kind, const double* params,
+                   double K_mean, double* phi, double* K, int S,
+                   cudaStream_t st);
+
+// ---- linalg.cu -----------------------------------------------------------
+// y = A x (or A^T x); mode 0: plain, 1: partial[0] = (a, y),
+// 2: partial[0] = (y, a), partial[1] = (y, y), 3: plain and unmasked.
+// Modes 0-2 mask the output at Dirichlet components.  partial layout
+// [S][2][nblk].
+template <class T>
+void launch_spmv(const Grid& G, const B4<T>* J, const uint8_t* bc,
+                 const V2<T>* x, V2<T>* y, int trans, int mode,
+                 const V2<T>* a, double* partial, const int* mask,
+                 int mask_stride, int S, cudaStream_t st);
+// xo = x + omega Dinv (b - A x) (x == nullptr: xo = omega Dinv b)
+template <class T>
+void launch_smooth(const Grid& G, const B4<T>* J, const B4<T>* Dinv,
+                   const uint8_t* bc, const V2<T>* b, const V2<T>* x,
+                   V2<T>* xo, double omega, int trans, const int* mask,
+                   int mask_stride, int S, cudaStream_t st);
+template <class T>
+void launch_mg_residual(const Grid& G, const B4<T>* J, const uint8_t* bc,
+                        const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
+                        const int* mask, int mask_stride, int S,
+                        cudaStream_t st);
+template <class T>
+void launch_restrict(const Grid& Gf, const Grid& Gc, const uint8_t* bcc,
+                     const V2<T>* rf, V2<T>* bc_out, const int* mask,
+                     int mask_stride, int S, cudaStream_t st);
+template <class T>
+void launch_prolong_add(const Grid& Gf, const Grid& Gc, const uint8_t* bcf,
+                        const V2<T>* xc, V2<T>* xf, const int* mask,
+                        int mask_stride, int S, cudaStream_t st);
+template <class T>
+void launch_coarse_apply(const Grid& G, const double* Ainv, const V2<T>* b,
+                         V2<T>* x, int trans, const int* mask, int mask_stride,
+                         int S, cudaStream_t st);
+
+// BiCGStab pieces (all skip samples whose KScal.active == 0)
+template <class T>
+void launch_bicg_init(const Grid& G, const uint8_t* bc, const V2<T>* b,
+                      V2<T>* x, V2<T>* r, V2<T>* rh, V2<T>* p, V2<T>* v,
+                      double* partial, KScal* ks, int S, cudaStream_t st);
+template <class T>
+void launch_bicg_p(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* p,
+                   const KScal* ks, int S, cudaStream_t st);
+template <class T>
+void launch_bicg_s(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* s,
+                   double* partial, const KScal* ks, int S, cudaStream_t st);
+template <class T>
+void launch_bicg_xr(const Grid& G, const V2<T>* ph, const V2<T>* sh,
+                    const V2<T>* s, const V2<T>* t, const V2<T>* rh, V2<T>* x,
+                    V2<T>* r, double* partial, const KScal* ks, int S,
+                    cudaStream_t st);
+// stage: 0 init, 1 alpha, 2 omega, 3 end of iteration
+void launch_bicg_finalize(int stage, const double* partial, int nblk,
+                          KScal* ks, double rtol, int maxit, int S,
+                          cudaStream_t st);
+
+// Newton pieces
+void launch_norm_finalize(const double* partial, int nblk, NScal* ns,
+                          int which, int S, cudaStream_t st);
+template <class T>
+void launch_newton_rhs(const Grid& G, const V2<double>* R, V2<T>* b,
+                       const NScal* ns, int S, cudaStream_t st);
+template <class T>
+void launch_newton_trial(const Grid& G, const double* p, const double* c,
+                         const V2<T>* dx, double* pt, double* ct,
+                         double* partial, const NScal* ns, int S,
+                         cudaStream_t st);
+void launch_newton_ls_finalize(const double* partial_res,
+                               const double* partial_max, int nblk,
+                               NScal* ns, int ls_max, int S, cudaStream_t st);
+void launch_newton_accept(const Grid& G, double* p, double* c,
+                          const double* pt, const double* ct,
+                          V2<double>* R, const V2<double>* Rt,
+                          const NScal* ns, int S, cudaStream_t st);
+void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
+                         double tol_c, int maxit, int S, cudaStream_t st);
+void launch_newton_restore_failed(const Grid& G, double* p, double* c,
+                                  const double* p_old, const double* c_old,
+                                  const NScal* ns, int S, cudaStream_t st);
+
+void launch_moments(int N, int S, const double* c, const double* w,
+                    double threshold, double* mean, double* var,
+                    double* pexc, cudaStream_t st);
+
+// ---- adjoint pieces (assembly.cu) ----------------------------------------
+void launch_objective(const Grid& G, const Phys& ph, const double* phi,
+                      const double* c, double* partial, double* dJdphi,
+                      V2<double>* dJdu, cudaStream_t st);
+void launch_adjoint_theta(const Grid& G, const Phys& ph, const uint8_t* bc,
+                          const double* phi, const double* K,
+                          const double* p, const double* c,
+                          const double* c_old, const V2<double>* lam,
+                          double* dJdphi, double* dJdK, cudaStream_t st);
+void launch_adjoint_prev_rhs(const Grid& G, const Phys& ph, const uint8_t* bc,
+                             const double* phi, const double* c_old,
+                             const V2<double>* lam, V2<double>* rhs,
+                             cudaStream_t st);
+
+// small helpers
+void launch_sum_partials(const double* partial, int nblk, double* out,
+                         int S, cudaStream_t st);
+template <class T>
+void launch_axpy_mask(const Grid& G, const uint8_t* bc, const V2<T>* x,
+                      V2<T>* y, double a, int which, int S, cudaStream_t st);
+template <class Ts, class Td>
+void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st);
+
+}  // namespace elder

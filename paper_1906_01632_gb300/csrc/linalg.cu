@@ -1,0 +1,931 @@
+// linalg.cu -- batched linear algebra of the Newton/BiCGStab/multigrid solve
+// (Section 2.3 and Section 5.1): 27-point 2x2-block stencil products,
+// damped block-Jacobi smoothing, full-weighting restriction / trilinear
+// prolongation on the vertex-centred 2:1 hierarchy, the dense coarse solve,
+// the BiCGStab vector updates (van der Vorst; Templates, Sec. 2.3.8) with
+// FP64 inner products, and the Newton line-search bookkeeping.
+//
+// Every node kernel runs one thread per node with grid.y = sample and skips
+// samples whose mask flag is 0 (converged or failed samples).  Reductions are
+// two-stage and deterministic: per-block partials [S][2][nblk], then one
+// block per sample sums them in a fixed order.
+//
+// Solver vectors hold the unknowns of the interior system: Dirichlet
+// components are kept at 0 by masking every kernel's output.
+#include "kernels.h"
+
+namespace elder {
+
+__device__ __forceinline__ bool on(const int* mask, int stride, int s)
+{
+    return mask == nullptr || mask[(size_t)s * stride] != 0;
+}
+
+constexpr int KS_STRIDE = sizeof(KScal) / sizeof(int);
+constexpr int NS_STRIDE = sizeof(NScal) / sizeof(int);
+static_assert(sizeof(KScal) % sizeof(int) == 0, "KScal layout");
+static_assert(sizeof(NScal) % sizeof(int) == 0, "NScal layout");
+
+// y_n = sum over the 27 neighbours of the 2x2 block times x (or the
+// transposed product, reading row m's block of offset -d).
+template <class T, bool TRANS>
+__device__ __forceinline__ void stencil_apply(const Grid& G,
+                                              const B4<T>* __restrict__ J,
+                                              const V2<T>* __restrict__ x,
+                                              int n, int i, int j, int k,
+                                              T& yp, T& yc)
+{
+    const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
+    yp = T(0);
+    yc = T(0);
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const bool ok = (dx < 0 ? i > 0 : (dx > 0 ? i < G.nx : true)) &&
+                                (dy < 0 ? j > 0 : (dy > 0 ? j < G.ny : true)) &&
+                                (dz < 0 ? k > 0 : (dz > 0 ? k < G.nz : true));
+                if (ok) {
+                    const int m = n + dx + dy * sy + dz * sz;
+                    const V2<T> xv = x[m];
+                    if (!TRANS) {
+                        const B4<T> b = J[(size_t)slot27(dx, dy, dz) * G.N + n];
+                        yp += b.pp * xv.p + b.pc * xv.c;
+                        yc += b.cp * xv.p + b.cc * xv.c;
+                    } else {
+                        const B4<T> b = J[(size_t)slot27(-dx, -dy, -dz) * G.N + m];
+                        yp += b.pp * xv.p + b.cp * xv.c;
+                        yc += b.pc * xv.p + b.cc * xv.c;
+                    }
+                }
+            }
+}
+
+// ---------------------------------------------------------------------------
+// SpMV with fused inner products
+// ---------------------------------------------------------------------------
+
+template <class T, bool TRANS, int MODE>
+__global__ void __launch_bounds__(kBS)
+    k_spmv(Grid G, const B4<T>* __restrict__ J, const uint8_t* __restrict__ bc,
+           const V2<T>* __restrict__ x, V2<T>* __restrict__ y,
+           const V2<T>* __restrict__ a, double* __restrict__ partial,
+           const int* mask, int mstride)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const size_t on_ = (size_t)s * G.N;
+    J += (size_t)s * 27 * G.N;
+    x += on_;
+    y += on_;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double d0 = 0.0, d1 = 0.0;
+    if (n < G.N) {
+        int i, j, k;
+        node_ijk(G, n, i, j, k);
+        T yp, yc;
+        stencil_apply<T, TRANS>(G, J, x, n, i, j, k, yp, yc);
+        if (MODE != 3) {
+            const uint8_t b = bc[n];
+            if (b & BC_P) yp = T(0);
+            if (b & BC_C) yc = T(0);
+        }
+        y[n] = V2<T>{yp, yc};
+        if (MODE == 1 || MODE == 2) {
+            const V2<T> av = a[on_ + n];
+            d0 = (double)av.p * (double)yp + (double)av.c * (double)yc;
+        }
+        if (MODE == 2) d1 = (double)yp * (double)yp + (double)yc * (double)yc;
+    }
+    if (MODE == 1 || MODE == 2) {
+        const double t0 = block_sum(d0, red);
+        if (threadIdx.x == 0) partial[((size_t)s * 2 + 0) * gridDim.x + blockIdx.x] = t0;
+    }
+    if (MODE == 2) {
+        const double t1 = block_sum(d1, red);
+        if (threadIdx.x == 0) partial[((size_t)s * 2 + 1) * gridDim.x + blockIdx.x] = t1;
+    }
+}
+
+template <class T>
+void launch_spmv(const Grid& G, const B4<T>* J, const uint8_t* bc,
+                 const V2<T>* x, V2<T>* y, int trans, int mode,
+                 const V2<T>* a, double* partial, const int* mask,
+                 int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+#define ELDER_SPMV(TR, MO) \
+    k_spmv<T, TR, MO><<<grid, kBS, 0, st>>>(G, J, bc, x, y, a, partial, mask, mstride)
+    if (!trans) {
+        if (mode == 0) ELDER_SPMV(false, 0);
+        else if (mode == 1) ELDER_SPMV(false, 1);
+        else if (mode == 2) ELDER_SPMV(false, 2);
+        else ELDER_SPMV(false, 3);
+    } else {
+        if (mode == 0) ELDER_SPMV(true, 0);
+        else if (mode == 1) ELDER_SPMV(true, 1);
+        else if (mode == 2) ELDER_SPMV(true, 2);
+        else ELDER_SPMV(true, 3);
+    }
+#undef ELDER_SPMV
+}
+
+// ---------------------------------------------------------------------------
+// multigrid: damped block-Jacobi smoother, residual, transfers, coarse solve
+// ---------------------------------------------------------------------------
+
+template <class T, bool TRANS, bool ZEROX>
+__global__ void __launch_bounds__(kBS)
+    k_smooth(Grid G, const B4<T>* __restrict__ J, const B4<T>* __restrict__ Dinv,
+             const uint8_t* __restrict__ bc, const V2<T>* __restrict__ b,
+             const V2<T>* __restrict__ x, V2<T>* __restrict__ xo, T omega,
+             const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const size_t on_ = (size_t)s * G.N;
+    const V2<T> bv = b[on_ + n];
+    T rp = bv.p, rc = bv.c;
+    V2<T> xn{T(0), T(0)};
+    if (!ZEROX) {
+        int i, j, k;
+        node_ijk(G, n, i, j, k);
+        T yp, yc;
+        stencil_apply<T, TRANS>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
+        rp -= yp;
+        rc -= yc;
+        xn = x[on_ + n];
+    }
+    const B4<T> d = Dinv[on_ + n];
+    T zp, zc;
+    if (!TRANS) { zp = d.pp * rp + d.pc * rc; zc = d.cp * rp + d.cc * rc; }
+    else { zp = d.pp * rp + d.cp * rc; zc = d.pc * rp + d.cc * rc; }
+    T op = xn.p + omega * zp, oc = xn.c + omega * zc;
+    const uint8_t m = bc[n];
+    if (m & BC_P) op = T(0);
+    if (m & BC_C) oc = T(0);
+    xo[on_ + n] = V2<T>{op, oc};
+}
+
+template <class T>
+void launch_smooth(const Grid& G, const B4<T>* J, const B4<T>* Dinv,
+                   const uint8_t* bc, const V2<T>* b, const V2<T>* x,
+                   V2<T>* xo, double omega, int trans, const int* mask,
+                   int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    const T w = T(omega);
+    if (x == nullptr) {
+        if (trans) k_smooth<T, true, true><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+        else k_smooth<T, false, true><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+    } else {
+        if (trans) k_smooth<T, true, false><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+        else k_smooth<T, false, false><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+    }
+}
+
+template <class T, bool TRANS>
+__global__ void __launch_bounds__(kBS)
+    k_mg_residual(Grid G, const B4<T>* __restrict__ J, const uint8_t* __restrict__ bc,
+                  const V2<T>* __restrict__ b, const V2<T>* __restrict__ x,
+                  V2<T>* __restrict__ r, const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const size_t on_ = (size_t)s * G.N;
+    int i, j, k;
+    node_ijk(G, n, i, j, k);
+    T yp, yc;
+    stencil_apply<T, TRANS>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
+    const V2<T> bv = b[on_ + n];
+    T rp = bv.p - yp, rc = bv.c - yc;
+    const uint8_t m = bc[n];
+    if (m & BC_P) rp = T(0);
+    if (m & BC_C) rc = T(0);
+    r[on_ + n] = V2<T>{rp, rc};
+}
+
+template <class T>
+void launch_mg_residual(const Grid& G, const B4<T>* J, const uint8_t* bc,
+                        const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
+                        const int* mask, int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    if (trans) k_mg_residual<T, true><<<grid, kBS, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
+    else k_mg_residual<T, false><<<grid, kBS, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
+}
+
+// Full weighting = transpose of trilinear interpolation on the vertex-centred
+// 2:1 hierarchy (coarse node (I,J,K) is fine node (2I,2J,2K)).
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_restrict(Grid Gf, Grid Gc, const uint8_t* __restrict__ bcc,
+               const V2<T>* __restrict__ rf, V2<T>* __restrict__ bco,
+               const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Gc.N) return;
+    int I, J, K;
+    node_ijk(Gc, n, I, J, K);
+    rf += (size_t)s * Gf.N;
+    T sp = T(0), sc = T(0);
+#pragma unroll
+    for (int c = -1; c <= 1; ++c)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b)
+#pragma unroll
+            for (int a = -1; a <= 1; ++a) {
+                const int fi = 2 * I + a, fj = 2 * J + b, fk = 2 * K + c;
+                if (fi < 0 || fi > Gf.nx || fj < 0 || fj > Gf.ny || fk < 0 || fk > Gf.nz)
+                    continue;
+                const T w = T((a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5) * (c == 0 ? 1.0 : 0.5));
+                const V2<T> v = rf[node_id(Gf, fi, fj, fk)];
+                sp += w * v.p;
+                sc += w * v.c;
+            }
+    const uint8_t m = bcc[n];
+    if (m & BC_P) sp = T(0);
+    if (m & BC_C) sc = T(0);
+    bco[(size_t)s * Gc.N + n] = V2<T>{sp, sc};
+}
+
+template <class T>
+void launch_restrict(const Grid& Gf, const Grid& Gc, const uint8_t* bcc,
+                     const V2<T>* rf, V2<T>* bco, const int* mask, int mstride,
+                     int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(Gc.N), S);
+    k_restrict<T><<<grid, kBS, 0, st>>>(Gf, Gc, bcc, rf, bco, mask, mstride);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_prolong_add(Grid Gf, Grid Gc, const uint8_t* __restrict__ bcf,
+                  const V2<T>* __restrict__ xc, V2<T>* __restrict__ xf,
+                  const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Gf.N) return;
+    int i, j, k;
+    node_ijk(Gf, n, i, j, k);
+    xc += (size_t)s * Gc.N;
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
+            wk = (k & 1) ? T(0.5) : T(1);
+    T sp = T(0), sc = T(0);
+    for (int c = 0; c < nk; ++c)
+        for (int b = 0; b < nj; ++b)
+            for (int a = 0; a < ni; ++a) {
+                const V2<T> v = xc[node_id(Gc, I0 + a, J0 + b, K0 + c)];
+                const T w = wi * wj * wk;
+                sp += w * v.p;
+                sc += w * v.c;
+            }
+    const uint8_t m = bcf[n];
+    V2<T> o = xf[(size_t)s * Gf.N + n];
+    o.p = (m & BC_P) ? T(0) : o.p + sp;
+    o.c = (m & BC_C) ? T(0) : o.c + sc;
+    xf[(size_t)s * Gf.N + n] = o;
+}
+
+template <class T>
+void launch_prolong_add(const Grid& Gf, const Grid& Gc, const uint8_t* bcf,
+                        const V2<T>* xc, V2<T>* xf, const int* mask,
+                        int mstride, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(Gf.N), S);
+    k_prolong_add<T><<<grid, kBS, 0, st>>>(Gf, Gc, bcf, xc, xf, mask, mstride);
+}
+
+// x = A_c^{-1} b on the coarsest grid (FP64 inverse), one block per sample.
+template <class T>
+__global__ void k_coarse_apply(int n, const double* __restrict__ Ainv,
+                               const V2<T>* __restrict__ b, V2<T>* __restrict__ x,
+                               int trans, const int* mask, int mstride)
+{
+    extern __shared__ double bs[];
+    const int s = blockIdx.x;
+    if (!on(mask, mstride, s)) return;
+    const T* bb = reinterpret_cast<const T*>(b + (size_t)s * (n / 2));
+    for (int q = threadIdx.x; q < n; q += blockDim.x) bs[q] = (double)bb[q];
+    __syncthreads();
+    const double* A = Ainv + (size_t)s * n * n;
+    T* xx = reinterpret_cast<T*>(x + (size_t)s * (n / 2));
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double acc = 0.0;
+        if (!trans)
+            for (int q = 0; q < n; ++q) acc = fma(A[(size_t)r * n + q], bs[q], acc);
+        else
+            for (int q = 0; q < n; ++q) acc = fma(A[(size_t)q * n + r], bs[q], acc);
+        xx[r] = T(acc);
+    }
+}
+
+template <class T>
+void launch_coarse_apply(const Grid& G, const double* Ainv, const V2<T>* b,
+                         V2<T>* x, int trans, const int* mask, int mstride,
+                         int S, cudaStream_t st)
+{
+    const int n = 2 * G.N;
+    k_coarse_apply<T><<<S, 128, sizeof(double) * n, st>>>(n, Ainv, b, x, trans, mask, mstride);
+}
+
+// ---------------------------------------------------------------------------
+// BiCGStab vector updates and per-sample scalars
+// ---------------------------------------------------------------------------
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_bicg_init(Grid G, const uint8_t* __restrict__ bc, const V2<T>* __restrict__ b,
+                V2<T>* x, V2<T>* r, V2<T>* rh, V2<T>* p, V2<T>* v,
+                double* __restrict__ partial, const KScal* ks)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    if (!ks[s].active) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double d = 0.0;
+    if (n < G.N) {
+        const size_t q = (size_t)s * G.N + n;
+        V2<T> bv = b[q];
+        const uint8_t m = bc[n];
+        if (m & BC_P) bv.p = T(0);
+        if (m & BC_C) bv.c = T(0);
+        const V2<T> z{T(0), T(0)};
+        x[q] = z;
+        p[q] = z;
+        v[q] = z;
+        r[q] = bv;
+        rh[q] = bv;
+        d = (double)bv.p * (double)bv.p + (double)bv.c * (double)bv.c;
+    }
+    const double t = block_sum(d, red);
+    if (threadIdx.x == 0) partial[((size_t)s * 2) * gridDim.x + blockIdx.x] = t;
+}
+
+template <class T>
+void launch_bicg_init(const Grid& G, const uint8_t* bc, const V2<T>* b,
+                      V2<T>* x, V2<T>* r, V2<T>* rh, V2<T>* p, V2<T>* v,
+                      double* partial, KScal* ks, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_bicg_init<T><<<grid, kBS, 0, st>>>(G, bc, b, x, r, rh, p, v, partial, ks);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_bicg_p(int N, const V2<T>* __restrict__ r, const V2<T>* __restrict__ v,
+             V2<T>* __restrict__ p, const KScal* ks)
+{
+    const int s = blockIdx.y;
+    const KScal k = ks[s];
+    if (!k.active) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double beta = (k.rho / k.rho_old) * (k.alpha / k.omega);
+    const T b = T(beta), w = T(k.omega);
+    const size_t q = (size_t)s * N + n;
+    const V2<T> rv = r[q], vv = v[q];
+    V2<T> pv = p[q];
+    pv.p = rv.p + b * (pv.p - w * vv.p);
+    pv.c = rv.c + b * (pv.c - w * vv.c);
+    p[q] = pv;
+}
+
+template <class T>
+void launch_bicg_p(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* p,
+                   const KScal* ks, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_bicg_p<T><<<grid, kBS, 0, st>>>(G.N, r, v, p, ks);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_bicg_s(int N, const V2<T>* __restrict__ r, const V2<T>* __restrict__ v,
+             V2<T>* __restrict__ sv, const KScal* ks)
+{
+    const int s = blockIdx.y;
+    const KScal k = ks[s];
+    if (!k.active) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const T a = T(k.alpha);
+    const size_t q = (size_t)s * N + n;
+    const V2<T> rv = r[q], vv = v[q];
+    sv[q] = V2<T>{rv.p - a * vv.p, rv.c - a * vv.c};
+}
+
+template <class T>
+void launch_bicg_s(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* s,
+                   double* partial, const KScal* ks, int S, cudaStream_t st)
+{
+    (void)partial;
+    dim3 grid(nblocks(G.N), S);
+    k_bicg_s<T><<<grid, kBS, 0, st>>>(G.N, r, v, s, ks);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_bicg_xr(int N, const V2<T>* __restrict__ ph, const V2<T>* __restrict__ sh,
+              const V2<T>* __restrict__ sv, const V2<T>* __restrict__ t,
+              const V2<T>* __restrict__ rh, V2<T>* __restrict__ x,
+              V2<T>* __restrict__ r, double* __restrict__ partial,
+              const KScal* ks)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    const KScal k = ks[s];
+    if (!k.active) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double d0 = 0.0, d1 = 0.0;
+    if (n < N) {
+        const T a = T(k.alpha), w = T(k.omega);
+        const size_t q = (size_t)s * N + n;
+        const V2<T> pv = ph[q], shv = sh[q], svv = sv[q], tv = t[q], rhv = rh[q];
+        V2<T> xv = x[q];
+        xv.p += a * pv.p + w * shv.p;
+        xv.c += a * pv.c + w * shv.c;
+        x[q] = xv;
+        const V2<T> rv{svv.p - w * tv.p, svv.c - w * tv.c};
+        r[q] = rv;
+        d0 = (double)rv.p * (double)rv.p + (double)rv.c * (double)rv.c;
+        d1 = (double)rhv.p * (double)rv.p + (double)rhv.c * (double)rv.c;
+    }
+    const double t0 = block_sum(d0, red);
+    const double t1 = block_sum(d1, red);
+    if (threadIdx.x == 0) {
+        partial[((size_t)s * 2 + 0) * gridDim.x + blockIdx.x] = t0;
+        partial[((size_t)s * 2 + 1) * gridDim.x + blockIdx.x] = t1;
+    }
+}
+
+template <class T>
+void launch_bicg_xr(const Grid& G, const V2<T>* ph, const V2<T>* sh,
+                    const V2<T>* s, const V2<T>* t, const V2<T>* rh, V2<T>* x,
+                    V2<T>* r, double* partial, const KScal* ks, int S,
+                    cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_bicg_xr<T><<<grid, kBS, 0, st>>>(G.N, ph, sh, s, t, rh, x, r, partial, ks);
+}
+
+// One block per sample: fixed-order sums of the partials and the BiCGStab
+// scalar recurrences.
+__global__ void k_bicg_finalize(int stage, const double* __restrict__ partial,
+                                int nblk, KScal* ks, double rtol, int maxit)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    KScal k = ks[s];
+    if (!k.active) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+        a0 += partial[((size_t)s * 2 + 0) * nblk + q];
+        a1 += partial[((size_t)s * 2 + 1) * nblk + q];
+    }
+    a0 = block_sum(a0, red);
+    a1 = block_sum(a1, red);
+    if (threadIdx.x != 0) return;
+    if (stage == 0) {  // after init: ||b||^2 = (rh, r)
+        k.bn2 = a0;
+        k.rn2 = a0;
+        k.rho = a0;
+        k.rho_old = 1.0;
+        k.alpha = 1.0;
+        k.omega = 1.0;
+        k.iters = 0;
+        k.status = 0;
+        if (!(a0 > 0.0)) {
+            k.active = 0;
+            if (!isfinite(a0)) k.status = ELDER_SAMPLE_NONFINITE_;
+        }
+    } else if (stage == 1) {  // alpha = rho / (rh, v)
+        if (a0 == 0.0 || !isfinite(a0)) {
+            k.active = 0;
+            k.status = ELDER_SAMPLE_BREAKDOWN_;
+        } else {
+            k.alpha = k.rho / a0;
+        }
+    } else if (stage == 2) {  // omega = (t, s) / (t, t)
+        k.omega = (a1 > 0.0) ? a0 / a1 : 0.0;
+    } else {  // end of iteration: ||r||^2 and the next rho = (rh, r)
+        k.rn2 = a0;
+        k.rho_old = k.rho;
+        k.rho = a1;
+        k.iters += 1;
+        if (!isfinite(a0)) {
+            k.active = 0;
+            k.status = ELDER_SAMPLE_NONFINITE_;
+        } else if (a0 <= rtol * rtol * k.bn2) {
+            k.active = 0;
+        } else if (k.iters >= maxit) {
+            k.active = 0;
+            k.status = ELDER_SAMPLE_KRYLOV_MAXIT_;
+        } else if (k.rho == 0.0 || k.omega == 0.0) {
+            k.active = 0;
+            k.status = ELDER_SAMPLE_BREAKDOWN_;
+        }
+    }
+    ks[s] = k;
+}
+
+void launch_bicg_finalize(int stage, const double* partial, int nblk,
+                          KScal* ks, double rtol, int maxit, int S,
+                          cudaStream_t st)
+{
+    k_bicg_finalize<<<S, 128, 0, st>>>(stage, partial, nblk, ks, rtol, maxit);
+}
+
+// ---------------------------------------------------------------------------
+// Newton with line search
+// ---------------------------------------------------------------------------
+
+// which = 0: ||R(u)|| (also res0), which = 1: ||R(u_trial)||
+__global__ void k_norm_finalize(const double* __restrict__ partial, int nblk,
+                                NScal* ns, int which)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    if (which == 1 && !ns[s].ls_active) return;
+    double a = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) a += partial[(size_t)s * nblk + q];
+    a = block_sum(a, red);
+    if (threadIdx.x != 0) return;
+    const double r = sqrt(a);
+    if (which == 0) {
+        ns[s].rn = r;
+        ns[s].res0 = r;
+        if (!isfinite(r)) {
+            ns[s].active = 0;
+            ns[s].ls_active = 0;
+            ns[s].status = ELDER_SAMPLE_NONFINITE_;
+        }
+    } else {
+        ns[s].rt = r;
+    }
+}
+
+void launch_norm_finalize(const double* partial, int nblk, NScal* ns,
+                          int which, int S, cudaStream_t st)
+{
+    k_norm_finalize<<<S, 128, 0, st>>>(partial, nblk, ns, which);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_newton_rhs(int N, const V2<double>* __restrict__ R, V2<T>* __restrict__ b,
+                 const NScal* ns)
+{
+    const int s = blockIdx.y;
+    if (!ns[s].active) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const size_t q = (size_t)s * N + n;
+    const V2<double> r = R[q];
+    b[q] = V2<T>{T(-r.p), T(-r.c)};
+}
+
+template <class T>
+void launch_newton_rhs(const Grid& G, const V2<double>* R, V2<T>* b,
+                       const NScal* ns, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_newton_rhs<T><<<grid, kBS, 0, st>>>(G.N, R, b, ns);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBS)
+    k_newton_trial(int N, const double* __restrict__ p, const double* __restrict__ c,
+                   const V2<T>* __restrict__ dx, double* __restrict__ pt,
+                   double* __restrict__ ct, double* __restrict__ partial,
+                   const NScal* ns)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    if (!ns[s].ls_active) return;
+    const double lam = ns[s].lambda;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double mp = 0.0, mc = 0.0;
+    if (n < N) {
+        const size_t q = (size_t)s * N + n;
+        const V2<T> d = dx[q];
+        const double dp = lam * (double)d.p, dc = lam * (double)d.c;
+        pt[q] = p[q] + dp;
+        ct[q] = c[q] + dc;
+        mp = fabs(dp);
+        mc = fabs(dc);
+    }
+    const double t0 = block_max(mp, red);
+    const double t1 = block_max(mc, red);
+    if (threadIdx.x == 0) {
+        partial[((size_t)s * 2 + 0) * gridDim.x + blockIdx.x] = t0;
+        partial[((size_t)s * 2 + 1) * gridDim.x + blockIdx.x] = t1;
+    }
+}
+
+template <class T>
+void launch_newton_trial(const Grid& G, const double* p, const double* c,
+                         const V2<T>* dx, double* pt, double* ct,
+                         double* partial, const NScal* ns, int S,
+                         cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_newton_trial<T><<<grid, kBS, 0, st>>>(G.N, p, c, dx, pt, ct, partial, ns);
+}
+
+// Armijo-type acceptance ||R(u + lambda d)|| < (1 - 1e-4 lambda) ||R(u)||;
+// after ls_max halvings the last trial is taken.
+__global__ void k_newton_ls_finalize(const double* __restrict__ pmax, int nblk,
+                                     NScal* ns, int ls_max)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    if (!ns[s].ls_active) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+        a0 = fmax(a0, pmax[((size_t)s * 2 + 0) * nblk + q]);
+        a1 = fmax(a1, pmax[((size_t)s * 2 + 1) * nblk + q]);
+    }
+    a0 = block_max(a0, red);
+    a1 = block_max(a1, red);
+    if (threadIdx.x != 0) return;
+    NScal k = ns[s];
+    k.dmax_p = a0;
+    k.dmax_c = a1;
+    const bool finite = isfinite(k.rt);
+    if ((finite && k.rt < (1.0 - 1e-4 * k.lambda) * k.rn) || k.ls_count >= ls_max) {
+        k.ls_active = 0;
+        if (finite) {
+            k.accepted = 1;
+        } else {
+            k.active = 0;
+            k.status = ELDER_SAMPLE_NONFINITE_;
+        }
+    } else {
+        k.lambda *= 0.5;
+        k.ls_count += 1;
+        k.ls_cuts += 1;
+    }
+    ns[s] = k;
+}
+
+void launch_newton_ls_finalize(const double* partial_res,
+                               const double* partial_max, int nblk,
+                               NScal* ns, int ls_max, int S, cudaStream_t st)
+{
+    (void)partial_res;
+    k_newton_ls_finalize<<<S, 128, 0, st>>>(partial_max, nblk, ns, ls_max);
+}
+
+__global__ void __launch_bounds__(kBS)
+    k_newton_accept(int N, double* __restrict__ p, double* __restrict__ c,
+                    const double* __restrict__ pt, const double* __restrict__ ct,
+                    V2<double>* __restrict__ R, const V2<double>* __restrict__ Rt,
+                    const NScal* ns)
+{
+    const int s = blockIdx.y;
+    if (!ns[s].accepted) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const size_t q = (size_t)s * N + n;
+    p[q] = pt[q];
+    c[q] = ct[q];
+    R[q] = Rt[q];
+}
+
+void launch_newton_accept(const Grid& G, double* p, double* c,
+                          const double* pt, const double* ct, V2<double>* R,
+                          const V2<double>* Rt, const NScal* ns, int S,
+                          cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_newton_accept<<<grid, kBS, 0, st>>>(G.N, p, c, pt, ct, R, Rt, ns);
+}
+
+__global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
+                               double tol_c, int maxit, int S)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    NScal k = ns[s];
+    if (!k.active) return;
+    k.kiters += ks[s].iters;
+    if (k.accepted) {
+        k.rn = k.rt;
+        k.iters += 1;
+        if (k.lambda == 1.0 && k.dmax_c <= tol_c && k.dmax_p <= tol_p) {
+            k.active = 0;
+            k.status = 0;
+        } else if (k.iters >= maxit) {
+            k.active = 0;
+            k.status = ELDER_SAMPLE_NEWTON_MAXIT_;
+        }
+    }
+    k.accepted = 0;
+    k.ls_count = 0;
+    k.lambda = 1.0;
+    k.ls_active = k.active;
+    ns[s] = k;
+}
+
+void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
+                         double tol_c, int maxit, int S, cudaStream_t st)
+{
+    k_newton_check<<<nblocks(S, 128), 128, 0, st>>>(ns, ks, tol_p, tol_c, maxit, S);
+}
+
+__global__ void k_newton_restore_failed(int N, double* __restrict__ p,
+                                        double* __restrict__ c,
+                                        const double* __restrict__ p_old,
+                                        const double* __restrict__ c_old,
+                                        const NScal* ns)
+{
+    const int s = blockIdx.y;
+    if (ns[s].status == 0) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const size_t q = (size_t)s * N + n;
+    p[q] = p_old[q];
+    c[q] = c_old[q];
+}
+
+void launch_newton_restore_failed(const Grid& G, double* p, double* c,
+                                  const double* p_old, const double* c_old,
+                                  const NScal* ns, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_newton_restore_failed<<<grid, kBS, 0, st>>>(G.N, p, c, p_old, c_old, ns);
+}
+
+// ---------------------------------------------------------------------------
+// sample statistics (Section 3: eqs. pdestat, numer_var; exceedance estimate)
+// ---------------------------------------------------------------------------
+//
+// One pass over the S fields per node, shifted by the first sample's value
+// for stability: with d_i = c_i - c_0, S1 = sum w d, S2 = sum w d^2,
+// W = sum w: mean = c_0 W + S1 and sum w (mean - c)^2 =
+// (mean - c_0)^2 W - 2 (mean - c_0) S1 + S2.
+__global__ void __launch_bounds__(kBS)
+    k_moments(int N, int S, const double* __restrict__ c,
+              const double* __restrict__ w, double threshold,
+              double* __restrict__ mean, double* __restrict__ var,
+              double* __restrict__ pexc)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double c0 = c[n];
+    const double wu = 1.0 / S;
+    double S1 = 0.0, S2 = 0.0, W = 0.0, P = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const double ws = w ? __ldg(w + s) : wu;
+        const double cv = __ldcs(c + (size_t)s * N + n);
+        const double d = cv - c0;
+        S1 = fma(ws, d, S1);
+        S2 = fma(ws * d, d, S2);
+        W += ws;
+        if (cv > threshold) P += ws;
+    }
+    const double m = fma(c0, W, S1);
+    const double dm = m - c0;
+    mean[n] = m;
+    var[n] = fmax(fma(dm * dm, W, fma(-2.0 * dm, S1, S2)), 0.0);
+    pexc[n] = P;
+}
+
+void launch_moments(int N, int S, const double* c, const double* w,
+                    double threshold, double* mean, double* var,
+                    double* pexc, cudaStream_t st)
+{
+    k_moments<<<nblocks(N), kBS, 0, st>>>(N, S, c, w, threshold, mean, var, pexc);
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int nblk,
+                               double* __restrict__ out)
+{
+    __shared__ double red[32];
+    double a = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) a += partial[(size_t)blockIdx.x * nblk + q];
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = a;
+}
+
+void launch_sum_partials(const double* partial, int nblk, double* out, int S,
+                         cudaStream_t st)
+{
+    k_sum_partials<<<S, 128, 0, st>>>(partial, nblk, out);
+}
+
+// which = 0: y = a x on Dirichlet components only, 0 elsewhere;
+// which = 1: y += a x on Dirichlet components only;
+// which = 2: y += a x on interior components only.
+template <class T>
+__global__ void k_axpy_mask(Grid G, const uint8_t* __restrict__ bc,
+                            const V2<T>* __restrict__ x, V2<T>* __restrict__ y,
+                            double a, int which)
+{
+    const int s = blockIdx.y;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const size_t q = (size_t)s * G.N + n;
+    const uint8_t m = bc[n];
+    const V2<T> xv = x[q];
+    V2<T> yv = (which == 0) ? V2<T>{T(0), T(0)} : y[q];
+    const bool dp = (m & BC_P) != 0, dc = (m & BC_C) != 0;
+    if (which <= 1) {
+        if (dp) yv.p += T(a) * xv.p;
+        if (dc) yv.c += T(a) * xv.c;
+    } else {
+        if (!dp) yv.p += T(a) * xv.p;
+        if (!dc) yv.c += T(a) * xv.c;
+    }
+    y[q] = yv;
+}
+
+template <class T>
+void launch_axpy_mask(const Grid& G, const uint8_t* bc, const V2<T>* x,
+                      V2<T>* y, double a, int which, int S, cudaStream_t st)
+{
+    dim3 grid(nblocks(G.N), S);
+    k_axpy_mask<T><<<grid, kBS, 0, st>>>(G, bc, x, y, a, which);
+}
+
+template <class Ts, class Td>
+__global__ void k_convert(const V2<Ts>* __restrict__ x, V2<Td>* __restrict__ y,
+                          size_t n)
+{
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const V2<Ts> v = x[q];
+    y[q] = V2<Td>{Td(v.p), Td(v.c)};
+}
+
+template <class Ts, class Td>
+void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
+{
+    k_convert<Ts, Td><<<(unsigned)((n + kBS - 1) / kBS), kBS, 0, st>>>(x, y, n);
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define ELDER_INST(T)                                                                    \
+    template void launch_spmv<T>(const Grid&, const B4<T>*, const uint8_t*,              \
+                                 const V2<T>*, V2<T>*, int, int, const V2<T>*,           \
+                                 double*, const int*, int, int, cudaStream_t);           \
+    template void launch_smooth<T>(const Grid&, const B4<T>*, const B4<T>*,              \
+                                   const uint8_t*, const V2<T>*, const V2<T>*, V2<T>*,   \
+                                   double, int, const int*, int, int, cudaStream_t);     \
+    template void launch_mg_residual<T>(const Grid&, const B4<T>*, const uint8_t*,       \
+                                        const V2<T>*, const V2<T>*, V2<T>*, int,         \
+                                        const int*, int, int, cudaStream_t);             \
+    template void launch_restrict<T>(const Grid&, const Grid&, const uint8_t*,           \
+                                     const V2<T>*, V2<T>*, const int*, int, int,         \
+                                     cudaStream_t);                                      \
+    template void launch_prolong_add<T>(const Grid&, const Grid&, const uint8_t*,        \
+                                        const V2<T>*, V2<T>*, const int*, int, int,      \
+                                        cudaStream_t);                                   \
+    template void launch_coarse_apply<T>(const Grid&, const double*, const V2<T>*,       \
+                                         V2<T>*, int, const int*, int, int,              \
+                                         cudaStream_t);                                  \
+    template void launch_bicg_init<T>(const Grid&, const uint8_t*, const V2<T>*, V2<T>*, \
+                                      V2<T>*, V2<T>*, V2<T>*, V2<T>*, double*, KScal*,   \
+                                      int, cudaStream_t);                                \
+    template void launch_bicg_p<T>(const Grid&, const V2<T>*, const V2<T>*, V2<T>*,      \
+                                   const KScal*, int, cudaStream_t);                     \
+    template void launch_bicg_s<T>(const Grid&, const V2<T>*, const V2<T>*, V2<T>*,      \
+                                   double*, const KScal*, int, cudaStream_t);            \
+    template void launch_bicg_xr<T>(const Grid&, const V2<T>*, const V2<T>*,             \
+                                    const V2<T>*, const V2<T>*, const V2<T>*, V2<T>*,    \
+                                    V2<T>*, double*, const KScal*, int, cudaStream_t);   \
+    template void launch_newton_rhs<T>(const Grid&, const V2<double>*, V2<T>*,           \
+                                       const NScal*, int, cudaStream_t);                 \
+    template void launch_newton_trial<T>(const Grid&, const double*, const double*,      \
+                                         const V2<T>*, double*, double*, double*,        \
+                                         const NScal*, int, cudaStream_t);               \
+    template void launch_axpy_mask<T>(const Grid&, const uint8_t*, const V2<T>*, V2<T>*, \
+                                      double, int, int, cudaStream_t);
+ELDER_INST(double)
+ELDER_INST(float)
+#undef ELDER_INST
+template void launch_convert<double, float>(const V2<double>*, V2<float>*, size_t, cudaStream_t);
+template void launch_convert<float, double>(const V2<float>*, V2<double>*, size_t, cudaStream_t);
+template void launch_convert<double, double>(const V2<double>*, V2<double>*, size_t, cudaStream_t);
+
+}  // namespace elder

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of the C ABI in include/elder.h.
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of libelder.so.  Tensors are torch CUDA float64 tensors (device
+memory and streams come from PyTorch); the calls are ordered on the current
+torch stream.  Importing this module fails loudly when the library is
+missing; ``paper_1906_01632_gb300.build.build()`` makes it.
+
+Names follow the C ABI: ``elder_config_default``, ``elder_create``,
+``elder_step``, ``elder_solve``, ``elder_moments``, ``elder_grad``,
+``elder_fields``, ``elder_residual``, ``elder_jacobian``, ``elder_destroy``;
+``Elder`` wraps a context with methods of the same names (without prefix).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+SECONDS_PER_YEAR = 365.25 * 86400.0
+
+ELDER_OK, ELDER_EINVAL, ELDER_ENOMEM, ELDER_ECUDA, ELDER_ENOTCONV, ELDER_ETIMEOUT = range(6)
+ELDER_FP64, ELDER_MIXED = 0, 1
+SAMPLE_STATUS = {0: "ok", 1: "newton_maxit", 2: "krylov_maxit", 3: "breakdown", 4: "nonfinite"}
+
+
+class elder_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("rho1", ctypes.c_double),
+                ("mu", ctypes.c_double), ("g", ctypes.c_double), ("Dm", ctypes.c_double),
+                ("bc_mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_samples", ctypes.c_int), ("newton_maxit", ctypes.c_int),
+                ("newton_tol_c", ctypes.c_double), ("newton_tol_p", ctypes.c_double),
+                ("ls_max", ctypes.c_int), ("lin_rtol", ctypes.c_double),
+                ("lin_maxit", ctypes.c_int), ("mg_levels", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+                ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+
+
+class elder_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("krylov_iters", ctypes.c_int32), ("ls_cuts", ctypes.c_int32),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double)]
+
+
+EXPORTS = ["elder_config_default", "elder_create", "elder_destroy", "elder_last_error",
+           "elder_sizes", "elder_fields", "elder_residual", "elder_jacobian", "elder_step",
+           "elder_solve", "elder_moments", "elder_grad"]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libelder.so not found at {path}: run paper_1906_01632_gb300.build.build() "
+            "(nvcc, sm_103a) first; there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.elder_config_default.argtypes = [ctypes.POINTER(elder_config), ip, ip, ip]
+    lib.elder_create.argtypes = [ctypes.POINTER(elder_config), ctypes.POINTER(vp)]
+    lib.elder_destroy.argtypes = [vp]
+    lib.elder_last_error.argtypes = [vp]
+    lib.elder_last_error.restype = ctypes.c_char_p
+    lib.elder_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]
+    lib.elder_fields.argtypes = [vp, ip, ip, vp, ctypes.c_double, vp, vp, vp]
+    lib.elder_residual.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
+    lib.elder_jacobian.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, vp, vp]
+    lib.elder_step.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double,
+                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(elder_stats), vp]
+    lib.elder_solve.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, vp, vp,
+                                ctypes.c_double, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.elder_moments.argtypes = [vp, ip, vp, vp, ctypes.c_double, vp, vp, vp, vp]
+    lib.elder_grad.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, dp, vp, vp, vp]
+    del dp
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(t: torch.Tensor | None, what: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{what}: must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class ElderError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"elder error {code}: {msg}")
+        self.code = code
+
+
+def elder_config_default(nx, ny, nz, **overrides) -> elder_config:
+    cfg = elder_config()
+    rc = _lib.elder_config_default(ctypes.byref(cfg), nx, ny, nz)
+    if rc != ELDER_OK:
+        raise ElderError(rc, "elder_config_default")
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(f"elder_config has no field {k}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Elder:
+    """A context of the C ABI (owns the hierarchy and device workspace)."""
+
+    def __init__(self, cfg: elder_config):
+        h = ctypes.c_void_p()
+        rc = _lib.elder_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != ELDER_OK:
+            raise ElderError(rc, _lib.elder_last_error(None).decode())
+        self._h = h
+        self.cfg = cfg
+        N = ctypes.c_int64()
+        C = ctypes.c_int64()
+        L = ctypes.c_int()
+        _lib.elder_sizes(h, ctypes.byref(N), ctypes.byref(C), ctypes.byref(L))
+        self.N, self.C, self.levels = N.value, C.value, L.value
+
+    def _check(self, rc, allow_notconv=False):
+        if rc == ELDER_OK or (allow_notconv and rc == ELDER_ENOTCONV):
+            return rc
+        raise ElderError(rc, _lib.elder_last_error(self._h).decode())
+
+    def destroy(self):
+        if self._h:
+            _lib.elder_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # --- entry points -----------------------------------------------------
+    def fields(self, S, kind, params, K_mean=4.845e-13, phi=None, K=None, stream=None):
+        dev = params.device
+        phi = phi if phi is not None else torch.empty(S * self.C, dtype=torch.float64, device=dev)
+        K = K if K is not None else torch.empty(S * self.C, dtype=torch.float64, device=dev)
+        self._check(_lib.elder_fields(self._h, S, kind, _ptr(params, "params"), K_mean,
+                                      _ptr(phi, "phi"), _ptr(K, "K"), _stream(stream)))
+        return phi, K
+
+    def residual(self, S, phi, K, p, c, p_old, c_old, dt, R=None, stream=None):
+        R = R if R is not None else torch.empty(S * self.N * 2, dtype=torch.float64, device=p.device)
+        self._check(_lib.elder_residual(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"), _ptr(p, "p"),
+                                        _ptr(c, "c"), _ptr(p_old, "p_old"), _ptr(c_old, "c_old"),
+                                        dt, _ptr(R, "R"), _stream(stream)))
+        return R
+
+    def jacobian(self, S, phi, K, p, c, dt, J=None, stream=None):
+        J = J if J is not None else torch.empty(S * 27 * self.N * 4, dtype=torch.float64, device=p.device)
+        self._check(_lib.elder_jacobian(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"), _ptr(p, "p"),
+                                        _ptr(c, "c"), dt, _ptr(J, "J"), _stream(stream)))
+        return J
+
+    def step(self, S, phi, K, p, c, dt, stream=None, raise_on_fail=False):
+        """One implicit Euler step in place on p, c; returns (status[S], stats list)."""
+        status = (ctypes.c_int32 * S)()
+        stats = (elder_stats * S)()
+        rc = _lib.elder_step(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"), _ptr(p, "p"),
+                             _ptr(c, "c"), dt, status, stats, _stream(stream))
+        self._check(rc, allow_notconv=not raise_on_fail)
+        st = np.frombuffer(status, dtype=np.int32).copy()
+        info = [{"status": s.status, "newton_iters": s.newton_iters,
+                 "krylov_iters": s.krylov_iters, "ls_cuts": s.ls_cuts, "res0": s.res0,
+                 "res": s.res} for s in stats]
+        return st, info
+
+    def solve(self, S, phi, K, p, c, dt, rhs, transpose=False, rtol=1e-10, x=None, stream=None):
+        x = x if x is not None else torch.empty_like(rhs)
+        status = (ctypes.c_int32 * S)()
+        rc = _lib.elder_solve(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"), _ptr(p, "p"),
+                              _ptr(c, "c"), dt, 1 if transpose else 0, _ptr(rhs, "rhs"),
+                              _ptr(x, "x"), rtol, status, _stream(stream))
+        self._check(rc, allow_notconv=True)
+        return x, np.frombuffer(status, dtype=np.int32).copy()
+
+    def moments(self, S, c, w=None, threshold=0.5, stream=None):
+        dev = c.device
+        mean = torch.empty(self.N, dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+        pexc = torch.empty_like(mean)
+        self._check(_lib.elder_moments(self._h, S, _ptr(c, "c"), _ptr(w, "w"), threshold,
+                                       _ptr(mean, "mean"), _ptr(var, "var"),
+                                       _ptr(pexc, "p_exceed"), _stream(stream)))
+        return mean, var, pexc
+
+    def grad(self, n_steps, phi, K, p0, c0, dt, ckpt_every=7, stream=None):
+        """Objective J and dJ/dphi, dJ/dK (per cell) by the discrete adjoint."""
+        Jv = ctypes.c_double(0.0)
+        gphi = torch.empty(self.C, dtype=torch.float64, device=phi.device)
+        gK = torch.empty_like(gphi)
+        rc = _lib.elder_grad(self._h, n_steps, _ptr(phi, "phi"), _ptr(K, "K"), _ptr(p0, "p0"),
+                             _ptr(c0, "c0"), dt, ckpt_every, ctypes.byref(Jv), _ptr(gphi, "dJ_dphi"),
+                             _ptr(gK, "dJ_dK"), _stream(stream))
+        self._check(rc)
+        return Jv.value, gphi, gK
+
+
+# module-level names of the C ABI
+def elder_create(cfg: elder_config) -> Elder:
+    return Elder(cfg)
+
+
+def elder_destroy(ctx: Elder):
+    ctx.destroy()
+
+
+def elder_step(ctx: Elder, *a, **k):
+    return ctx.step(*a, **k)
+
+
+def elder_solve(ctx: Elder, *a, **k):
+    return ctx.solve(*a, **k)
+
+
+def elder_moments(ctx: Elder, *a, **k):
+    return ctx.moments(*a, **k)
+
+
+def elder_grad(ctx: Elder, *a, **k):
+    return ctx.grad(*a, **k)
+
+
+def elder_fields(ctx: Elder, *a, **k):
+    return ctx.fields(*a, **k)
+
+
+def elder_residual(ctx: Elder, *a, **k):
+    return ctx.residual(*a, **k)
+
+
+def elder_jacobian(ctx: Elder, *a, **k):
+    return ctx.jacobian(*a, **k)
+
+
+class ElderRollout(torch.autograd.Function):
+    """Salt mass below mid-depth after n_steps implicit steps of one sample,
+    differentiable w.r.t. the per-cell porosity and permeability through the
+    library's discrete adjoint (elder_grad)."""
+
+    @staticmethod
+    def forward(ctx, phi, K, p0, c0, elder: Elder, n_steps: int, dt: float, ckpt_every: int = 7):
+        J, gphi, gK = elder.grad(n_steps, phi.detach().contiguous(), K.detach().contiguous(),
+                                 p0.contiguous(), c0.contiguous(), dt, ckpt_every)
+        ctx.save_for_backward(gphi, gK)
+        return torch.tensor(J, dtype=torch.float64, device=phi.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        gphi, gK = ctx.saved_tensors
+        return gout * gphi, gout * gK, None, None, None, None, None, None

@@ -1,0 +1,277 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 path 1e-10 max-abs in c per step (and the matching relative
+level in p); mixed precision 1e-6 after Newton's FP64 defect correction;
+residual and Jacobian agree to round-off (summation order differs).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+YEAR = O.SECONDS_PER_YEAR
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_01632_gb300 import build
+    build.build()
+    from paper_1906_01632_gb300 import elder
+    return elder
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device=DEV)
+
+
+def H(t):
+    return t.detach().cpu().numpy()
+
+
+def _fields(P, S, seed):
+    rng = np.random.default_rng(seed)
+    phi = np.zeros((S, P.C))
+    K = np.zeros((S, P.C))
+    for s in range(S):
+        phi[s], K[s] = O.fields_lognormal(P, rng.standard_normal(P.C))
+    return phi, K
+
+
+def _random_states(P, S, seed):
+    rng = np.random.default_rng(seed)
+    p0, c0 = O.initial_state(P)
+    p = np.stack([p0 + rng.normal(0, 2e3, P.N) for _ in range(S)])
+    c = np.stack([np.clip(c0 + rng.uniform(0, 0.7, P.N), 0, 1) for _ in range(S)])
+    return p, c
+
+
+def _ctx(E, nx, ny, nz, S=1, **kw):
+    return E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, **kw))
+
+
+# --------------------------------------------------------------------------
+# residual, Jacobian, fields
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,S", [((8, 8, 2), 1), ((12, 8, 6), 3), ((16, 16, 4), 4)])
+def test_residual_matches_oracle(E, dims, S):
+    P = O.Problem(*dims)
+    ctx = _ctx(E, *dims, S=S)
+    phi, K = _fields(P, S, 1)
+    p, c = _random_states(P, S, 2)
+    po, co = _random_states(P, S, 3)
+    dt = YEAR / 12
+    R = H(ctx.residual(S, T(phi), T(K), T(p), T(c), T(po), T(co), dt)).reshape(S, P.N, 2)
+    for s in range(S):
+        Rp, Rc = O.residual(P, phi[s], K[s], p[s], c[s], po[s], co[s], dt)
+        scale = max(np.abs(Rp).max(), np.abs(Rc).max())
+        assert np.abs(R[s, :, 0] - Rp).max() <= 1e-12 * scale
+        assert np.abs(R[s, :, 1] - Rc).max() <= 1e-12 * scale
+
+
+def _oracle_dia(P, rowptr, col, val):
+    """Oracle CSR -> the library's [27][N][4] block layout."""
+    D = np.zeros((27, P.N, 4))
+    nx1, ny1 = P.nx + 1, P.ny + 1
+    for n in range(P.N):
+        i, j, k = n % nx1, (n // nx1) % ny1, n // (nx1 * ny1)
+        for v in range(2):
+            r = 2 * n + v
+            for q in range(rowptr[r], rowptr[r + 1]):
+                m, w = divmod(int(col[q]), 2)
+                mi, mj, mk = m % nx1, (m // nx1) % ny1, m // (nx1 * ny1)
+                sl = (mi - i + 1) + 3 * (mj - j + 1) + 9 * (mk - k + 1)
+                D[sl, n, 2 * v + w] += val[q]
+    return D
+
+
+def test_jacobian_matches_oracle(E):
+    dims, S = (8, 8, 4), 2
+    P = O.Problem(*dims)
+    ctx = _ctx(E, *dims, S=S)
+    phi, K = _fields(P, S, 4)
+    p, c = _random_states(P, S, 5)
+    dt = YEAR / 12
+    J = H(ctx.jacobian(S, T(phi), T(K), T(p), T(c), dt)).reshape(S, 27, P.N, 4)
+    for s in range(S):
+        D = _oracle_dia(P, *O.jacobian_csr(P, phi[s], K[s], p[s], c[s], dt))
+        scale = np.abs(D).max(axis=(0, 2))  # per row node
+        err = np.abs(J[s] - D).max(axis=(0, 2)) / scale
+        assert err.max() <= 1e-11
+
+
+def test_fields_match_oracle(E):
+    from paper_1906_01632_gb300 import inputs as I
+    P = O.Problem(16, 16, 4)
+    S = 5
+    ctx = _ctx(E, 16, 16, 4, S=S)
+    xi = I.sobol_xi(S)
+    phi, K = ctx.fields(S, 0, T(xi))
+    phi, K = H(phi).reshape(S, -1), H(K).reshape(S, -1)
+    for s in range(S):
+        rp, rk = O.fields_sobol(P, xi[s])
+        np.testing.assert_allclose(phi[s], rp, rtol=1e-14)
+        np.testing.assert_allclose(K[s], rk, rtol=1e-13)
+    Z = np.stack([I.lognormal_z(P.C, seed=s + 1) for s in range(S)])
+    phi, K = ctx.fields(S, 1, T(Z))
+    phi, K = H(phi).reshape(S, -1), H(K).reshape(S, -1)
+    for s in range(S):
+        rp, rk = O.fields_lognormal(P, Z[s])
+        np.testing.assert_allclose(phi[s], rp, rtol=1e-14)
+        np.testing.assert_allclose(K[s], rk, rtol=1e-13)
+    phi, K = ctx.fields(S, 2, T(xi))
+    phi, K = H(phi).reshape(S, -1), H(K).reshape(S, -1)
+    for s in range(S):
+        rp, rk = O.fields_paper3rv(P, xi[s])
+        np.testing.assert_allclose(phi[s], rp, rtol=1e-14)
+        np.testing.assert_allclose(K[s], rk, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# linear solves: test (d) on 4x4x2 against the oracle's dense LU
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_solve_matches_dense_lu(E, transpose):
+    P = O.Problem(4, 4, 2)
+    S = 2
+    ctx = _ctx(E, 4, 4, 2, S=S)
+    phi, K = _fields(P, S, 6)
+    p, c = _random_states(P, S, 7)
+    rng = np.random.default_rng(8)
+    rhs = rng.standard_normal((S, P.N, 2))
+    dt = YEAR / 12
+    x, st = ctx.solve(S, T(phi), T(K), T(p), T(c), dt, T(rhs), transpose=transpose, rtol=1e-12)
+    assert (st == 0).all()
+    x = H(x).reshape(S, 2 * P.N)
+    for s in range(S):
+        A = O.jacobian_dense(P, phi[s], K[s], p[s], c[s], dt)
+        ref = O.dense_solve(A.T if transpose else A, rhs[s].ravel())
+        scale = np.abs(ref).reshape(-1, 2).max(axis=0)
+        err = np.abs(x[s] - ref).reshape(-1, 2).max(axis=0)
+        assert (err <= 1e-9 * scale).all(), (err, scale)
+
+
+# --------------------------------------------------------------------------
+# time steps
+# --------------------------------------------------------------------------
+
+def _run_gpu(E, P, phi, K, p, c, steps, dt, **kw):
+    S = phi.shape[0]
+    ctx = _ctx(E, P.nx, P.ny, P.nz, S=S, **kw)
+    pt, ct = T(p), T(c)
+    phit, Kt = T(phi), T(K)
+    traj = []
+    infos = []
+    for _ in range(steps):
+        st, info = ctx.step(S, phit, Kt, pt, ct, dt)
+        assert (st == 0).all(), info
+        traj.append((H(pt).reshape(S, -1).copy(), H(ct).reshape(S, -1).copy()))
+        infos.append(info)
+    return traj, infos
+
+
+def _oracle_traj(P, phi, K, p, c, steps, dt):
+    traj = []
+    for _ in range(steps):
+        p, c, info = O.newton_step(P, phi, K, p, c, dt)
+        assert info["status"] == 0
+        traj.append((p.copy(), c.copy()))
+    return traj
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+def test_steps_match_oracle_16x16x4(E, precision, tol):
+    P = O.Problem(16, 16, 4)
+    S = 3
+    phi, K = _fields(P, S, 9)
+    p0, c0 = O.initial_state(P)
+    p = np.tile(p0, (S, 1))
+    c = np.tile(c0, (S, 1))
+    dt = YEAR / 12
+    steps = 5
+    traj, _ = _run_gpu(E, P, phi, K, p, c, steps, dt, precision=precision)
+    pscale = P.rho0 * P.g * P.Lz
+    for s in range(S):
+        ref = _oracle_traj(P, phi[s], K[s], p0, c0, steps, dt)
+        for n in range(steps):
+            assert np.abs(traj[n][1][s] - ref[n][1]).max() <= tol, (s, n)
+            assert np.abs(traj[n][0][s] - ref[n][0]).max() <= tol * pscale, (s, n)
+
+
+def test_config1_32x32x8_24_steps_fp64(E):
+    """32x32x8, uniform phi = 0.1, K = 4.845e-13, dt = 1/12 yr, 24 steps."""
+    P = O.Problem(32, 32, 8)
+    phi = np.full((1, P.C), 0.1)
+    K = np.full((1, P.C), 4.845e-13)
+    p0, c0 = O.initial_state(P)
+    dt = YEAR / 12
+    steps = 24
+    traj, infos = _run_gpu(E, P, phi, K, p0[None], c0[None], steps, dt)
+    p, c = p0, c0
+    for n in range(steps):
+        p, c, info = O.newton_step(P, phi[0], K[0], p, c, dt, O.NewtonOpts(lin_rtol=1e-10))
+        assert info["status"] == 0
+        assert np.abs(traj[n][1][0] - c).max() <= 1e-10, n
+        assert np.abs(traj[n][0][0] - p).max() <= 1e-10 * P.rho0 * P.g * P.Lz, n
+
+
+def test_moments_match_oracle(E):
+    P = O.Problem(16, 16, 4)
+    S = 37
+    ctx = _ctx(E, 16, 16, 4, S=S)
+    rng = np.random.default_rng(10)
+    cs = rng.uniform(0, 1, (S, P.N))
+    cs[:, :7] = 0.5  # ties at the threshold: strict ">"
+    m, v, pe = ctx.moments(S, T(cs))
+    mo, vo, po = O.moments(cs)
+    np.testing.assert_allclose(H(m), mo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(H(v), vo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(H(pe), po, rtol=0, atol=1e-14)
+    w = rng.uniform(0.5, 1.5, S)
+    w /= w.sum()
+    m, v, pe = ctx.moments(S, T(cs), w=T(w), threshold=0.3)
+    mo, vo, po = O.moments(cs, w=w, threshold=0.3)
+    np.testing.assert_allclose(H(m), mo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(H(v), vo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(H(pe), po, rtol=0, atol=1e-14)
+
+
+def test_grad_matches_oracle_adjoint(E):
+    P = O.Problem(8, 8, 4)
+    ctx = _ctx(E, 8, 8, 4)
+    phi, K = _fields(P, 1, 11)
+    p0, c0 = O.initial_state(P)
+    dt = YEAR / 12
+    steps = 5
+    J, gphi, gK = ctx.grad(steps, T(phi), T(K), T(p0), T(c0), dt, ckpt_every=2)
+    Jo, gphio, gKo, rc = O.adjoint_gradient(P, phi[0], K[0], p0, c0, dt, steps)
+    assert rc == 0
+    assert abs(J - Jo) <= 1e-10 * abs(Jo)
+    np.testing.assert_allclose(H(gphi), gphio, rtol=0, atol=1e-7 * np.abs(gphio).max())
+    np.testing.assert_allclose(H(gK), gKo, rtol=0, atol=1e-7 * np.abs(gKo).max())
+
+
+def test_failed_sample_keeps_old_state(E):
+    """A NaN porosity in one sample: that sample reports a non-finite status
+    and keeps u^n; the other samples advance as usual."""
+    P = O.Problem(8, 8, 2)
+    S = 2
+    phi = np.full((S, P.C), 0.1)
+    K = np.full((S, P.C), 4.845e-13)
+    phi[1, 5] = np.nan
+    p0, c0 = O.initial_state(P)
+    ctx = _ctx(E, 8, 8, 2, S=S)
+    pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+    st, info = ctx.step(S, T(phi), T(K), pt, ct, YEAR / 12)
+    assert st[0] == 0 and st[1] == 4
+    c = H(ct).reshape(S, -1)
+    np.testing.assert_array_equal(c[1], c0)
+    _, cref, _ = O.newton_step(P, phi[0], K[0], p0, c0, YEAR / 12)
+    assert np.abs(c[0] - cref).max() <= 1e-10
