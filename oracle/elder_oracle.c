@@ -523,16 +523,50 @@ static void ilu0_apply(int n, const int* rowptr, const int* col,
     }
 }
 
-/* BiCGStab of van der Vorst, right preconditioned (Barrett et al.,
- * Templates, Sec. 2.3.8). */
+/* preconditioner z = M r */
+typedef void (*precond_fn)(void* ctx, const double* r, double* z);
+
+typedef struct {
+    int n;
+    const int *rowptr, *col;
+    const double* lu;
+    const int* diag;
+} ilu_ctx;
+
+static void ilu_precond(void* vctx, const double* r, double* z)
+{
+    ilu_ctx* c = (ilu_ctx*)vctx;
+    ilu0_apply(c->n, c->rowptr, c->col, c->lu, c->diag, r, z);
+}
+
+static int bicgstab(int n, const int* rowptr, const int* col,
+                    const double* val, const double* b, double* x, double rtol,
+                    int maxit, precond_fn M, void* mctx, int* iters,
+                    double* relres);
+
 int orc_bicgstab_ilu0(int n, const int* rowptr, const int* col,
                       const double* val, const double* b, double* x,
                       double rtol, int maxit, int* iters, double* relres)
 {
-    size_t sz = sizeof(double) * (size_t)n;
     double* lu = (double*)malloc(sizeof(double) * (size_t)rowptr[n]);
     int* diag = (int*)malloc(sizeof(int) * (size_t)n);
     ilu0(n, rowptr, col, val, lu, diag);
+    ilu_ctx ic = {n, rowptr, col, lu, diag};
+    int rc = bicgstab(n, rowptr, col, val, b, x, rtol, maxit, ilu_precond, &ic,
+                      iters, relres);
+    free(lu);
+    free(diag);
+    return rc;
+}
+
+/* BiCGStab of van der Vorst, right preconditioned (Barrett et al.,
+ * Templates, Sec. 2.3.8); the method the paper names in Section 5.1. */
+static int bicgstab(int n, const int* rowptr, const int* col,
+                    const double* val, const double* b, double* x, double rtol,
+                    int maxit, precond_fn M, void* mctx, int* iters,
+                    double* relres)
+{
+    size_t sz = sizeof(double) * (size_t)n;
     double *r = malloc(sz), *rh = malloc(sz), *pv = malloc(sz), *v = malloc(sz),
            *s = malloc(sz), *t = malloc(sz), *ph = malloc(sz), *sh = malloc(sz);
     csr_matvec(n, rowptr, col, val, x, r);
@@ -552,7 +586,7 @@ int orc_bicgstab_ilu0(int n, const int* rowptr, const int* col,
         if (rho == 0.0) break;
         double beta = (rho / rho_old) * (alpha / omega);
         for (int i = 0; i < n; ++i) pv[i] = r[i] + beta * (pv[i] - omega * v[i]);
-        ilu0_apply(n, rowptr, col, lu, diag, pv, ph);
+        M(mctx, pv, ph);
         csr_matvec(n, rowptr, col, val, ph, v);
         double rv = dot(n, rh, v);
         if (rv == 0.0) break;
@@ -563,7 +597,7 @@ int orc_bicgstab_ilu0(int n, const int* rowptr, const int* col,
             ok = 1;
             break;
         }
-        ilu0_apply(n, rowptr, col, lu, diag, s, sh);
+        M(mctx, s, sh);
         csr_matvec(n, rowptr, col, val, sh, t);
         double tt = dot(n, t, t);
         omega = (tt > 0.0) ? dot(n, t, s) / tt : 0.0;
@@ -582,7 +616,7 @@ int orc_bicgstab_ilu0(int n, const int* rowptr, const int* col,
     double tr = sqrt(dot(n, r, r)) / bn;
     if (iters) *iters = it;
     if (relres) *relres = tr;
-    free(lu); free(diag); free(r); free(rh); free(pv); free(v); free(s);
+    free(r); free(rh); free(pv); free(v); free(s);
     free(t); free(ph); free(sh);
     return (tr <= 10.0 * rtol) ? 0 : 1;
 }
@@ -606,6 +640,321 @@ int orc_linear_solve(int n, const int* rowptr, const int* col,
     double rr;
     return orc_bicgstab_ilu0(n, rowptr, col, val, b, x, o->lin_rtol,
                              o->lin_maxit, iters, &rr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* geometric multigrid V-cycle preconditioner (Section 5.1)                 */
+/* ------------------------------------------------------------------------ */
+/* Levels: the grid halved in every direction while that keeps the top
+ * square node-aligned; the matrix of every level is the Jacobian of the
+ * discretised system on that grid (Section 5.1), at the injected state and
+ * with cell-averaged phi and K.  Each level matrix is taken on the interior
+ * unknowns: Dirichlet rows and columns are replaced by the identity and the
+ * Dirichlet components of every multigrid vector are kept at zero.
+ * Smoother: damped 2x2-block Jacobi (the paper's ILU_beta smoother is not
+ * specified further); transfers: trilinear interpolation and its
+ * transpose; coarsest level: dense LU. */
+
+#define ORC_MAXLEV 16
+
+typedef struct {
+    int nlev;
+    orc_problem P[ORC_MAXLEV];
+    int n[ORC_MAXLEV];
+    int *rp[ORC_MAXLEV], *ci[ORC_MAXLEV];
+    double* A[ORC_MAXLEV];
+    double* Dinv[ORC_MAXLEV];     /* [N][4]: inverse of the 2x2 diagonal block */
+    unsigned char* dm[ORC_MAXLEV];/* [2N]: 1 on Dirichlet unknowns            */
+    double *b[ORC_MAXLEV], *x[ORC_MAXLEV], *r[ORC_MAXLEV];
+    double* LU;
+    int* piv;
+    int nu1, nu2;
+    double omega;
+} orc_mg;
+
+static int mg_can_coarsen(const orc_problem* P)
+{
+    if (P->nx % 2 || P->ny % 2 || P->nz % 2) return 0;
+    if ((P->bc_mode == 0 || P->bc_mode == 1) &&
+        (((P->nx / 2) % 4) || ((P->ny / 2) % 4)))
+        return 0;
+    return 1;
+}
+
+static void mg_free(orc_mg* mg)
+{
+    for (int l = 0; l < mg->nlev; ++l) {
+        free(mg->rp[l]); free(mg->ci[l]); free(mg->A[l]); free(mg->Dinv[l]);
+        free(mg->dm[l]); free(mg->b[l]); free(mg->x[l]); free(mg->r[l]);
+    }
+    free(mg->LU);
+    free(mg->piv);
+}
+
+static double csr_get(const int* rp, const int* ci, const double* A, int r,
+                      int c)
+{
+    for (int q = rp[r]; q < rp[r + 1]; ++q)
+        if (ci[q] == c) return A[q];
+    return 0.0;
+}
+
+static int mg_setup(orc_mg* mg, const orc_problem* P0, const double* phi0,
+                    const double* K0, const double* p0, const double* c0,
+                    double dt, int transpose)
+{
+    memset(mg, 0, sizeof(*mg));
+    mg->nu1 = 2;
+    mg->nu2 = 2;
+    mg->omega = 0.7;
+    orc_problem P = *P0;
+    double *phi = (double*)phi0, *K = (double*)K0, *p = (double*)p0,
+           *c = (double*)c0;
+    int owned = 0;
+    int l = 0;
+    for (;; ++l) {
+        mg->P[l] = P;
+        int N = orc_num_nodes(&P), n2 = 2 * N;
+        mg->n[l] = n2;
+        int nnz = orc_jac_nnz(&P);
+        int* rp = malloc(sizeof(int) * ((size_t)n2 + 1));
+        int* ci = malloc(sizeof(int) * (size_t)nnz);
+        double* A = malloc(sizeof(double) * (size_t)nnz);
+        orc_jac_pattern(&P, rp, ci);
+        orc_jacobian(&P, phi, K, p, c, dt, rp, ci, A);
+        unsigned char* pm = malloc((size_t)N);
+        unsigned char* cm = malloc((size_t)N);
+        orc_dirichlet(&P, pm, cm, NULL);
+        unsigned char* dm = malloc((size_t)n2);
+        for (int n = 0; n < N; ++n) {
+            dm[2 * n] = pm[n];
+            dm[2 * n + 1] = cm[n];
+        }
+        free(pm);
+        free(cm);
+        for (int r = 0; r < n2; ++r)
+            for (int q = rp[r]; q < rp[r + 1]; ++q) {
+                if (dm[r]) A[q] = (ci[q] == r) ? 1.0 : 0.0;
+                else if (dm[ci[q]]) A[q] = 0.0;
+            }
+        if (transpose) {
+            int* trp = malloc(sizeof(int) * ((size_t)n2 + 1));
+            int* tci = malloc(sizeof(int) * (size_t)nnz);
+            double* tA = malloc(sizeof(double) * (size_t)nnz);
+            orc_csr_transpose(n2, rp, ci, A, trp, tci, tA);
+            free(rp); free(ci); free(A);
+            rp = trp; ci = tci; A = tA;
+        }
+        double* Dinv = malloc(sizeof(double) * 4 * (size_t)N);
+        for (int n = 0; n < N; ++n) {
+            double a = csr_get(rp, ci, A, 2 * n, 2 * n);
+            double b = csr_get(rp, ci, A, 2 * n, 2 * n + 1);
+            double cc = csr_get(rp, ci, A, 2 * n + 1, 2 * n);
+            double d = csr_get(rp, ci, A, 2 * n + 1, 2 * n + 1);
+            double det = a * d - b * cc;
+            Dinv[4 * n + 0] = d / det;
+            Dinv[4 * n + 1] = -b / det;
+            Dinv[4 * n + 2] = -cc / det;
+            Dinv[4 * n + 3] = a / det;
+        }
+        mg->rp[l] = rp; mg->ci[l] = ci; mg->A[l] = A; mg->Dinv[l] = Dinv;
+        mg->dm[l] = dm;
+        mg->b[l] = calloc((size_t)n2, sizeof(double));
+        mg->x[l] = calloc((size_t)n2, sizeof(double));
+        mg->r[l] = calloc((size_t)n2, sizeof(double));
+        if (!mg_can_coarsen(&P) || l == ORC_MAXLEV - 1) break;
+        /* next level: injected state, arithmetic means of phi and K */
+        orc_problem Pc = P;
+        Pc.nx /= 2; Pc.ny /= 2; Pc.nz /= 2;
+        int Nc = orc_num_nodes(&Pc), Cc = orc_num_cells(&Pc);
+        double* phic = malloc(sizeof(double) * (size_t)Cc);
+        double* Kc = malloc(sizeof(double) * (size_t)Cc);
+        double* pc = malloc(sizeof(double) * (size_t)Nc);
+        double* cc = malloc(sizeof(double) * (size_t)Nc);
+        for (int k = 0; k < Pc.nz; ++k)
+            for (int j = 0; j < Pc.ny; ++j)
+                for (int i = 0; i < Pc.nx; ++i) {
+                    double sp = 0.0, sk = 0.0;
+                    for (int q = 0; q < 8; ++q) {
+                        int f = (2 * i + (q & 1)) +
+                                P.nx * ((2 * j + ((q >> 1) & 1)) +
+                                        P.ny * (2 * k + (q >> 2)));
+                        sp += phi[f];
+                        sk += K[f];
+                    }
+                    phic[i + Pc.nx * (j + Pc.ny * k)] = sp / 8.0;
+                    Kc[i + Pc.nx * (j + Pc.ny * k)] = sk / 8.0;
+                }
+        for (int k = 0; k <= Pc.nz; ++k)
+            for (int j = 0; j <= Pc.ny; ++j)
+                for (int i = 0; i <= Pc.nx; ++i) {
+                    int f = node_id(&P, 2 * i, 2 * j, 2 * k);
+                    pc[node_id(&Pc, i, j, k)] = p[f];
+                    cc[node_id(&Pc, i, j, k)] = c[f];
+                }
+        if (owned) { free(phi); free(K); free(p); free(c); }
+        phi = phic; K = Kc; p = pc; c = cc;
+        owned = 1;
+        P = Pc;
+    }
+    if (owned) { free(phi); free(K); free(p); free(c); }
+    mg->nlev = l + 1;
+    /* dense LU (partial pivoting) of the coarsest level */
+    int L = mg->nlev - 1, n = mg->n[L];
+    if (n > 4000) return 1;
+    mg->LU = calloc((size_t)n * n, sizeof(double));
+    mg->piv = malloc(sizeof(int) * (size_t)n);
+    for (int r = 0; r < n; ++r)
+        for (int q = mg->rp[L][r]; q < mg->rp[L][r + 1]; ++q)
+            mg->LU[(size_t)r * n + mg->ci[L][q]] += mg->A[L][q];
+    double* M = mg->LU;
+    for (int k = 0; k < n; ++k) {
+        int pv = k;
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(M[(size_t)r * n + k]) > fabs(M[(size_t)pv * n + k])) pv = r;
+        mg->piv[k] = pv;
+        if (M[(size_t)pv * n + k] == 0.0) return 1;
+        if (pv != k)
+            for (int q = 0; q < n; ++q) {
+                double t = M[(size_t)k * n + q];
+                M[(size_t)k * n + q] = M[(size_t)pv * n + q];
+                M[(size_t)pv * n + q] = t;
+            }
+        for (int r = k + 1; r < n; ++r) {
+            double f = M[(size_t)r * n + k] / M[(size_t)k * n + k];
+            M[(size_t)r * n + k] = f;
+            for (int q = k + 1; q < n; ++q) M[(size_t)r * n + q] -= f * M[(size_t)k * n + q];
+        }
+    }
+    return 0;
+}
+
+static void mg_coarse_solve(const orc_mg* mg, double* x)
+{
+    int n = mg->n[mg->nlev - 1];
+    const double* M = mg->LU;
+    for (int k = 0; k < n; ++k) {
+        int pv = mg->piv[k];
+        if (pv != k) { double t = x[k]; x[k] = x[pv]; x[pv] = t; }
+        for (int r = k + 1; r < n; ++r) x[r] -= M[(size_t)r * n + k] * x[k];
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = x[r];
+        for (int q = r + 1; q < n; ++q) s -= M[(size_t)r * n + q] * x[q];
+        x[r] = s / M[(size_t)r * n + r];
+    }
+}
+
+static void mg_zero_dirichlet(const orc_mg* mg, int l, double* v)
+{
+    for (int i = 0; i < mg->n[l]; ++i)
+        if (mg->dm[l][i]) v[i] = 0.0;
+}
+
+/* one damped block-Jacobi sweep: x += omega D^{-1} (b - A x) */
+static void mg_smooth(const orc_mg* mg, int l, const double* b, double* x,
+                      double* tmp)
+{
+    int n = mg->n[l];
+    csr_matvec(n, mg->rp[l], mg->ci[l], mg->A[l], x, tmp);
+    for (int node = 0; node < n / 2; ++node) {
+        double rp = b[2 * node] - tmp[2 * node];
+        double rc = b[2 * node + 1] - tmp[2 * node + 1];
+        const double* D = mg->Dinv[l] + 4 * node;
+        x[2 * node] += mg->omega * (D[0] * rp + D[1] * rc);
+        x[2 * node + 1] += mg->omega * (D[2] * rp + D[3] * rc);
+    }
+    mg_zero_dirichlet(mg, l, x);
+}
+
+/* Trilinear interpolation from level l+1 to level l, written as a scatter
+ * of every coarse value to the fine nodes within one fine cell of it, with
+ * weight prod_d (1 - |offset_d|/2); restriction is its transpose. */
+static void mg_transfer(const orc_mg* mg, int l, double* fine, double* coarse,
+                        int restrict_)
+{
+    const orc_problem* Pf = &mg->P[l];
+    const orc_problem* Pc = &mg->P[l + 1];
+    if (restrict_)
+        for (int q = 0; q < mg->n[l + 1]; ++q) coarse[q] = 0.0;
+    for (int K = 0; K <= Pc->nz; ++K)
+        for (int J = 0; J <= Pc->ny; ++J)
+            for (int I = 0; I <= Pc->nx; ++I) {
+                int nc = node_id(Pc, I, J, K);
+                for (int c = -1; c <= 1; ++c)
+                    for (int b = -1; b <= 1; ++b)
+                        for (int a = -1; a <= 1; ++a) {
+                            int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+                            if (i < 0 || i > Pf->nx || j < 0 || j > Pf->ny || k < 0 ||
+                                k > Pf->nz)
+                                continue;
+                            double w = (a ? 0.5 : 1.0) * (b ? 0.5 : 1.0) * (c ? 0.5 : 1.0);
+                            int nf = node_id(Pf, i, j, k);
+                            for (int v = 0; v < 2; ++v) {
+                                if (restrict_) coarse[2 * nc + v] += w * fine[2 * nf + v];
+                                else fine[2 * nf + v] += w * coarse[2 * nc + v];
+                            }
+                        }
+            }
+}
+
+static void mg_vcycle(const orc_mg* mg, int l, const double* b, double* x)
+{
+    int n = mg->n[l];
+    if (l == mg->nlev - 1) {
+        memcpy(x, b, sizeof(double) * (size_t)n);
+        mg_coarse_solve(mg, x);
+        mg_zero_dirichlet(mg, l, x);
+        return;
+    }
+    double* tmp = mg->r[l];
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    for (int s = 0; s < mg->nu1; ++s) mg_smooth(mg, l, b, x, tmp);
+    csr_matvec(n, mg->rp[l], mg->ci[l], mg->A[l], x, tmp);
+    for (int i = 0; i < n; ++i) tmp[i] = b[i] - tmp[i];
+    mg_zero_dirichlet(mg, l, tmp);
+    mg_transfer(mg, l, tmp, mg->b[l + 1], 1);
+    mg_zero_dirichlet(mg, l + 1, mg->b[l + 1]);
+    mg_vcycle(mg, l + 1, mg->b[l + 1], mg->x[l + 1]);
+    mg_transfer(mg, l, x, mg->x[l + 1], 0);
+    mg_zero_dirichlet(mg, l, x);
+    for (int s = 0; s < mg->nu2; ++s) mg_smooth(mg, l, b, x, tmp);
+}
+
+/* z = M r for the full Jacobian: the V-cycle on the interior unknowns and
+ * the identity on the Dirichlet unknowns (whose rows are identity rows). */
+static void mg_precond(void* vctx, const double* r, double* z)
+{
+    orc_mg* mg = (orc_mg*)vctx;
+    int n = mg->n[0];
+    double* b = mg->b[0];
+    memcpy(b, r, sizeof(double) * (size_t)n);
+    mg_zero_dirichlet(mg, 0, b);
+    mg_vcycle(mg, 0, b, z);
+    for (int i = 0; i < n; ++i)
+        if (mg->dm[0][i]) z[i] = r[i];
+}
+
+/* Solve J x = b (or J^T x = b) at state (p, c); (rowptr, col, val) hold the
+ * full J (or J^T).  Dense LU for small systems, else BiCGStab + V-cycle. */
+static int solve_at_state(const orc_problem* P, const double* phi,
+                          const double* K, const double* p, const double* c,
+                          double dt, int transpose, const int* rowptr,
+                          const int* col, const double* val, const double* b,
+                          double* x, const orc_newton_opts* o, int* iters)
+{
+    int n = 2 * orc_num_nodes(P);
+    if (n <= o->dense_max) return orc_linear_solve(n, rowptr, col, val, b, x, o, iters);
+    orc_mg mg;
+    int rc = mg_setup(&mg, P, phi, K, p, c, dt, transpose);
+    if (rc == 0) {
+        for (int i = 0; i < n; ++i) x[i] = 0.0;
+        double rr;
+        rc = bicgstab(n, rowptr, col, val, b, x, o->lin_rtol, o->lin_maxit,
+                      mg_precond, &mg, iters, &rr);
+    }
+    mg_free(&mg);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -658,7 +1007,7 @@ int orc_newton_step(const orc_problem* P, const double* phi, const double* K,
             rhs[2 * n + 1] = -Rc[n];
         }
         int li = 0;
-        if (orc_linear_solve(n2, rowptr, col, val, rhs, du, o, &li) != 0) {
+        if (solve_at_state(P, phi, K, p, c, dt, 0, rowptr, col, val, rhs, du, o, &li) != 0) {
             /* keep going: Newton only needs a descent direction */
             inf.status = 2;
         }
@@ -894,7 +1243,7 @@ int orc_adjoint_gradient(const orc_problem* P, const double* phi,
         orc_jacobian(P, phi, K, pn, cn, dt, rowptr, col, val);
         orc_csr_transpose(n2, rowptr, col, val, trowptr, tcol, tval);
         int li;
-        if (orc_linear_solve(n2, trowptr, tcol, tval, rhs, lam, o, &li) != 0)
+        if (solve_at_state(P, phi, K, pn, cn, dt, 1, trowptr, tcol, tval, rhs, lam, o, &li) != 0)
             rc = 1;
         /* gradient contributions -lambda_n^T dR_n/dtheta (non-Dirichlet
          * rows only: Dirichlet rows do not depend on theta) */
