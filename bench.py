@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Throughput of the batched implicit Elder time step on GB300.
+
+Workload: the batched qMC ensemble at 64x64x16 cells (71,825 nodes, 143,650
+unknowns per sample), 256 samples of scrambled-Sobol porosity fields
+phi = 0.1*(1 + 0.3*(xi1 cos(pi x/600) + xi2 cos(pi y/600) + xi3 sin(2 pi
+z/150))/3) with normalised Kozeny-Carman permeability, dt = 1/12 yr, mixed
+precision (FP32 multigrid and Krylov storage inside FP64 Newton with FP64
+residual and inner products).  One bench step = one implicit Euler step of
+every sample (elder_step) plus the ensemble moments of that step
+(elder_moments).  Metric: sample-timesteps/s, higher is better.
+
+Under torchrun each rank takes its own 256 samples (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one implicit step of several samples, one per
+worker process, per bench step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sample-timesteps/s at 64x64x16 batched (mixed vs FP64); GMG HBM GB/s vs peak"
+UNIT = "sample-timesteps/s"
+YEAR = 365.25 * 86400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--samples", type=int, default=256)
+    ap.add_argument("--grid", type=int, nargs=3, default=[64, 64, 16])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-workers", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload_config(a):
+    nx, ny, nz = a.grid
+    return {
+        "workload": f"elder3d-box-{nx}x{ny}x{nz}-qmc{a.samples}",
+        "grid_cells": [nx, ny, nz],
+        "nodes_per_sample": (nx + 1) * (ny + 1) * (nz + 1),
+        "samples_per_gpu": a.samples,
+        "dt_yr": 1.0 / 12.0,
+        "precision": a.precision,
+        "fields": "scrambled Sobol (torch SobolEngine seed 0) -> phi (cosine field), Kozeny-Carman K",
+        "l2": "no flush: per-step working set (Jacobians of all levels, vectors) ~10 GB >> 129 MB L2",
+        "parallelism": f"samples sharded, dp{a.gpus}",
+    }
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on the host cores
+# --------------------------------------------------------------------------
+
+def _oracle_one_step(args):
+    nx, ny, nz, xi = args
+    import numpy as np  # noqa: F401
+    import oracle as O
+    P = O.Problem(nx, ny, nz)
+    phi, K = O.fields_sobol(P, xi)
+    p, c = O.initial_state(P)
+    t = time.perf_counter()
+    p, c, info = O.newton_step(P, phi, K, p, c, YEAR / 12)
+    return time.perf_counter() - t, info["status"]
+
+
+def cpu_baseline(a, workers=None):
+    import multiprocessing as mp
+    from paper_1906_01632_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    nproc = os.cpu_count() or 1
+    workers = workers or a.cpu_workers or min(8, nproc)
+    xi = I.sobol_xi(workers)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_one_step, [(a.grid[0], a.grid[1], a.grid[2], xi[i]) for i in range(workers)])
+    wall = time.perf_counter() - t0
+    return {"value": workers / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{workers} samples x 1 implicit step (first step from t=0) at "
+                      f"{a.grid[0]}x{a.grid[1]}x{a.grid[2]}, one sample per process, wall {wall:.1f} s",
+            "per_sample_step_s": [round(r[0], 2) for r in res]}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = workload_config(a)
+    cfg["precision"] = "fp64"
+    steps = []
+    for i in range(a.warmup + a.steps):
+        r = cpu_baseline(a)
+        if i >= a.warmup:
+            steps.append(r)
+    total_samples = sum(r["cores"] for r in steps)
+    total_wall = sum(r["cores"] / r["value"] for r in steps)
+    value = total_samples / total_wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * total_wall / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": steps[0]["cores"], "kind": "oracle",
+                             "sample": steps[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the CUDA path
+# --------------------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def ncu_traffic(kernel_class: str, precision: str):
+    """DRAM bytes per node and sample of one launch from the committed ncu
+    summary (profiles/*.md lines 'traffic_bytes_per_node <class> <precision> <value>')."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for f in sorted(os.listdir(d)):
+        if not f.endswith(".md"):
+            continue
+        for line in open(os.path.join(d, f)):
+            parts = line.strip().strip("`").split()
+            if len(parts) == 4 and parts[0] == "traffic_bytes_per_node" and parts[1] == kernel_class \
+                    and parts[2] == precision:
+                return float(parts[3])
+    return None
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1906_01632_gb300 import build as B
+    B.build()
+    from paper_1906_01632_gb300 import elder as E
+    from paper_1906_01632_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    nx, ny, nz = a.grid
+    S = a.samples
+    dt = YEAR / 12
+    prec = E.ELDER_MIXED if a.precision == "mixed" else E.ELDER_FP64
+    ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=prec))
+    N, C = ctx.N, ctx.C
+    xi_all = I.sobol_xi(S * world, seed=0)
+    xi = torch.tensor(xi_all[rank * S:(rank + 1) * S].ravel(), dtype=torch.float64, device=dev)
+    phi, K = ctx.fields(S, 0, xi)
+    p, c = ctx.initial_state(S, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def bench_step(p_, c_):
+        st, info = ctx.step(S, phi, K, p_, c_, dt)
+        mom = ctx.moments(S, c_)
+        return st, info, mom
+
+    stats_log = []
+    for _ in range(a.warmup):
+        st, info, _ = bench_step(p, c)
+        stats_log.append(info)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region ------------------------------------------------
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.profile(True)
+    l0 = E.elder_launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fails = 0
+    retries = 0
+    newton, krylov = [], []
+    for _ in range(a.steps):
+        st, info, _ = bench_step(p, c)
+        fails += int((st != 0).sum())
+        retries += sum(x["fp64_retry"] for x in info)
+        newton.append(np.mean([x["newton_iters"] for x in info]))
+        krylov.append(np.mean([x["krylov_iters"] for x in info]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = E.elder_launch_count() - l0
+    ctx.profile(False)
+    clk = clocks.stop()
+    prof = {E.KERNEL_CLASSES[k]: ctx.profile_read(k) for k in E.KERNEL_CLASSES}
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = S * world * a.steps / (ms / 1000.0)
+
+    # ---- roofline of the dominant kernel class ------------------------------
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    pk = prof[top]
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    tsize = 4 if a.precision == "mixed" else 8
+    per_launch_ms = pk["ms"] / max(pk["launches"], 1)
+    bytes_per_launch = pk["bytes"] / max(pk["launches"], 1)
+    achieved = (pk["bytes"] / 1e9) / (pk["ms"] / 1e3) if pk["ms"] > 0 else None
+    tr = ncu_traffic(top, a.precision)
+    roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak if achieved else None,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "traffic": (tr * bytes_per_launch / max(1e-30, E_model_bytes(top, tsize, nx, ny, nz))
+                            if tr is not None else None),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_ms,
+                "launches": pk["launches"]}
+    classes = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share": round(v["ms"] / ms, 4) if ms else None,
+                   "GB/s": round((v["bytes"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None,
+                   "GFLOP/s": round((v["flops"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None}
+               for k, v in prof.items()}
+
+    # ---- end to end through host buffers -------------------------------------
+    e2e = None
+    if not a.no_e2e:
+        hp = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
+        hc = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
+        hphi = torch.empty(S * C, dtype=torch.float64, pin_memory=True)
+        hK = torch.empty(S * C, dtype=torch.float64, pin_memory=True)
+        hmom = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+        hp.copy_(p)
+        hc.copy_(c)
+        hphi.copy_(phi)
+        hK.copy_(K)
+        dp_, dc_ = torch.empty_like(p), torch.empty_like(c)
+        dphi, dK = torch.empty_like(phi), torch.empty_like(K)
+        ctx.step(S, phi, K, p, c, dt)  # keep the state moving as in the timed run
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            dp_.copy_(hp, non_blocking=True)
+            dc_.copy_(hc, non_blocking=True)
+            dphi.copy_(hphi, non_blocking=True)
+            dK.copy_(hK, non_blocking=True)
+            ctx.step(S, dphi, dK, dp_, dc_, dt)
+            m, v, pe = ctx.moments(S, dc_)
+            hp.copy_(dp_, non_blocking=True)
+            hc.copy_(dc_, non_blocking=True)
+            hmom[:N].copy_(m, non_blocking=True)
+            hmom[N:2 * N].copy_(v, non_blocking=True)
+            hmom[2 * N:].copy_(pe, non_blocking=True)
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": S * world * a.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * S * (2 * N + 2 * C),
+               "d2h_bytes_per_step": 8 * (S * 2 * N + 3 * N)}
+
+    # ---- FP64 path on the same workload and state ---------------------------
+    fp64 = None
+    if not a.no_fp64 and a.precision == "mixed":
+        ctx64 = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=E.ELDER_FP64))
+        p64, c64 = p.clone(), c.clone()
+        pm, cm = p.clone(), c.clone()
+        ctx64.step(S, phi, K, p64, c64, dt)  # warm-up (graph capture) from the same state
+        ctx.step(S, phi, K, pm, cm, dt)
+        diff = float((c64 - cm).abs().max().item())
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        k64 = max(1, min(a.steps, 2))
+        f0.record(stream)
+        for _ in range(k64):
+            ctx64.step(S, phi, K, p64, c64, dt)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"value": S * world * k64 / (ms64 / 1000.0), "unit": UNIT, "steps": k64,
+                "ms_per_step": ms64 / k64,
+                "mixed_vs_fp64_max_abs_c_same_state": diff}
+        ctx64.destroy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64+f32" if a.precision == "mixed" else "f64",
+                "data": "synthetic", "config": workload_config(a), "clocks": clk,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "fp64_path": fp64, "kernel_classes": classes,
+                "iterations": {"newton_per_step": float(np.mean(newton)),
+                               "krylov_per_step": float(np.mean(krylov)), "failed_samples": fails,
+                               "fp64_retries": retries},
+                "timing": "CUDA events on the launching stream; per-class CUDA events inside the "
+                          "timed region (graph replay bypassed while they are recorded)"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def E_model_bytes(cls, tsize, nx, ny, nz):
+    """Algorithmic bytes per node of one launch (mirrors the library's model)."""
+    N = (nx + 1) * (ny + 1) * (nz + 1)
+    cpn = nx * ny * nz / N
+    return {"smooth": 118 * tsize + 1, "smooth0": 8 * tsize + 1, "spmv": 114 * tsize + 1,
+            "mg_residual": 114 * tsize + 1, "residual": 57 + 16 * cpn,
+            "jacobian": 108 * tsize + 17 + 16 * cpn}[cls]
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

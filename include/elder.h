@@ -54,7 +54,8 @@ enum {
     ELDER_SAMPLE_NEWTON_MAXIT = 1,  /* Newton iteration cap reached        */
     ELDER_SAMPLE_KRYLOV_MAXIT = 2,  /* BiCGStab cap reached (elder_solve)  */
     ELDER_SAMPLE_BREAKDOWN = 3,     /* BiCGStab breakdown (rho or omega 0) */
-    ELDER_SAMPLE_NONFINITE = 4      /* NaN/Inf in a residual norm          */
+    ELDER_SAMPLE_NONFINITE = 4,     /* NaN/Inf in a residual norm          */
+    ELDER_SAMPLE_LINESEARCH = 5     /* no step length decreased ||R||      */
 };
 
 enum { ELDER_FP64 = 0, ELDER_MIXED = 1 };
@@ -101,6 +102,9 @@ typedef struct {
     int32_t ls_cuts;          /* step halvings                              */
     double res0;              /* ||R(u^n)||_2 with Dirichlet data imposed   */
     double res;               /* ||R(u^{n+1})||_2                           */
+    int32_t fp64_retry;       /* 1: ELDER_MIXED failed and the step was
+                                 solved again with the FP64 solver          */
+    int32_t pad;
 } elder_stats;
 
 typedef struct elder_ctx elder_ctx;
@@ -157,7 +161,9 @@ int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
 /* One implicit Euler step for S samples (Sections 2.3 and 5.1): Newton with
  * line search on the FP64 residual, each Newton system solved by
  * multigrid-preconditioned BiCGStab (FP64, or FP32 multigrid and Krylov
- * storage with FP64 inner products in ELDER_MIXED).
+ * storage with FP64 inner products in ELDER_MIXED).  In ELDER_MIXED a
+ * sample whose Newton iteration fails is solved again from u^n with the
+ * FP64 solver (packed into batches of at most 32 samples).
  *  phi, K: [S][C] inputs.  p, c: [S][N] in: u^n, out: u^{n+1}.
  *  dt: time step [s].  status, stats: HOST arrays of S entries (stats may
  *  be NULL), written after the stream is synchronised.  A failed sample
@@ -194,6 +200,44 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi,
                const double* K, const double* p0, const double* c0, double dt,
                int ckpt_every, double* J_out, double* dJ_dphi, double* dJ_dK,
                void* stream);
+
+/* Initial state of the benchmark problem (Section 2.1): c = its Dirichlet
+ * value on c-Dirichlet nodes and 0 elsewhere; p = rho0 g (Lz - z), the
+ * hydrostatic pressure of pure water, which only seeds Newton (p has no time
+ * derivative).  p, c: [S][N] device outputs. */
+int elder_initial_state(elder_ctx* ctx, int S, double* p, double* c,
+                        void* stream);
+
+/* ---- measurement (no counterpart in the paper) ------------------------ */
+
+/* Kernel classes timed by elder_profile. */
+enum {
+    ELDER_K_SMOOTH = 0,     /* block-Jacobi sweeps with a nonzero iterate   */
+    ELDER_K_SPMV = 1,       /* BiCGStab stencil products (+ inner products) */
+    ELDER_K_MGRES = 2,      /* multigrid residuals b - A x                  */
+    ELDER_K_RESIDUAL = 3,   /* FP64 Newton residual                         */
+    ELDER_K_JACOBIAN = 4,   /* Jacobian assembly, all levels                */
+    ELDER_K_SMOOTH0 = 5,    /* first sweep from a zero iterate              */
+    ELDER_K_CLASSES = 6
+};
+
+/* on=1 resets the counters and brackets every launch of the classes above
+ * with CUDA events on the launching stream (CUDA-graph replay is bypassed
+ * while profiling); on=0 stops.  Event times are drained at the host
+ * synchronisation points the step already has. */
+int elder_profile(elder_ctx* ctx, int on);
+
+/* Totals since elder_profile(ctx, 1) for one class: launches, summed event
+ * time [ms], algorithmic DRAM bytes and FP64/FP32 flops of those launches
+ * (per-node model x nodes x active samples; see the design notes).  Any
+ * output pointer may be NULL.  Host outputs. */
+int elder_profile_read(const elder_ctx* ctx, int kernel_class,
+                       int64_t* launches, double* ms, double* bytes,
+                       double* flops);
+
+/* Number of kernels this library has launched in the process (graph
+ * replays count every kernel node).  Host output. */
+int elder_launch_count(int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -79,6 +79,14 @@ void orc_residual(const orc_problem* P, const double* phi, const double* K,
                   const double* c_old, double dt, int apply_dirichlet,
                   double* Rp, double* Rc);
 
+/* Round-off scale of R: 2-norm over non-Dirichlet rows of the per-row sums
+ * of the magnitudes of all terms of orc_residual (storage at both levels;
+ * for each Darcy flux rho (K/mu)(|grad p| + [z] g rho) A, the size of the two
+ * terms it cancels).  Newton treats ||R|| <= 2 eps times this as solved. */
+double orc_residual_magnitude(const orc_problem* P, const double* phi,
+                              const double* K, const double* p,
+                              const double* c, const double* c_old, double dt);
+
 /* Sparse pattern (CSR, 0-based, sorted columns) of the 2N x 2N Jacobian. */
 int  orc_jac_nnz(const orc_problem* P);
 void orc_jac_pattern(const orc_problem* P, int* rowptr, int* col);

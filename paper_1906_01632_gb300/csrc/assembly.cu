@@ -42,7 +42,7 @@ __device__ __forceinline__ void flux_face(const double (&p8)[8],
                                           const double (&c8)[8], double phi_e,
                                           double kmu, const Phys& ph,
                                           double invh, double area, double& m,
-                                          double& F)
+                                          double& F, double& mmag, double& Fmag)
 {
     double gp = 0.0, gc = 0.0, ci = 0.0;
 #pragma unroll
@@ -63,7 +63,11 @@ __device__ __forceinline__ void flux_face(const double (&p8)[8],
     m = rho * (-kmu * G) * area;
     const double cup =
         (m >= 0.0) ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
-    F = cup * m - rho * phi_e * ph.Dm * gc * area;
+    const double dif = rho * phi_e * ph.Dm * area;
+    F = cup * m - dif * gc;
+    // rounding scale: the Darcy flux cancels grad p against rho g
+    mmag = rho * kmu * area * (fabs(gp) + (D == 2 ? ph.g * rho : 0.0));
+    Fmag = fabs(cup) * mmag + dif * fabs(gc);
 }
 
 struct CellGeom {
@@ -76,7 +80,7 @@ __device__ __forceinline__ void residual_cell(
     const Grid& G, const Phys& ph, const CellGeom& cg, int i, int j, int k,
     const double* __restrict__ phi, const double* __restrict__ K,
     const double* __restrict__ p, const double* __restrict__ c, double& Rp,
-    double& Rc, double& phis)
+    double& Rc, double& phis, double& Ap, double& Ac)
 {
     const int ci = i + OX, cj = j + OY, ck = k + OZ;
     if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz)
@@ -95,13 +99,19 @@ __device__ __forceinline__ void residual_cell(
         c8[L] = __ldg(c + base + off);
     }
     constexpr int lx = -OX, ly = -OY, lz = -OZ;  // this node's local corner
-    double m, F;
-    flux_face<0, ly, lz>(p8, c8, phi_e, kmu, ph, cg.ih[0], cg.area[0], m, F);
+    double m, F, mm, Fm;
+    flux_face<0, ly, lz>(p8, c8, phi_e, kmu, ph, cg.ih[0], cg.area[0], m, F, mm, Fm);
     if (lx == 0) { Rp += m; Rc += F; } else { Rp -= m; Rc -= F; }
-    flux_face<1, lx, lz>(p8, c8, phi_e, kmu, ph, cg.ih[1], cg.area[1], m, F);
+    Ap += mm;
+    Ac += Fm;
+    flux_face<1, lx, lz>(p8, c8, phi_e, kmu, ph, cg.ih[1], cg.area[1], m, F, mm, Fm);
     if (ly == 0) { Rp += m; Rc += F; } else { Rp -= m; Rc -= F; }
-    flux_face<2, lx, ly>(p8, c8, phi_e, kmu, ph, cg.ih[2], cg.area[2], m, F);
+    Ap += mm;
+    Ac += Fm;
+    flux_face<2, lx, ly>(p8, c8, phi_e, kmu, ph, cg.ih[2], cg.area[2], m, F, mm, Fm);
     if (lz == 0) { Rp += m; Rc += F; } else { Rp -= m; Rc -= F; }
+    Ap += mm;
+    Ac += Fm;
 }
 
 __host__ __device__ inline CellGeom make_geom(const Grid& G)
@@ -122,7 +132,8 @@ __global__ void __launch_bounds__(kBS)
                const double* __restrict__ K, const double* __restrict__ p,
                const double* __restrict__ c, const double* __restrict__ p_old,
                const double* __restrict__ c_old, V2<double>* __restrict__ R,
-               double* __restrict__ partial, const int* mask, int mstride)
+               double* __restrict__ partial, double* __restrict__ act, const int* mask,
+               int mstride)
 {
     __shared__ double red[32];
     const int s = blockIdx.y;
@@ -130,33 +141,42 @@ __global__ void __launch_bounds__(kBS)
     const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
     phi += oc; K += oc; p += on; c += on; p_old += on; c_old += on; R += on;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double sq = 0.0;
+    double sq = 0.0, aq = 0.0;
     if (n < G.N) {
         int i, j, k;
         node_ijk(G, n, i, j, k);
-        double Rp = 0.0, Rc = 0.0, phis = 0.0;
-        residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
-        residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis);
+        double Rp = 0.0, Rc = 0.0, phis = 0.0, Ap = 0.0, Ac = 0.0;
+        residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
         const double vscv = 0.125 * G.hx * G.hy * G.hz;
         const double cn = c[n], co = c_old[n];
         const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
-        Rp += phis * vscv * (rn - ro) / ph.dt;
-        Rc += phis * vscv * (rn * cn - ro * co) / ph.dt;
+        const double sp = phis * vscv * (rn - ro) / ph.dt;
+        const double sc = phis * vscv * (rn * cn - ro * co) / ph.dt;
+        Rp += sp;
+        Rc += sc;
+        Ap += fabs(phis * vscv * rn / ph.dt) + fabs(phis * vscv * ro / ph.dt);
+        Ac += fabs(phis * vscv * rn * cn / ph.dt) + fabs(phis * vscv * ro * co / ph.dt);
         const uint8_t b = bc[n];
-        if (b & BC_P) Rp = p[n];
-        if (b & BC_C) Rc = cn - cval[n];
+        if (b & BC_P) { Rp = p[n]; Ap = 0.0; }
+        if (b & BC_C) { Rc = cn - cval[n]; Ac = 0.0; }
         R[n] = V2<double>{Rp, Rc};
         sq = Rp * Rp + Rc * Rc;
+        aq = Ap * Ap + Ac * Ac;
     }
     if (partial) {
         const double t = block_sum(sq, red);
         if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = t;
+    }
+    if (act) {  // magnitude of the summed terms: the round-off scale of R
+        const double t = block_sum(aq, red);
+        if (threadIdx.x == 0) act[(size_t)s * gridDim.x + blockIdx.x] = t;
     }
 }
 
@@ -164,11 +184,13 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* cval, const double* phi, const double* K,
                      const double* p, const double* c, const double* p_old,
                      const double* c_old, V2<double>* R, double* partial,
-                     const int* mask, int mstride, int S, cudaStream_t st)
+                     double* act, const int* mask, int mstride, int S,
+                     cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_residual<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), bc, cval, phi, K, p,
-                                     c, p_old, c_old, R, partial, mask, mstride);
+                                     c, p_old, c_old, R, partial, act, mask, mstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,6 +364,7 @@ void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* c, B4<T>* J, const int* mask, int mstride,
                      int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N, 128), S);
     k_jacobian<T><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c,
                                          J, mask, mstride);
@@ -379,6 +402,7 @@ void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
                    const double* cf, double* pc, double* cc, const int* mask,
                    int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(Gc.N), S);
     k_inject<<<grid, kBS, 0, st>>>(Gf, Gc, pf, cf, pc, cc, mask, mstride);
 }
@@ -408,6 +432,7 @@ void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
                           const double* Kf, double* phic, double* Kc,
                           int harmonic, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(Gc.C), S);
     k_average_cells<<<grid, kBS, 0, st>>>(Gf, Gc, phif, Kf, phic, Kc, harmonic);
 }
@@ -439,6 +464,7 @@ void launch_block_diag_inverse(const Grid& G, const uint8_t* bc,
                                const B4<T>* J, B4<T>* Dinv, const int* mask,
                                int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_block_diag_inverse<T><<<grid, kBS, 0, st>>>(G, bc, J, Dinv, mask, mstride);
 }
@@ -561,9 +587,11 @@ void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<T>* J,
                            double* work, double* Ainv, const int* mask,
                            int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N, 64), S);
     k_coarse_build<T><<<grid, 64, 0, st>>>(G, bc, J, work, mask, mstride);
     const int n = 2 * G.N;
+    count_launch(1);
     k_gauss_jordan<<<S, 256, sizeof(double) * n, st>>>(n, work, Ainv, mask, mstride);
 }
 template void launch_coarse_inverse<double>(const Grid&, const uint8_t*,
@@ -590,10 +618,34 @@ __global__ void k_impose_dirichlet(Grid G, const uint8_t* __restrict__ bc,
     if (b & BC_C) c[(size_t)s * G.N + n] = cval[n];
 }
 
+// Initial state (Section 2.1): Dirichlet c values, c = 0 elsewhere, and the
+// hydrostatic pressure of pure water p = rho0 g (Lz - z).
+__global__ void k_initial_state(Grid G, double rho0g, const uint8_t* __restrict__ bc,
+                                const double* __restrict__ cval, double* p, double* c)
+{
+    const int s = blockIdx.y;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    int i, j, k;
+    node_ijk(G, n, i, j, k);
+    p[(size_t)s * G.N + n] = rho0g * (G.Lz - k * G.hz);
+    c[(size_t)s * G.N + n] = (bc[n] & BC_C) ? cval[n] : 0.0;
+}
+
+void launch_initial_state(const Grid& G, double rho0g, const uint8_t* bc,
+                          const double* cval, double* p, double* c, int S,
+                          cudaStream_t st)
+{
+    count_launch(1);
+    dim3 grid(nblocks(G.N), S);
+    k_initial_state<<<grid, kBS, 0, st>>>(G, rho0g, bc, cval, p, c);
+}
+
 void launch_impose_dirichlet(const Grid& G, const uint8_t* bc,
                              const double* cval, double* p, double* c, int S,
                              cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_impose_dirichlet<<<grid, kBS, 0, st>>>(G, bc, cval, p, c);
 }
@@ -636,6 +688,7 @@ void launch_fields(const Grid& G, int kind, const double* params,
                    double K_mean, double* phi, double* K, int S,
                    cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.C), S);
     k_fields<<<grid, kBS, 0, st>>>(G, kind, params, K_mean, phi, K);
 }
@@ -696,7 +749,9 @@ void launch_objective(const Grid& G, const Phys& ph, const double* phi,
                       const double* c, double* partial, double* dJdphi,
                       V2<double>* dJdu, cudaStream_t st)
 {
+    count_launch(1);
     k_objective_cells<<<nblocks(G.C), kBS, 0, st>>>(G, ph, phi, c, partial, dJdphi);
+    count_launch(1);
     k_objective_nodes<<<nblocks(G.N), kBS, 0, st>>>(G, ph, phi, c, dJdu);
 }
 
@@ -801,6 +856,7 @@ void launch_adjoint_theta(const Grid& G, const Phys& ph, const uint8_t* bc,
                           const V2<double>* lam, double* dJdphi, double* dJdK,
                           cudaStream_t st)
 {
+    count_launch(1);
     k_adjoint_theta<<<nblocks(G.C), kBS, 0, st>>>(G, ph, make_geom(G), bc, phi, K,
                                                   p, c, c_old, lam, dJdphi, dJdK);
 }
@@ -837,6 +893,7 @@ void launch_adjoint_prev_rhs(const Grid& G, const Phys& ph, const uint8_t* bc,
                              const V2<double>* lam, V2<double>* rhs,
                              cudaStream_t st)
 {
+    count_launch(1);
     k_adjoint_prev_rhs<<<nblocks(G.N), kBS, 0, st>>>(G, ph, bc, phi, c_old, lam, rhs);
 }
 

@@ -30,6 +30,7 @@ constexpr int ELDER_SAMPLE_NEWTON_MAXIT_ = 1;
 constexpr int ELDER_SAMPLE_KRYLOV_MAXIT_ = 2;
 constexpr int ELDER_SAMPLE_BREAKDOWN_ = 3;
 constexpr int ELDER_SAMPLE_NONFINITE_ = 4;
+constexpr int ELDER_SAMPLE_LINESEARCH_ = 5;
 
 // Dirichlet bits per node (the same on every sample).
 enum : uint8_t { BC_P = 1, BC_C = 2 };

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -147,15 +148,39 @@ template <class T> struct Solver : SolverBase {
     double *Ainv = nullptr, *work = nullptr;
     DevFree mem;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (S, trans)
+    std::map<std::pair<int, int>, long long> graph_kernels;  // kernel nodes
     ~Solver()
     {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     }
 };
 
+// Per-class CUDA-event accounting (elder_profile).
+struct ProfRec {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes, flops;
+};
+
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<ProfRec> pending;
+    long long launches[ELDER_K_CLASSES] = {};
+    double ms[ELDER_K_CLASSES] = {}, bytes[ELDER_K_CLASSES] = {}, flops[ELDER_K_CLASSES] = {};
+    ~Prof()
+    {
+        for (auto& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
 struct elder_ctx {
     elder_config cfg;
     int device = 0;
+    Prof prof;
+    // sample counts behind the byte model of the profiled launches
+    int n_active_newton = 0, n_active_ls = 0, n_active_k = 0;
     std::string err = "no error";
     std::vector<Grid> grids;
     std::vector<uint8_t*> bc;          // per level [N]
@@ -165,6 +190,8 @@ struct elder_ctx {
     V2<double> *R = nullptr, *Rt = nullptr, *tmp2 = nullptr;
     double* partial = nullptr;         // [S][2][nblk0]
     double* partial2 = nullptr;
+    double* partial3 = nullptr;
+    double* pk = nullptr;              // packed batch for the FP64 re-solve
     NScal* ns = nullptr;
     KScal* ks = nullptr;
     NScal* h_ns = nullptr;             // pinned
@@ -184,6 +211,12 @@ struct elder_ctx {
     }
 };
 
+std::atomic<long long> g_launches{0};
+
+namespace elder {
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace elder
+
 namespace {
 
 Phys make_phys(const elder_config& c, double dt)
@@ -191,19 +224,112 @@ Phys make_phys(const elder_config& c, double dt)
     return Phys{c.rho0, c.rho1 - c.rho0, c.mu, c.g, c.Dm, dt};
 }
 
-template <class T> Solver<T>& solver(elder_ctx* ctx);
-template <> Solver<double>& solver<double>(elder_ctx* ctx)
+// Algorithmic DRAM bytes and flops per node of one launch (every array the
+// kernel must touch, read or written once; neighbour reuse of x is free).
+// T = bytes of the solver type.  J row: 27 blocks of 4; vectors: 2 values.
+double model_bytes(int cls, int T, const Grid& G)
 {
-    if (!ctx->s64) ctx->s64.reset(new Solver<double>());
-    return *ctx->s64;
-}
-template <> Solver<float>& solver<float>(elder_ctx* ctx)
-{
-    if (!ctx->s32) ctx->s32.reset(new Solver<float>());
-    return *ctx->s32;
+    const double cells_per_node = (double)G.C / G.N;
+    switch (cls) {
+    case ELDER_K_SMOOTH: return (108 + 4 + 2 + 2 + 2) * T + 1;     // J, Dinv, b, x, xo, bc
+    case ELDER_K_SMOOTH0: return (4 + 2 + 2) * T + 1;               // Dinv, b, xo, bc
+    case ELDER_K_SPMV: return (108 + 2 + 2 + 2) * T + 1;            // J, x, y, a, bc
+    case ELDER_K_MGRES: return (108 + 2 + 2 + 2) * T + 1;           // J, x, b, r, bc
+    case ELDER_K_RESIDUAL:                                          // p,c,p_old,c_old,R,cval,bc,phi,K
+        return 4 * 8 + 16 + 8 + 1 + 16 * cells_per_node;
+    case ELDER_K_JACOBIAN:                                          // J written; p, c, bc, phi, K
+        return 108 * T + 16 + 1 + 16 * cells_per_node;
+    }
+    return 0.0;
 }
 
-template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv)
+double model_flops(int cls)
+{
+    switch (cls) {
+    case ELDER_K_SMOOTH: return 216 + 8 + 4 + 4;
+    case ELDER_K_SMOOTH0: return 8 + 2;
+    case ELDER_K_SPMV: return 216 + 8;
+    case ELDER_K_MGRES: return 216 + 2;
+    case ELDER_K_RESIDUAL: return 24 * 54 + 20;   // 24 face fluxes + storage
+    case ELDER_K_JACOBIAN: return 24 * (54 + 66) + 10;
+    }
+    return 0.0;
+}
+
+int prof_begin(elder_ctx* ctx, cudaStream_t st)
+{
+    Prof& P = ctx->prof;
+    if (!P.on) return -1;
+    ProfRec r;
+    for (cudaEvent_t* e : {&r.a, &r.b}) {
+        if (!P.pool.empty()) {
+            *e = P.pool.back();
+            P.pool.pop_back();
+        } else {
+            CK(cudaEventCreate(e));
+        }
+    }
+    CK(cudaEventRecord(r.a, st));
+    r.cls = -1;
+    P.pending.push_back(r);
+    return (int)P.pending.size() - 1;
+}
+
+void prof_end(elder_ctx* ctx, int idx, int cls, const Grid& G, int T, int samples,
+              cudaStream_t st)
+{
+    if (idx < 0) return;
+    ProfRec& r = ctx->prof.pending[idx];
+    CK(cudaEventRecord(r.b, st));
+    r.cls = cls;
+    r.bytes = model_bytes(cls, T, G) * G.N * samples;
+    r.flops = model_flops(cls) * G.N * samples;
+}
+
+// after a stream synchronisation: accumulate and recycle the events
+void prof_drain(elder_ctx* ctx)
+{
+    Prof& P = ctx->prof;
+    for (auto& r : P.pending) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(r.b));
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        if (r.cls >= 0) {
+            P.launches[r.cls] += 1;
+            P.ms[r.cls] += ms;
+            P.bytes[r.cls] += r.bytes;
+            P.flops[r.cls] += r.flops;
+        }
+        P.pool.push_back(r.a);
+        P.pool.push_back(r.b);
+    }
+    P.pending.clear();
+}
+
+template <class T> std::unique_ptr<Solver<T>>& solver_slot(elder_ctx* ctx);
+template <> std::unique_ptr<Solver<double>>& solver_slot<double>(elder_ctx* ctx)
+{
+    return ctx->s64;
+}
+template <> std::unique_ptr<Solver<float>>& solver_slot<float>(elder_ctx* ctx)
+{
+    return ctx->s32;
+}
+
+template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap);
+
+// The solver of precision T with room for at least `cap` samples (its
+// workspace is reallocated when a call needs more).
+template <class T> Solver<T>& solver_reserve(elder_ctx* ctx, int cap)
+{
+    std::unique_ptr<Solver<T>>& up = solver_slot<T>(ctx);
+    if (up && up->S >= cap) return *up;
+    up.reset(new Solver<T>());
+    solver_alloc<T>(ctx, *up, cap);
+    return *up;
+}
+
+template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap)
 {
     if (sv.S) return;
     // the coarsest level is solved by a dense inverse: bound its size
@@ -216,7 +342,7 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv)
                       2 * ctx->grids.back().N, MAX_COARSE_UNKNOWNS);
         throw Fail{ELDER_EINVAL, buf};
     }
-    const int S = ctx->cfg.max_samples;
+    const int S = cap;
     const int L = (int)ctx->grids.size();
     for (int l = 0; l < L; ++l) {
         const Grid& G = ctx->grids[l];
@@ -249,7 +375,8 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv)
 template <class T>
 void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
               const double* K0, const double* p0, const double* c0,
-              const Phys& ph, const int* mask, int mstride, cudaStream_t st)
+              const Phys& ph, const int* mask, int mstride, int n_active,
+              cudaStream_t st)
 {
     const int L = (int)ctx->grids.size();
     for (int l = 0; l < L; ++l) {
@@ -264,7 +391,9 @@ void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
             launch_inject(ctx->grids[l - 1], G, pf, cf, ctx->pl[l], ctx->cl[l], mask,
                           mstride, S, st);
         }
+        const int pi = prof_begin(ctx, st);
         launch_jacobian<T>(G, ph, ctx->bc[l], phi, K, p, c, sv.J[l], mask, mstride, S, st);
+        prof_end(ctx, pi, ELDER_K_JACOBIAN, G, sizeof(T), n_active, st);
         launch_block_diag_inverse<T>(G, ctx->bc[l], sv.J[l], sv.Dinv[l], mask, mstride, S, st);
     }
     launch_coarse_inverse<T>(ctx->grids.back(), ctx->bc.back(), sv.J.back(), sv.work,
@@ -304,23 +433,32 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     // choose the first buffer so that the last sweep lands in `out`
     V2<T>* cur = ((sweeps - 1) % 2 == 0) ? bufA : bufB;
     V2<T>* oth = (cur == bufA) ? bufB : bufA;
+    const int na = ctx->n_active_k;
+    int pi = prof_begin(ctx, st);
     launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, nullptr, cur, cf.omega, trans,
                      mask, KSTRIDE, S, st);
+    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), na, st);
     for (int q = 1; q < nu1; ++q) {
+        pi = prof_begin(ctx, st);
         launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
                          mask, KSTRIDE, S, st);
+        prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), na, st);
         std::swap(cur, oth);
     }
+    pi = prof_begin(ctx, st);
     launch_mg_residual<T>(G, sv.J[l], ctx->bc[l], b, cur, sv.mr[l], trans, mask, KSTRIDE, S,
                           st);
+    prof_end(ctx, pi, ELDER_K_MGRES, G, sizeof(T), na, st);
     launch_restrict<T>(G, ctx->grids[l + 1], ctx->bc[l + 1], sv.mr[l], sv.mb[l + 1], mask,
                        KSTRIDE, S, st);
     vcycle<T>(ctx, sv, l + 1, sv.mb[l + 1], sv.mx[l + 1], trans, S, st);
     launch_prolong_add<T>(G, ctx->grids[l + 1], ctx->bc[l], sv.mx[l + 1], cur, mask, KSTRIDE,
                           S, st);
     for (int q = 0; q < nu2; ++q) {
+        pi = prof_begin(ctx, st);
         launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
                          mask, KSTRIDE, S, st);
+        prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), na, st);
         std::swap(cur, oth);
     }
     if (cur != out) CK(cudaMemcpyAsync(out, cur, sizeof(V2<T>) * (size_t)S * G.N,
@@ -337,13 +475,17 @@ void bicg_iteration(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int m
     const int* mask = &ks[0].active;
     launch_bicg_p<T>(G, sv.r, sv.v, sv.p, ks, S, st);
     vcycle<T>(ctx, sv, 0, sv.p, sv.ph, trans, S, st);
+    int pi = prof_begin(ctx, st);
     launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.ph, sv.v, trans, 1, sv.rh, ctx->partial, mask,
                    KSTRIDE, S, st);
+    prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), ctx->n_active_k, st);
     launch_bicg_finalize(1, ctx->partial, nb, ks, rtol, maxit, S, st);
     launch_bicg_s<T>(G, sv.r, sv.v, sv.s, nullptr, ks, S, st);
     vcycle<T>(ctx, sv, 0, sv.s, sv.sh, trans, S, st);
+    pi = prof_begin(ctx, st);
     launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.sh, sv.t, trans, 2, sv.s, ctx->partial, mask,
                    KSTRIDE, S, st);
+    prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), ctx->n_active_k, st);
     launch_bicg_finalize(2, ctx->partial, nb, ks, rtol, maxit, S, st);
     launch_bicg_xr<T>(G, sv.ph, sv.sh, sv.s, sv.t, sv.rh, sv.x, sv.r, ctx->partial, ks, S, st);
     launch_bicg_finalize(3, ctx->partial, nb, ks, rtol, maxit, S, st);
@@ -362,9 +504,11 @@ bool any_krylov_active(elder_ctx* ctx, int S, cudaStream_t st)
 {
     CK(cudaMemcpyAsync(ctx->h_ks, ctx->ks, sizeof(KScal) * S, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    for (int s = 0; s < S; ++s)
-        if (ctx->h_ks[s].active) return true;
-    return false;
+    prof_drain(ctx);
+    int n = 0;
+    for (int s = 0; s < S; ++s) n += ctx->h_ks[s].active ? 1 : 0;
+    ctx->n_active_k = n;
+    return n > 0;
 }
 
 // Solve A x = b (or A^T x = b) on the interior system for the samples whose
@@ -376,38 +520,51 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
 {
     const Grid& G = ctx->grids[0];
     k_arm_krylov<<<nblocks(S, 128), 128, 0, st>>>(ctx->ks, ns, S);
+    count_launch(1);
+    ctx->n_active_k = ns ? ctx->n_active_newton : S;
     launch_bicg_init<T>(G, ctx->bc[0], sv.b, sv.x, sv.r, sv.rh, sv.p, sv.v, ctx->partial,
                         ctx->ks, S, st);
     launch_bicg_finalize(0, ctx->partial, ctx->nblk0, ctx->ks, rtol, maxit, S, st);
     CKL();
-    const bool graphs = ctx->cfg.use_graphs != 0;
+    // The captured finalize kernels bake in rtol and maxit; graphs are keyed
+    // on (S, trans) only, so they serve the configured values only, and are
+    // bypassed while per-launch events are recorded.
+    const bool use_exec = ctx->cfg.use_graphs != 0 && !ctx->prof.on &&
+                          rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit;
     cudaGraphExec_t exec = nullptr;
-    if (graphs) {
+    long long per_replay = 0;
+    if (use_exec) {
         auto key = std::make_pair(S, trans);
         auto it = sv.graphs.find(key);
         if (it == sv.graphs.end()) {
             cudaStream_t cs;
             CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             cudaGraph_t g;
+            const long long before = g_launches.load();
             CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             bicg_iteration<T>(ctx, sv, trans, rtol, maxit, S, cs);
             CK(cudaStreamEndCapture(cs, &g));
+            per_replay = g_launches.load() - before;
+            g_launches.fetch_sub(per_replay);  // captured, not launched
             CK(cudaGraphInstantiate(&exec, g, 0));
             CK(cudaGraphDestroy(g));
             CK(cudaStreamDestroy(cs));
             sv.graphs[key] = exec;
+            sv.graph_kernels[key] = per_replay;
         } else {
             exec = it->second;
+            per_replay = sv.graph_kernels[key];
         }
     }
-    // The captured finalize kernels bake in rtol and maxit; graphs are keyed
-    // on (S, trans) only, so they are used only with the configured values.
-    const bool use_exec = graphs && rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit;
-    const int poll = 2;
+    const int poll = ctx->prof.on ? 1 : 2;
     for (int it = 0; it < maxit; ++it) {
         if (it % poll == 0 && !any_krylov_active(ctx, S, st)) break;
-        if (use_exec) CK(cudaGraphLaunch(exec, st));
-        else bicg_iteration<T>(ctx, sv, trans, rtol, maxit, S, st);
+        if (use_exec) {
+            CK(cudaGraphLaunch(exec, st));
+            count_launch((int)per_replay);
+        } else {
+            bicg_iteration<T>(ctx, sv, trans, rtol, maxit, S, st);
+        }
         CKL();
     }
 }
@@ -416,8 +573,7 @@ template <class T>
 int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st)
 {
-    Solver<T>& sv = solver<T>(ctx);
-    solver_alloc<T>(ctx, sv);
+    Solver<T>& sv = solver_reserve<T>(ctx, S);
     const elder_config& cf = ctx->cfg;
     const Grid& G = ctx->grids[0];
     const Phys ph = make_phys(cf, dt);
@@ -440,32 +596,42 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         ctx->h_ns[s] = z;
     }
     CK(cudaMemcpyAsync(ns, ctx->h_ns, sizeof(NScal) * S, cudaMemcpyHostToDevice, st));
+    int pi = prof_begin(ctx, st);
     launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, p, c, ctx->p_old, ctx->c_old, ctx->R,
-                    ctx->partial, nullptr, 0, S, st);
-    launch_norm_finalize(ctx->partial, nb, ns, 0, S, st);
+                    ctx->partial, ctx->partial2, nullptr, 0, S, st);
+    prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, S, st);
+    launch_norm_finalize(ctx->partial, ctx->partial2, nb, ns, 0, S, st);
     CKL();
 
     for (int it = 0; it < cf.newton_maxit; ++it) {
         CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        bool any = false;
-        for (int s = 0; s < S; ++s) any = any || ctx->h_ns[s].active;
-        if (!any) break;
-        assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, st);
+        prof_drain(ctx);
+        int na = 0;
+        for (int s = 0; s < S; ++s) na += ctx->h_ns[s].active ? 1 : 0;
+        if (na == 0) break;
+        ctx->n_active_newton = na;
+        ctx->n_active_ls = na;
+        assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, na, st);
         launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
         bicgstab<T>(ctx, sv, 0, cf.lin_rtol, cf.lin_maxit, ns, S, st);
         for (int ls = 0; ls <= cf.ls_max; ++ls) {
             launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
+            pi = prof_begin(ctx, st);
             launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
-                            ctx->c_old, ctx->Rt, ctx->partial, lsmask, NSTRIDE, S, st);
-            launch_norm_finalize(ctx->partial, nb, ns, 1, S, st);
+                            ctx->c_old, ctx->Rt, ctx->partial, ctx->partial3, lsmask, NSTRIDE,
+                            S, st);
+            prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, ctx->n_active_ls, st);
+            launch_norm_finalize(ctx->partial, ctx->partial3, nb, ns, 1, S, st);
             launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, cf.ls_max, S, st);
             CKL();
             CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            bool searching = false;
-            for (int s = 0; s < S; ++s) searching = searching || ctx->h_ns[s].ls_active;
-            if (!searching) break;
+            prof_drain(ctx);
+            int nls = 0;
+            for (int s = 0; s < S; ++s) nls += ctx->h_ns[s].ls_active ? 1 : 0;
+            ctx->n_active_ls = nls;
+            if (nls == 0) break;
         }
         launch_newton_accept(G, p, c, ctx->pt, ctx->ct, ctx->R, ctx->Rt, ns, S, st);
         launch_newton_check(ns, ctx->ks, cf.newton_tol_p, cf.newton_tol_c, cf.newton_maxit, S,
@@ -487,6 +653,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     launch_newton_restore_failed(G, p, c, ctx->p_old, ctx->c_old, ns, S, st);
     CKL();
     CK(cudaStreamSynchronize(st));
+    prof_drain(ctx);
     int rc = ELDER_OK;
     for (int s = 0; s < S; ++s) {
         const NScal& k = ctx->h_ns[s];
@@ -498,8 +665,70 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
             stats[s].ls_cuts = k.ls_cuts;
             stats[s].res0 = k.res0;
             stats[s].res = k.rn;
+            stats[s].fp64_retry = 0;
+            stats[s].pad = 0;
         }
         if (k.status != 0) rc = ELDER_ENOTCONV;
+    }
+    return rc;
+}
+
+// ELDER_MIXED: FP32 multigrid/Krylov first; samples whose Newton iteration
+// fails are packed into batches and solved again from u^n with the FP64
+// solver.
+int step_mixed(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
+               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st)
+{
+    std::vector<int32_t> st1(S);
+    std::vector<elder_stats> sts(S);
+    step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st);
+    std::vector<int> failed;
+    for (int s = 0; s < S; ++s)
+        if (st1[s] != 0) failed.push_back(s);
+    if (!failed.empty()) {
+        const Grid& G = ctx->grids[0];
+        const size_t N = G.N, C = G.C;
+        const int chunk = std::min(32, ctx->cfg.max_samples);
+        if (!ctx->pk) {
+            ctx->pk = dalloc<double>((size_t)chunk * (2 * N + 2 * C));
+            ctx->mem.add(ctx->pk);
+        }
+        double* pk_p = ctx->pk;
+        double* pk_c = pk_p + chunk * N;
+        double* pk_phi = pk_c + chunk * N;
+        double* pk_K = pk_phi + chunk * C;
+        for (size_t b0 = 0; b0 < failed.size(); b0 += chunk) {
+            const int F = (int)std::min<size_t>(chunk, failed.size() - b0);
+            for (int q = 0; q < F; ++q) {
+                const size_t s = failed[b0 + q];
+                CK(cudaMemcpyAsync(pk_p + q * N, p + s * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(pk_c + q * N, c + s * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(pk_phi + q * C, phi + s * C, 8 * C, cudaMemcpyDeviceToDevice,
+                                   st));
+                CK(cudaMemcpyAsync(pk_K + q * C, K + s * C, 8 * C, cudaMemcpyDeviceToDevice, st));
+            }
+            std::vector<int32_t> st2(F);
+            std::vector<elder_stats> s2(F);
+            step_impl<double>(ctx, F, pk_phi, pk_K, pk_p, pk_c, dt, st2.data(), s2.data(), st);
+            for (int q = 0; q < F; ++q) {
+                const size_t s = failed[b0 + q];
+                CK(cudaMemcpyAsync(p + s * N, pk_p + q * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(c + s * N, pk_c + q * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+                st1[s] = st2[q];
+                s2[q].newton_iters += sts[s].newton_iters;
+                s2[q].krylov_iters += sts[s].krylov_iters;
+                s2[q].ls_cuts += sts[s].ls_cuts;
+                s2[q].fp64_retry = 1;
+                sts[s] = s2[q];
+            }
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    int rc = ELDER_OK;
+    for (int s = 0; s < S; ++s) {
+        if (status) status[s] = st1[s];
+        if (stats) stats[s] = sts[s];
+        if (st1[s] != 0) rc = ELDER_ENOTCONV;
     }
     return rc;
 }
@@ -509,13 +738,12 @@ int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const 
                const double* c, double dt, int trans, const double* rhs, double* x,
                double rtol, int32_t* status, cudaStream_t st)
 {
-    Solver<T>& sv = solver<T>(ctx);
-    solver_alloc<T>(ctx, sv);
+    Solver<T>& sv = solver_reserve<T>(ctx, S);
     const Grid& G = ctx->grids[0];
     const Phys ph = make_phys(ctx->cfg, dt);
     const size_t nN = (size_t)S * G.N;
     average_coefficients(ctx, S, phi, K, st);
-    assemble<T>(ctx, sv, S, phi, K, p, c, ph, nullptr, 0, st);
+    assemble<T>(ctx, sv, S, phi, K, p, c, ph, nullptr, 0, S, st);
     const V2<double>* rhs2 = reinterpret_cast<const V2<double>*>(rhs);
     V2<double>* x2 = reinterpret_cast<V2<double>*>(x);
     // rhs in solver precision
@@ -604,11 +832,11 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->newton_tol_p = 1e-11 * 1000.0 * 9.81 * 150.0;
     cfg->ls_max = 6;
     cfg->lin_rtol = 1e-4;
-    cfg->lin_maxit = 200;
+    cfg->lin_maxit = 100;
     cfg->mg_levels = 0;
-    cfg->nu1 = 2;
-    cfg->nu2 = 2;
-    cfg->omega = 0.7;
+    cfg->nu1 = 1;
+    cfg->nu2 = 1;
+    cfg->omega = 0.5;
     cfg->coarse_K_harmonic = 0;
     cfg->use_graphs = 1;
     return ELDER_OK;
@@ -696,6 +924,8 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         }
         ctx->partial = dalloc<double>((size_t)S * 2 * ctx->nblk0);
         ctx->partial2 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
+        ctx->partial3 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
+        ctx->mem.add(ctx->partial3);
         ctx->ns = dalloc<NScal>(S);
         ctx->ks = dalloc<KScal>(S);
         for (void* q : {(void*)ctx->partial, (void*)ctx->partial2, (void*)ctx->ns,
@@ -710,9 +940,9 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         // that do not still serve the residual, Jacobian and moment calls)
         if (2 * ctx->grids.back().N <= MAX_COARSE_UNKNOWNS) {
             if (c.precision == ELDER_MIXED)
-                solver_alloc<float>(ctx.get(), solver<float>(ctx.get()));
+                solver_reserve<float>(ctx.get(), S);
             else
-                solver_alloc<double>(ctx.get(), solver<double>(ctx.get()));
+                solver_reserve<double>(ctx.get(), S);
         }
         CK(cudaDeviceSynchronize());
     } catch (const Fail& f) {
@@ -777,7 +1007,7 @@ int elder_residual(elder_ctx* ctx, int S, const double* phi, const double* K,
     try {
         launch_residual(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], ctx->cval, phi, K,
                         p, c, p_old, c_old, reinterpret_cast<V2<double>*>(R), nullptr, nullptr,
-                        0, S, (cudaStream_t)stream);
+                        nullptr, 0, S, (cudaStream_t)stream);
         CKL();
     } catch (const Fail& f) {
         return set_error(ctx, f);
@@ -816,8 +1046,7 @@ int elder_step(elder_ctx* ctx, int S, const double* phi, const double* K, double
     }
     try {
         if (ctx->cfg.precision == ELDER_MIXED)
-            return step_impl<float>(ctx, S, phi, K, p, c, dt, status, stats,
-                                    (cudaStream_t)stream);
+            return step_mixed(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream);
         return step_impl<double>(ctx, S, phi, K, p, c, dt, status, stats,
                                  (cudaStream_t)stream);
     } catch (const Fail& f) {
@@ -844,6 +1073,62 @@ int elder_solve(elder_ctx* ctx, int S, const double* phi, const double* K, const
     } catch (const Fail& f) {
         return set_error(ctx, f);
     }
+}
+
+int elder_initial_state(elder_ctx* ctx, int S, double* p, double* c, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (S < 1 || !p || !c) {
+        ctx->err = "elder_initial_state: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        launch_initial_state(ctx->grids[0], ctx->cfg.rho0 * ctx->cfg.g, ctx->bc[0], ctx->cval,
+                             p, c, S, (cudaStream_t)stream);
+        CKL();
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    return ELDER_OK;
+}
+
+int elder_profile(elder_ctx* ctx, int on)
+{
+    if (!ctx) return ELDER_EINVAL;
+    try {
+        CK(cudaDeviceSynchronize());
+        prof_drain(ctx);
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    Prof& P = ctx->prof;
+    if (on) {
+        for (int k = 0; k < ELDER_K_CLASSES; ++k) {
+            P.launches[k] = 0;
+            P.ms[k] = P.bytes[k] = P.flops[k] = 0.0;
+        }
+    }
+    P.on = on != 0;
+    return ELDER_OK;
+}
+
+int elder_profile_read(const elder_ctx* ctx, int kernel_class, int64_t* launches, double* ms,
+                       double* bytes, double* flops)
+{
+    if (!ctx || kernel_class < 0 || kernel_class >= ELDER_K_CLASSES) return ELDER_EINVAL;
+    const Prof& P = ctx->prof;
+    if (launches) *launches = P.launches[kernel_class];
+    if (ms) *ms = P.ms[kernel_class];
+    if (bytes) *bytes = P.bytes[kernel_class];
+    if (flops) *flops = P.flops[kernel_class];
+    return ELDER_OK;
+}
+
+int elder_launch_count(int64_t* launches)
+{
+    if (!launches) return ELDER_EINVAL;
+    *launches = g_launches.load();
+    return ELDER_OK;
 }
 
 int elder_moments(elder_ctx* ctx, int S, const double* c, const double* w, double threshold,
@@ -879,8 +1164,7 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
     const Phys ph = make_phys(ctx->cfg, dt);
     const size_t N = G.N;
     try {
-        Solver<double>& sv = solver<double>(ctx);
-        solver_alloc<double>(ctx, sv);
+        Solver<double>& sv = solver_reserve<double>(ctx, 1);
         DevFree local;
         const int nck = (n_steps + ckpt_every - 1) / ckpt_every + 1;
         double* ck = dalloc<double>(2 * N * nck);  // checkpoints (p, c) every k steps
@@ -897,8 +1181,7 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
         int32_t stat = 0;
         auto fwd_step = [&](double* pc) -> int {
             const int rc = (ctx->cfg.precision == ELDER_MIXED)
-                               ? step_impl<float>(ctx, 1, phi, K, pc, pc + N, dt, &stat,
-                                                  nullptr, st)
+                               ? step_mixed(ctx, 1, phi, K, pc, pc + N, dt, &stat, nullptr, st)
                                : step_impl<double>(ctx, 1, phi, K, pc, pc + N, dt, &stat,
                                                    nullptr, st);
             return rc;
@@ -941,7 +1224,7 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
                 // J_n^T lambda_n = rhs (interior part; the Dirichlet rows of R_n
                 // neither depend on theta nor on u_{n-1}, so lambda_D is not needed)
                 average_coefficients(ctx, 1, phi, K, st);
-                assemble<double>(ctx, sv, 1, phi, K, un, un + N, ph, nullptr, 0, st);
+                assemble<double>(ctx, sv, 1, phi, K, un, un + N, ph, nullptr, 0, 1, st);
                 CK(cudaMemcpyAsync(sv.b, rhs, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice,
                                    st));
                 bicgstab<double>(ctx, sv, 1, 1e-12, std::max(ctx->cfg.lin_maxit, 400), nullptr,

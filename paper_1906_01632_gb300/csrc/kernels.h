@@ -17,6 +17,7 @@ struct NScal {
     double rn, rt, lambda;       // ||R(u)||, ||R(u_trial)||, step length
     double res0;
     double dmax_p, dmax_c;       // max |lambda * delta| of the last step
+    double rfloor, rfloor_t;     // round-off level of ||R(u)||, ||R(u_trial)||
     int active;                  // still iterating
     int ls_active;               // line search still running
     int accepted;                // trial accepted in this Newton iteration
@@ -27,12 +28,15 @@ constexpr int kBS = 256;  // threads per block of the node kernels
 
 inline int nblocks(int n, int bs = kBS) { return (n + bs - 1) / bs; }
 
+// Process-wide count of kernel launches made by this library.
+void count_launch(int n);
+
 // ---- assembly.cu ---------------------------------------------------------
 void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* cval, const double* phi, const double* K,
                      const double* p, const double* c, const double* p_old,
                      const double* c_old, V2<double>* R, double* partial,
-                     const int* mask, int mask_stride, int S,
+                     double* act, const int* mask, int mask_stride, int S,
                      cudaStream_t st);
 template <class T>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
@@ -56,6 +60,9 @@ void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<T>* J,
 void launch_impose_dirichlet(const Grid& G, const uint8_t* bc,
                              const double* cval, double* p, double* c, int S,
                              cudaStream_t st);
+void launch_initial_state(const Grid& G, double rho0g, const uint8_t* bc,
+                          const double* cval, double* p, double* c, int S,
+                          cudaStream_t st);
 void launch_fields(const Grid& G, int kind, const double* params,
                    double K_mean, double* phi, double* K, int S,
                    cudaStream_t st);
@@ -116,8 +123,10 @@ void launch_bicg_finalize(int stage, const double* partial, int nblk,
                           cudaStream_t st);
 
 // Newton pieces
-void launch_norm_finalize(const double* partial, int nblk, NScal* ns,
-                          int which, int S, cudaStream_t st);
+// which = 0: ||R(u)|| (also res0 and, from act, the round-off floor),
+// which = 1: ||R(u_trial)||
+void launch_norm_finalize(const double* partial, const double* act, int nblk,
+                          NScal* ns, int which, int S, cudaStream_t st);
 template <class T>
 void launch_newton_rhs(const Grid& G, const V2<double>* R, V2<T>* b,
                        const NScal* ns, int S, cudaStream_t st);

@@ -21,8 +21,6 @@ __device__ __forceinline__ bool on(const int* mask, int stride, int s)
     return mask == nullptr || mask[(size_t)s * stride] != 0;
 }
 
-constexpr int KS_STRIDE = sizeof(KScal) / sizeof(int);
-constexpr int NS_STRIDE = sizeof(NScal) / sizeof(int);
 static_assert(sizeof(KScal) % sizeof(int) == 0, "KScal layout");
 static_assert(sizeof(NScal) % sizeof(int) == 0, "NScal layout");
 
@@ -116,6 +114,7 @@ void launch_spmv(const Grid& G, const B4<T>* J, const uint8_t* bc,
                  const V2<T>* a, double* partial, const int* mask,
                  int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
 #define ELDER_SPMV(TR, MO) \
     k_spmv<T, TR, MO><<<grid, kBS, 0, st>>>(G, J, bc, x, y, a, partial, mask, mstride)
@@ -178,6 +177,7 @@ void launch_smooth(const Grid& G, const B4<T>* J, const B4<T>* Dinv,
                    V2<T>* xo, double omega, int trans, const int* mask,
                    int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     const T w = T(omega);
     if (x == nullptr) {
@@ -217,6 +217,7 @@ void launch_mg_residual(const Grid& G, const B4<T>* J, const uint8_t* bc,
                         const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
                         const int* mask, int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     if (trans) k_mg_residual<T, true><<<grid, kBS, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
     else k_mg_residual<T, false><<<grid, kBS, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
@@ -263,6 +264,7 @@ void launch_restrict(const Grid& Gf, const Grid& Gc, const uint8_t* bcc,
                      const V2<T>* rf, V2<T>* bco, const int* mask, int mstride,
                      int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(Gc.N), S);
     k_restrict<T><<<grid, kBS, 0, st>>>(Gf, Gc, bcc, rf, bco, mask, mstride);
 }
@@ -305,6 +307,7 @@ void launch_prolong_add(const Grid& Gf, const Grid& Gc, const uint8_t* bcf,
                         const V2<T>* xc, V2<T>* xf, const int* mask,
                         int mstride, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(Gf.N), S);
     k_prolong_add<T><<<grid, kBS, 0, st>>>(Gf, Gc, bcf, xc, xf, mask, mstride);
 }
@@ -338,6 +341,7 @@ void launch_coarse_apply(const Grid& G, const double* Ainv, const V2<T>* b,
                          V2<T>* x, int trans, const int* mask, int mstride,
                          int S, cudaStream_t st)
 {
+    count_launch(1);
     const int n = 2 * G.N;
     k_coarse_apply<T><<<S, 128, sizeof(double) * n, st>>>(n, Ainv, b, x, trans, mask, mstride);
 }
@@ -380,6 +384,7 @@ void launch_bicg_init(const Grid& G, const uint8_t* bc, const V2<T>* b,
                       V2<T>* x, V2<T>* r, V2<T>* rh, V2<T>* p, V2<T>* v,
                       double* partial, KScal* ks, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_bicg_init<T><<<grid, kBS, 0, st>>>(G, bc, b, x, r, rh, p, v, partial, ks);
 }
@@ -408,6 +413,7 @@ template <class T>
 void launch_bicg_p(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* p,
                    const KScal* ks, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_bicg_p<T><<<grid, kBS, 0, st>>>(G.N, r, v, p, ks);
 }
@@ -432,6 +438,7 @@ template <class T>
 void launch_bicg_s(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* s,
                    double* partial, const KScal* ks, int S, cudaStream_t st)
 {
+    count_launch(1);
     (void)partial;
     dim3 grid(nblocks(G.N), S);
     k_bicg_s<T><<<grid, kBS, 0, st>>>(G.N, r, v, s, ks);
@@ -478,6 +485,7 @@ void launch_bicg_xr(const Grid& G, const V2<T>* ph, const V2<T>* sh,
                     V2<T>* r, double* partial, const KScal* ks, int S,
                     cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_bicg_xr<T><<<grid, kBS, 0, st>>>(G.N, ph, sh, s, t, rh, x, r, partial, ks);
 }
@@ -546,6 +554,7 @@ void launch_bicg_finalize(int stage, const double* partial, int nblk,
                           KScal* ks, double rtol, int maxit, int S,
                           cudaStream_t st)
 {
+    count_launch(1);
     k_bicg_finalize<<<S, 128, 0, st>>>(stage, partial, nblk, ks, rtol, maxit);
 }
 
@@ -553,35 +562,50 @@ void launch_bicg_finalize(int stage, const double* partial, int nblk,
 // Newton with line search
 // ---------------------------------------------------------------------------
 
-// which = 0: ||R(u)|| (also res0), which = 1: ||R(u_trial)||
-__global__ void k_norm_finalize(const double* __restrict__ partial, int nblk,
-                                NScal* ns, int which)
+// which = 0: ||R(u)||, res0 and the round-off floor of ||R|| (2 eps times the
+// norm of the per-row sums of the magnitudes of the summed terms);
+// which = 1: ||R(u_trial)|| and the floor at the trial state
+__global__ void k_norm_finalize(const double* __restrict__ partial,
+                                const double* __restrict__ act, int nblk, NScal* ns,
+                                int which)
 {
     __shared__ double red[32];
     const int s = blockIdx.x;
     if (which == 1 && !ns[s].ls_active) return;
-    double a = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += blockDim.x) a += partial[(size_t)s * nblk + q];
+    if (which == 0 && !ns[s].active) return;
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+        a += partial[(size_t)s * nblk + q];
+        if (act) b += act[(size_t)s * nblk + q];
+    }
     a = block_sum(a, red);
+    b = block_sum(b, red);
     if (threadIdx.x != 0) return;
     const double r = sqrt(a);
     if (which == 0) {
         ns[s].rn = r;
         ns[s].res0 = r;
+        ns[s].rfloor = 2.0 * 2.220446049250313e-16 * sqrt(b);
         if (!isfinite(r)) {
             ns[s].active = 0;
             ns[s].ls_active = 0;
             ns[s].status = ELDER_SAMPLE_NONFINITE_;
+        } else if (r <= ns[s].rfloor) {  // already a solution to round-off
+            ns[s].active = 0;
+            ns[s].ls_active = 0;
+            ns[s].status = 0;
         }
     } else {
         ns[s].rt = r;
+        ns[s].rfloor_t = 2.0 * 2.220446049250313e-16 * sqrt(b);
     }
 }
 
-void launch_norm_finalize(const double* partial, int nblk, NScal* ns,
+void launch_norm_finalize(const double* partial, const double* act, int nblk, NScal* ns,
                           int which, int S, cudaStream_t st)
 {
-    k_norm_finalize<<<S, 128, 0, st>>>(partial, nblk, ns, which);
+    count_launch(1);
+    k_norm_finalize<<<S, 128, 0, st>>>(partial, act, nblk, ns, which);
 }
 
 template <class T>
@@ -602,6 +626,7 @@ template <class T>
 void launch_newton_rhs(const Grid& G, const V2<double>* R, V2<T>* b,
                        const NScal* ns, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_newton_rhs<T><<<grid, kBS, 0, st>>>(G.N, R, b, ns);
 }
@@ -642,6 +667,7 @@ void launch_newton_trial(const Grid& G, const double* p, const double* c,
                          double* partial, const NScal* ns, int S,
                          cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_newton_trial<T><<<grid, kBS, 0, st>>>(G.N, p, c, dx, pt, ct, partial, ns);
 }
@@ -666,14 +692,15 @@ __global__ void k_newton_ls_finalize(const double* __restrict__ pmax, int nblk,
     k.dmax_p = a0;
     k.dmax_c = a1;
     const bool finite = isfinite(k.rt);
-    if ((finite && k.rt < (1.0 - 1e-4 * k.lambda) * k.rn) || k.ls_count >= ls_max) {
+    // a trial at the round-off floor of ||R|| is accepted as it is: below
+    // that level the decrease test compares rounding noise
+    if (finite && (k.rt < (1.0 - 1e-4 * k.lambda) * k.rn || k.rt <= k.rfloor_t)) {
         k.ls_active = 0;
-        if (finite) {
-            k.accepted = 1;
-        } else {
-            k.active = 0;
-            k.status = ELDER_SAMPLE_NONFINITE_;
-        }
+        k.accepted = 1;
+    } else if (k.ls_count >= ls_max) {  // no step length decreased ||R||
+        k.ls_active = 0;
+        k.active = 0;
+        k.status = ELDER_SAMPLE_LINESEARCH_;
     } else {
         k.lambda *= 0.5;
         k.ls_count += 1;
@@ -686,6 +713,7 @@ void launch_newton_ls_finalize(const double* partial_res,
                                const double* partial_max, int nblk,
                                NScal* ns, int ls_max, int S, cudaStream_t st)
 {
+    count_launch(1);
     (void)partial_res;
     k_newton_ls_finalize<<<S, 128, 0, st>>>(partial_max, nblk, ns, ls_max);
 }
@@ -711,6 +739,7 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
                           const V2<double>* Rt, const NScal* ns, int S,
                           cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_newton_accept<<<grid, kBS, 0, st>>>(G.N, p, c, pt, ct, R, Rt, ns);
 }
@@ -725,8 +754,9 @@ __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
     k.kiters += ks[s].iters;
     if (k.accepted) {
         k.rn = k.rt;
+        k.rfloor = k.rfloor_t;
         k.iters += 1;
-        if (k.lambda == 1.0 && k.dmax_c <= tol_c && k.dmax_p <= tol_p) {
+        if ((k.lambda == 1.0 && k.dmax_c <= tol_c && k.dmax_p <= tol_p) || k.rn <= k.rfloor) {
             k.active = 0;
             k.status = 0;
         } else if (k.iters >= maxit) {
@@ -744,6 +774,7 @@ __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
 void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
                          double tol_c, int maxit, int S, cudaStream_t st)
 {
+    count_launch(1);
     k_newton_check<<<nblocks(S, 128), 128, 0, st>>>(ns, ks, tol_p, tol_c, maxit, S);
 }
 
@@ -766,6 +797,7 @@ void launch_newton_restore_failed(const Grid& G, double* p, double* c,
                                   const double* p_old, const double* c_old,
                                   const NScal* ns, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_newton_restore_failed<<<grid, kBS, 0, st>>>(G.N, p, c, p_old, c_old, ns);
 }
@@ -809,6 +841,7 @@ void launch_moments(int N, int S, const double* c, const double* w,
                     double threshold, double* mean, double* var,
                     double* pexc, cudaStream_t st)
 {
+    count_launch(1);
     k_moments<<<nblocks(N), kBS, 0, st>>>(N, S, c, w, threshold, mean, var, pexc);
 }
 
@@ -829,6 +862,7 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nblk,
 void launch_sum_partials(const double* partial, int nblk, double* out, int S,
                          cudaStream_t st)
 {
+    count_launch(1);
     k_sum_partials<<<S, 128, 0, st>>>(partial, nblk, out);
 }
 
@@ -862,6 +896,7 @@ template <class T>
 void launch_axpy_mask(const Grid& G, const uint8_t* bc, const V2<T>* x,
                       V2<T>* y, double a, int which, int S, cudaStream_t st)
 {
+    count_launch(1);
     dim3 grid(nblocks(G.N), S);
     k_axpy_mask<T><<<grid, kBS, 0, st>>>(G, bc, x, y, a, which);
 }
@@ -879,6 +914,7 @@ __global__ void k_convert(const V2<Ts>* __restrict__ x, V2<Td>* __restrict__ y,
 template <class Ts, class Td>
 void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
 {
+    count_launch(1);
     k_convert<Ts, Td><<<(unsigned)((n + kBS - 1) / kBS), kBS, 0, st>>>(x, y, n);
 }
 

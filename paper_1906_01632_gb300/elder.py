@@ -25,7 +25,8 @@ SECONDS_PER_YEAR = 365.25 * 86400.0
 
 ELDER_OK, ELDER_EINVAL, ELDER_ENOMEM, ELDER_ECUDA, ELDER_ENOTCONV, ELDER_ETIMEOUT = range(6)
 ELDER_FP64, ELDER_MIXED = 0, 1
-SAMPLE_STATUS = {0: "ok", 1: "newton_maxit", 2: "krylov_maxit", 3: "breakdown", 4: "nonfinite"}
+SAMPLE_STATUS = {0: "ok", 1: "newton_maxit", 2: "krylov_maxit", 3: "breakdown", 4: "nonfinite",
+                 5: "linesearch"}
 
 
 class elder_config(ctypes.Structure):
@@ -45,12 +46,13 @@ class elder_config(ctypes.Structure):
 class elder_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("krylov_iters", ctypes.c_int32), ("ls_cuts", ctypes.c_int32),
-                ("res0", ctypes.c_double), ("res", ctypes.c_double)]
+                ("res0", ctypes.c_double), ("res", ctypes.c_double),
+                ("fp64_retry", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
-EXPORTS = ["elder_config_default", "elder_create", "elder_destroy", "elder_last_error",
-           "elder_sizes", "elder_fields", "elder_residual", "elder_jacobian", "elder_step",
-           "elder_solve", "elder_moments", "elder_grad"]
+K_SMOOTH, K_SPMV, K_MGRES, K_RESIDUAL, K_JACOBIAN, K_SMOOTH0 = range(6)
+KERNEL_CLASSES = {K_SMOOTH: "smooth", K_SPMV: "spmv", K_MGRES: "mg_residual",
+                  K_RESIDUAL: "residual", K_JACOBIAN: "jacobian", K_SMOOTH0: "smooth0"}
 
 
 def _load():
@@ -77,6 +79,10 @@ def _load():
                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int32), vp]
     lib.elder_moments.argtypes = [vp, ip, vp, vp, ctypes.c_double, vp, vp, vp, vp]
     lib.elder_grad.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, dp, vp, vp, vp]
+    lib.elder_initial_state.argtypes = [vp, ip, vp, vp, vp]
+    lib.elder_profile.argtypes = [vp, ip]
+    lib.elder_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
+    lib.elder_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     del dp
     return lib
 
@@ -159,6 +165,23 @@ class Elder:
             pass
 
     # --- entry points -----------------------------------------------------
+    def initial_state(self, S, p=None, c=None, device="cuda", stream=None):
+        p = p if p is not None else torch.empty(S * self.N, dtype=torch.float64, device=device)
+        c = c if c is not None else torch.empty(S * self.N, dtype=torch.float64, device=device)
+        self._check(_lib.elder_initial_state(self._h, S, _ptr(p, "p"), _ptr(c, "c"),
+                                             _stream(stream)))
+        return p, c
+
+    def profile(self, on: bool):
+        self._check(_lib.elder_profile(self._h, 1 if on else 0))
+
+    def profile_read(self, kernel_class: int):
+        n = ctypes.c_int64()
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(_lib.elder_profile_read(self._h, kernel_class, ctypes.byref(n),
+                                            ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
+
     def fields(self, S, kind, params, K_mean=4.845e-13, phi=None, K=None, stream=None):
         dev = params.device
         phi = phi if phi is not None else torch.empty(S * self.C, dtype=torch.float64, device=dev)
@@ -190,7 +213,7 @@ class Elder:
         st = np.frombuffer(status, dtype=np.int32).copy()
         info = [{"status": s.status, "newton_iters": s.newton_iters,
                  "krylov_iters": s.krylov_iters, "ls_cuts": s.ls_cuts, "res0": s.res0,
-                 "res": s.res} for s in stats]
+                 "res": s.res, "fp64_retry": s.fp64_retry} for s in stats]
         return st, info
 
     def solve(self, S, phi, K, p, c, dt, rhs, transpose=False, rtol=1e-10, x=None, stream=None):
@@ -225,6 +248,24 @@ class Elder:
 
 
 # module-level names of the C ABI
+def elder_launch_count() -> int:
+    n = ctypes.c_int64()
+    _lib.elder_launch_count(ctypes.byref(n))
+    return n.value
+
+
+def elder_initial_state(ctx: Elder, *a, **k):
+    return ctx.initial_state(*a, **k)
+
+
+def elder_profile(ctx: Elder, on: bool):
+    return ctx.profile(on)
+
+
+def elder_profile_read(ctx: Elder, kernel_class: int):
+    return ctx.profile_read(kernel_class)
+
+
 def elder_create(cfg: elder_config) -> Elder:
     return Elder(cfg)
 
