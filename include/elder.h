@@ -122,8 +122,8 @@ int elder_create(const elder_config* cfg, elder_ctx** out);
 /* Frees the context and its device workspace (NULL is accepted). */
 int elder_destroy(elder_ctx* ctx);
 
-/* Message of the last failure on ctx (or of the last failed elder_create
- * when ctx is NULL); never NULL. */
+/* Message of the last failure on ctx (or, when ctx is NULL, of the last
+ * failed elder_create or context-free call of this thread); never NULL. */
 const char* elder_last_error(const elder_ctx* ctx);
 
 /* Number of nodes N and cells C of the context's grid (host outputs). */
@@ -238,6 +238,35 @@ int elder_profile_read(const elder_ctx* ctx, int kernel_class,
 /* Number of kernels this library has launched in the process (graph
  * replays count every kernel node).  Host output. */
 int elder_launch_count(int64_t* launches);
+
+/* ---- allocation-free entry point (no counterpart in the paper) -------- */
+
+/* The residual of elder_residual plus its per-sample 2-norm, for callers
+ * that may not allocate device memory at all: it needs no context (which
+ * would allocate the solver workspace) and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Typical callers: code running after another
+ * runtime has taken over the device's memory pool, or a thread that may only
+ * enqueue work.
+ *  cfg: host pointer; its grid, physics constants and bc_mode are used
+ *  (the Dirichlet sets are evaluated from the node indices).
+ *  phi, K: [S][C]; p, c, p_old, c_old: [S][N] device inputs.
+ *  R: [S][N][2] device output, the same values as elder_residual's.
+ *  norms: [S] device output, ||R_s||_2.
+ * Scratch: the per-block partial sums live in a file-scope device array of
+ * 262144 doubles (2 MiB), which every GPU that loads the library holds until
+ * the process exits.  S * ceil(N/256) must not exceed 262144, otherwise
+ * ELDER_EINVAL is returned before anything is launched.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the array and overwrites the entries it uses (nothing
+ * in it has to start at zero); calls that overlap on the GPU race on it.
+ * Errors: elder_last_error(NULL). */
+int elder_residual_norms_static(const elder_config* cfg, int S,
+                                const double* phi, const double* K,
+                                const double* p, const double* c,
+                                const double* p_old, const double* c_old,
+                                double dt, double* R, double* norms,
+                                void* stream);
 
 #ifdef __cplusplus
 }

@@ -897,4 +897,177 @@ void launch_adjoint_prev_rhs(const Grid& G, const Phys& ph, const uint8_t* bc,
     k_adjoint_prev_rhs<<<nblocks(G.N), kBS, 0, st>>>(G, ph, bc, phi, c_old, lam, rhs);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free residual with per-sample norms.
+//
+// For callers that may not allocate device memory at all (not even through a
+// context: elder_create allocates the multigrid workspace), e.g. code that
+// runs after another runtime has taken over the device's memory pool, or a
+// host thread that is only allowed to enqueue work.  The only scratch this
+// needs, the per-block partial sums of ||R||^2, lives in the file-scope
+// array below; the Dirichlet sets are evaluated from the grid indices
+// instead of being read from a context.
+// ---------------------------------------------------------------------------
+
+// Scratch capacity in doubles: 2 MiB on every device that loads the library,
+// held until the process exits.  A call needs S * ceil(N / 256) entries.
+constexpr size_t kStaticScratchDoubles = size_t(1) << 18;
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+// Dirichlet bits and c value of node (i,j,k) (the sets listed in elder.h).
+__device__ __forceinline__ uint8_t dirichlet_inline(int mode, const Grid& G, int i, int j,
+                                                    int k, double& cv)
+{
+    const bool top = (k == G.nz), bottom = (k == 0);
+    const bool xe = (i == 0 || i == G.nx), ye = (j == 0 || j == G.ny);
+    const bool sq = (4 * i >= G.nx && 4 * i <= 3 * G.nx && 4 * j >= G.ny && 4 * j <= 3 * G.ny);
+    uint8_t b = 0;
+    cv = 0.0;
+    if (mode == 1) {
+        if (top && (xe || ye)) b |= BC_P;
+        if (top) { b |= BC_C; cv = sq ? 1.0 : 0.0; }
+        else if (bottom) b |= BC_C;
+    } else {
+        if (top && xe && ye) b |= BC_P;
+        if (mode == 0) {
+            if (top && sq) { b |= BC_C; cv = 1.0; }
+            else if (bottom) b |= BC_C;
+        } else if (mode == 2) {
+            if (top) { b |= BC_C; cv = 1.0; }
+            else if (bottom) b |= BC_C;
+        }
+    }
+    return b;
+}
+
+__global__ void __launch_bounds__(kBS)
+    k_residual_static(Grid G, Phys ph, CellGeom cg, int bc_mode,
+                      const double* __restrict__ phi, const double* __restrict__ K,
+                      const double* __restrict__ p, const double* __restrict__ c,
+                      const double* __restrict__ p_old, const double* __restrict__ c_old,
+                      V2<double>* __restrict__ R, double* __restrict__ scratch)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
+    phi += oc; K += oc; p += on; c += on; p_old += on; c_old += on; R += on;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (n < G.N) {
+        int i, j, k;
+        node_ijk(G, n, i, j, k);
+        double Rp = 0.0, Rc = 0.0, phis = 0.0, Ap = 0.0, Ac = 0.0;
+        residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
+        const double vscv = 0.125 * G.hx * G.hy * G.hz;
+        const double cn = c[n], co = c_old[n];
+        const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
+        Rp += phis * vscv * (rn - ro) / ph.dt;
+        Rc += phis * vscv * (rn * cn - ro * co) / ph.dt;
+        double cv;
+        const uint8_t b = dirichlet_inline(bc_mode, G, i, j, k, cv);
+        if (b & BC_P) Rp = p[n];
+        if (b & BC_C) Rc = cn - cv;
+        R[n] = V2<double>{Rp, Rc};
+        sq = Rp * Rp + Rc * Rc;
+    }
+    const double t = block_sum(sq, red);
+    if (threadIdx.x == 0) scratch[(size_t)s * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_norms_static(int nblk, const double* __restrict__ scratch,
+                               double* __restrict__ norms)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    double a = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) a += scratch[(size_t)s * nblk + q];
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) norms[s] = sqrt(a);
+}
+
 }  // namespace elder
+
+#include <mutex>
+
+#include "../../include/elder.h"
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
+std::mutex g_scratch_mutex;
+}  // namespace
+
+extern "C" int elder_residual_norms_static(const elder_config* cfg, int S, const double* phi,
+                                           const double* K, const double* p, const double* c,
+                                           const double* p_old, const double* c_old,
+                                           double dt, double* R, double* norms, void* stream)
+{
+    using namespace elder;
+    if (!cfg || S < 1 || !phi || !K || !p || !c || !p_old || !c_old || !R || !norms ||
+        !(dt > 0)) {
+        set_static_error("elder_residual_norms_static: bad argument");
+        return ELDER_EINVAL;
+    }
+    const elder_config& f = *cfg;
+    if (f.nx < 1 || f.ny < 1 || f.nz < 1 || f.bc_mode < 0 || f.bc_mode > 3 ||
+        ((f.bc_mode == 0 || f.bc_mode == 1) && (f.nx % 4 || f.ny % 4)) || !(f.mu > 0)) {
+        set_static_error("elder_residual_norms_static: invalid elder_config");
+        return ELDER_EINVAL;
+    }
+    Grid G;
+    G.nx = f.nx;
+    G.ny = f.ny;
+    G.nz = f.nz;
+    G.N = (f.nx + 1) * (f.ny + 1) * (f.nz + 1);
+    G.C = f.nx * f.ny * f.nz;
+    G.hx = f.Lx / f.nx;
+    G.hy = f.Ly / f.ny;
+    G.hz = f.Lz / f.nz;
+    G.Lz = f.Lz;
+    const int nblk = nblocks(G.N);
+    if ((size_t)S * (size_t)nblk > kStaticScratchDoubles) {
+        set_static_error("elder_residual_norms_static: S * ceil(N/256) exceeds the static "
+                         "scratch capacity (262144 partial sums)");
+        return ELDER_EINVAL;
+    }
+    // once per device, with that device current: the device address of the
+    // file-scope array (its host-side name is only a stand-in)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_static_error("elder_residual_norms_static: no usable current device");
+        return ELDER_ECUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* ptr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess || !ptr) {
+                set_static_error(cudaGetErrorString(e));
+                return ELDER_ECUDA;
+            }
+            g_scratch_addr[dev] = static_cast<double*>(ptr);
+        }
+    }
+    const Phys ph{f.rho0, f.rho1 - f.rho0, f.mu, f.g, f.Dm, dt};
+    cudaStream_t st = (cudaStream_t)stream;
+    count_launch(2);
+    k_residual_static<<<dim3(nblk, S), kBS, 0, st>>>(G, ph, make_geom(G), f.bc_mode, phi, K, p,
+                                                     c, p_old, c_old,
+                                                     reinterpret_cast<V2<double>*>(R),
+                                                     g_scratch_addr[dev]);
+    k_norms_static<<<S, 128, 0, st>>>(nblk, g_scratch_addr[dev], norms);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_static_error(cudaGetErrorString(e));
+        return ELDER_ECUDA;
+    }
+    return ELDER_OK;
+}

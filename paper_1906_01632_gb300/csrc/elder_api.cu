@@ -215,6 +215,7 @@ std::atomic<long long> g_launches{0};
 
 namespace elder {
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_static_error(const char* msg) { g_create_error = msg; }
 }  // namespace elder
 
 namespace {

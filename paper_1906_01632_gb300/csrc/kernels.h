@@ -30,6 +30,8 @@ inline int nblocks(int n, int bs = kBS) { return (n + bs - 1) / bs; }
 
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n);
+// Message returned by elder_last_error(NULL) after a failed context-free call.
+void set_static_error(const char* msg);
 
 // ---- assembly.cu ---------------------------------------------------------
 void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,

@@ -83,6 +83,8 @@ def _load():
     lib.elder_profile.argtypes = [vp, ip]
     lib.elder_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
     lib.elder_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    lib.elder_residual_norms_static.argtypes = [ctypes.POINTER(elder_config), ip, vp, vp, vp, vp,
+                                                vp, vp, ctypes.c_double, vp, vp, vp]
     del dp
     return lib
 
@@ -252,6 +254,23 @@ def elder_launch_count() -> int:
     n = ctypes.c_int64()
     _lib.elder_launch_count(ctypes.byref(n))
     return n.value
+
+
+def elder_residual_norms_static(cfg: elder_config, S, phi, K, p, c, p_old, c_old, dt,
+                                R=None, norms=None, stream=None):
+    """Residual and per-sample ||R|| without a context and without any device
+    allocation inside the library (its scratch is a fixed 2 MiB device
+    array).  R and norms are allocated here by torch unless passed in."""
+    N = (cfg.nx + 1) * (cfg.ny + 1) * (cfg.nz + 1)
+    R = R if R is not None else torch.empty(S * N * 2, dtype=torch.float64, device=p.device)
+    norms = norms if norms is not None else torch.empty(S, dtype=torch.float64, device=p.device)
+    rc = _lib.elder_residual_norms_static(ctypes.byref(cfg), S, _ptr(phi, "phi"), _ptr(K, "K"),
+                                          _ptr(p, "p"), _ptr(c, "c"), _ptr(p_old, "p_old"),
+                                          _ptr(c_old, "c_old"), dt, _ptr(R, "R"),
+                                          _ptr(norms, "norms"), _stream(stream))
+    if rc != ELDER_OK:
+        raise ElderError(rc, _lib.elder_last_error(None).decode())
+    return R, norms
 
 
 def elder_initial_state(ctx: Elder, *a, **k):
