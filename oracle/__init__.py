@@ -109,7 +109,7 @@ class NewtonOpts:
     tol_c: float = 1e-12
     tol_p: float = 1e-12 * 1000.0 * 9.81 * 150.0
     lin_rtol: float = 1e-12
-    lin_maxit: int = 20000
+    lin_maxit: int = 2000
     ls_max: int = 6
     dense_max: int = 1200
 
@@ -168,6 +168,15 @@ def residual(P: Problem, phi, K, p, c, p_old, c_old, dt, apply_dirichlet=True):
                        _dp(p_old), _dp(c_old), ctypes.c_double(dt),
                        ctypes.c_int(1 if apply_dirichlet else 0), _dp(Rp), _dp(Rc))
     return Rp, Rc
+
+
+def residual_magnitude(P: Problem, phi, K, p, c, c_old, dt) -> float:
+    """2-norm of the per-row sums of the magnitudes of the residual's terms
+    (its round-off scale); Newton treats ||R|| <= 2 eps times this as solved."""
+    lib().orc_residual_magnitude.restype = ctypes.c_double
+    return float(lib().orc_residual_magnitude(ctypes.byref(P._c()), _dp(_f64(phi)), _dp(_f64(K)),
+                                              _dp(_f64(p)), _dp(_f64(c)), _dp(_f64(c_old)),
+                                              ctypes.c_double(dt)))
 
 
 def jacobian_csr(P: Problem, phi, K, p, c, dt):
