@@ -92,6 +92,11 @@ typedef struct {
     double omega;             /* damping of the block-Jacobi smoother       */
     int coarse_K_harmonic;    /* 0 arithmetic, 1 harmonic mean of K         */
     int use_graphs;           /* capture the Krylov iteration in CUDA graphs*/
+    int autotune;             /* time threads-per-block candidates of the
+                                 stencil kernels on the first step          */
+    int newton_estimate;      /* also accept when the linear-convergence
+                                 error estimate theta/(1-theta)|d| is within
+                                 the Newton tolerances                      */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */
@@ -105,6 +110,12 @@ typedef struct {
     int32_t fp64_retry;       /* 1: ELDER_MIXED failed and the step was
                                  solved again with the FP64 solver          */
     int32_t pad;
+    /* FP64 salt-mass balance of the step: M = sum_e sum_corners phi_e
+     * |scv| rho(c) c at u^n and at the returned state, and the salt that
+     * entered through the c-Dirichlet nodes (dt times their net face
+     * inflow); at convergence salt_mass - salt_mass0 = salt_inflow up to
+     * the Newton tolerance. */
+    double salt_mass0, salt_mass, salt_inflow;
 } elder_stats;
 
 typedef struct elder_ctx elder_ctx;
@@ -238,6 +249,14 @@ int elder_profile_read(const elder_ctx* ctx, int kernel_class,
 /* Number of kernels this library has launched in the process (graph
  * replays count every kernel node).  Host output. */
 int elder_launch_count(int64_t* launches);
+
+/* Threads per block chosen by the autotuner for the smoother, the Krylov
+ * stencil product and the multigrid residual (256 until the first step has
+ * run), and the measured milliseconds per launch of every candidate
+ * (ms[3][3]: class x {128, 256, 512}, 0 when not tuned).  Host outputs; any
+ * may be NULL. */
+int elder_autotune_result(const elder_ctx* ctx, int* bs_smooth, int* bs_spmv,
+                          int* bs_mgres, float* ms);
 
 /* ---- allocation-free entry point (no counterpart in the paper) -------- */
 

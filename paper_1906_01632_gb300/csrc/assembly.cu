@@ -126,43 +126,138 @@ __host__ __device__ inline CellGeom make_geom(const Grid& G)
     return cg;
 }
 
+// ---------------------------------------------------------------------------
+// Edge-based residual: each face flux computed once.
+//
+// k_edge_flux: node n owns the edges to (i+1,j,k), (i,j+1,k), (i,j,k+1); the
+// dual face of an edge consists of the quarter faces of the up to 4 cells
+// around it.  The node writes, per direction, the summed mass and salt flux
+// out of n through that face and the magnitudes of their terms (the
+// round-off scale).  k_edge_residual forms R_n = storage + sum_d (flux_d(n) -
+// flux_d(n - e_d)): the same value is added at one end of an edge and
+// subtracted at the other, so the balance telescopes exactly.
+// ---------------------------------------------------------------------------
+
+// One cell of the edge gather: cell (i+OX, j+OY, k+OZ); this node is its
+// corner (-OX,-OY,-OZ); FX/FY/FZ select the faces of this node's forward
+// x/y/z edges that lie in this cell.
+template <int OX, int OY, int OZ, bool FX, bool FY, bool FZ>
+__device__ __forceinline__ void edge_cell(const Grid& G, const Phys& ph, const CellGeom& cg,
+                                          int i, int j, int k,
+                                          const double* __restrict__ phi,
+                                          const double* __restrict__ K,
+                                          const double* __restrict__ p,
+                                          const double* __restrict__ c, E4 (&acc)[3])
+{
+    const int ci = i + OX, cj = j + OY, ck = k + OZ;
+    if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) return;
+    const int e = ci + G.nx * (cj + G.ny * ck);
+    const double phi_e = __ldg(phi + e);
+    const double kmu = __ldg(K + e) / ph.mu;
+    const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
+    const int base = ci + sy * cj + sz * ck;
+    double p8[8], c8[8];
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
+        p8[L] = __ldg(p + base + off);
+        c8[L] = __ldg(c + base + off);
+    }
+    double m, F, mm, Fm;
+    if (FX) {
+        flux_face<0, -OY, -OZ>(p8, c8, phi_e, kmu, ph, cg.ih[0], cg.area[0], m, F, mm, Fm);
+        acc[0].m += m; acc[0].F += F; acc[0].mm += mm; acc[0].Fm += Fm;
+    }
+    if (FY) {
+        flux_face<1, -OX, -OZ>(p8, c8, phi_e, kmu, ph, cg.ih[1], cg.area[1], m, F, mm, Fm);
+        acc[1].m += m; acc[1].F += F; acc[1].mm += mm; acc[1].Fm += Fm;
+    }
+    if (FZ) {
+        flux_face<2, -OX, -OY>(p8, c8, phi_e, kmu, ph, cg.ih[2], cg.area[2], m, F, mm, Fm);
+        acc[2].m += m; acc[2].F += F; acc[2].mm += mm; acc[2].Fm += Fm;
+    }
+}
+
 __global__ void __launch_bounds__(kBS)
-    k_residual(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
-               const double* __restrict__ cval, const double* __restrict__ phi,
-               const double* __restrict__ K, const double* __restrict__ p,
-               const double* __restrict__ c, const double* __restrict__ p_old,
-               const double* __restrict__ c_old, V2<double>* __restrict__ R,
-               double* __restrict__ partial, double* __restrict__ act, const int* mask,
-               int mstride)
+    k_edge_flux(Grid G, Phys ph, CellGeom cg, const double* __restrict__ phi,
+                const double* __restrict__ K, const double* __restrict__ p,
+                const double* __restrict__ c, E4* __restrict__ edge, const int* mask,
+                int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.N) return;
+    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
+    phi += oc; K += oc; p += on; c += on;
+    int i, j, k;
+    node_ijk(G, n, i, j, k);
+    E4 acc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) acc[d] = E4{0.0, 0.0, 0.0, 0.0};
+    edge_cell<0, 0, 0, true, true, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    edge_cell<0, -1, 0, true, false, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    edge_cell<0, 0, -1, true, true, false>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    edge_cell<-1, 0, 0, false, true, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    edge_cell<0, -1, -1, true, false, false>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    edge_cell<-1, 0, -1, false, true, false>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    edge_cell<-1, -1, 0, false, false, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
+    E4* out = edge + (size_t)s * 3 * G.N;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[(size_t)d * G.N + n] = acc[d];
+}
+
+__global__ void __launch_bounds__(kBS)
+    k_edge_residual(Grid G, Phys ph, const uint8_t* __restrict__ bc,
+                    const double* __restrict__ cval, const double* __restrict__ phi,
+                    const double* __restrict__ p, const double* __restrict__ c,
+                    const double* __restrict__ c_old, const E4* __restrict__ edge,
+                    V2<double>* __restrict__ R, double* __restrict__ partial,
+                    double* __restrict__ act, const int* mask, int mstride)
 {
     __shared__ double red[32];
     const int s = blockIdx.y;
     if (!sample_on(mask, mstride, s)) return;
     const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
-    phi += oc; K += oc; p += on; c += on; p_old += on; c_old += on; R += on;
+    phi += oc; p += on; c += on; c_old += on; R += on;
+    edge += (size_t)s * 3 * G.N;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0, aq = 0.0;
     if (n < G.N) {
         int i, j, k;
         node_ijk(G, n, i, j, k);
-        double Rp = 0.0, Rc = 0.0, phis = 0.0, Ap = 0.0, Ac = 0.0;
-        residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, phis, Ap, Ac);
-        const double vscv = 0.125 * G.hx * G.hy * G.hz;
+        const int st[3] = {1, G.nx + 1, (G.nx + 1) * (G.ny + 1)};
+        const bool back[3] = {i > 0, j > 0, k > 0};
+        double Rp = 0.0, Rc = 0.0, Ap = 0.0, Ac = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const E4 f = edge[(size_t)d * G.N + n];
+            Rp += f.m;
+            Rc += f.F;
+            Ap += f.mm;
+            Ac += f.Fm;
+            if (back[d]) {
+                const E4 b = edge[(size_t)d * G.N + n - st[d]];
+                Rp -= b.m;
+                Rc -= b.F;
+                Ap += b.mm;
+                Ac += b.Fm;
+            }
+        }
+        double phis = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ci = i - (q & 1), cj = j - ((q >> 1) & 1), ck = k - (q >> 2);
+            if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
+            phis += __ldg(phi + ci + G.nx * (cj + G.ny * ck));
+        }
+        const double vdt = phis * 0.125 * G.hx * G.hy * G.hz / ph.dt;
         const double cn = c[n], co = c_old[n];
         const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
-        const double sp = phis * vscv * (rn - ro) / ph.dt;
-        const double sc = phis * vscv * (rn * cn - ro * co) / ph.dt;
-        Rp += sp;
-        Rc += sc;
-        Ap += fabs(phis * vscv * rn / ph.dt) + fabs(phis * vscv * ro / ph.dt);
-        Ac += fabs(phis * vscv * rn * cn / ph.dt) + fabs(phis * vscv * ro * co / ph.dt);
+        Rp += vdt * (rn - ro);
+        Rc += vdt * (rn * cn - ro * co);
+        Ap += vdt * (fabs(rn) + fabs(ro));
+        Ac += vdt * (fabs(rn * cn) + fabs(ro * co));
         const uint8_t b = bc[n];
         if (b & BC_P) { Rp = p[n]; Ap = 0.0; }
         if (b & BC_C) { Rc = cn - cval[n]; Ac = 0.0; }
@@ -174,7 +269,7 @@ __global__ void __launch_bounds__(kBS)
         const double t = block_sum(sq, red);
         if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = t;
     }
-    if (act) {  // magnitude of the summed terms: the round-off scale of R
+    if (act) {
         const double t = block_sum(aq, red);
         if (threadIdx.x == 0) act[(size_t)s * gridDim.x + blockIdx.x] = t;
     }
@@ -185,12 +280,14 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* p, const double* c, const double* p_old,
                      const double* c_old, V2<double>* R, double* partial,
                      double* act, const int* mask, int mstride, int S,
-                     cudaStream_t st)
+                     cudaStream_t st, E4* edge)
 {
-    count_launch(1);
+    (void)p_old;  // p has no time derivative
+    count_launch(2);
     dim3 grid(nblocks(G.N), S);
-    k_residual<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), bc, cval, phi, K, p,
-                                     c, p_old, c_old, R, partial, act, mask, mstride);
+    k_edge_flux<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), phi, K, p, c, edge, mask, mstride);
+    k_edge_residual<<<grid, kBS, 0, st>>>(G, ph, bc, cval, phi, p, c, c_old, edge, R, partial,
+                                          act, mask, mstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -306,12 +403,17 @@ __device__ __forceinline__ void jac_cell(const Grid& G, const Phys& ph,
     jac_face<T, 2, lx, ly, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[2]), T(cg.area[2]), acc);
 }
 
-template <class T>
+// Writes the row blocks as T (JT, the Krylov operator) and/or as the
+// multigrid storage type M (JM), and the inverse of the interior diagonal
+// block (Dinv, Dirichlet rows and columns replaced by the identity); any of
+// the three outputs may be null.
+template <class T, class M>
 __global__ void __launch_bounds__(128)
     k_jacobian(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
                const double* __restrict__ phi, const double* __restrict__ K,
                const double* __restrict__ p, const double* __restrict__ c,
-               B4<T>* __restrict__ J, const int* mask, int mstride)
+               B4<T>* __restrict__ JT, B4<M>* __restrict__ JM, B4<T>* __restrict__ Dinv,
+               const int* mask, int mstride)
 {
     const int s = blockIdx.y;
     if (!sample_on(mask, mstride, s)) return;
@@ -319,7 +421,6 @@ __global__ void __launch_bounds__(128)
     if (n >= G.N) return;
     const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
     phi += oc; K += oc; p += on; c += on;
-    J += (size_t)s * 27 * G.N;
     PhysT<T> pt{T(ph.rho0), T(ph.drho), T(ph.g), T(ph.Dm)};
     int i, j, k;
     node_ijk(G, n, i, j, k);
@@ -353,31 +454,49 @@ __global__ void __launch_bounds__(128)
         for (int q = 0; q < 27; ++q) { acc[q][2] = T(0); acc[q][3] = T(0); }
         acc[13][3] = T(1);
     }
+    if (JT) {
+        JT += (size_t)s * 27 * G.N;
 #pragma unroll
-    for (int q = 0; q < 27; ++q)
-        J[(size_t)q * G.N + n] = B4<T>{acc[q][0], acc[q][1], acc[q][2], acc[q][3]};
+        for (int q = 0; q < 27; ++q)
+            JT[(size_t)q * G.N + n] = B4<T>{acc[q][0], acc[q][1], acc[q][2], acc[q][3]};
+    }
+    if (JM) {
+        JM += (size_t)s * 27 * G.N;
+#pragma unroll
+        for (int q = 0; q < 27; ++q)
+            JM[(size_t)q * G.N + n] =
+                B4<M>{mg_store<M>(acc[q][0]), mg_store<M>(acc[q][1]), mg_store<M>(acc[q][2]),
+                      mg_store<M>(acc[q][3])};
+    }
+    if (Dinv) {
+        double a = acc[13][0], bb = acc[13][1], cc = acc[13][2], e = acc[13][3];
+        if (b & BC_P) { a = 1.0; bb = 0.0; cc = 0.0; }
+        if (b & BC_C) { e = 1.0; bb = 0.0; cc = 0.0; }
+        const double id = 1.0 / (a * e - bb * cc);
+        Dinv[(size_t)s * G.N + n] = B4<T>{T(e * id), T(-bb * id), T(-cc * id), T(a * id)};
+    }
 }
 
-template <class T>
+template <class T, class M>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* phi, const double* K, const double* p,
-                     const double* c, B4<T>* J, const int* mask, int mstride,
-                     int S, cudaStream_t st)
+                     const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv, const int* mask,
+                     int mstride, int S, cudaStream_t st)
 {
     count_launch(1);
     dim3 grid(nblocks(G.N, 128), S);
-    k_jacobian<T><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c,
-                                         J, mask, mstride);
+    k_jacobian<T, M><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c, JT, JM,
+                                            Dinv, mask, mstride);
 }
-template void launch_jacobian<double>(const Grid&, const Phys&, const uint8_t*,
-                                      const double*, const double*,
-                                      const double*, const double*,
-                                      B4<double>*, const int*, int, int,
-                                      cudaStream_t);
-template void launch_jacobian<float>(const Grid&, const Phys&, const uint8_t*,
-                                     const double*, const double*,
-                                     const double*, const double*, B4<float>*,
-                                     const int*, int, int, cudaStream_t);
+template void launch_jacobian<double, double>(const Grid&, const Phys&, const uint8_t*,
+                                              const double*, const double*, const double*,
+                                              const double*, B4<double>*, B4<double>*,
+                                              B4<double>*, const int*, int, int, cudaStream_t);
+template void launch_jacobian<float, __nv_bfloat16>(const Grid&, const Phys&, const uint8_t*,
+                                                    const double*, const double*,
+                                                    const double*, const double*, B4<float>*,
+                                                    B4<__nv_bfloat16>*, B4<float>*,
+                                                    const int*, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // hierarchy: state injection, cell averaging, block-diagonal inverse
@@ -437,54 +556,14 @@ void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
     k_average_cells<<<grid, kBS, 0, st>>>(Gf, Gc, phif, Kf, phic, Kc, harmonic);
 }
 
-// Inverse of the 2x2 diagonal block of the interior operator: rows and
-// columns of Dirichlet components are replaced by the identity.
-template <class T>
-__global__ void k_block_diag_inverse(Grid G, const uint8_t* __restrict__ bc,
-                                     const B4<T>* __restrict__ J,
-                                     B4<T>* __restrict__ Dinv, const int* mask,
-                                     int mstride)
-{
-    const int s = blockIdx.y;
-    if (!sample_on(mask, mstride, s)) return;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= G.N) return;
-    const B4<T> d = J[((size_t)s * 27 + 13) * G.N + n];
-    double a = d.pp, b = d.pc, c = d.cp, e = d.cc;
-    const uint8_t m = bc[n];
-    if (m & BC_P) { a = 1.0; b = 0.0; c = 0.0; }
-    if (m & BC_C) { e = 1.0; b = 0.0; c = 0.0; }
-    const double det = a * e - b * c;
-    const double id = 1.0 / det;
-    Dinv[(size_t)s * G.N + n] = B4<T>{T(e * id), T(-b * id), T(-c * id), T(a * id)};
-}
-
-template <class T>
-void launch_block_diag_inverse(const Grid& G, const uint8_t* bc,
-                               const B4<T>* J, B4<T>* Dinv, const int* mask,
-                               int mstride, int S, cudaStream_t st)
-{
-    count_launch(1);
-    dim3 grid(nblocks(G.N), S);
-    k_block_diag_inverse<T><<<grid, kBS, 0, st>>>(G, bc, J, Dinv, mask, mstride);
-}
-template void launch_block_diag_inverse<double>(const Grid&, const uint8_t*,
-                                                const B4<double>*, B4<double>*,
-                                                const int*, int, int,
-                                                cudaStream_t);
-template void launch_block_diag_inverse<float>(const Grid&, const uint8_t*,
-                                               const B4<float>*, B4<float>*,
-                                               const int*, int, int,
-                                               cudaStream_t);
-
 // ---------------------------------------------------------------------------
 // coarsest level: dense inverse of the interior operator (Gauss-Jordan with
 // partial pivoting, FP64), one block per sample.  work: [S][n][2n].
 // ---------------------------------------------------------------------------
 
-template <class T>
+template <class M>
 __global__ void k_coarse_build(Grid G, const uint8_t* __restrict__ bc,
-                               const B4<T>* __restrict__ J, double* __restrict__ W,
+                               const B4<M>* __restrict__ J, double* __restrict__ W,
                                const int* mask, int mstride)
 {
     const int s = blockIdx.y;
@@ -506,14 +585,14 @@ __global__ void k_coarse_build(Grid G, const uint8_t* __restrict__ bc,
                     continue;
                 const int m = node_id(G, ii, jj, kk);
                 const uint8_t mc = bc[m];
-                const B4<T> B = J[((size_t)s * 27 + slot27(dx, dy, dz)) * G.N + node];
+                const B4<M> B = J[((size_t)s * 27 + slot27(dx, dy, dz)) * G.N + node];
                 if (!(mr & BC_P)) {
-                    if (!(mc & BC_P)) row0[2 * m] = B.pp;
-                    if (!(mc & BC_C)) row0[2 * m + 1] = B.pc;
+                    if (!(mc & BC_P)) row0[2 * m] = mg_load<double>(B.pp);
+                    if (!(mc & BC_C)) row0[2 * m + 1] = mg_load<double>(B.pc);
                 }
                 if (!(mr & BC_C)) {
-                    if (!(mc & BC_P)) row1[2 * m] = B.cp;
-                    if (!(mc & BC_C)) row1[2 * m + 1] = B.cc;
+                    if (!(mc & BC_P)) row1[2 * m] = mg_load<double>(B.cp);
+                    if (!(mc & BC_C)) row1[2 * m + 1] = mg_load<double>(B.cc);
                 }
             }
     if (mr & BC_P) row0[2 * node] = 1.0;
@@ -582,14 +661,14 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ W,
     }
 }
 
-template <class T>
-void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<T>* J,
+template <class M>
+void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<M>* J,
                            double* work, double* Ainv, const int* mask,
                            int mstride, int S, cudaStream_t st)
 {
     count_launch(1);
     dim3 grid(nblocks(G.N, 64), S);
-    k_coarse_build<T><<<grid, 64, 0, st>>>(G, bc, J, work, mask, mstride);
+    k_coarse_build<M><<<grid, 64, 0, st>>>(G, bc, J, work, mask, mstride);
     const int n = 2 * G.N;
     count_launch(1);
     k_gauss_jordan<<<S, 256, sizeof(double) * n, st>>>(n, work, Ainv, mask, mstride);
@@ -598,9 +677,10 @@ template void launch_coarse_inverse<double>(const Grid&, const uint8_t*,
                                             const B4<double>*, double*,
                                             double*, const int*, int, int,
                                             cudaStream_t);
-template void launch_coarse_inverse<float>(const Grid&, const uint8_t*,
-                                           const B4<float>*, double*, double*,
-                                           const int*, int, int, cudaStream_t);
+template void launch_coarse_inverse<__nv_bfloat16>(const Grid&, const uint8_t*,
+                                                   const B4<__nv_bfloat16>*, double*,
+                                                   double*, const int*, int, int,
+                                                   cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Dirichlet data and sample fields
@@ -1071,3 +1151,74 @@ extern "C" int elder_residual_norms_static(const elder_config* cfg, int S, const
     }
     return ELDER_OK;
 }
+
+namespace elder {
+
+// ---------------------------------------------------------------------------
+// Salt-mass balance of a step (FP64): M = sum_i sum_{e ni i} phi_e |scv|
+// rho(c_i) c_i at u^n and u^{n+1}, and the salt that entered through the
+// c-Dirichlet nodes, dt * sum_{i in D} (net face salt flux out of i).
+// The face fluxes telescope, so M^{n+1} - M^n = inflow + dt * sum of the
+// interior salt residuals.  partial: [S][3][nblk].
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kBS)
+    k_mass_balance(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
+                   const double* __restrict__ phi, const double* __restrict__ K,
+                   const double* __restrict__ p, const double* __restrict__ c,
+                   const double* __restrict__ c_old, double* __restrict__ partial)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.y;
+    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
+    phi += oc; K += oc; p += on; c += on; c_old += on;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double m1 = 0.0, m0 = 0.0, in = 0.0;
+    if (n < G.N) {
+        int i, j, k;
+        node_ijk(G, n, i, j, k);
+        double phis = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            const int ci = i - (q & 1), cj = j - ((q >> 1) & 1), ck = k - (q >> 2);
+            if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
+            phis += phi[ci + G.nx * (cj + G.ny * ck)];
+        }
+        const double vscv = 0.125 * G.hx * G.hy * G.hz;
+        const double cn = c[n], co = c_old[n];
+        m1 = phis * vscv * fma(ph.drho, cn, ph.rho0) * cn;
+        m0 = phis * vscv * fma(ph.drho, co, ph.rho0) * co;
+        if (bc[n] & BC_C) {
+            double Rp = 0.0, Rc = 0.0, ps = 0.0, Ap = 0.0, Ac = 0.0;
+            residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            in = ph.dt * Rc;  // net salt flux out of this Dirichlet node
+
+        }
+    }
+    const double t0 = block_sum(m0, red);
+    const double t1 = block_sum(m1, red);
+    const double t2 = block_sum(in, red);
+    if (threadIdx.x == 0) {
+        partial[((size_t)s * 3 + 0) * gridDim.x + blockIdx.x] = t0;
+        partial[((size_t)s * 3 + 1) * gridDim.x + blockIdx.x] = t1;
+        partial[((size_t)s * 3 + 2) * gridDim.x + blockIdx.x] = t2;
+    }
+}
+
+void launch_mass_balance(const Grid& G, const Phys& ph, const uint8_t* bc, const double* phi,
+                         const double* K, const double* p, const double* c,
+                         const double* c_old, double* partial, int S, cudaStream_t st)
+{
+    count_launch(1);
+    dim3 grid(nblocks(G.N), S);
+    k_mass_balance<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c, c_old,
+                                         partial);
+}
+
+}  // namespace elder

@@ -6,6 +6,7 @@
 // e = i + nx*(j + ny*k).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +45,24 @@ __host__ __device__ constexpr int slot27(int dx, int dy, int dz)
 template <class T> struct alignas(2 * sizeof(T)) V2 { T p, c; };
 // 2x2 Jacobian block: rows (p-eq, c-eq) x cols (p, c).
 template <class T> struct alignas(4 * sizeof(T)) B4 { T pp, pc, cp, cc; };
+
+// Storage type of the multigrid matrices for solver precision T: the FP32
+// solver keeps them in bfloat16 (the V-cycle is only a preconditioner; the
+// Krylov operator keeps its FP32 copy), the FP64 solver in double.
+template <class T> struct MgType { using type = T; };
+template <> struct MgType<float> { using type = __nv_bfloat16; };
+
+template <class T> __device__ __forceinline__ T mg_load(__nv_bfloat16 v)
+{
+    return T(__bfloat162float(v));
+}
+template <class T> __device__ __forceinline__ T mg_load(float v) { return T(v); }
+template <class T> __device__ __forceinline__ T mg_load(double v) { return T(v); }
+template <class M> __device__ __forceinline__ M mg_store(double v) { return M(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 mg_store<__nv_bfloat16>(double v)
+{
+    return __float2bfloat16_rn(float(v));
+}
 
 __host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
 {

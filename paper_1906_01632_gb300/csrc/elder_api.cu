@@ -141,7 +141,10 @@ struct SolverBase {
 
 template <class T> struct Solver : SolverBase {
     int S = 0;
-    std::vector<B4<T>*> J, Dinv;
+    using M = typename MgType<T>::type;
+    B4<T>* J0 = nullptr;           // level-0 Krylov operator (T)
+    std::vector<B4<M>*> Jm;        // multigrid matrices per level (M)
+    std::vector<B4<T>*> Dinv;      // inverse interior diagonal blocks per level
     std::vector<V2<T>*> mb, mx, mx2, mr;  // multigrid vectors per level
     V2<T> *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr,
           *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr;
@@ -192,6 +195,9 @@ struct elder_ctx {
     double* partial2 = nullptr;
     double* partial3 = nullptr;
     double* pk = nullptr;              // packed batch for the FP64 re-solve
+    E4* edge = nullptr;                // [S][3][N] edge fluxes of the residual
+    double* mass = nullptr;            // [S][3] salt-mass balance
+    double* h_mass = nullptr;          // pinned
     NScal* ns = nullptr;
     KScal* ks = nullptr;
     NScal* h_ns = nullptr;             // pinned
@@ -201,6 +207,10 @@ struct elder_ctx {
     std::unique_ptr<Solver<double>> s64;
     std::unique_ptr<Solver<float>> s32;
     int nblk0 = 0;
+    // threads per block of the autotuned kernel classes (indexed by ELDER_K_*)
+    int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, kBS};
+    bool tuned[2] = {false, false};    // per precision (FP64, FP32)
+    float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
     ~elder_ctx()
     {
         s64.reset();
@@ -208,6 +218,7 @@ struct elder_ctx {
         if (h_ns) cudaFreeHost(h_ns);
         if (h_ks) cudaFreeHost(h_ks);
         if (h_scalar) cudaFreeHost(h_scalar);
+        if (h_mass) cudaFreeHost(h_mass);
     }
 };
 
@@ -228,18 +239,21 @@ Phys make_phys(const elder_config& c, double dt)
 // Algorithmic DRAM bytes and flops per node of one launch (every array the
 // kernel must touch, read or written once; neighbour reuse of x is free).
 // T = bytes of the solver type.  J row: 27 blocks of 4; vectors: 2 values.
-double model_bytes(int cls, int T, const Grid& G)
+double model_bytes(int cls, int T, int Mz, const Grid& G)
 {
+    // T: bytes of a vector / Dinv entry; Mz: bytes of a stored matrix entry
+    // (for the Jacobian class: Mz of the multigrid copy, T of the Krylov copy
+    // or 0 when the level has none)
     const double cells_per_node = (double)G.C / G.N;
     switch (cls) {
-    case ELDER_K_SMOOTH: return (108 + 4 + 2 + 2 + 2) * T + 1;     // J, Dinv, b, x, xo, bc
-    case ELDER_K_SMOOTH0: return (4 + 2 + 2) * T + 1;               // Dinv, b, xo, bc
-    case ELDER_K_SPMV: return (108 + 2 + 2 + 2) * T + 1;            // J, x, y, a, bc
-    case ELDER_K_MGRES: return (108 + 2 + 2 + 2) * T + 1;           // J, x, b, r, bc
-    case ELDER_K_RESIDUAL:                                          // p,c,p_old,c_old,R,cval,bc,phi,K
-        return 4 * 8 + 16 + 8 + 1 + 16 * cells_per_node;
-    case ELDER_K_JACOBIAN:                                          // J written; p, c, bc, phi, K
-        return 108 * T + 16 + 1 + 16 * cells_per_node;
+    case ELDER_K_SMOOTH: return 108 * Mz + (4 + 2 + 2 + 2) * T + 1;  // J, Dinv, b, x, xo, bc
+    case ELDER_K_SMOOTH0: return (4 + 2 + 2) * T + 1;                // Dinv, b, xo, bc
+    case ELDER_K_SPMV: return 108 * Mz + (2 + 2 + 2) * T + 1;        // J, x, y, a, bc
+    case ELDER_K_MGRES: return 108 * Mz + (2 + 2 + 2) * T + 1;       // J, x, b, r, bc
+    case ELDER_K_RESIDUAL:  // p, c, c_old, R, cval, bc, phi, K
+        return 3 * 8 + 16 + 8 + 1 + 16 * cells_per_node;
+    case ELDER_K_JACOBIAN:  // J written (Krylov + multigrid copies), Dinv; p, c, bc, phi, K
+        return 108 * T + 108 * Mz + 4 * (T ? T : Mz) + 16 + 1 + 16 * cells_per_node;
     }
     return 0.0;
 }
@@ -251,7 +265,7 @@ double model_flops(int cls)
     case ELDER_K_SMOOTH0: return 8 + 2;
     case ELDER_K_SPMV: return 216 + 8;
     case ELDER_K_MGRES: return 216 + 2;
-    case ELDER_K_RESIDUAL: return 24 * 54 + 20;   // 24 face fluxes + storage
+    case ELDER_K_RESIDUAL: return 12 * 54 + 40;   // 12 face fluxes per node + storage
     case ELDER_K_JACOBIAN: return 24 * (54 + 66) + 10;
     }
     return 0.0;
@@ -276,14 +290,14 @@ int prof_begin(elder_ctx* ctx, cudaStream_t st)
     return (int)P.pending.size() - 1;
 }
 
-void prof_end(elder_ctx* ctx, int idx, int cls, const Grid& G, int T, int samples,
+void prof_end(elder_ctx* ctx, int idx, int cls, const Grid& G, int T, int Mz, int samples,
               cudaStream_t st)
 {
     if (idx < 0) return;
     ProfRec& r = ctx->prof.pending[idx];
     CK(cudaEventRecord(r.b, st));
     r.cls = cls;
-    r.bytes = model_bytes(cls, T, G) * G.N * samples;
+    r.bytes = model_bytes(cls, T, Mz, G) * G.N * samples;
     r.flops = model_flops(cls) * G.N * samples;
 }
 
@@ -348,8 +362,16 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap)
     for (int l = 0; l < L; ++l) {
         const Grid& G = ctx->grids[l];
         const size_t nN = (size_t)S * G.N;
-        sv.J.push_back(dalloc<B4<T>>(nN * 27));
-        sv.mem.add(sv.J.back());
+        sv.Jm.push_back(dalloc<B4<typename Solver<T>::M>>(nN * 27));
+        sv.mem.add(sv.Jm.back());
+        if (l == 0) {
+            if (std::is_same<T, typename Solver<T>::M>::value) {
+                sv.J0 = reinterpret_cast<B4<T>*>(sv.Jm[0]);  // one array serves both
+            } else {
+                sv.J0 = dalloc<B4<T>>(nN * 27);
+                sv.mem.add(sv.J0);
+            }
+        }
         sv.Dinv.push_back(dalloc<B4<T>>(nN));
         sv.mem.add(sv.Dinv.back());
         for (auto* vec : {&sv.mb, &sv.mx, &sv.mx2, &sv.mr}) {
@@ -393,11 +415,15 @@ void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
                           mstride, S, st);
         }
         const int pi = prof_begin(ctx, st);
-        launch_jacobian<T>(G, ph, ctx->bc[l], phi, K, p, c, sv.J[l], mask, mstride, S, st);
-        prof_end(ctx, pi, ELDER_K_JACOBIAN, G, sizeof(T), n_active, st);
-        launch_block_diag_inverse<T>(G, ctx->bc[l], sv.J[l], sv.Dinv[l], mask, mstride, S, st);
+        using M = typename Solver<T>::M;
+        B4<T>* JT = (l == 0 && !std::is_same<T, M>::value) ? sv.J0 : nullptr;
+        launch_jacobian<T, M>(G, ph, ctx->bc[l], phi, K, p, c, JT, sv.Jm[l], sv.Dinv[l], mask,
+                              mstride, S, st);
+        prof_end(ctx, pi, ELDER_K_JACOBIAN, G, JT ? (int)sizeof(T) : 0, (int)sizeof(M), n_active,
+                 st);
     }
-    launch_coarse_inverse<T>(ctx->grids.back(), ctx->bc.back(), sv.J.back(), sv.work,
+    launch_coarse_inverse<typename Solver<T>::M>(ctx->grids.back(), ctx->bc.back(), sv.Jm.back(),
+                                                 sv.work,
                              sv.Ainv, mask, mstride, S, st);
     CKL();
 }
@@ -434,22 +460,24 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     // choose the first buffer so that the last sweep lands in `out`
     V2<T>* cur = ((sweeps - 1) % 2 == 0) ? bufA : bufB;
     V2<T>* oth = (cur == bufA) ? bufB : bufA;
+    using M = typename Solver<T>::M;
     const int na = ctx->n_active_k;
+    const int bs_sm = ctx->bs[ELDER_K_SMOOTH], bs_mr = ctx->bs[ELDER_K_MGRES];
     int pi = prof_begin(ctx, st);
-    launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, nullptr, cur, cf.omega, trans,
-                     mask, KSTRIDE, S, st);
-    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), na, st);
+    launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, nullptr, cur, cf.omega, trans,
+                        mask, KSTRIDE, S, st);
+    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), sizeof(M), na, st);
     for (int q = 1; q < nu1; ++q) {
         pi = prof_begin(ctx, st);
-        launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
-                         mask, KSTRIDE, S, st);
-        prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), na, st);
+        launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
+                            mask, KSTRIDE, S, st, bs_sm);
+        prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), sizeof(M), na, st);
         std::swap(cur, oth);
     }
     pi = prof_begin(ctx, st);
-    launch_mg_residual<T>(G, sv.J[l], ctx->bc[l], b, cur, sv.mr[l], trans, mask, KSTRIDE, S,
-                          st);
-    prof_end(ctx, pi, ELDER_K_MGRES, G, sizeof(T), na, st);
+    launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, cur, sv.mr[l], trans, mask, KSTRIDE, S,
+                             st, bs_mr);
+    prof_end(ctx, pi, ELDER_K_MGRES, G, sizeof(T), sizeof(M), na, st);
     launch_restrict<T>(G, ctx->grids[l + 1], ctx->bc[l + 1], sv.mr[l], sv.mb[l + 1], mask,
                        KSTRIDE, S, st);
     vcycle<T>(ctx, sv, l + 1, sv.mb[l + 1], sv.mx[l + 1], trans, S, st);
@@ -457,13 +485,66 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
                           S, st);
     for (int q = 0; q < nu2; ++q) {
         pi = prof_begin(ctx, st);
-        launch_smooth<T>(G, sv.J[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
-                         mask, KSTRIDE, S, st);
-        prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), na, st);
+        launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
+                            mask, KSTRIDE, S, st, bs_sm);
+        prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), sizeof(M), na, st);
         std::swap(cur, oth);
     }
     if (cur != out) CK(cudaMemcpyAsync(out, cur, sizeof(V2<T>) * (size_t)S * G.N,
                                        cudaMemcpyDeviceToDevice, st));
+}
+
+// Autotuner: threads per block of the three J-streaming kernel classes,
+// chosen once per context and precision by timing every candidate (CUDA
+// events, 3 launches after a warm-up) on the first assembled level-0
+// operator of a step with all S samples active.
+template <class T>
+void autotune(elder_ctx* ctx, Solver<T>& sv, int S, cudaStream_t st)
+{
+    const int idx = std::is_same<T, float>::value ? 1 : 0;
+    if (ctx->tuned[idx] || !ctx->cfg.autotune) return;
+    using M = typename Solver<T>::M;
+    const Grid& G = ctx->grids[0];
+    const size_t nv = (size_t)S * G.N;
+    CK(cudaMemsetAsync(sv.mb[0], 0, sizeof(V2<T>) * nv, st));
+    CK(cudaMemsetAsync(sv.mx[0], 0, sizeof(V2<T>) * nv, st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int cand[3] = {kMinBS, kBS, kMaxBS};
+    const int cls[3] = {ELDER_K_SMOOTH, ELDER_K_SPMV, ELDER_K_MGRES};
+    for (int c = 0; c < 3; ++c) {
+        float best = 1e30f;
+        for (int q = 0; q < 3; ++q) {
+            auto run = [&]() {
+                if (c == 0)
+                    launch_smooth<T, M>(G, sv.Jm[0], sv.Dinv[0], ctx->bc[0], sv.mb[0], sv.mx[0],
+                                        sv.mx2[0], ctx->cfg.omega, 0, nullptr, 0, S, st, cand[q]);
+                else if (c == 1)
+                    launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.mx[0], sv.mx2[0], 0, 0, nullptr,
+                                   nullptr, nullptr, 0, S, st, cand[q]);
+                else
+                    launch_mg_residual<T, M>(G, sv.Jm[0], ctx->bc[0], sv.mb[0], sv.mx[0],
+                                             sv.mx2[0], 0, nullptr, 0, S, st, cand[q]);
+            };
+            run();
+            CK(cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; ++r) run();
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ctx->tune_ms[c][q] = ms / 3.f;
+            if (ms < best) {
+                best = ms;
+                ctx->bs[cls[c]] = cand[q];
+            }
+        }
+    }
+    CK(cudaEventDestroy(e0));
+    CK(cudaEventDestroy(e1));
+    CKL();
+    ctx->tuned[idx] = true;
 }
 
 template <class T>
@@ -472,22 +553,24 @@ void bicg_iteration(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int m
 {
     const Grid& G = ctx->grids[0];
     const int nb = ctx->nblk0;
+    const int bs_mv = ctx->bs[ELDER_K_SPMV];
+    const int nb_mv = nblocks(G.N, bs_mv);  // partials of the stencil products
     KScal* ks = ctx->ks;
     const int* mask = &ks[0].active;
     launch_bicg_p<T>(G, sv.r, sv.v, sv.p, ks, S, st);
     vcycle<T>(ctx, sv, 0, sv.p, sv.ph, trans, S, st);
     int pi = prof_begin(ctx, st);
-    launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.ph, sv.v, trans, 1, sv.rh, ctx->partial, mask,
-                   KSTRIDE, S, st);
-    prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), ctx->n_active_k, st);
-    launch_bicg_finalize(1, ctx->partial, nb, ks, rtol, maxit, S, st);
+    launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.ph, sv.v, trans, 1, sv.rh, ctx->partial, mask,
+                   KSTRIDE, S, st, bs_mv);
+    prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), sizeof(T), ctx->n_active_k, st);
+    launch_bicg_finalize(1, ctx->partial, nb_mv, ks, rtol, maxit, S, st);
     launch_bicg_s<T>(G, sv.r, sv.v, sv.s, nullptr, ks, S, st);
     vcycle<T>(ctx, sv, 0, sv.s, sv.sh, trans, S, st);
     pi = prof_begin(ctx, st);
-    launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.sh, sv.t, trans, 2, sv.s, ctx->partial, mask,
-                   KSTRIDE, S, st);
-    prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), ctx->n_active_k, st);
-    launch_bicg_finalize(2, ctx->partial, nb, ks, rtol, maxit, S, st);
+    launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.sh, sv.t, trans, 2, sv.s, ctx->partial, mask,
+                   KSTRIDE, S, st, bs_mv);
+    prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), sizeof(T), ctx->n_active_k, st);
+    launch_bicg_finalize(2, ctx->partial, nb_mv, ks, rtol, maxit, S, st);
     launch_bicg_xr<T>(G, sv.ph, sv.sh, sv.s, sv.t, sv.rh, sv.x, sv.r, ctx->partial, ks, S, st);
     launch_bicg_finalize(3, ctx->partial, nb, ks, rtol, maxit, S, st);
 }
@@ -599,8 +682,8 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     CK(cudaMemcpyAsync(ns, ctx->h_ns, sizeof(NScal) * S, cudaMemcpyHostToDevice, st));
     int pi = prof_begin(ctx, st);
     launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, p, c, ctx->p_old, ctx->c_old, ctx->R,
-                    ctx->partial, ctx->partial2, nullptr, 0, S, st);
-    prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, S, st);
+                    ctx->partial, ctx->partial2, nullptr, 0, S, st, ctx->edge);
+    prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, 8, S, st);
     launch_norm_finalize(ctx->partial, ctx->partial2, nb, ns, 0, S, st);
     CKL();
 
@@ -614,6 +697,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         ctx->n_active_newton = na;
         ctx->n_active_ls = na;
         assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, na, st);
+        if (it == 0) autotune<T>(ctx, sv, S, st);
         launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
         bicgstab<T>(ctx, sv, 0, cf.lin_rtol, cf.lin_maxit, ns, S, st);
         for (int ls = 0; ls <= cf.ls_max; ++ls) {
@@ -621,8 +705,8 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
             pi = prof_begin(ctx, st);
             launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
                             ctx->c_old, ctx->Rt, ctx->partial, ctx->partial3, lsmask, NSTRIDE,
-                            S, st);
-            prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, ctx->n_active_ls, st);
+                            S, st, ctx->edge);
+            prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, 8, ctx->n_active_ls, st);
             launch_norm_finalize(ctx->partial, ctx->partial3, nb, ns, 1, S, st);
             launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, cf.ls_max, S, st);
             CKL();
@@ -635,8 +719,8 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
             if (nls == 0) break;
         }
         launch_newton_accept(G, p, c, ctx->pt, ctx->ct, ctx->R, ctx->Rt, ns, S, st);
-        launch_newton_check(ns, ctx->ks, cf.newton_tol_p, cf.newton_tol_c, cf.newton_maxit, S,
-                            st);
+        launch_newton_check(ns, ctx->ks, cf.newton_tol_p, cf.newton_tol_c, cf.newton_maxit,
+                            cf.newton_estimate, S, st);
         CKL();
     }
     // samples still active here ran out of Newton iterations
@@ -652,6 +736,10 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     if (changed)
         CK(cudaMemcpyAsync(ns, ctx->h_ns, sizeof(NScal) * S, cudaMemcpyHostToDevice, st));
     launch_newton_restore_failed(G, p, c, ctx->p_old, ctx->c_old, ns, S, st);
+    launch_mass_balance(G, ph, ctx->bc[0], phi, K, p, c, ctx->c_old, ctx->partial3, S, st);
+    launch_sum_partials(ctx->partial3, nb, ctx->mass, 3 * S, st);
+    CK(cudaMemcpyAsync(ctx->h_mass, ctx->mass, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost,
+                       st));
     CKL();
     CK(cudaStreamSynchronize(st));
     prof_drain(ctx);
@@ -668,6 +756,9 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
             stats[s].res = k.rn;
             stats[s].fp64_retry = 0;
             stats[s].pad = 0;
+            stats[s].salt_mass0 = ctx->h_mass[3 * s + 0];
+            stats[s].salt_mass = ctx->h_mass[3 * s + 1];
+            stats[s].salt_inflow = ctx->h_mass[3 * s + 2];
         }
         if (k.status != 0) rc = ELDER_ENOTCONV;
     }
@@ -758,7 +849,7 @@ int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const 
     // transpose: interior J_II^T y_I = rhs_I, then y_D = rhs_D - J_ID^T y_I
     if (!trans) {
         launch_axpy_mask<T>(G, ctx->bc[0], bT, sv.mr[0], 1.0, 0, S, st);  // mr = b on D
-        launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.mr[0], sv.mx2[0], 0, 0, nullptr, nullptr,
+        launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.mr[0], sv.mx2[0], 0, 0, nullptr, nullptr,
                        nullptr, 0, S, st);                                 // J x_D (interior)
         launch_axpy_mask<T>(G, ctx->bc[0], sv.mx2[0], bT, -1.0, 2, S, st);
     }
@@ -767,7 +858,7 @@ int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const 
         launch_axpy_mask<T>(G, ctx->bc[0], sv.mr[0], sv.x, 1.0, 1, S, st);
     } else {
         // (A^T y_I) on Dirichlet rows, unmasked
-        launch_spmv<T>(G, sv.J[0], ctx->bc[0], sv.x, sv.mx2[0], 1, 3, nullptr, nullptr,
+        launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.x, sv.mx2[0], 1, 3, nullptr, nullptr,
                        nullptr, 0, S, st);
         // x_D = rhs_D - (A^T y_I)_D : rebuild rhs in mr then combine
         if (std::is_same<T, double>::value)
@@ -840,6 +931,8 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->omega = 0.5;
     cfg->coarse_K_harmonic = 0;
     cfg->use_graphs = 1;
+    cfg->autotune = 1;
+    cfg->newton_estimate = 1;
     return ELDER_OK;
 }
 
@@ -923,9 +1016,15 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
             *q = dalloc<V2<double>>(nN);
             ctx->mem.add(*q);
         }
-        ctx->partial = dalloc<double>((size_t)S * 2 * ctx->nblk0);
+        // sized for the smallest autotuned block (most partials per sample)
+        ctx->partial = dalloc<double>((size_t)S * 2 * nblocks(G.N, kMinBS));
         ctx->partial2 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
-        ctx->partial3 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
+        ctx->partial3 = dalloc<double>((size_t)S * 3 * ctx->nblk0);
+        ctx->edge = dalloc<E4>((size_t)S * 3 * G.N);
+        ctx->mem.add(ctx->edge);
+        ctx->mass = dalloc<double>((size_t)3 * S);
+        ctx->mem.add(ctx->mass);
+        CK(cudaMallocHost((void**)&ctx->h_mass, sizeof(double) * 3 * S));
         ctx->mem.add(ctx->partial3);
         ctx->ns = dalloc<NScal>(S);
         ctx->ks = dalloc<KScal>(S);
@@ -1008,7 +1107,7 @@ int elder_residual(elder_ctx* ctx, int S, const double* phi, const double* K,
     try {
         launch_residual(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], ctx->cval, phi, K,
                         p, c, p_old, c_old, reinterpret_cast<V2<double>*>(R), nullptr, nullptr,
-                        nullptr, 0, S, (cudaStream_t)stream);
+                        nullptr, 0, S, (cudaStream_t)stream, ctx->edge);
         CKL();
     } catch (const Fail& f) {
         return set_error(ctx, f);
@@ -1026,9 +1125,9 @@ int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
         return ELDER_EINVAL;
     }
     try {
-        launch_jacobian<double>(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], phi, K, p,
-                                c, reinterpret_cast<B4<double>*>(J), nullptr, 0, S,
-                                (cudaStream_t)stream);
+        launch_jacobian<double, double>(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], phi,
+                                        K, p, c, reinterpret_cast<B4<double>*>(J), nullptr,
+                                        nullptr, nullptr, 0, S, (cudaStream_t)stream);
         CKL();
     } catch (const Fail& f) {
         return set_error(ctx, f);
@@ -1125,6 +1224,19 @@ int elder_profile_read(const elder_ctx* ctx, int kernel_class, int64_t* launches
     return ELDER_OK;
 }
 
+int elder_autotune_result(const elder_ctx* ctx, int* bs_smooth, int* bs_spmv, int* bs_mgres,
+                          float* ms)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bs_smooth) *bs_smooth = ctx->bs[ELDER_K_SMOOTH];
+    if (bs_spmv) *bs_spmv = ctx->bs[ELDER_K_SPMV];
+    if (bs_mgres) *bs_mgres = ctx->bs[ELDER_K_MGRES];
+    if (ms)
+        for (int c = 0; c < 3; ++c)
+            for (int q = 0; q < 3; ++q) ms[3 * c + q] = ctx->tune_ms[c][q];
+    return ELDER_OK;
+}
+
 int elder_launch_count(int64_t* launches)
 {
     if (!launches) return ELDER_EINVAL;
@@ -1193,7 +1305,11 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
         CK(cudaMemcpyAsync(ck, cur, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, st));
         int rc_all = ELDER_OK;
         for (int n = 1; n <= n_steps; ++n) {
-            if (fwd_step(cur) != ELDER_OK) rc_all = ELDER_ENOTCONV;
+            if (fwd_step(cur) != ELDER_OK) {
+                rc_all = ELDER_ENOTCONV;
+                ctx->err = "elder_grad: forward step " + std::to_string(n) +
+                           " failed with sample status " + std::to_string(stat);
+            }
             if (n % ckpt_every == 0)
                 CK(cudaMemcpyAsync(ck + 2 * N * (n / ckpt_every), cur, sizeof(double) * 2 * N,
                                    cudaMemcpyDeviceToDevice, st));
@@ -1217,7 +1333,11 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
                 double* dst = seg + 2 * N * (n - k0);
                 CK(cudaMemcpyAsync(dst, seg + 2 * N * (n - k0 - 1), sizeof(double) * 2 * N,
                                    cudaMemcpyDeviceToDevice, st));
-                if (fwd_step(dst) != ELDER_OK) rc_all = ELDER_ENOTCONV;
+                if (fwd_step(dst) != ELDER_OK) {
+                    rc_all = ELDER_ENOTCONV;
+                    ctx->err = "elder_grad: recomputed step " + std::to_string(n) +
+                               " failed with sample status " + std::to_string(stat);
+                }
             }
             for (int n = k1; n >= k0 + 1; --n) {
                 const double* un = seg + 2 * N * (n - k0);

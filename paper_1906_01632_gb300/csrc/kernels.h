@@ -18,13 +18,23 @@ struct NScal {
     double res0;
     double dmax_p, dmax_c;       // max |lambda * delta| of the last step
     double rfloor, rfloor_t;     // round-off level of ||R(u)||, ||R(u_trial)||
+    double dprev_p, dprev_c;     // max |delta| of the previous Newton step
+    int full_prev, pad0;         // previous step was a full (lambda = 1) step
     int active;                  // still iterating
     int ls_active;               // line search still running
     int accepted;                // trial accepted in this Newton iteration
     int iters, ls_cuts, kiters, ls_count, status;
 };
 
-constexpr int kBS = 256;  // threads per block of the node kernels
+// Flux through the dual face of one edge, out of its lower node: mass and
+// salt flux and the magnitudes of their terms.
+struct alignas(32) E4 {
+    double m, F, mm, Fm;
+};
+
+constexpr int kBS = 256;     // threads per block of the node kernels
+constexpr int kMaxBS = 512;  // largest block of the autotuned stencil kernels
+constexpr int kMinBS = 128;  // smallest block of the autotuned stencil kernels
 
 inline int nblocks(int n, int bs = kBS) { return (n + bs - 1) / bs; }
 
@@ -39,24 +49,22 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* p, const double* c, const double* p_old,
                      const double* c_old, V2<double>* R, double* partial,
                      double* act, const int* mask, int mask_stride, int S,
-                     cudaStream_t st);
-template <class T>
+                     cudaStream_t st, E4* edge);
+// Jacobian rows as T (JT) and/or as the multigrid type M (JM), and the inverse
+// interior diagonal blocks (Dinv); null outputs are skipped.
+template <class T, class M>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* phi, const double* K, const double* p,
-                     const double* c, B4<T>* J, const int* mask,
-                     int mask_stride, int S, cudaStream_t st);
+                     const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv,
+                     const int* mask, int mask_stride, int S, cudaStream_t st);
 void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
                    const double* cf, double* pc, double* cc, const int* mask,
                    int mask_stride, int S, cudaStream_t st);
 void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
                           const double* Kf, double* phic, double* Kc,
                           int harmonic, int S, cudaStream_t st);
-template <class T>
-void launch_block_diag_inverse(const Grid& G, const uint8_t* bc,
-                               const B4<T>* J, B4<T>* Dinv, const int* mask,
-                               int mask_stride, int S, cudaStream_t st);
-template <class T>
-void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<T>* J,
+template <class M>
+void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<M>* J,
                            double* work, double* Ainv, const int* mask,
                            int mask_stride, int S, cudaStream_t st);
 void launch_impose_dirichlet(const Grid& G, const uint8_t* bc,
@@ -78,18 +86,19 @@ template <class T>
 void launch_spmv(const Grid& G, const B4<T>* J, const uint8_t* bc,
                  const V2<T>* x, V2<T>* y, int trans, int mode,
                  const V2<T>* a, double* partial, const int* mask,
-                 int mask_stride, int S, cudaStream_t st);
-// xo = x + omega Dinv (b - A x) (x == nullptr: xo = omega Dinv b)
-template <class T>
-void launch_smooth(const Grid& G, const B4<T>* J, const B4<T>* Dinv,
+                 int mask_stride, int S, cudaStream_t st, int bs = kBS);
+// xo = x + omega Dinv (b - A x) (x == nullptr: xo = omega Dinv b); the
+// matrix is stored as M (MgType<T>), vectors and Dinv as T
+template <class T, class M>
+void launch_smooth(const Grid& G, const B4<M>* J, const B4<T>* Dinv,
                    const uint8_t* bc, const V2<T>* b, const V2<T>* x,
                    V2<T>* xo, double omega, int trans, const int* mask,
-                   int mask_stride, int S, cudaStream_t st);
-template <class T>
-void launch_mg_residual(const Grid& G, const B4<T>* J, const uint8_t* bc,
+                   int mask_stride, int S, cudaStream_t st, int bs = kBS);
+template <class T, class M>
+void launch_mg_residual(const Grid& G, const B4<M>* J, const uint8_t* bc,
                         const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
                         const int* mask, int mask_stride, int S,
-                        cudaStream_t st);
+                        cudaStream_t st, int bs = kBS);
 template <class T>
 void launch_restrict(const Grid& Gf, const Grid& Gc, const uint8_t* bcc,
                      const V2<T>* rf, V2<T>* bc_out, const int* mask,
@@ -145,7 +154,7 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
                           V2<double>* R, const V2<double>* Rt,
                           const NScal* ns, int S, cudaStream_t st);
 void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
-                         double tol_c, int maxit, int S, cudaStream_t st);
+                         double tol_c, int maxit, int estimate, int S, cudaStream_t st);
 void launch_newton_restore_failed(const Grid& G, double* p, double* c,
                                   const double* p_old, const double* c_old,
                                   const NScal* ns, int S, cudaStream_t st);
@@ -153,6 +162,11 @@ void launch_newton_restore_failed(const Grid& G, double* p, double* c,
 void launch_moments(int N, int S, const double* c, const double* w,
                     double threshold, double* mean, double* var,
                     double* pexc, cudaStream_t st);
+
+// salt mass at u^n, u^{n+1} and the Dirichlet inflow; partial [S][3][nblk]
+void launch_mass_balance(const Grid& G, const Phys& ph, const uint8_t* bc, const double* phi,
+                         const double* K, const double* p, const double* c,
+                         const double* c_old, double* partial, int S, cudaStream_t st);
 
 // ---- adjoint pieces (assembly.cu) ----------------------------------------
 void launch_objective(const Grid& G, const Phys& ph, const double* phi,

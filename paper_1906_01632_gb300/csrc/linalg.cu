@@ -26,9 +26,9 @@ static_assert(sizeof(NScal) % sizeof(int) == 0, "NScal layout");
 
 // y_n = sum over the 27 neighbours of the 2x2 block times x (or the
 // transposed product, reading row m's block of offset -d).
-template <class T, bool TRANS>
+template <class T, bool TRANS, class M>
 __device__ __forceinline__ void stencil_apply(const Grid& G,
-                                              const B4<T>* __restrict__ J,
+                                              const B4<M>* __restrict__ J,
                                               const V2<T>* __restrict__ x,
                                               int n, int i, int j, int k,
                                               T& yp, T& yc)
@@ -49,13 +49,13 @@ __device__ __forceinline__ void stencil_apply(const Grid& G,
                     const int m = n + dx + dy * sy + dz * sz;
                     const V2<T> xv = x[m];
                     if (!TRANS) {
-                        const B4<T> b = J[(size_t)slot27(dx, dy, dz) * G.N + n];
-                        yp += b.pp * xv.p + b.pc * xv.c;
-                        yc += b.cp * xv.p + b.cc * xv.c;
+                        const B4<M> b = J[(size_t)slot27(dx, dy, dz) * G.N + n];
+                        yp += mg_load<T>(b.pp) * xv.p + mg_load<T>(b.pc) * xv.c;
+                        yc += mg_load<T>(b.cp) * xv.p + mg_load<T>(b.cc) * xv.c;
                     } else {
-                        const B4<T> b = J[(size_t)slot27(-dx, -dy, -dz) * G.N + m];
-                        yp += b.pp * xv.p + b.cp * xv.c;
-                        yc += b.pc * xv.p + b.cc * xv.c;
+                        const B4<M> b = J[(size_t)slot27(-dx, -dy, -dz) * G.N + m];
+                        yp += mg_load<T>(b.pp) * xv.p + mg_load<T>(b.cp) * xv.c;
+                        yc += mg_load<T>(b.pc) * xv.p + mg_load<T>(b.cc) * xv.c;
                     }
                 }
             }
@@ -66,7 +66,7 @@ __device__ __forceinline__ void stencil_apply(const Grid& G,
 // ---------------------------------------------------------------------------
 
 template <class T, bool TRANS, int MODE>
-__global__ void __launch_bounds__(kBS)
+__global__ void __launch_bounds__(kMaxBS)
     k_spmv(Grid G, const B4<T>* __restrict__ J, const uint8_t* __restrict__ bc,
            const V2<T>* __restrict__ x, V2<T>* __restrict__ y,
            const V2<T>* __restrict__ a, double* __restrict__ partial,
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kBS)
         int i, j, k;
         node_ijk(G, n, i, j, k);
         T yp, yc;
-        stencil_apply<T, TRANS>(G, J, x, n, i, j, k, yp, yc);
+        stencil_apply<T, TRANS, T>(G, J, x, n, i, j, k, yp, yc);
         if (MODE != 3) {
             const uint8_t b = bc[n];
             if (b & BC_P) yp = T(0);
@@ -112,12 +112,12 @@ template <class T>
 void launch_spmv(const Grid& G, const B4<T>* J, const uint8_t* bc,
                  const V2<T>* x, V2<T>* y, int trans, int mode,
                  const V2<T>* a, double* partial, const int* mask,
-                 int mstride, int S, cudaStream_t st)
+                 int mstride, int S, cudaStream_t st, int bs)
 {
     count_launch(1);
-    dim3 grid(nblocks(G.N), S);
+    dim3 grid(nblocks(G.N, bs), S);
 #define ELDER_SPMV(TR, MO) \
-    k_spmv<T, TR, MO><<<grid, kBS, 0, st>>>(G, J, bc, x, y, a, partial, mask, mstride)
+    k_spmv<T, TR, MO><<<grid, bs, 0, st>>>(G, J, bc, x, y, a, partial, mask, mstride)
     if (!trans) {
         if (mode == 0) ELDER_SPMV(false, 0);
         else if (mode == 1) ELDER_SPMV(false, 1);
@@ -136,9 +136,9 @@ void launch_spmv(const Grid& G, const B4<T>* J, const uint8_t* bc,
 // multigrid: damped block-Jacobi smoother, residual, transfers, coarse solve
 // ---------------------------------------------------------------------------
 
-template <class T, bool TRANS, bool ZEROX>
-__global__ void __launch_bounds__(kBS)
-    k_smooth(Grid G, const B4<T>* __restrict__ J, const B4<T>* __restrict__ Dinv,
+template <class T, class M, bool TRANS, bool ZEROX>
+__global__ void __launch_bounds__(kMaxBS)
+    k_smooth(Grid G, const B4<M>* __restrict__ J, const B4<T>* __restrict__ Dinv,
              const uint8_t* __restrict__ bc, const V2<T>* __restrict__ b,
              const V2<T>* __restrict__ x, V2<T>* __restrict__ xo, T omega,
              const int* mask, int mstride)
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kBS)
         int i, j, k;
         node_ijk(G, n, i, j, k);
         T yp, yc;
-        stencil_apply<T, TRANS>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
+        stencil_apply<T, TRANS, M>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
         rp -= yp;
         rc -= yc;
         xn = x[on_ + n];
@@ -171,27 +171,27 @@ __global__ void __launch_bounds__(kBS)
     xo[on_ + n] = V2<T>{op, oc};
 }
 
-template <class T>
-void launch_smooth(const Grid& G, const B4<T>* J, const B4<T>* Dinv,
+template <class T, class M>
+void launch_smooth(const Grid& G, const B4<M>* J, const B4<T>* Dinv,
                    const uint8_t* bc, const V2<T>* b, const V2<T>* x,
                    V2<T>* xo, double omega, int trans, const int* mask,
-                   int mstride, int S, cudaStream_t st)
+                   int mstride, int S, cudaStream_t st, int bs)
 {
     count_launch(1);
-    dim3 grid(nblocks(G.N), S);
+    dim3 grid(nblocks(G.N, bs), S);
     const T w = T(omega);
     if (x == nullptr) {
-        if (trans) k_smooth<T, true, true><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
-        else k_smooth<T, false, true><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+        if (trans) k_smooth<T, M, true, true><<<grid, bs, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+        else k_smooth<T, M, false, true><<<grid, bs, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
     } else {
-        if (trans) k_smooth<T, true, false><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
-        else k_smooth<T, false, false><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+        if (trans) k_smooth<T, M, true, false><<<grid, bs, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
+        else k_smooth<T, M, false, false><<<grid, bs, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride);
     }
 }
 
-template <class T, bool TRANS>
-__global__ void __launch_bounds__(kBS)
-    k_mg_residual(Grid G, const B4<T>* __restrict__ J, const uint8_t* __restrict__ bc,
+template <class T, class M, bool TRANS>
+__global__ void __launch_bounds__(kMaxBS)
+    k_mg_residual(Grid G, const B4<M>* __restrict__ J, const uint8_t* __restrict__ bc,
                   const V2<T>* __restrict__ b, const V2<T>* __restrict__ x,
                   V2<T>* __restrict__ r, const int* mask, int mstride)
 {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kBS)
     int i, j, k;
     node_ijk(G, n, i, j, k);
     T yp, yc;
-    stencil_apply<T, TRANS>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
+    stencil_apply<T, TRANS, M>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
     const V2<T> bv = b[on_ + n];
     T rp = bv.p - yp, rc = bv.c - yc;
     const uint8_t m = bc[n];
@@ -212,15 +212,15 @@ __global__ void __launch_bounds__(kBS)
     r[on_ + n] = V2<T>{rp, rc};
 }
 
-template <class T>
-void launch_mg_residual(const Grid& G, const B4<T>* J, const uint8_t* bc,
+template <class T, class M>
+void launch_mg_residual(const Grid& G, const B4<M>* J, const uint8_t* bc,
                         const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
-                        const int* mask, int mstride, int S, cudaStream_t st)
+                        const int* mask, int mstride, int S, cudaStream_t st, int bs)
 {
     count_launch(1);
-    dim3 grid(nblocks(G.N), S);
-    if (trans) k_mg_residual<T, true><<<grid, kBS, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
-    else k_mg_residual<T, false><<<grid, kBS, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
+    dim3 grid(nblocks(G.N, bs), S);
+    if (trans) k_mg_residual<T, M, true><<<grid, bs, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
+    else k_mg_residual<T, M, false><<<grid, bs, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
 }
 
 // Full weighting = transpose of trilinear interpolation on the vertex-centred
@@ -745,7 +745,7 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
 }
 
 __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
-                               double tol_c, int maxit, int S)
+                               double tol_c, int maxit, int estimate, int S)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
@@ -756,7 +756,24 @@ __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
         k.rn = k.rt;
         k.rfloor = k.rfloor_t;
         k.iters += 1;
-        if ((k.lambda == 1.0 && k.dmax_c <= tol_c && k.dmax_p <= tol_p) || k.rn <= k.rfloor) {
+        // With inexact linear solves Newton converges linearly: from two
+        // consecutive full steps the contraction is theta = |d_k| / |d_{k-1}|
+        // and the remaining error about theta / (1 - theta) |d_k|.  The
+        // iterate is accepted when that estimate, or the last correction
+        // itself, is within tolerance (or R is at its round-off floor).
+        bool small = k.lambda == 1.0 && k.dmax_c <= tol_c && k.dmax_p <= tol_p;
+        if (estimate && !small && k.lambda == 1.0 && k.full_prev && k.dprev_c > 0.0 &&
+            k.dprev_p > 0.0) {
+            const double th = fmax(k.dmax_c / k.dprev_c, k.dmax_p / k.dprev_p);
+            if (th < 0.5) {
+                const double f = th / (1.0 - th);
+                small = f * k.dmax_c <= tol_c && f * k.dmax_p <= tol_p;
+            }
+        }
+        k.full_prev = (k.lambda == 1.0);
+        k.dprev_c = k.dmax_c;
+        k.dprev_p = k.dmax_p;
+        if (small || k.rn <= k.rfloor) {
             k.active = 0;
             k.status = 0;
         } else if (k.iters >= maxit) {
@@ -772,10 +789,10 @@ __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
 }
 
 void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
-                         double tol_c, int maxit, int S, cudaStream_t st)
+                         double tol_c, int maxit, int estimate, int S, cudaStream_t st)
 {
     count_launch(1);
-    k_newton_check<<<nblocks(S, 128), 128, 0, st>>>(ns, ks, tol_p, tol_c, maxit, S);
+    k_newton_check<<<nblocks(S, 128), 128, 0, st>>>(ns, ks, tol_p, tol_c, maxit, estimate, S);
 }
 
 __global__ void k_newton_restore_failed(int N, double* __restrict__ p,
@@ -924,13 +941,14 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
 #define ELDER_INST(T)                                                                    \
     template void launch_spmv<T>(const Grid&, const B4<T>*, const uint8_t*,              \
                                  const V2<T>*, V2<T>*, int, int, const V2<T>*,           \
-                                 double*, const int*, int, int, cudaStream_t);           \
-    template void launch_smooth<T>(const Grid&, const B4<T>*, const B4<T>*,              \
-                                   const uint8_t*, const V2<T>*, const V2<T>*, V2<T>*,   \
-                                   double, int, const int*, int, int, cudaStream_t);     \
-    template void launch_mg_residual<T>(const Grid&, const B4<T>*, const uint8_t*,       \
-                                        const V2<T>*, const V2<T>*, V2<T>*, int,         \
-                                        const int*, int, int, cudaStream_t);             \
+                                 double*, const int*, int, int, cudaStream_t, int);      \
+    template void launch_smooth<T, MgType<T>::type>(                                     \
+        const Grid&, const B4<MgType<T>::type>*, const B4<T>*, const uint8_t*,           \
+        const V2<T>*, const V2<T>*, V2<T>*, double, int, const int*, int, int,           \
+        cudaStream_t, int);                                                              \
+    template void launch_mg_residual<T, MgType<T>::type>(                                \
+        const Grid&, const B4<MgType<T>::type>*, const uint8_t*, const V2<T>*,           \
+        const V2<T>*, V2<T>*, int, const int*, int, int, cudaStream_t, int);             \
     template void launch_restrict<T>(const Grid&, const Grid&, const uint8_t*,           \
                                      const V2<T>*, V2<T>*, const int*, int, int,         \
                                      cudaStream_t);                                      \

@@ -40,14 +40,17 @@ class elder_config(ctypes.Structure):
                 ("ls_max", ctypes.c_int), ("lin_rtol", ctypes.c_double),
                 ("lin_maxit", ctypes.c_int), ("mg_levels", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
-                ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("newton_estimate", ctypes.c_int)]
 
 
 class elder_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("krylov_iters", ctypes.c_int32), ("ls_cuts", ctypes.c_int32),
                 ("res0", ctypes.c_double), ("res", ctypes.c_double),
-                ("fp64_retry", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("fp64_retry", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("salt_mass0", ctypes.c_double), ("salt_mass", ctypes.c_double),
+                ("salt_inflow", ctypes.c_double)]
 
 
 K_SMOOTH, K_SPMV, K_MGRES, K_RESIDUAL, K_JACOBIAN, K_SMOOTH0 = range(6)
@@ -83,6 +86,10 @@ def _load():
     lib.elder_profile.argtypes = [vp, ip]
     lib.elder_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
     lib.elder_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    lib.elder_autotune_result.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_float)]
     lib.elder_residual_norms_static.argtypes = [ctypes.POINTER(elder_config), ip, vp, vp, vp, vp,
                                                 vp, vp, ctypes.c_double, vp, vp, vp]
     del dp
@@ -174,6 +181,16 @@ class Elder:
                                              _stream(stream)))
         return p, c
 
+    def autotune_result(self):
+        b = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+        ms = (ctypes.c_float * 9)()
+        self._check(_lib.elder_autotune_result(self._h, *[ctypes.byref(x) for x in b], ms))
+        cand = (128, 256, 512)
+        names = ("smooth", "spmv", "mg_residual")
+        return {"threads_per_block": dict(zip(names, (x.value for x in b))),
+                "ms_per_launch": {n: dict(zip(cand, [round(ms[3 * i + q], 4) for q in range(3)]))
+                                  for i, n in enumerate(names)}}
+
     def profile(self, on: bool):
         self._check(_lib.elder_profile(self._h, 1 if on else 0))
 
@@ -215,7 +232,8 @@ class Elder:
         st = np.frombuffer(status, dtype=np.int32).copy()
         info = [{"status": s.status, "newton_iters": s.newton_iters,
                  "krylov_iters": s.krylov_iters, "ls_cuts": s.ls_cuts, "res0": s.res0,
-                 "res": s.res, "fp64_retry": s.fp64_retry} for s in stats]
+                 "res": s.res, "fp64_retry": s.fp64_retry, "salt_mass0": s.salt_mass0,
+                 "salt_mass": s.salt_mass, "salt_inflow": s.salt_inflow} for s in stats]
         return st, info
 
     def solve(self, S, phi, K, p, c, dt, rhs, transpose=False, rtol=1e-10, x=None, stream=None):
@@ -275,6 +293,10 @@ def elder_residual_norms_static(cfg: elder_config, S, phi, K, p, c, p_old, c_old
 
 def elder_initial_state(ctx: Elder, *a, **k):
     return ctx.initial_state(*a, **k)
+
+
+def elder_autotune_result(ctx: Elder):
+    return ctx.autotune_result()
 
 
 def elder_profile(ctx: Elder, on: bool):
