@@ -82,7 +82,8 @@ typedef struct {
     int newton_maxit;         /* iteration cap                              */
     double newton_tol_c;      /* converged: max|dc| <= tol_c ...            */
     double newton_tol_p;      /* ... and max|dp| <= tol_p at a full step    */
-    int ls_max;               /* step halvings before a step is forced      */
+    int ls_max;               /* step halvings before the sample's line
+                                 search fails (status LINESEARCH)           */
     /* BiCGStab (Section 5.1) */
     double lin_rtol;          /* relative residual target per Newton solve  */
     int lin_maxit;            /* iteration cap                              */
@@ -107,8 +108,14 @@ typedef struct {
     int32_t ls_cuts;          /* step halvings                              */
     double res0;              /* ||R(u^n)||_2 with Dirichlet data imposed   */
     double res;               /* ||R(u^{n+1})||_2                           */
-    int32_t fp64_retry;       /* 1: ELDER_MIXED failed and the step was
-                                 solved again with the FP64 solver          */
+    int32_t fp64_retry;       /* 0: solved by the configured solver; 1: the
+                                 ELDER_MIXED solve failed and the step was
+                                 solved again from u^n with the FP64 solver;
+                                 2: that failed too and a last FP64 solve
+                                 with robust settings was made (Krylov
+                                 rtol <= 1e-6 keeping its best iterate,
+                                 >= 2000 Krylov and >= 50 Newton
+                                 iterations, >= 16 step halvings)           */
     int32_t pad;
     /* FP64 salt-mass balance of the step: M = sum_e sum_corners phi_e
      * |scv| rho(c) c at u^n and at the returned state, and the salt that
@@ -286,6 +293,55 @@ int elder_residual_norms_static(const elder_config* cfg, int S,
                                 const double* p_old, const double* c_old,
                                 double dt, double* R, double* norms,
                                 void* stream);
+
+/* ------------------------------------------------------------------------
+ * gPC surrogate (Section 3: truncated expansion eq. PCEdecom2, projection
+ * eq. PCEcoef, mean eq. PCEcoef2, variance eq. var, surrogate evaluation
+ * eq. PCEpoint and the exceedance estimate; Appendix A: Legendre basis of
+ * uniform variables on [-1, 1]).  Context-free; errors are reported through
+ * elder_last_error(NULL).
+ * ---------------------------------------------------------------------- */
+
+/* q-point Gauss-Legendre rule on [-1, 1] (host): x[q] ascending, w[q]
+ * summing to 2; exact for polynomials of degree <= 2q - 1.  Newton
+ * iteration on the Legendre recurrence.  1 <= q <= 64, else ELDER_EINVAL. */
+int elder_gauss_legendre(int q, double* x, double* w);
+
+/* Truncated multi-index set J_{M,p} (host): rule 0 total degree <= p (rule
+ * b of Section 3), rule 1 every degree <= p (rule c), rule 2
+ * prod_j (beta_j + 1) <= p + 1 (the reading taken of rule a).  Sorted by
+ * total degree, then lexicographically; the zero index comes first.  Writes
+ * *n_terms; with beta != NULL also the indices, beta[t*M + j], when
+ * capacity >= *n_terms (else ELDER_EINVAL).  1 <= M <= 8, 0 <= p <= 16. */
+int elder_gpc_indices(int M, int p, int rule, int* n_terms, int32_t* beta, int capacity);
+
+/* Expansion coefficients by quadrature projection (FP64):
+ *   coef[t][n] = 0.5^M / Q_t * sum_i w[i] P_{beta_t}(theta_i) u[i][n],
+ *   Q_t = prod_j 1 / (2 beta_tj + 1);
+ * mean[n] = coef[0][n] and var[n] = sum_{t >= 1} Q_t coef[t][n]^2 (nullable).
+ * Device arrays: beta [T][M] int32 with entries in [0, maxdeg] (beta[0] the
+ * zero index for mean/var to be meaningful), theta [Nq][M], w [Nq],
+ * u [Nq][N] (one field per quadrature point, e.g. c of a batched elder_step
+ * run), coef [T][N], mean [N], var [N].  T <= 64, maxdeg <= 16 and
+ * 8 (T Nq + T) <= 200 KiB; stream-ordered, no synchronisation. */
+int elder_gpc_project(int M, int T, const int32_t* beta, int maxdeg, int Nq,
+                      const double* theta, const double* w, int N, const double* u,
+                      double* coef, double* mean, double* var, void* stream);
+
+/* Exceedance probability from the surrogate: for each listed node n
+ * (nodes[k], or n = k for k < n_pts when nodes is NULL), the fraction of the
+ * Ns points theta [Ns][M] at which sum_t coef[t][n] P_{beta_t}(theta) is
+ * above threshold.  The surrogate is evaluated in FP32 (coefficients and
+ * basis values rounded to FP32, FP32 fused multiply-adds in the order of
+ * t); its error is below about 4 T 2^-24 sum_t |coef[t][n]|.  Device arrays:
+ * beta [T][M], coef [T][N] (from elder_gpc_project), nodes [n_pts] int32 or
+ * NULL, theta [Ns][M] (the caller draws the points), p_exceed [n_pts]
+ * output (used as 64-bit counters until the last kernel converts them).
+ * Stream-ordered, no synchronisation. */
+int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N,
+                     const double* coef, int n_pts, const int32_t* nodes, int Ns,
+                     const double* theta, double threshold, double* p_exceed,
+                     void* stream);
 
 #ifdef __cplusplus
 }

@@ -81,6 +81,12 @@ __device__ __forceinline__ void node_ijk(const Grid& G, int n, int& i, int& j,
 
 // Block-wide sum of one double per thread (blockDim.x a multiple of 32,
 // at most 1024); every thread receives the result.
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* smem32)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

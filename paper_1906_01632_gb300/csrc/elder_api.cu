@@ -147,7 +147,8 @@ template <class T> struct Solver : SolverBase {
     std::vector<B4<T>*> Dinv;      // inverse interior diagonal blocks per level
     std::vector<V2<T>*> mb, mx, mx2, mr;  // multigrid vectors per level
     V2<T> *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr,
-          *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr;
+          *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr,
+          *xbest = nullptr;
     double *Ainv = nullptr, *work = nullptr;
     DevFree mem;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (S, trans)
@@ -380,7 +381,8 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap)
         }
     }
     const size_t n0 = (size_t)S * ctx->grids[0].N;
-    for (V2<T>** q : {&sv.x, &sv.r, &sv.rh, &sv.p, &sv.v, &sv.s, &sv.t, &sv.ph, &sv.sh, &sv.b}) {
+    for (V2<T>** q : {&sv.x, &sv.r, &sv.rh, &sv.p, &sv.v, &sv.s, &sv.t, &sv.ph, &sv.sh, &sv.b,
+                      &sv.xbest}) {
         *q = dalloc<V2<T>>(n0);
         sv.mem.add(*q);
     }
@@ -554,7 +556,7 @@ void bicg_iteration(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int m
     const Grid& G = ctx->grids[0];
     const int nb = ctx->nblk0;
     const int bs_mv = ctx->bs[ELDER_K_SPMV];
-    const int nb_mv = nblocks(G.N, bs_mv);  // partials of the stencil products
+    const int nb_mv = nblocks(G.N, 32);  // per-warp partials of the stencil products
     KScal* ks = ctx->ks;
     const int* mask = &ks[0].active;
     launch_bicg_p<T>(G, sv.r, sv.v, sv.p, ks, S, st);
@@ -597,10 +599,11 @@ bool any_krylov_active(elder_ctx* ctx, int S, cudaStream_t st)
 
 // Solve A x = b (or A^T x = b) on the interior system for the samples whose
 // Newton flag is set (all samples when ns == nullptr).  b and the result
-// live in sv.b and sv.x.
+// live in sv.b and sv.x.  With keep_best, a sample that stops without
+// reaching rtol returns its iterate of smallest residual instead of the last.
 template <class T>
 void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
-              const NScal* ns, int S, cudaStream_t st)
+              const NScal* ns, int S, cudaStream_t st, int keep_best = 0)
 {
     const Grid& G = ctx->grids[0];
     k_arm_krylov<<<nblocks(S, 128), 128, 0, st>>>(ctx->ks, ns, S);
@@ -609,6 +612,8 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
     launch_bicg_init<T>(G, ctx->bc[0], sv.b, sv.x, sv.r, sv.rh, sv.p, sv.v, ctx->partial,
                         ctx->ks, S, st);
     launch_bicg_finalize(0, ctx->partial, ctx->nblk0, ctx->ks, rtol, maxit, S, st);
+    if (keep_best)
+        CK(cudaMemsetAsync(sv.xbest, 0, sizeof(V2<T>) * S * G.N, st));
     CKL();
     // The captured finalize kernels bake in rtol and maxit; graphs are keyed
     // on (S, trans) only, so they serve the configured values only, and are
@@ -649,13 +654,45 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
         } else {
             bicg_iteration<T>(ctx, sv, trans, rtol, maxit, S, st);
         }
+        if (keep_best) launch_bicg_keep<T>(G, sv.x, sv.xbest, ctx->ks, 1, S, st);
         CKL();
     }
+    if (keep_best) launch_bicg_keep<T>(G, sv.x, sv.xbest, ctx->ks, 2, S, st);
+}
+
+// Solver settings of one Newton solve (Section 2.3 and Section 5.1).
+struct NewtonSettings {
+    double lin_rtol;
+    int lin_maxit, ls_max, newton_maxit, estimate, keep_best;
+};
+
+NewtonSettings configured_settings(const elder_config& cf)
+{
+    return NewtonSettings{cf.lin_rtol, cf.lin_maxit, cf.ls_max, cf.newton_maxit,
+                          cf.newton_estimate, 0};
+}
+
+// Settings of the last re-solve of a failed sample: a tighter and longer
+// Krylov solve that returns its best iterate, more step halvings and Newton
+// iterations, and only the plain correction-size stop.  Steep initial fronts
+// on rough permeability fields can need hundreds of Krylov iterations per
+// Newton step.
+NewtonSettings robust_settings(const elder_config& cf)
+{
+    NewtonSettings r = configured_settings(cf);
+    r.lin_rtol = std::min(cf.lin_rtol, 1e-6);
+    r.lin_maxit = std::max(20 * cf.lin_maxit, 2000);
+    r.ls_max = std::max(cf.ls_max, 16);
+    r.newton_maxit = std::max(2 * cf.newton_maxit, 50);
+    r.estimate = 0;
+    r.keep_best = 1;
+    return r;
 }
 
 template <class T>
 int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
-              double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st)
+              double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st,
+              const NewtonSettings& set)
 {
     Solver<T>& sv = solver_reserve<T>(ctx, S);
     const elder_config& cf = ctx->cfg;
@@ -687,7 +724,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     launch_norm_finalize(ctx->partial, ctx->partial2, nb, ns, 0, S, st);
     CKL();
 
-    for (int it = 0; it < cf.newton_maxit; ++it) {
+    for (int it = 0; it < set.newton_maxit; ++it) {
         CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         prof_drain(ctx);
@@ -699,8 +736,8 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, na, st);
         if (it == 0) autotune<T>(ctx, sv, S, st);
         launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
-        bicgstab<T>(ctx, sv, 0, cf.lin_rtol, cf.lin_maxit, ns, S, st);
-        for (int ls = 0; ls <= cf.ls_max; ++ls) {
+        bicgstab<T>(ctx, sv, 0, set.lin_rtol, set.lin_maxit, ns, S, st, set.keep_best);
+        for (int ls = 0; ls <= set.ls_max; ++ls) {
             launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
             pi = prof_begin(ctx, st);
             launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
@@ -708,7 +745,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
                             S, st, ctx->edge);
             prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, 8, ctx->n_active_ls, st);
             launch_norm_finalize(ctx->partial, ctx->partial3, nb, ns, 1, S, st);
-            launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, cf.ls_max, S, st);
+            launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, set.ls_max, S, st);
             CKL();
             CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -719,8 +756,8 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
             if (nls == 0) break;
         }
         launch_newton_accept(G, p, c, ctx->pt, ctx->ct, ctx->R, ctx->Rt, ns, S, st);
-        launch_newton_check(ns, ctx->ks, cf.newton_tol_p, cf.newton_tol_c, cf.newton_maxit,
-                            cf.newton_estimate, S, st);
+        launch_newton_check(ns, ctx->ks, cf.newton_tol_p, cf.newton_tol_c, set.newton_maxit,
+                            set.estimate, S, st);
         CKL();
     }
     // samples still active here ran out of Newton iterations
@@ -765,57 +802,81 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     return rc;
 }
 
-// ELDER_MIXED: FP32 multigrid/Krylov first; samples whose Newton iteration
-// fails are packed into batches and solved again from u^n with the FP64
-// solver.
-int step_mixed(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
+// Solves the step again from u^n, in FP64 with the settings `set`, for the
+// samples listed in `idx` (packed into batches of at most 32 samples).  Their
+// entries of st1 and sts are replaced; the iteration counts accumulate and
+// fp64_retry records `tier`.
+void resolve_fp64(elder_ctx* ctx, const std::vector<int>& idx, const double* phi,
+                  const double* K, double* p, double* c, double dt, const NewtonSettings& set,
+                  int tier, std::vector<int32_t>& st1, std::vector<elder_stats>& sts,
+                  cudaStream_t st)
+{
+    const Grid& G = ctx->grids[0];
+    const size_t N = G.N, C = G.C;
+    const int chunk = std::min(32, ctx->cfg.max_samples);
+    if (!ctx->pk) {
+        ctx->pk = dalloc<double>((size_t)chunk * (2 * N + 2 * C));
+        ctx->mem.add(ctx->pk);
+    }
+    double* pk_p = ctx->pk;
+    double* pk_c = pk_p + chunk * N;
+    double* pk_phi = pk_c + chunk * N;
+    double* pk_K = pk_phi + chunk * C;
+    for (size_t b0 = 0; b0 < idx.size(); b0 += chunk) {
+        const int F = (int)std::min<size_t>(chunk, idx.size() - b0);
+        for (int q = 0; q < F; ++q) {
+            const size_t s = idx[b0 + q];
+            CK(cudaMemcpyAsync(pk_p + q * N, p + s * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(pk_c + q * N, c + s * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(pk_phi + q * C, phi + s * C, 8 * C, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(pk_K + q * C, K + s * C, 8 * C, cudaMemcpyDeviceToDevice, st));
+        }
+        std::vector<int32_t> st2(F);
+        std::vector<elder_stats> s2(F);
+        step_impl<double>(ctx, F, pk_phi, pk_K, pk_p, pk_c, dt, st2.data(), s2.data(), st, set);
+        for (int q = 0; q < F; ++q) {
+            const size_t s = idx[b0 + q];
+            CK(cudaMemcpyAsync(p + s * N, pk_p + q * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(c + s * N, pk_c + q * N, 8 * N, cudaMemcpyDeviceToDevice, st));
+            st1[s] = st2[q];
+            s2[q].newton_iters += sts[s].newton_iters;
+            s2[q].krylov_iters += sts[s].krylov_iters;
+            s2[q].ls_cuts += sts[s].ls_cuts;
+            s2[q].fp64_retry = tier;
+            sts[s] = s2[q];
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+}
+
+// One implicit step of S samples.  ELDER_MIXED runs the FP32 multigrid and
+// Krylov solver first and solves the samples whose Newton iteration fails
+// again from u^n in FP64 (tier 1); samples that still fail (in either
+// precision) get a last FP64 solve with robust settings (tier 2).
+int step_tiers(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
                double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st)
 {
     std::vector<int32_t> st1(S);
     std::vector<elder_stats> sts(S);
-    step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st);
-    std::vector<int> failed;
-    for (int s = 0; s < S; ++s)
-        if (st1[s] != 0) failed.push_back(s);
-    if (!failed.empty()) {
-        const Grid& G = ctx->grids[0];
-        const size_t N = G.N, C = G.C;
-        const int chunk = std::min(32, ctx->cfg.max_samples);
-        if (!ctx->pk) {
-            ctx->pk = dalloc<double>((size_t)chunk * (2 * N + 2 * C));
-            ctx->mem.add(ctx->pk);
-        }
-        double* pk_p = ctx->pk;
-        double* pk_c = pk_p + chunk * N;
-        double* pk_phi = pk_c + chunk * N;
-        double* pk_K = pk_phi + chunk * C;
-        for (size_t b0 = 0; b0 < failed.size(); b0 += chunk) {
-            const int F = (int)std::min<size_t>(chunk, failed.size() - b0);
-            for (int q = 0; q < F; ++q) {
-                const size_t s = failed[b0 + q];
-                CK(cudaMemcpyAsync(pk_p + q * N, p + s * N, 8 * N, cudaMemcpyDeviceToDevice, st));
-                CK(cudaMemcpyAsync(pk_c + q * N, c + s * N, 8 * N, cudaMemcpyDeviceToDevice, st));
-                CK(cudaMemcpyAsync(pk_phi + q * C, phi + s * C, 8 * C, cudaMemcpyDeviceToDevice,
-                                   st));
-                CK(cudaMemcpyAsync(pk_K + q * C, K + s * C, 8 * C, cudaMemcpyDeviceToDevice, st));
-            }
-            std::vector<int32_t> st2(F);
-            std::vector<elder_stats> s2(F);
-            step_impl<double>(ctx, F, pk_phi, pk_K, pk_p, pk_c, dt, st2.data(), s2.data(), st);
-            for (int q = 0; q < F; ++q) {
-                const size_t s = failed[b0 + q];
-                CK(cudaMemcpyAsync(p + s * N, pk_p + q * N, 8 * N, cudaMemcpyDeviceToDevice, st));
-                CK(cudaMemcpyAsync(c + s * N, pk_c + q * N, 8 * N, cudaMemcpyDeviceToDevice, st));
-                st1[s] = st2[q];
-                s2[q].newton_iters += sts[s].newton_iters;
-                s2[q].krylov_iters += sts[s].krylov_iters;
-                s2[q].ls_cuts += sts[s].ls_cuts;
-                s2[q].fp64_retry = 1;
-                sts[s] = s2[q];
-            }
-        }
-        CK(cudaStreamSynchronize(st));
+    const NewtonSettings conf = configured_settings(ctx->cfg);
+    const bool mixed = ctx->cfg.precision == ELDER_MIXED;
+    if (mixed)
+        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf);
+    else
+        step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf);
+    auto failed = [&]() {
+        std::vector<int> f;
+        for (int s = 0; s < S; ++s)
+            if (st1[s] != 0) f.push_back(s);
+        return f;
+    };
+    std::vector<int> f = failed();
+    if (!f.empty() && mixed) {
+        resolve_fp64(ctx, f, phi, K, p, c, dt, conf, 1, st1, sts, st);
+        f = failed();
     }
+    if (!f.empty())
+        resolve_fp64(ctx, f, phi, K, p, c, dt, robust_settings(ctx->cfg), 2, st1, sts, st);
     int rc = ELDER_OK;
     for (int s = 0; s < S; ++s) {
         if (status) status[s] = st1[s];
@@ -1016,8 +1077,8 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
             *q = dalloc<V2<double>>(nN);
             ctx->mem.add(*q);
         }
-        // sized for the smallest autotuned block (most partials per sample)
-        ctx->partial = dalloc<double>((size_t)S * 2 * nblocks(G.N, kMinBS));
+        // the stencil products write one partial per warp of 32 nodes
+        ctx->partial = dalloc<double>((size_t)S * 2 * nblocks(G.N, 32));
         ctx->partial2 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
         ctx->partial3 = dalloc<double>((size_t)S * 3 * ctx->nblk0);
         ctx->edge = dalloc<E4>((size_t)S * 3 * G.N);
@@ -1145,10 +1206,7 @@ int elder_step(elder_ctx* ctx, int S, const double* phi, const double* K, double
         return ELDER_EINVAL;
     }
     try {
-        if (ctx->cfg.precision == ELDER_MIXED)
-            return step_mixed(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream);
-        return step_impl<double>(ctx, S, phi, K, p, c, dt, status, stats,
-                                 (cudaStream_t)stream);
+        return step_tiers(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream);
     } catch (const Fail& f) {
         return set_error(ctx, f);
     }
@@ -1293,11 +1351,7 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
         local.add(cur);
         int32_t stat = 0;
         auto fwd_step = [&](double* pc) -> int {
-            const int rc = (ctx->cfg.precision == ELDER_MIXED)
-                               ? step_mixed(ctx, 1, phi, K, pc, pc + N, dt, &stat, nullptr, st)
-                               : step_impl<double>(ctx, 1, phi, K, pc, pc + N, dt, &stat,
-                                                   nullptr, st);
-            return rc;
+            return step_tiers(ctx, 1, phi, K, pc, pc + N, dt, &stat, nullptr, st);
         };
         // forward sweep with checkpoints
         CK(cudaMemcpyAsync(cur, p0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));

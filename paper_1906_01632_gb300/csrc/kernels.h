@@ -9,7 +9,9 @@ namespace elder {
 struct KScal {
     double rho, rho_old, alpha, omega;
     double bn2, rn2;
-    int active, iters, status, pad;
+    double best_rn2;             // smallest ||r||^2 seen (x = 0 counts)
+    int active, iters, status;
+    int improved;                // the last iteration lowered best_rn2
 };
 
 // Per-sample Newton state (Section 2.3: Newton with line search).
@@ -153,6 +155,12 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
                           const double* pt, const double* ct,
                           V2<double>* R, const V2<double>* Rt,
                           const NScal* ns, int S, cudaStream_t st);
+// Keeps the iterate of smallest residual: copies x into xbest for the
+// samples whose last iteration improved it (keep == 1), or x <- xbest for
+// the samples that did not converge (keep == 2).
+template <class T>
+void launch_bicg_keep(const Grid& G, V2<T>* x, V2<T>* xbest, const KScal* ks, int keep, int S,
+                      cudaStream_t st);
 void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
                          double tol_c, int maxit, int estimate, int S, cudaStream_t st);
 void launch_newton_restore_failed(const Grid& G, double* p, double* c,

@@ -72,7 +72,6 @@ __global__ void __launch_bounds__(kMaxBS)
            const V2<T>* __restrict__ a, double* __restrict__ partial,
            const int* mask, int mstride)
 {
-    __shared__ double red[32];
     const int s = blockIdx.y;
     if (!on(mask, mstride, s)) return;
     const size_t on_ = (size_t)s * G.N;
@@ -98,13 +97,17 @@ __global__ void __launch_bounds__(kMaxBS)
         }
         if (MODE == 2) d1 = (double)yp * (double)yp + (double)yc * (double)yc;
     }
+    // One partial per warp of 32 nodes, so the sums do not depend on the
+    // (tuned) block size: the inner products are bitwise reproducible.
     if (MODE == 1 || MODE == 2) {
-        const double t0 = block_sum(d0, red);
-        if (threadIdx.x == 0) partial[((size_t)s * 2 + 0) * gridDim.x + blockIdx.x] = t0;
-    }
-    if (MODE == 2) {
-        const double t1 = block_sum(d1, red);
-        if (threadIdx.x == 0) partial[((size_t)s * 2 + 1) * gridDim.x + blockIdx.x] = t1;
+        const int W = (G.N + 31) >> 5;
+        const int wg = n >> 5;
+        const double t0 = warp_sum(d0);
+        const double t1 = (MODE == 2) ? warp_sum(d1) : 0.0;
+        if ((threadIdx.x & 31) == 0 && wg < W) {
+            partial[((size_t)s * 2 + 0) * W + wg] = t0;
+            if (MODE == 2) partial[((size_t)s * 2 + 1) * W + wg] = t1;
+        }
     }
 }
 
@@ -516,6 +519,8 @@ __global__ void k_bicg_finalize(int stage, const double* __restrict__ partial,
         k.omega = 1.0;
         k.iters = 0;
         k.status = 0;
+        k.best_rn2 = a0;
+        k.improved = 0;
         if (!(a0 > 0.0)) {
             k.active = 0;
             if (!isfinite(a0)) k.status = ELDER_SAMPLE_NONFINITE_;
@@ -534,6 +539,8 @@ __global__ void k_bicg_finalize(int stage, const double* __restrict__ partial,
         k.rho_old = k.rho;
         k.rho = a1;
         k.iters += 1;
+        k.improved = a0 < k.best_rn2;
+        if (k.improved) k.best_rn2 = a0;
         if (!isfinite(a0)) {
             k.active = 0;
             k.status = ELDER_SAMPLE_NONFINITE_;
@@ -556,6 +563,31 @@ void launch_bicg_finalize(int stage, const double* partial, int nblk,
 {
     count_launch(1);
     k_bicg_finalize<<<S, 128, 0, st>>>(stage, partial, nblk, ks, rtol, maxit);
+}
+
+template <class T>
+__global__ void k_bicg_keep(int N, V2<T>* __restrict__ x, V2<T>* __restrict__ xbest,
+                            const KScal* ks, int keep)
+{
+    const int s = blockIdx.y;
+    const KScal& k = ks[s];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const size_t q = (size_t)s * N + n;
+    if (keep == 1) {
+        if (k.improved) xbest[q] = x[q];
+    } else if (k.status != 0 || k.active) {
+        x[q] = xbest[q];
+    }
+}
+
+template <class T>
+void launch_bicg_keep(const Grid& G, V2<T>* x, V2<T>* xbest, const KScal* ks, int keep, int S,
+                      cudaStream_t st)
+{
+    count_launch(1);
+    dim3 grid(nblocks(G.N), S);
+    k_bicg_keep<T><<<grid, kBS, 0, st>>>(G.N, x, xbest, ks, keep);
 }
 
 // ---------------------------------------------------------------------------
@@ -974,7 +1006,9 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
                                          const V2<T>*, double*, double*, double*,        \
                                          const NScal*, int, cudaStream_t);               \
     template void launch_axpy_mask<T>(const Grid&, const uint8_t*, const V2<T>*, V2<T>*, \
-                                      double, int, int, cudaStream_t);
+                                      double, int, int, cudaStream_t);                   \
+    template void launch_bicg_keep<T>(const Grid&, V2<T>*, V2<T>*, const KScal*, int,    \
+                                      int, cudaStream_t);
 ELDER_INST(double)
 ELDER_INST(float)
 #undef ELDER_INST

@@ -92,6 +92,12 @@ def _load():
                                           ctypes.POINTER(ctypes.c_float)]
     lib.elder_residual_norms_static.argtypes = [ctypes.POINTER(elder_config), ip, vp, vp, vp, vp,
                                                 vp, vp, ctypes.c_double, vp, vp, vp]
+    lib.elder_gauss_legendre.argtypes = [ip, dp, dp]
+    lib.elder_gpc_indices.argtypes = [ip, ip, ip, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int32), ip]
+    lib.elder_gpc_project.argtypes = [ip, ip, vp, ip, ip, vp, vp, ip, vp, vp, vp, vp, vp]
+    lib.elder_gpc_exceed.argtypes = [ip, ip, vp, ip, ip, vp, ip, vp, ip, vp, ctypes.c_double,
+                                     vp, vp]
     del dp
     return lib
 
@@ -289,6 +295,77 @@ def elder_residual_norms_static(cfg: elder_config, S, phi, K, p, c, p_old, c_old
     if rc != ELDER_OK:
         raise ElderError(rc, _lib.elder_last_error(None).decode())
     return R, norms
+
+
+def _static_check(rc):
+    if rc != ELDER_OK:
+        raise ElderError(rc, _lib.elder_last_error(None).decode())
+
+
+def _iptr(t: torch.Tensor | None, what: str):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32
+            and t.is_contiguous()):
+        raise ValueError(f"{what}: must be a contiguous int32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+GPC_RULES = {"total": 0, "tensor": 1, "hyperbolic": 2}
+
+
+def elder_gauss_legendre(q: int):
+    """q-point Gauss-Legendre rule on [-1, 1] (host numpy arrays x, w)."""
+    x = np.zeros(q)
+    w = np.zeros(q)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _static_check(_lib.elder_gauss_legendre(q, x.ctypes.data_as(dp), w.ctypes.data_as(dp)))
+    return x, w
+
+
+def elder_gpc_indices(M: int, p: int, rule: str = "total") -> np.ndarray:
+    """Truncated multi-index set J_{M,p} as an int32 [T, M] host array."""
+    n = ctypes.c_int(0)
+    _static_check(_lib.elder_gpc_indices(M, p, GPC_RULES[rule], ctypes.byref(n), None, 0))
+    beta = np.zeros((n.value, M), dtype=np.int32)
+    _static_check(_lib.elder_gpc_indices(M, p, GPC_RULES[rule], ctypes.byref(n),
+                                         beta.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         n.value))
+    return beta
+
+
+def elder_gpc_project(beta: torch.Tensor, theta: torch.Tensor, w: torch.Tensor, u: torch.Tensor,
+                      coef=None, mean=None, var=None, stream=None):
+    """Expansion coefficients [T, N] (FP64) plus mean and variance [N] from the
+    fields u [Nq, N] at the quadrature points theta [Nq, M] with weights w."""
+    T, M = beta.shape
+    Nq, N = u.shape
+    maxdeg = int(beta.max().item()) if beta.numel() else 0
+    dev = u.device
+    coef = coef if coef is not None else torch.empty(T, N, dtype=torch.float64, device=dev)
+    mean = mean if mean is not None else torch.empty(N, dtype=torch.float64, device=dev)
+    var = var if var is not None else torch.empty(N, dtype=torch.float64, device=dev)
+    _static_check(_lib.elder_gpc_project(M, T, _iptr(beta, "beta"), maxdeg, Nq,
+                                         _ptr(theta, "theta"), _ptr(w, "w"), N, _ptr(u, "u"),
+                                         _ptr(coef, "coef"), _ptr(mean, "mean"),
+                                         _ptr(var, "var"), _stream(stream)))
+    return coef, mean, var
+
+
+def elder_gpc_exceed(beta: torch.Tensor, coef: torch.Tensor, theta: torch.Tensor,
+                     threshold: float, nodes: torch.Tensor | None = None, out=None, stream=None):
+    """P(u_hat > threshold) per node from the surrogate at the sample points
+    theta [Ns, M] (all N nodes, or the int32 node list)."""
+    T, M = beta.shape
+    N = coef.shape[1]
+    n_pts = N if nodes is None else nodes.numel()
+    maxdeg = int(beta.max().item()) if beta.numel() else 0
+    out = out if out is not None else torch.empty(n_pts, dtype=torch.float64, device=coef.device)
+    _static_check(_lib.elder_gpc_exceed(M, T, _iptr(beta, "beta"), maxdeg, N, _ptr(coef, "coef"),
+                                        n_pts, _iptr(nodes, "nodes"), theta.shape[0],
+                                        _ptr(theta, "theta"), float(threshold), _ptr(out, "out"),
+                                        _stream(stream)))
+    return out
 
 
 def elder_initial_state(ctx: Elder, *a, **k):
