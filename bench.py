@@ -50,19 +50,31 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-workers", type=int, default=0)
+    ap.add_argument("--fields", choices=["sobol", "paper3rv"], default="sobol",
+                    help="sobol: the cosine porosity field at scrambled-Sobol points; paper3rv: "
+                         "the paper's parallelepiped field at Halton points")
+    ap.add_argument("--dt-yr", type=float, default=1.0 / 12.0)
+    ap.add_argument("--no-gpc", action="store_true", help="skip the gPC kernel timings")
+    ap.add_argument("--smoother", choices=["jacobi", "zline"], default="jacobi")
     return ap.parse_args()
 
 
 def workload_config(a):
     nx, ny, nz = a.grid
+    fields = ("scrambled Sobol (torch SobolEngine seed 0) -> phi (cosine field), Kozeny-Carman K"
+              if a.fields == "sobol" else
+              "Halton points (bases 2,3,5) -> the paper's parallelepiped porosity field, "
+              "Kozeny-Carman K")
+    tag = "qmc" if a.fields == "sobol" else "paper3rv-halton"
     return {
-        "workload": f"elder3d-box-{nx}x{ny}x{nz}-qmc{a.samples}",
+        "workload": f"elder3d-box-{nx}x{ny}x{nz}-{tag}{a.samples}",
         "grid_cells": [nx, ny, nz],
         "nodes_per_sample": (nx + 1) * (ny + 1) * (nz + 1),
         "samples_per_gpu": a.samples,
-        "dt_yr": 1.0 / 12.0,
+        "dt_yr": a.dt_yr,
         "precision": a.precision,
-        "fields": "scrambled Sobol (torch SobolEngine seed 0) -> phi (cosine field), Kozeny-Carman K",
+        "smoother": a.smoother,
+        "fields": fields,
         "l2": "no flush: per-step working set (Jacobians of all levels, vectors) ~10 GB >> 129 MB L2",
         "parallelism": f"samples sharded, dp{a.gpus}",
     }
@@ -233,13 +245,15 @@ def run_ours(a):
 
     nx, ny, nz = a.grid
     S = a.samples
-    dt = YEAR / 12
+    dt = YEAR * a.dt_yr
     prec = E.ELDER_MIXED if a.precision == "mixed" else E.ELDER_FP64
-    ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=prec))
+    smoother = E.ELDER_SMOOTH_ZLINE if a.smoother == "zline" else E.ELDER_SMOOTH_JACOBI
+    ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=prec,
+                                                smoother=smoother))
     N, C = ctx.N, ctx.C
-    xi_all = I.sobol_xi(S * world, seed=0)
+    xi_all = I.sobol_xi(S * world, seed=0) if a.fields == "sobol" else I.halton_xi(S * world)
     xi = torch.tensor(xi_all[rank * S:(rank + 1) * S].ravel(), dtype=torch.float64, device=dev)
-    phi, K = ctx.fields(S, 0, xi)
+    phi, K = ctx.fields(S, 0 if a.fields == "sobol" else 2, xi)
     p, c = ctx.initial_state(S, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -273,7 +287,7 @@ def run_ours(a):
     for _ in range(a.steps):
         st, info, _ = bench_step(p, c)
         fails += int((st != 0).sum())
-        retries += sum(x["fp64_retry"] for x in info)
+        retries += sum(1 for x in info if x["fp64_retry"])
         newton.append(np.mean([x["newton_iters"] for x in info]))
         krylov.append(np.mean([x["krylov_iters"] for x in info]))
     e1.record(stream)
@@ -367,7 +381,8 @@ def run_ours(a):
     # ---- FP64 path on the same workload and state ---------------------------
     fp64 = None
     if not a.no_fp64 and a.precision == "mixed":
-        ctx64 = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=E.ELDER_FP64))
+        ctx64 = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S,
+                                                      precision=E.ELDER_FP64, smoother=smoother))
         p64, c64 = p.clone(), c.clone()
         pm, cm = p.clone(), c.clone()
         ctx64.step(S, phi, K, p64, c64, dt)  # warm-up (graph capture) from the same state
@@ -388,6 +403,10 @@ def run_ours(a):
                 "mixed_vs_fp64_max_abs_c_same_state": diff}
         ctx64.destroy()
 
+    gpc = None
+    if rank == 0 and not a.no_gpc and S >= 1:
+        gpc = gpc_timings(E, torch, c.reshape(S, N), stream)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a)
@@ -399,7 +418,7 @@ def run_ours(a):
                 "dtype": "f64+f32" if a.precision == "mixed" else "f64",
                 "data": "synthetic", "config": workload_config(a), "clocks": clk,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-                "fp64_path": fp64, "kernel_classes": classes,
+                "fp64_path": fp64, "gpc": gpc, "kernel_classes": classes,
                 "iterations": {"newton_per_step": float(np.mean(newton)),
                                "krylov_per_step": float(np.mean(krylov)), "failed_samples": fails,
                                "fp64_retries": retries},
@@ -408,6 +427,57 @@ def run_ours(a):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x FMA x max SM clock (GHz)
+
+
+def gpc_timings(E, torch, cfield, stream):
+    """Kernel timings of the gPC surrogate (Section 3) on this GPU: FP64
+    projection of 125 fields (the 5^3 Gauss-Legendre points, total degree
+    <= 4, 35 terms) onto every node, and the FP32 surrogate evaluated
+    at 10^6 uniform points per node for P(c > 0.5).  The bench's current
+    concentration fields stand in for the quadrature-point fields (the
+    kernels' cost does not depend on the values)."""
+    S, N = cfield.shape
+    M, p, q, Ns = 3, 4, 5, 1_000_000
+    x, w1 = E.elder_gauss_legendre(q)
+    import numpy as np
+    g = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3)[:, ::-1].copy()
+    wq = np.prod(np.stack(np.meshgrid(w1, w1, w1, indexing="ij"), -1).reshape(-1, 3), 1)
+    Nq = q ** M
+    dev = cfield.device
+    beta = torch.tensor(E.elder_gpc_indices(M, p), device=dev)
+    T = beta.shape[0]
+    theta_q = torch.tensor(g, dtype=torch.float64, device=dev)
+    wt = torch.tensor(wq, dtype=torch.float64, device=dev)
+    u = cfield[torch.arange(Nq, device=dev) % S].contiguous()
+    gen = torch.Generator(device=dev).manual_seed(5)
+    theta_s = (torch.rand(Ns, M, generator=gen, dtype=torch.float64, device=dev) * 2 - 1).contiguous()
+    coef, mean, var = E.elder_gpc_project(beta, theta_q, wt, u)
+    out = E.elder_gpc_exceed(beta, coef, theta_s, 0.5)
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn, flops, unit_peak in (
+            ("project", lambda: E.elder_gpc_project(beta, theta_q, wt, u, coef, mean, var),
+             2.0 * T * Nq * N, ("FP64 nominal", FP64_NOMINAL_GFLOPS)),
+            ("exceed", lambda: E.elder_gpc_exceed(beta, coef, theta_s, 0.5, out=out),
+             2.0 * T * Ns * N, ("FP32 nominal", FP32_NOMINAL_GFLOPS))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gf = flops / 1e9 / (ms / 1e3)
+        res[name] = {"ms": ms, "GFLOP/s": gf, "bound": "alu", "peak_GFLOP/s": unit_peak[1],
+                     "peak_source": unit_peak[0], "frac": gf / unit_peak[1]}
+    res["config"] = {"M": M, "order": p, "terms": T, "quadrature_points": Nq, "nodes": N,
+                     "surrogate_samples": Ns}
+    return res
 
 
 def E_model_bytes(cls, tsize, nx, ny, nz):

@@ -60,6 +60,9 @@ enum {
 
 enum { ELDER_FP64 = 0, ELDER_MIXED = 1 };
 
+/* multigrid smoothers (Section 5.1) */
+enum { ELDER_SMOOTH_JACOBI = 0, ELDER_SMOOTH_ZLINE = 1 };
+
 /* Boundary-condition sets (Section 2.1 and the caption of Fig. 1):
  *  0 benchmark: c=1 on the closed top square [Lx/4,3Lx/4]x[Ly/4,3Ly/4],
  *    c=0 on the bottom, p=0 at the four top corners; no-flow elsewhere;
@@ -98,6 +101,12 @@ typedef struct {
     int newton_estimate;      /* also accept when the linear-convergence
                                  error estimate theta/(1-theta)|d| is within
                                  the Newton tolerances                      */
+    int smoother;             /* ELDER_SMOOTH_JACOBI: damped 2x2 block
+                                 Jacobi; ELDER_SMOOTH_ZLINE: damped block
+                                 Jacobi over vertical grid lines (block
+                                 tridiagonal solve per line, nz <= 128).
+                                 The robust re-solve of failed samples
+                                 always uses the z-line smoother.           */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */
@@ -112,8 +121,9 @@ typedef struct {
                                  ELDER_MIXED solve failed and the step was
                                  solved again from u^n with the FP64 solver;
                                  2: that failed too and a last FP64 solve
-                                 with robust settings was made (Krylov
-                                 rtol <= 1e-6 keeping its best iterate,
+                                 with robust settings was made (z-line
+                                 smoother, Krylov rtol <= 1e-6 keeping its
+                                 best iterate,
                                  >= 2000 Krylov and >= 50 Newton
                                  iterations, >= 16 step halvings)           */
     int32_t pad;

@@ -148,7 +148,7 @@ template <class T> struct Solver : SolverBase {
     std::vector<V2<T>*> mb, mx, mx2, mr;  // multigrid vectors per level
     V2<T> *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr,
           *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr,
-          *xbest = nullptr;
+          *xbest = nullptr, *xd = nullptr;
     double *Ainv = nullptr, *work = nullptr;
     DevFree mem;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (S, trans)
@@ -210,6 +210,7 @@ struct elder_ctx {
     int nblk0 = 0;
     // threads per block of the autotuned kernel classes (indexed by ELDER_K_*)
     int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, kBS};
+    int smoother_now = ELDER_SMOOTH_JACOBI;  // smoother of the solve in progress
     bool tuned[2] = {false, false};    // per precision (FP64, FP32)
     float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
     ~elder_ctx()
@@ -382,7 +383,7 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap)
     }
     const size_t n0 = (size_t)S * ctx->grids[0].N;
     for (V2<T>** q : {&sv.x, &sv.r, &sv.rh, &sv.p, &sv.v, &sv.s, &sv.t, &sv.ph, &sv.sh, &sv.b,
-                      &sv.xbest}) {
+                      &sv.xbest, &sv.xd}) {
         *q = dalloc<V2<T>>(n0);
         sv.mem.add(*q);
     }
@@ -465,14 +466,21 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     using M = typename Solver<T>::M;
     const int na = ctx->n_active_k;
     const int bs_sm = ctx->bs[ELDER_K_SMOOTH], bs_mr = ctx->bs[ELDER_K_MGRES];
+    const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
+    auto sweep = [&](const V2<T>* xin, V2<T>* xout) {
+        if (line)
+            launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout,
+                                      cf.omega, trans, mask, KSTRIDE, S, st);
+        else
+            launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout, cf.omega,
+                                trans, mask, KSTRIDE, S, st, bs_sm);
+    };
     int pi = prof_begin(ctx, st);
-    launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, nullptr, cur, cf.omega, trans,
-                        mask, KSTRIDE, S, st);
+    sweep(nullptr, cur);
     prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), sizeof(M), na, st);
     for (int q = 1; q < nu1; ++q) {
         pi = prof_begin(ctx, st);
-        launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
-                            mask, KSTRIDE, S, st, bs_sm);
+        sweep(cur, oth);
         prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), sizeof(M), na, st);
         std::swap(cur, oth);
     }
@@ -487,8 +495,7 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
                           S, st);
     for (int q = 0; q < nu2; ++q) {
         pi = prof_begin(ctx, st);
-        launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, cur, oth, cf.omega, trans,
-                            mask, KSTRIDE, S, st, bs_sm);
+        sweep(cur, oth);
         prof_end(ctx, pi, ELDER_K_SMOOTH, G, sizeof(T), sizeof(M), na, st);
         std::swap(cur, oth);
     }
@@ -619,7 +626,8 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
     // on (S, trans) only, so they serve the configured values only, and are
     // bypassed while per-launch events are recorded.
     const bool use_exec = ctx->cfg.use_graphs != 0 && !ctx->prof.on &&
-                          rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit;
+                          rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit &&
+                          ctx->smoother_now == ctx->cfg.smoother;
     cudaGraphExec_t exec = nullptr;
     long long per_replay = 0;
     if (use_exec) {
@@ -663,23 +671,24 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
 // Solver settings of one Newton solve (Section 2.3 and Section 5.1).
 struct NewtonSettings {
     double lin_rtol;
-    int lin_maxit, ls_max, newton_maxit, estimate, keep_best;
+    int lin_maxit, ls_max, newton_maxit, estimate, keep_best, smoother;
 };
 
 NewtonSettings configured_settings(const elder_config& cf)
 {
     return NewtonSettings{cf.lin_rtol, cf.lin_maxit, cf.ls_max, cf.newton_maxit,
-                          cf.newton_estimate, 0};
+                          cf.newton_estimate, 0, cf.smoother};
 }
 
-// Settings of the last re-solve of a failed sample: a tighter and longer
-// Krylov solve that returns its best iterate, more step halvings and Newton
-// iterations, and only the plain correction-size stop.  Steep initial fronts
-// on rough permeability fields can need hundreds of Krylov iterations per
-// Newton step.
+// Settings of the last re-solve of a failed sample: the z-line smoother, a
+// tighter and longer Krylov solve that returns its best iterate, more step
+// halvings and Newton iterations, and only the plain correction-size stop.
+// Steep initial fronts on rough permeability fields make the point smoother
+// diverge locally and the Krylov solve stall.
 NewtonSettings robust_settings(const elder_config& cf)
 {
     NewtonSettings r = configured_settings(cf);
+    r.smoother = ELDER_SMOOTH_ZLINE;
     r.lin_rtol = std::min(cf.lin_rtol, 1e-6);
     r.lin_maxit = std::max(20 * cf.lin_maxit, 2000);
     r.ls_max = std::max(cf.ls_max, 16);
@@ -687,6 +696,14 @@ NewtonSettings robust_settings(const elder_config& cf)
     r.estimate = 0;
     r.keep_best = 1;
     return r;
+}
+
+// Sample 0's Krylov solve ended by reaching its tolerance.
+bool krylov_converged(elder_ctx* ctx, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(ctx->h_ks, ctx->ks, sizeof(KScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return ctx->h_ks[0].status == 0 && !ctx->h_ks[0].active;
 }
 
 template <class T>
@@ -736,7 +753,9 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, na, st);
         if (it == 0) autotune<T>(ctx, sv, S, st);
         launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
+        ctx->smoother_now = set.smoother;
         bicgstab<T>(ctx, sv, 0, set.lin_rtol, set.lin_maxit, ns, S, st, set.keep_best);
+        ctx->smoother_now = cf.smoother;
         for (int ls = 0; ls <= set.ls_max; ++ls) {
             launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
             pi = prof_begin(ctx, st);
@@ -908,15 +927,16 @@ int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const 
     // Dirichlet rows of J are identity rows (R = u - u_D).
     // forward:   x_D = rhs_D, interior rhs_I - J_ID x_D
     // transpose: interior J_II^T y_I = rhs_I, then y_D = rhs_D - J_ID^T y_I
+    // (x_D is kept in sv.xd: the multigrid vectors are overwritten by the solve)
     if (!trans) {
-        launch_axpy_mask<T>(G, ctx->bc[0], bT, sv.mr[0], 1.0, 0, S, st);  // mr = b on D
-        launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.mr[0], sv.mx2[0], 0, 0, nullptr, nullptr,
+        launch_axpy_mask<T>(G, ctx->bc[0], bT, sv.xd, 1.0, 0, S, st);     // xd = b on D
+        launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.xd, sv.mx2[0], 0, 0, nullptr, nullptr,
                        nullptr, 0, S, st);                                 // J x_D (interior)
         launch_axpy_mask<T>(G, ctx->bc[0], sv.mx2[0], bT, -1.0, 2, S, st);
     }
     bicgstab<T>(ctx, sv, trans, rtol, ctx->cfg.lin_maxit, nullptr, S, st);
     if (!trans) {
-        launch_axpy_mask<T>(G, ctx->bc[0], sv.mr[0], sv.x, 1.0, 1, S, st);
+        launch_axpy_mask<T>(G, ctx->bc[0], sv.xd, sv.x, 1.0, 1, S, st);
     } else {
         // (A^T y_I) on Dirichlet rows, unmasked
         launch_spmv<T>(G, sv.J0, ctx->bc[0], sv.x, sv.mx2[0], 1, 3, nullptr, nullptr,
@@ -994,6 +1014,7 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->use_graphs = 1;
     cfg->autotune = 1;
     cfg->newton_estimate = 1;
+    cfg->smoother = ELDER_SMOOTH_JACOBI;
     return ELDER_OK;
 }
 
@@ -1014,8 +1035,13 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
     if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.max_samples < 1 || !(c.Lx > 0) ||
         !(c.Ly > 0) || !(c.Lz > 0) || !(c.mu > 0) || c.bc_mode < 0 || c.bc_mode > 3 ||
         (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
-        c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0) {
+        c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0 ||
+        (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE)) {
         g_create_error = "invalid elder_config";
+        return ELDER_EINVAL;
+    }
+    if (c.smoother == ELDER_SMOOTH_ZLINE && c.nz + 1 > kMaxLine) {
+        g_create_error = "the z-line smoother needs nz <= 128";
         return ELDER_EINVAL;
     }
     if ((c.bc_mode == 0 || c.bc_mode == 1) && (c.nx % 4 || c.ny % 4)) {
@@ -1024,6 +1050,7 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
     }
     std::unique_ptr<elder_ctx> ctx(new elder_ctx());
     ctx->cfg = c;
+    ctx->smoother_now = c.smoother;
     try {
         CK(cudaGetDevice(&ctx->device));
         // hierarchy: halve while all three counts are even (and the top square
@@ -1404,6 +1431,19 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
                                    st));
                 bicgstab<double>(ctx, sv, 1, 1e-12, std::max(ctx->cfg.lin_maxit, 400), nullptr,
                                  1, st);
+                if (!krylov_converged(ctx, st)) {
+                    // the transposed system of a step on a steep front: again
+                    // with the z-line smoother and a longer solve
+                    ctx->smoother_now = ELDER_SMOOTH_ZLINE;
+                    bicgstab<double>(ctx, sv, 1, 1e-12, std::max(20 * ctx->cfg.lin_maxit, 4000),
+                                     nullptr, 1, st, 1);
+                    ctx->smoother_now = ctx->cfg.smoother;
+                    if (!krylov_converged(ctx, st)) {
+                        rc_all = ELDER_ENOTCONV;
+                        ctx->err = "elder_grad: adjoint solve of step " + std::to_string(n) +
+                                   " did not reach its tolerance";
+                    }
+                }
                 launch_adjoint_theta(G, ph, ctx->bc[0], phi, K, un, un + N, uo + N, sv.x,
                                      dJ_dphi, dJ_dK, st);
                 if (n > 1)

@@ -155,6 +155,15 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
                           const double* pt, const double* ct,
                           V2<double>* R, const V2<double>* Rt,
                           const NScal* ns, int S, cudaStream_t st);
+// Damped z-line block-Jacobi sweep (x == nullptr: zero initial guess);
+// lines of at most kMaxLine nodes.
+constexpr int kMaxLine = 129;
+constexpr int kLineBS = 128;
+template <class T, class M>
+void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
+                         const V2<T>* b, const V2<T>* x, V2<T>* xo, double omega, int trans,
+                         const int* mask, int mstride, int S, cudaStream_t st);
+
 // Keeps the iterate of smallest residual: copies x into xbest for the
 // samples whose last iteration improved it (keep == 1), or x <- xbest for
 // the samples that did not converge (keep == 2).

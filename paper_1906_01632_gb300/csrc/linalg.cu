@@ -192,6 +192,143 @@ void launch_smooth(const Grid& G, const B4<M>* J, const B4<T>* Dinv,
     }
 }
 
+// ---------------------------------------------------------------------------
+// z-line block Jacobi: x_out = x + omega L^{-1} (b - A x), L the block
+// tridiagonal part of A along each vertical grid line (2x2 blocks of the
+// offsets (0,0,-1), (0,0,0), (0,0,+1)).  One thread solves one line by the
+// block Thomas algorithm.  It keeps the node-local pressure/salt coupling and
+// the vertical (gravity) coupling implicit: next to a steep salt front on a
+// rough permeability field the 2x2 diagonal blocks become nearly singular and
+// point block Jacobi diverges locally, while the line solve stays stable.
+// The diagonal block is recovered from Dinv (the inverse of the interior-
+// masked block, kept in T precision); the off-diagonal line blocks come from
+// the stored matrix, masked to the interior operator.
+// ---------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ B4<T> inv2(const B4<T>& a)
+{
+    const T det = a.pp * a.cc - a.pc * a.cp;
+    const T r = T(1) / det;
+    return B4<T>{a.cc * r, -a.pc * r, -a.cp * r, a.pp * r};
+}
+
+template <class T>
+__device__ __forceinline__ B4<T> mul2(const B4<T>& a, const B4<T>& b)
+{
+    return B4<T>{a.pp * b.pp + a.pc * b.cp, a.pp * b.pc + a.pc * b.cc,
+                 a.cp * b.pp + a.cc * b.cp, a.cp * b.pc + a.cc * b.cc};
+}
+
+template <class T, class M, bool TRANS>
+__device__ __forceinline__ B4<T> line_block(const B4<M>* __restrict__ Js, int N, int slot, int m,
+                                            uint8_t row_bc, uint8_t col_bc)
+{
+    const B4<M> q = Js[(size_t)slot * N + m];
+    B4<T> a;
+    if (!TRANS) a = B4<T>{mg_load<T>(q.pp), mg_load<T>(q.pc), mg_load<T>(q.cp), mg_load<T>(q.cc)};
+    else a = B4<T>{mg_load<T>(q.pp), mg_load<T>(q.cp), mg_load<T>(q.pc), mg_load<T>(q.cc)};
+    if (row_bc & BC_P) { a.pp = T(0); a.pc = T(0); }
+    if (row_bc & BC_C) { a.cp = T(0); a.cc = T(0); }
+    if (col_bc & BC_P) { a.pp = T(0); a.cp = T(0); }
+    if (col_bc & BC_C) { a.pc = T(0); a.cc = T(0); }
+    return a;
+}
+
+template <class T, class M, bool TRANS, bool ZEROX>
+__global__ void __launch_bounds__(kLineBS)
+    k_smooth_zline(Grid G, const B4<M>* __restrict__ J, const B4<T>* __restrict__ Dinv,
+                   const uint8_t* __restrict__ bc, const V2<T>* __restrict__ b,
+                   const V2<T>* __restrict__ x, V2<T>* __restrict__ xo, T omega,
+                   const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int sz = (G.nx + 1) * (G.ny + 1);
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= sz) return;
+    const size_t on_ = (size_t)s * G.N;
+    const B4<M>* Js = J + (size_t)s * 27 * G.N;
+    const int i = col % (G.nx + 1), j = col / (G.nx + 1);
+    B4<T> Cl[kMaxLine];   // M_k^{-1} U_k
+    V2<T> gl[kMaxLine];   // M_k^{-1} (r_k - L_k g_{k-1})
+    for (int k = 0; k <= G.nz; ++k) {
+        const int n = col + k * sz;
+        const V2<T> bv = b[on_ + n];
+        T rp = bv.p, rc = bv.c;
+        if (!ZEROX) {
+            T yp, yc;
+            stencil_apply<T, TRANS, M>(G, Js, x + on_, n, i, j, k, yp, yc);
+            rp -= yp;
+            rc -= yc;
+        }
+        const uint8_t mk = bc[n];
+        if (mk & BC_P) rp = T(0);
+        if (mk & BC_C) rc = T(0);
+        B4<T> di = Dinv[on_ + n];
+        if (TRANS) di = B4<T>{di.pp, di.cp, di.pc, di.cc};
+        B4<T> Mk = inv2(di);
+        if (k > 0) {
+            const B4<T> L = TRANS ? line_block<T, M, true>(Js, G.N, slot27(0, 0, 1), n - sz, mk,
+                                                          bc[n - sz])
+                                  : line_block<T, M, false>(Js, G.N, slot27(0, 0, -1), n, mk,
+                                                           bc[n - sz]);
+            const B4<T> LC = mul2(L, Cl[k - 1]);
+            Mk.pp -= LC.pp; Mk.pc -= LC.pc; Mk.cp -= LC.cp; Mk.cc -= LC.cc;
+            const V2<T> g = gl[k - 1];
+            rp -= L.pp * g.p + L.pc * g.c;
+            rc -= L.cp * g.p + L.cc * g.c;
+        }
+        const B4<T> Mi = inv2(Mk);
+        if (k < G.nz) {
+            const B4<T> U = TRANS ? line_block<T, M, true>(Js, G.N, slot27(0, 0, -1), n + sz, mk,
+                                                          bc[n + sz])
+                                  : line_block<T, M, false>(Js, G.N, slot27(0, 0, 1), n, mk,
+                                                           bc[n + sz]);
+            Cl[k] = mul2(Mi, U);
+        }
+        gl[k] = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
+    }
+    V2<T> d = gl[G.nz];
+    for (int k = G.nz;; --k) {
+        const int n = col + k * sz;
+        if (k < G.nz) {
+            const B4<T>& C = Cl[k];
+            const V2<T> g = gl[k];
+            d = V2<T>{g.p - (C.pp * d.p + C.pc * d.c), g.c - (C.cp * d.p + C.cc * d.c)};
+        }
+        V2<T> xn{T(0), T(0)};
+        if (!ZEROX) xn = x[on_ + n];
+        T op = xn.p + omega * d.p, oc = xn.c + omega * d.c;
+        const uint8_t mk = bc[n];
+        if (mk & BC_P) op = T(0);
+        if (mk & BC_C) oc = T(0);
+        xo[on_ + n] = V2<T>{op, oc};
+        if (k == 0) break;
+    }
+}
+
+template <class T, class M>
+void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
+                         const V2<T>* b, const V2<T>* x, V2<T>* xo, double omega, int trans,
+                         const int* mask, int mstride, int S, cudaStream_t st)
+{
+    if (G.nz + 1 > kMaxLine) return;  // callers check the line limit first
+    count_launch(1);
+    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), kLineBS), S);
+    const T w = T(omega);
+#define ELDER_ZL(TR, ZX) \
+    k_smooth_zline<T, M, TR, ZX><<<grid, kLineBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride)
+    if (x == nullptr) {
+        if (trans) ELDER_ZL(true, true);
+        else ELDER_ZL(false, true);
+    } else {
+        if (trans) ELDER_ZL(true, false);
+        else ELDER_ZL(false, false);
+    }
+#undef ELDER_ZL
+}
+
 template <class T, class M, bool TRANS>
 __global__ void __launch_bounds__(kMaxBS)
     k_mg_residual(Grid G, const B4<M>* __restrict__ J, const uint8_t* __restrict__ bc,
@@ -1008,7 +1145,11 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
     template void launch_axpy_mask<T>(const Grid&, const uint8_t*, const V2<T>*, V2<T>*, \
                                       double, int, int, cudaStream_t);                   \
     template void launch_bicg_keep<T>(const Grid&, V2<T>*, V2<T>*, const KScal*, int,    \
-                                      int, cudaStream_t);
+                                      int, cudaStream_t);                                \
+    template void launch_smooth_zline<T, typename MgType<T>::type>(                      \
+        const Grid&, const B4<typename MgType<T>::type>*, const B4<T>*, const uint8_t*,  \
+        const V2<T>*, const V2<T>*, V2<T>*, double, int, const int*, int, int,           \
+        cudaStream_t);
 ELDER_INST(double)
 ELDER_INST(float)
 #undef ELDER_INST

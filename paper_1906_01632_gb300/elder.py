@@ -25,6 +25,7 @@ SECONDS_PER_YEAR = 365.25 * 86400.0
 
 ELDER_OK, ELDER_EINVAL, ELDER_ENOMEM, ELDER_ECUDA, ELDER_ENOTCONV, ELDER_ETIMEOUT = range(6)
 ELDER_FP64, ELDER_MIXED = 0, 1
+ELDER_SMOOTH_JACOBI, ELDER_SMOOTH_ZLINE = 0, 1
 SAMPLE_STATUS = {0: "ok", 1: "newton_maxit", 2: "krylov_maxit", 3: "breakdown", 4: "nonfinite",
                  5: "linesearch"}
 
@@ -41,7 +42,8 @@ class elder_config(ctypes.Structure):
                 ("lin_maxit", ctypes.c_int), ("mg_levels", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("newton_estimate", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("newton_estimate", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
 
 
 class elder_stats(ctypes.Structure):

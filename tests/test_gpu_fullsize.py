@@ -147,7 +147,12 @@ def test_config4_adjoint_matches_central_fd(E, I):
     p0, c0 = O.initial_state(P)
     dt = YEAR / 12
     steps = 40
-    ctx = E.elder_create(E.elder_config_default(64, 64, 16, max_samples=64))
+    # Newton to round-off (no error-estimate stop): a central difference of
+    # J at h = 1e-3 moves J by ~1 kg, and a step accepted at |dc| ~ 1e-11
+    # leaves ~1e-2 kg of error in J
+    ctx = E.elder_create(E.elder_config_default(
+        64, 64, 16, max_samples=64, newton_estimate=0, newton_tol_c=1e-13,
+        newton_tol_p=1e-13 * P.rho0 * P.g * P.Lz))
     J, gphi, gK = ctx.grad(steps, T(phi), T(K), T(p0), T(c0), dt, ckpt_every=7)
     gphi, gK = H(gphi), H(gK)
     rel = 1e-3

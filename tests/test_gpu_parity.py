@@ -160,6 +160,31 @@ def test_solve_matches_dense_lu(E, transpose):
         assert (err <= 1e-9 * scale).all(), (err, scale)
 
 
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zline_smoother_solve_matches_dense_lu(E, transpose, precision):
+    """The z-line smoother (block tridiagonal solve along each vertical
+    line) as the multigrid smoother of elder_solve, 8x8x4 (lines of 5 nodes,
+    a ragged 81-column batch), against a dense LU of the oracle Jacobian."""
+    P = O.Problem(8, 8, 4)
+    S = 3
+    ctx = _ctx(E, 8, 8, 4, S=S, smoother=E.ELDER_SMOOTH_ZLINE, precision=precision)
+    phi, K = _fields(P, S, 16)
+    p, c = _random_states(P, S, 17)
+    rng = np.random.default_rng(18)
+    rhs = rng.standard_normal((S, P.N, 2))
+    dt = YEAR / 12
+    x, st = ctx.solve(S, T(phi), T(K), T(p), T(c), dt, T(rhs), transpose=transpose, rtol=1e-12)
+    assert (st == 0).all()
+    x = H(x).reshape(S, 2 * P.N)
+    for s in range(S):
+        A = O.jacobian_dense(P, phi[s], K[s], p[s], c[s], dt)
+        ref = O.dense_solve(A.T if transpose else A, rhs[s].ravel())
+        scale = np.abs(ref).reshape(-1, 2).max(axis=0)
+        err = np.abs(x[s] - ref).reshape(-1, 2).max(axis=0)
+        assert (err <= 1e-9 * scale).all(), (err, scale)
+
+
 # --------------------------------------------------------------------------
 # time steps
 # --------------------------------------------------------------------------
@@ -188,8 +213,9 @@ def _oracle_traj(P, phi, K, p, c, steps, dt):
     return traj
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
-def test_steps_match_oracle_16x16x4(E, precision, tol):
+def test_steps_match_oracle_16x16x4(E, precision, tol, smoother):
     P = O.Problem(16, 16, 4)
     S = 3
     phi, K = _fields(P, S, 9)
@@ -198,7 +224,7 @@ def test_steps_match_oracle_16x16x4(E, precision, tol):
     c = np.tile(c0, (S, 1))
     dt = YEAR / 12
     steps = 5
-    traj, _ = _run_gpu(E, P, phi, K, p, c, steps, dt, precision=precision)
+    traj, _ = _run_gpu(E, P, phi, K, p, c, steps, dt, precision=precision, smoother=smoother)
     pscale = P.rho0 * P.g * P.Lz
     for s in range(S):
         ref = _oracle_traj(P, phi[s], K[s], p0, c0, steps, dt)
