@@ -55,7 +55,7 @@ def parse():
                          "the paper's parallelepiped field at Halton points")
     ap.add_argument("--dt-yr", type=float, default=1.0 / 12.0)
     ap.add_argument("--no-gpc", action="store_true", help="skip the gPC kernel timings")
-    ap.add_argument("--smoother", choices=["jacobi", "zline"], default="jacobi")
+    ap.add_argument("--smoother", choices=["jacobi", "zline"], default="zline")
     return ap.parse_args()
 
 

@@ -104,9 +104,10 @@ typedef struct {
     int smoother;             /* ELDER_SMOOTH_JACOBI: damped 2x2 block
                                  Jacobi; ELDER_SMOOTH_ZLINE: damped block
                                  Jacobi over vertical grid lines (block
-                                 tridiagonal solve per line, nz <= 128).
-                                 The robust re-solve of failed samples
-                                 always uses the z-line smoother.           */
+                                 tridiagonal solve per line, nz <= 128;
+                                 the default).  The robust re-solve of
+                                 failed samples always uses the z-line
+                                 smoother.                                  */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */

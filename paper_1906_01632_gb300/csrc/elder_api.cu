@@ -1014,7 +1014,7 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->use_graphs = 1;
     cfg->autotune = 1;
     cfg->newton_estimate = 1;
-    cfg->smoother = ELDER_SMOOTH_JACOBI;
+    cfg->smoother = ELDER_SMOOTH_ZLINE;
     return ELDER_OK;
 }
 
