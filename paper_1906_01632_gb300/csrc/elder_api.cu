@@ -468,10 +468,17 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     const int bs_sm = ctx->bs[ELDER_K_SMOOTH], bs_mr = ctx->bs[ELDER_K_MGRES];
     const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
     auto sweep = [&](const V2<T>* xin, V2<T>* xout) {
-        if (line)
+        if (line && xin == nullptr) {
             launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout,
-                                      cf.omega, trans, mask, KSTRIDE, S, st);
-        else
+                                      cf.omega, trans, mask, KSTRIDE, S, st, 1);
+        } else if (line) {
+            // residual at full stream rate into the level's residual vector
+            // (free once the restriction has been made), then the line solves
+            launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, xin, sv.mr[l], trans, mask,
+                                     KSTRIDE, S, st, bs_mr);
+            launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], sv.mr[l], xin, xout,
+                                      cf.omega, trans, mask, KSTRIDE, S, st, 2);
+        } else
             launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout, cf.omega,
                                 trans, mask, KSTRIDE, S, st, bs_sm);
     };

@@ -155,14 +155,15 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
                           const double* pt, const double* ct,
                           V2<double>* R, const V2<double>* Rt,
                           const NScal* ns, int S, cudaStream_t st);
-// Damped z-line block-Jacobi sweep (x == nullptr: zero initial guess);
-// lines of at most kMaxLine nodes.
+// Damped z-line block-Jacobi line solves; lines of at most kMaxLine nodes.
+// mode 1: zero initial guess (x unused), x_out = omega L^{-1} b; mode 2: b
+// is the masked residual b - A x of x, x_out = x + omega L^{-1} b.
 constexpr int kMaxLine = 129;
 constexpr int kLineBS = 128;
 template <class T, class M>
 void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
                          const V2<T>* b, const V2<T>* x, V2<T>* xo, double omega, int trans,
-                         const int* mask, int mstride, int S, cudaStream_t st);
+                         const int* mask, int mstride, int S, cudaStream_t st, int mode);
 
 // Keeps the iterate of smallest residual: copies x into xbest for the
 // samples whose last iteration improved it (keep == 1), or x <- xbest for

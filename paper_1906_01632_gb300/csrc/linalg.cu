@@ -24,6 +24,31 @@ __device__ __forceinline__ bool on(const int* mask, int stride, int s)
 static_assert(sizeof(KScal) % sizeof(int) == 0, "KScal layout");
 static_assert(sizeof(NScal) % sizeof(int) == 0, "NScal layout");
 
+// One neighbour term of the 27-point product.  The loads are unconditional
+// (a missing neighbour reads node n itself and its term is selected to 0),
+// so a thread issues all 54 loads of its row before the first use: the
+// stencil kernels are memory-latency bound and need that parallelism.
+template <class T, bool TRANS, class M>
+__device__ __forceinline__ void stencil_term(const Grid& G, const B4<M>* __restrict__ J,
+                                             const V2<T>* __restrict__ x, int n, int m,
+                                             int slot, int tslot, bool ok, T& yp, T& yc,
+                                             B4<M>* raw = nullptr)
+{
+    const int mm = ok ? m : n;
+    const V2<T> xv = x[mm];
+    const B4<M> b = !TRANS ? J[(size_t)slot * G.N + n] : J[(size_t)tslot * G.N + mm];
+    if (raw) *raw = b;
+    const T pp = ok ? mg_load<T>(b.pp) : T(0), pc = ok ? mg_load<T>(b.pc) : T(0);
+    const T cp = ok ? mg_load<T>(b.cp) : T(0), cc = ok ? mg_load<T>(b.cc) : T(0);
+    if (!TRANS) {
+        yp += pp * xv.p + pc * xv.c;
+        yc += cp * xv.p + cc * xv.c;
+    } else {
+        yp += pp * xv.p + cp * xv.c;
+        yc += pc * xv.p + cc * xv.c;
+    }
+}
+
 // y_n = sum over the 27 neighbours of the 2x2 block times x (or the
 // transposed product, reading row m's block of offset -d).
 template <class T, bool TRANS, class M>
@@ -45,19 +70,8 @@ __device__ __forceinline__ void stencil_apply(const Grid& G,
                 const bool ok = (dx < 0 ? i > 0 : (dx > 0 ? i < G.nx : true)) &&
                                 (dy < 0 ? j > 0 : (dy > 0 ? j < G.ny : true)) &&
                                 (dz < 0 ? k > 0 : (dz > 0 ? k < G.nz : true));
-                if (ok) {
-                    const int m = n + dx + dy * sy + dz * sz;
-                    const V2<T> xv = x[m];
-                    if (!TRANS) {
-                        const B4<M> b = J[(size_t)slot27(dx, dy, dz) * G.N + n];
-                        yp += mg_load<T>(b.pp) * xv.p + mg_load<T>(b.pc) * xv.c;
-                        yc += mg_load<T>(b.cp) * xv.p + mg_load<T>(b.cc) * xv.c;
-                    } else {
-                        const B4<M> b = J[(size_t)slot27(-dx, -dy, -dz) * G.N + m];
-                        yp += mg_load<T>(b.pp) * xv.p + mg_load<T>(b.cp) * xv.c;
-                        yc += mg_load<T>(b.pc) * xv.p + mg_load<T>(b.cc) * xv.c;
-                    }
-                }
+                stencil_term<T, TRANS, M>(G, J, x, n, n + dx + dy * sy + dz * sz,
+                                          slot27(dx, dy, dz), slot27(-dx, -dy, -dz), ok, yp, yc);
             }
 }
 
@@ -220,14 +234,19 @@ __device__ __forceinline__ B4<T> mul2(const B4<T>& a, const B4<T>& b)
                  a.cp * b.pp + a.cc * b.cp, a.cp * b.pc + a.cc * b.cc};
 }
 
+// Raw (unmasked) line block of row n for the vertical offset dz = -1 or +1:
+// the block of slot (0,0,dz) at row n, or for the transposed operator the
+// block of slot (0,0,-dz) at row n + dz*sz read transposed.
 template <class T, class M, bool TRANS>
-__device__ __forceinline__ B4<T> line_block(const B4<M>* __restrict__ Js, int N, int slot, int m,
-                                            uint8_t row_bc, uint8_t col_bc)
+__device__ __forceinline__ B4<T> raw_line_block(const B4<M>& q)
 {
-    const B4<M> q = Js[(size_t)slot * N + m];
-    B4<T> a;
-    if (!TRANS) a = B4<T>{mg_load<T>(q.pp), mg_load<T>(q.pc), mg_load<T>(q.cp), mg_load<T>(q.cc)};
-    else a = B4<T>{mg_load<T>(q.pp), mg_load<T>(q.cp), mg_load<T>(q.pc), mg_load<T>(q.cc)};
+    if (!TRANS) return B4<T>{mg_load<T>(q.pp), mg_load<T>(q.pc), mg_load<T>(q.cp), mg_load<T>(q.cc)};
+    return B4<T>{mg_load<T>(q.pp), mg_load<T>(q.cp), mg_load<T>(q.pc), mg_load<T>(q.cc)};
+}
+
+template <class T>
+__device__ __forceinline__ B4<T> mask_block(B4<T> a, uint8_t row_bc, uint8_t col_bc)
+{
     if (row_bc & BC_P) { a.pp = T(0); a.pc = T(0); }
     if (row_bc & BC_C) { a.cp = T(0); a.cc = T(0); }
     if (col_bc & BC_P) { a.pp = T(0); a.cp = T(0); }
@@ -235,96 +254,132 @@ __device__ __forceinline__ B4<T> line_block(const B4<M>* __restrict__ Js, int N,
     return a;
 }
 
-template <class T, class M, bool TRANS, bool ZEROX>
+// The Thomas factors C_k = M_k^{-1} U_k and g_k of the forward sweep live in
+// shared memory, [k][thread], for the backward sweep; the forward recursion
+// carries C_{k-1} and g_{k-1} in registers.
+// MODE 1: x = 0, x_out = omega L^{-1} b;
+// MODE 2: b holds the residual b - A x (masked), x_out = x + omega L^{-1} b.
+// A sweep from a nonzero x is the multigrid residual kernel (all nodes in
+// parallel, at stream rate) followed by MODE 2: folding the 27-point
+// residual into the line kernel runs at a third of the bandwidth, because
+// each thread walks its line serially and few warps fit an SM.
+template <class T, class M, bool TRANS, int MODE>
 __global__ void __launch_bounds__(kLineBS)
     k_smooth_zline(Grid G, const B4<M>* __restrict__ J, const B4<T>* __restrict__ Dinv,
                    const uint8_t* __restrict__ bc, const V2<T>* __restrict__ b,
                    const V2<T>* __restrict__ x, V2<T>* __restrict__ xo, T omega,
                    const int* mask, int mstride)
 {
+    extern __shared__ __align__(16) unsigned char zl_smem[];
     const int s = blockIdx.y;
     if (!on(mask, mstride, s)) return;
+    const int bsz = blockDim.x, tx = threadIdx.x;
+    B4<T>* Cs = reinterpret_cast<B4<T>*>(zl_smem);               // [nz][bsz]
+    V2<T>* gs = reinterpret_cast<V2<T>*>(Cs + (size_t)G.nz * bsz); // [nz+1][bsz]
     const int sz = (G.nx + 1) * (G.ny + 1);
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int col = blockIdx.x * bsz + tx;
     if (col >= sz) return;
     const size_t on_ = (size_t)s * G.N;
     const B4<M>* Js = J + (size_t)s * 27 * G.N;
-    const int i = col % (G.nx + 1), j = col / (G.nx + 1);
-    B4<T> Cl[kMaxLine];   // M_k^{-1} U_k
-    V2<T> gl[kMaxLine];   // M_k^{-1} (r_k - L_k g_{k-1})
+    const V2<T>* xs = (MODE == 1) ? nullptr : x + on_;
+    B4<T> Cp{T(0), T(0), T(0), T(0)};
+    V2<T> gp{T(0), T(0)};
+    uint8_t bc_prev = 0;
+    uint8_t mk = bc[col];
     for (int k = 0; k <= G.nz; ++k) {
         const int n = col + k * sz;
+        const uint8_t bc_next = (k < G.nz) ? bc[n + sz] : uint8_t(0);
         const V2<T> bv = b[on_ + n];
         T rp = bv.p, rc = bv.c;
-        if (!ZEROX) {
-            T yp, yc;
-            stencil_apply<T, TRANS, M>(G, Js, x + on_, n, i, j, k, yp, yc);
-            rp -= yp;
-            rc -= yc;
-        }
-        const uint8_t mk = bc[n];
+        B4<M> qL{}, qU{};
+        if (k > 0)
+            qL = !TRANS ? Js[(size_t)slot27(0, 0, -1) * G.N + n]
+                        : Js[(size_t)slot27(0, 0, 1) * G.N + n - sz];
+        if (k < G.nz)
+            qU = !TRANS ? Js[(size_t)slot27(0, 0, 1) * G.N + n]
+                        : Js[(size_t)slot27(0, 0, -1) * G.N + n + sz];
         if (mk & BC_P) rp = T(0);
         if (mk & BC_C) rc = T(0);
         B4<T> di = Dinv[on_ + n];
         if (TRANS) di = B4<T>{di.pp, di.cp, di.pc, di.cc};
         B4<T> Mk = inv2(di);
         if (k > 0) {
-            const B4<T> L = TRANS ? line_block<T, M, true>(Js, G.N, slot27(0, 0, 1), n - sz, mk,
-                                                          bc[n - sz])
-                                  : line_block<T, M, false>(Js, G.N, slot27(0, 0, -1), n, mk,
-                                                           bc[n - sz]);
-            const B4<T> LC = mul2(L, Cl[k - 1]);
+            const B4<T> L = mask_block(raw_line_block<T, M, TRANS>(qL), mk, bc_prev);
+            const B4<T> LC = mul2(L, Cp);
             Mk.pp -= LC.pp; Mk.pc -= LC.pc; Mk.cp -= LC.cp; Mk.cc -= LC.cc;
-            const V2<T> g = gl[k - 1];
-            rp -= L.pp * g.p + L.pc * g.c;
-            rc -= L.cp * g.p + L.cc * g.c;
+            rp -= L.pp * gp.p + L.pc * gp.c;
+            rc -= L.cp * gp.p + L.cc * gp.c;
         }
         const B4<T> Mi = inv2(Mk);
         if (k < G.nz) {
-            const B4<T> U = TRANS ? line_block<T, M, true>(Js, G.N, slot27(0, 0, -1), n + sz, mk,
-                                                          bc[n + sz])
-                                  : line_block<T, M, false>(Js, G.N, slot27(0, 0, 1), n, mk,
-                                                           bc[n + sz]);
-            Cl[k] = mul2(Mi, U);
+            const B4<T> U = mask_block(raw_line_block<T, M, TRANS>(qU), mk, bc_next);
+            Cp = mul2(Mi, U);
+            Cs[(size_t)k * bsz + tx] = Cp;
         }
-        gl[k] = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
+        gp = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
+        gs[(size_t)k * bsz + tx] = gp;
+        bc_prev = mk;
+        mk = bc_next;
     }
-    V2<T> d = gl[G.nz];
+    V2<T> d = gp;
     for (int k = G.nz;; --k) {
         const int n = col + k * sz;
         if (k < G.nz) {
-            const B4<T>& C = Cl[k];
-            const V2<T> g = gl[k];
+            const B4<T> C = Cs[(size_t)k * bsz + tx];
+            const V2<T> g = gs[(size_t)k * bsz + tx];
             d = V2<T>{g.p - (C.pp * d.p + C.pc * d.c), g.c - (C.cp * d.p + C.cc * d.c)};
         }
         V2<T> xn{T(0), T(0)};
-        if (!ZEROX) xn = x[on_ + n];
+        if (MODE != 1) xn = xs[n];
         T op = xn.p + omega * d.p, oc = xn.c + omega * d.c;
-        const uint8_t mk = bc[n];
-        if (mk & BC_P) op = T(0);
-        if (mk & BC_C) oc = T(0);
+        const uint8_t m = bc[n];
+        if (m & BC_P) op = T(0);
+        if (m & BC_C) oc = T(0);
         xo[on_ + n] = V2<T>{op, oc};
         if (k == 0) break;
     }
 }
 
+// Threads per block of the z-line sweep: as many as fit the per-thread
+// Thomas storage in 96 KiB of shared memory (at least one warp).
+template <class T>
+inline int zline_block(const Grid& G, size_t* smem)
+{
+    const size_t per = (size_t)G.nz * sizeof(B4<T>) + (size_t)(G.nz + 1) * sizeof(V2<T>);
+    int bs = (int)std::min<size_t>(kLineBS, (96 * 1024 / per) / 32 * 32);
+    if (bs < 32) bs = 32;
+    *smem = per * bs;
+    return bs;
+}
+
 template <class T, class M>
 void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
                          const V2<T>* b, const V2<T>* x, V2<T>* xo, double omega, int trans,
-                         const int* mask, int mstride, int S, cudaStream_t st)
+                         const int* mask, int mstride, int S, cudaStream_t st, int mode)
 {
     if (G.nz + 1 > kMaxLine) return;  // callers check the line limit first
     count_launch(1);
-    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), kLineBS), S);
+    size_t smem = 0;
+    const int bs = zline_block<T>(G, &smem);
+    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), bs), S);
     const T w = T(omega);
-#define ELDER_ZL(TR, ZX) \
-    k_smooth_zline<T, M, TR, ZX><<<grid, kLineBS, 0, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, mstride)
-    if (x == nullptr) {
-        if (trans) ELDER_ZL(true, true);
-        else ELDER_ZL(false, true);
+#define ELDER_ZL(TR, MO)                                                                       \
+    do {                                                                                       \
+        static bool attr_set = false;                                                          \
+        if (!attr_set) {                                                                       \
+            cudaFuncSetAttribute(k_smooth_zline<T, M, TR, MO>,                                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);     \
+            attr_set = true;                                                                   \
+        }                                                                                      \
+        k_smooth_zline<T, M, TR, MO><<<grid, bs, smem, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, \
+                                                             mstride);                         \
+    } while (0)
+    if (mode == 1) {
+        if (trans) ELDER_ZL(true, 1);
+        else ELDER_ZL(false, 1);
     } else {
-        if (trans) ELDER_ZL(true, false);
-        else ELDER_ZL(false, false);
+        if (trans) ELDER_ZL(true, 2);
+        else ELDER_ZL(false, 2);
     }
 #undef ELDER_ZL
 }
@@ -1149,7 +1204,7 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
     template void launch_smooth_zline<T, typename MgType<T>::type>(                      \
         const Grid&, const B4<typename MgType<T>::type>*, const B4<T>*, const uint8_t*,  \
         const V2<T>*, const V2<T>*, V2<T>*, double, int, const int*, int, int,           \
-        cudaStream_t);
+        cudaStream_t, int);
 ELDER_INST(double)
 ELDER_INST(float)
 #undef ELDER_INST

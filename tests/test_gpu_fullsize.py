@@ -137,8 +137,15 @@ def test_config4_adjoint_matches_central_fd(E, I):
     """64x64x16, lognormal porosity (median 0.1, sigma_log 0.2, clipped to
     [0.05, 0.2]), Kozeny-Carman K, 40 steps of 1/12 yr, objective = salt
     mass below mid-depth: elder_grad (checkpoints every 7 steps) against
-    central differences (h = 1e-3 relative) on 16 cells for phi and 16 for K,
-    whose 64 perturbed runs go through one batched step loop."""
+    central differences (h = 1e-5 relative) on 16 cells for phi and 16 for K,
+    whose 64 perturbed runs go through one batched step loop.
+
+    Agreement: 1e-5 relative, plus the round-off of the difference of two
+    FP64 objective values, 100 eps |J| / (2 h theta_e).  The step map is
+    only piecewise smooth (upwinding switches with the sign of each face
+    flux), so the quotient approaches the adjoint roughly linearly in h:
+    at h = 1e-3 cells on the plume path differ by ~1e-3, at 1e-4 by ~6e-5,
+    at 1e-5 by ~1.4e-6; below that the round-off term dominates."""
     P = O.Problem(64, 64, 16)
     Z = I.lognormal_z(P.C, seed=1)
     phi, K = O.fields_lognormal(P, Z)
@@ -155,7 +162,7 @@ def test_config4_adjoint_matches_central_fd(E, I):
         newton_tol_p=1e-13 * P.rho0 * P.g * P.Lz))
     J, gphi, gK = ctx.grad(steps, T(phi), T(K), T(p0), T(c0), dt, ckpt_every=7)
     gphi, gK = H(gphi), H(gK)
-    rel = 1e-3
+    rel = 1e-5
     phis, Ks = [], []
     for e in cells:
         for sgn in (1, -1):
@@ -182,7 +189,8 @@ def test_config4_adjoint_matches_central_fd(E, I):
         for e in cells:
             fd = (Js[q] - Js[q + 1]) / (2 * rel * base[e])
             q += 2
-            assert abs(fd - g[e]) <= 1e-5 * max(abs(g[e]), 1e-3 * np.abs(g).max()), (which, e, fd, g[e])
+            noise = 100 * EPS * abs(J) / (2 * rel * base[e])
+            assert abs(fd - g[e]) <= 1e-5 * abs(g[e]) + noise, (which, e, fd, g[e], noise)
 
 
 def test_paper_boundary_variant_matches_oracle(E):

@@ -303,3 +303,25 @@ def test_failed_sample_keeps_old_state(E):
     np.testing.assert_array_equal(c[1], c0)
     _, cref, _ = O.newton_step(P, phi[0], K[0], p0, c0, YEAR / 12)
     assert np.abs(c[0] - cref).max() <= 1e-10
+
+
+def test_paper_parallelepiped_workload_steps_match_oracle(E):
+    """The paper's own workload (Section 5.3): the parallelepiped porosity
+    field of eq. poro-paral3RVS at Halton points, dt = 0.005 yr, batched, on a
+    16x16x4 grid; c within 1e-10 and p within 1e-9 rho0 g Lz per step."""
+    from paper_1906_01632_gb300 import inputs as I
+    P = O.Problem(16, 16, 4)
+    S = 4
+    xi = I.halton_xi(S)
+    ctx = _ctx(E, 16, 16, 4, S=S)
+    phi_t, K_t = ctx.fields(S, 2, T(xi))
+    phi, K = H(phi_t).reshape(S, -1), H(K_t).reshape(S, -1)
+    p0, c0 = O.initial_state(P)
+    dt = 0.005 * YEAR
+    steps = 4
+    traj, _ = _run_gpu(E, P, phi, K, np.tile(p0, (S, 1)), np.tile(c0, (S, 1)), steps, dt)
+    for s in range(S):
+        ref = _oracle_traj(P, phi[s], K[s], p0, c0, steps, dt)
+        for n in range(steps):
+            assert np.abs(traj[n][1][s] - ref[n][1]).max() <= 1e-10, (s, n)
+            assert np.abs(traj[n][0][s] - ref[n][0]).max() <= 1e-9 * P.rho0 * P.g * P.Lz, (s, n)
