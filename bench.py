@@ -344,7 +344,8 @@ def run_ours(a):
     roofline = {"kernel": top, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak if achieved else None,
                 "peak_source": src,
-                "traffic": (tr * bytes_per_launch / max(1e-30, E_model_bytes(top, tsize, nx, ny, nz))
+                "traffic": (tr * bytes_per_launch /
+                            max(1e-30, E_model_bytes(top, tsize, nx, ny, nz, a.smoother == "zline"))
                             if tr is not None else None),
                 "algorithmic_flops_per_launch": pk["flops"] / max(pk["launches"], 1),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_ms,
@@ -503,13 +504,14 @@ def gpc_timings(E, torch, cfield, stream):
     return res
 
 
-def E_model_bytes(cls, tsize, nx, ny, nz):
+def E_model_bytes(cls, tsize, nx, ny, nz, line=True):
     """Algorithmic bytes per node of one launch (mirrors the library's model);
-    the mixed path stores the multigrid matrices in bfloat16."""
+    the mixed path stores the multigrid matrices in bfloat16; the z-line
+    sweep from x = 0 also reads the two vertical line blocks."""
     N = (nx + 1) * (ny + 1) * (nz + 1)
     cpn = nx * ny * nz / N
     mz = 2 if tsize == 4 else 8
-    return {"smooth": 108 * mz + 10 * tsize + 1, "smooth0": 8 * tsize + 1,
+    return {"smooth": 108 * mz + 10 * tsize + 1, "smooth0": 8 * tsize + 1 + (8 * mz if line else 0),
             "spmv": 108 * tsize + 6 * tsize + 1, "mg_residual": 108 * mz + 6 * tsize + 1,
             "residual": 49 + 16 * cpn,
             "jacobian": 108 * tsize + 108 * mz + 4 * tsize + 17 + 16 * cpn}[cls]

@@ -369,38 +369,59 @@ __device__ __forceinline__ void jac_face(const T (&p8)[8], const T (&c8)[8],
 }
 
 template <class T, int OX, int OY, int OZ>
-__device__ __forceinline__ void jac_cell(const Grid& G, const Phys& ph,
-                                         const PhysT<T>& pt,
-                                         const CellGeom& cg, int i, int j,
-                                         int k, const double* __restrict__ phi,
-                                         const double* __restrict__ K,
-                                         const double* __restrict__ p,
-                                         const double* __restrict__ c,
-                                         T (&acc)[27][4], double& phis)
+__device__ __forceinline__ void jac_cell(const Grid& G, const PhysT<T>& pt,
+                                         const CellGeom& cg, int i, int j, int k,
+                                         const V2<T>* __restrict__ cellT,
+                                         const V2<T>* __restrict__ nodeT,
+                                         T (&acc)[27][4], T& phis)
 {
     const int ci = i + OX, cj = j + OY, ck = k + OZ;
     if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz)
         return;
     const int e = ci + G.nx * (cj + G.ny * ck);
-    const double phid = __ldg(phi + e);
-    phis += phid;
-    const T phi_e = T(phid);
-    const T kmu = T(__ldg(K + e) / ph.mu);
+    const V2<T> fk = cellT[e];  // (phi, K/mu)
+    phis += fk.p;
     const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
     const int base = ci + sy * cj + sz * ck;
-    const double rg = ph.rho0 * ph.g;
     T p8[8], c8[8];
 #pragma unroll
     for (int L = 0; L < 8; ++L) {
         const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
-        const double z = (ck + (L >> 2)) * G.hz;
-        p8[L] = T(fma(rg, z - G.Lz, __ldg(p + base + off)));
-        c8[L] = T(__ldg(c + base + off));
+        const V2<T> u = nodeT[base + off];
+        p8[L] = u.p;
+        c8[L] = u.c;
     }
     constexpr int lx = -OX, ly = -OY, lz = -OZ;
-    jac_face<T, 0, ly, lz, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[0]), T(cg.area[0]), acc);
-    jac_face<T, 1, lx, lz, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[1]), T(cg.area[1]), acc);
-    jac_face<T, 2, lx, ly, OX, OY, OZ>(p8, c8, phi_e, kmu, pt, T(cg.ih[2]), T(cg.area[2]), acc);
+    jac_face<T, 0, ly, lz, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, T(cg.ih[0]), T(cg.area[0]), acc);
+    jac_face<T, 1, lx, lz, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, T(cg.ih[1]), T(cg.area[1]), acc);
+    jac_face<T, 2, lx, ly, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, T(cg.ih[2]), T(cg.area[2]), acc);
+}
+
+// Inputs of the Jacobian in its arithmetic type T, converted once per level
+// instead of once per use: nodeT = (p - rho0 g (Lz - z), c) per node and
+// cellT = (phi, K/mu) per cell.  (On GB300 an FP64-to-FP32 conversion issues
+// on the FP64 pipe; doing the 16 corner conversions of each of 8 cells per
+// node kept that pipe saturated in the FP32 assembly.)
+template <class T>
+__global__ void k_jac_inputs(Grid G, Phys ph, const double* __restrict__ phi,
+                             const double* __restrict__ K, const double* __restrict__ p,
+                             const double* __restrict__ c, V2<T>* __restrict__ cellT,
+                             V2<T>* __restrict__ nodeT, const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < G.N) {
+        const size_t o = (size_t)s * G.N + q;
+        int i, j, k;
+        node_ijk(G, q, i, j, k);
+        const double z = k * G.hz;
+        nodeT[o] = V2<T>{T(fma(ph.rho0 * ph.g, z - G.Lz, p[o])), T(c[o])};
+    }
+    if (q < G.C) {
+        const size_t o = (size_t)s * G.C + q;
+        cellT[o] = V2<T>{T(phi[o]), T(K[o] / ph.mu)};
+    }
 }
 
 // Writes the row blocks as T (JT, the Krylov operator) and/or as the
@@ -410,8 +431,7 @@ __device__ __forceinline__ void jac_cell(const Grid& G, const Phys& ph,
 template <class T, class M>
 __global__ void __launch_bounds__(128)
     k_jacobian(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
-               const double* __restrict__ phi, const double* __restrict__ K,
-               const double* __restrict__ p, const double* __restrict__ c,
+               const V2<T>* __restrict__ cellT, const V2<T>* __restrict__ nodeT,
                B4<T>* __restrict__ JT, B4<M>* __restrict__ JM, B4<T>* __restrict__ Dinv,
                const int* mask, int mstride)
 {
@@ -420,7 +440,7 @@ __global__ void __launch_bounds__(128)
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.N) return;
     const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
-    phi += oc; K += oc; p += on; c += on;
+    cellT += oc; nodeT += on;
     PhysT<T> pt{T(ph.rho0), T(ph.drho), T(ph.g), T(ph.Dm)};
     int i, j, k;
     node_ijk(G, n, i, j, k);
@@ -429,20 +449,20 @@ __global__ void __launch_bounds__(128)
     for (int q = 0; q < 27; ++q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[q][r] = T(0);
-    double phis = 0.0;
-    jac_cell<T, -1, -1, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, 0, -1, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, -1, 0, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, 0, 0, -1>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, -1, -1, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, 0, -1, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, -1, 0, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
-    jac_cell<T, 0, 0, 0>(G, ph, pt, cg, i, j, k, phi, K, p, c, acc, phis);
+    T phis = T(0);
+    jac_cell<T, -1, -1, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, 0, -1, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, -1, 0, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, 0, 0, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, -1, -1, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, 0, -1, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, -1, 0, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+    jac_cell<T, 0, 0, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     // lumped storage: d/dc of rho(c) and rho(c) c
-    const double vdt = phis * 0.125 * G.hx * G.hy * G.hz / ph.dt;
-    const double cn = c[n];
-    acc[13][1] += T(vdt * ph.drho);
-    acc[13][3] += T(vdt * (ph.rho0 + 2.0 * ph.drho * cn));
+    const T vdt = phis * T(0.125 * G.hx * G.hy * G.hz / ph.dt);
+    const T cn = nodeT[n].c;
+    acc[13][1] += vdt * pt.drho;
+    acc[13][3] += vdt * (pt.rho0 + T(2) * pt.drho * cn);
     const uint8_t b = bc[n];
     if (b & BC_P) {
 #pragma unroll
@@ -480,23 +500,27 @@ __global__ void __launch_bounds__(128)
 template <class T, class M>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* phi, const double* K, const double* p,
-                     const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv, const int* mask,
-                     int mstride, int S, cudaStream_t st)
+                     const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv, V2<T>* cellT,
+                     V2<T>* nodeT, const int* mask, int mstride, int S, cudaStream_t st)
 {
-    count_launch(1);
+    count_launch(2);
+    dim3 gin(nblocks(std::max(G.N, G.C)), S);
+    k_jac_inputs<T><<<gin, kBS, 0, st>>>(G, ph, phi, K, p, c, cellT, nodeT, mask, mstride);
     dim3 grid(nblocks(G.N, 128), S);
-    k_jacobian<T, M><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c, JT, JM,
-                                            Dinv, mask, mstride);
+    k_jacobian<T, M><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, cellT, nodeT, JT, JM, Dinv,
+                                            mask, mstride);
 }
 template void launch_jacobian<double, double>(const Grid&, const Phys&, const uint8_t*,
                                               const double*, const double*, const double*,
                                               const double*, B4<double>*, B4<double>*,
-                                              B4<double>*, const int*, int, int, cudaStream_t);
+                                              B4<double>*, V2<double>*, V2<double>*, const int*,
+                                              int, int, cudaStream_t);
 template void launch_jacobian<float, __nv_bfloat16>(const Grid&, const Phys&, const uint8_t*,
                                                     const double*, const double*,
                                                     const double*, const double*, B4<float>*,
-                                                    B4<__nv_bfloat16>*, B4<float>*,
-                                                    const int*, int, int, cudaStream_t);
+                                                    B4<__nv_bfloat16>*, B4<float>*, V2<float>*,
+                                                    V2<float>*, const int*, int, int,
+                                                    cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // hierarchy: state injection, cell averaging, block-diagonal inverse

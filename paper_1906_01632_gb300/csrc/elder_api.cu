@@ -211,6 +211,7 @@ struct elder_ctx {
     // threads per block of the autotuned kernel classes (indexed by ELDER_K_*)
     int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, kBS};
     int smoother_now = ELDER_SMOOTH_JACOBI;  // smoother of the solve in progress
+    double* jin = nullptr;  // Jacobian input scratch, [S][N] + [S][C] pairs
     bool tuned[2] = {false, false};    // per precision (FP64, FP32)
     float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
     ~elder_ctx()
@@ -241,15 +242,18 @@ Phys make_phys(const elder_config& c, double dt)
 // Algorithmic DRAM bytes and flops per node of one launch (every array the
 // kernel must touch, read or written once; neighbour reuse of x is free).
 // T = bytes of the solver type.  J row: 27 blocks of 4; vectors: 2 values.
-double model_bytes(int cls, int T, int Mz, const Grid& G)
+double model_bytes(int cls, int T, int Mz, const Grid& G, bool line)
 {
     // T: bytes of a vector / Dinv entry; Mz: bytes of a stored matrix entry
     // (for the Jacobian class: Mz of the multigrid copy, T of the Krylov copy
-    // or 0 when the level has none)
+    // or 0 when the level has none).  line: the z-line smoother, whose sweep
+    // from x = 0 also reads the two vertical line blocks of J (its sweep from
+    // a nonzero x reads all of J anyway).
     const double cells_per_node = (double)G.C / G.N;
     switch (cls) {
     case ELDER_K_SMOOTH: return 108 * Mz + (4 + 2 + 2 + 2) * T + 1;  // J, Dinv, b, x, xo, bc
-    case ELDER_K_SMOOTH0: return (4 + 2 + 2) * T + 1;                // Dinv, b, xo, bc
+    case ELDER_K_SMOOTH0:                                            // Dinv, b, xo, bc (+ L, U)
+        return (4 + 2 + 2) * T + 1 + (line ? 8 * Mz : 0);
     case ELDER_K_SPMV: return 108 * Mz + (2 + 2 + 2) * T + 1;        // J, x, y, a, bc
     case ELDER_K_MGRES: return 108 * Mz + (2 + 2 + 2) * T + 1;       // J, x, b, r, bc
     case ELDER_K_RESIDUAL:  // p, c, c_old, R, cval, bc, phi, K
@@ -299,7 +303,8 @@ void prof_end(elder_ctx* ctx, int idx, int cls, const Grid& G, int T, int Mz, in
     ProfRec& r = ctx->prof.pending[idx];
     CK(cudaEventRecord(r.b, st));
     r.cls = cls;
-    r.bytes = model_bytes(cls, T, Mz, G) * G.N * samples;
+    const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
+    r.bytes = model_bytes(cls, T, Mz, G, line) * G.N * samples;
     r.flops = model_flops(cls) * G.N * samples;
 }
 
@@ -420,8 +425,10 @@ void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
         const int pi = prof_begin(ctx, st);
         using M = typename Solver<T>::M;
         B4<T>* JT = (l == 0 && !std::is_same<T, M>::value) ? sv.J0 : nullptr;
-        launch_jacobian<T, M>(G, ph, ctx->bc[l], phi, K, p, c, JT, sv.Jm[l], sv.Dinv[l], mask,
-                              mstride, S, st);
+        V2<T>* nodeT = reinterpret_cast<V2<T>*>(ctx->jin);
+        V2<T>* cellT = nodeT + (size_t)S * G.N;
+        launch_jacobian<T, M>(G, ph, ctx->bc[l], phi, K, p, c, JT, sv.Jm[l], sv.Dinv[l], cellT,
+                              nodeT, mask, mstride, S, st);
         prof_end(ctx, pi, ELDER_K_JACOBIAN, G, JT ? (int)sizeof(T) : 0, (int)sizeof(M), n_active,
                  st);
     }
@@ -1117,6 +1124,9 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         ctx->partial3 = dalloc<double>((size_t)S * 3 * ctx->nblk0);
         ctx->edge = dalloc<E4>((size_t)S * 3 * G.N);
         ctx->mem.add(ctx->edge);
+        // Jacobian inputs in the solver's arithmetic type, reused level by level
+        ctx->jin = dalloc<double>((size_t)S * 2 * (G.N + G.C));
+        ctx->mem.add(ctx->jin);
         ctx->mass = dalloc<double>((size_t)3 * S);
         ctx->mem.add(ctx->mass);
         CK(cudaMallocHost((void**)&ctx->h_mass, sizeof(double) * 3 * S));
@@ -1220,9 +1230,12 @@ int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
         return ELDER_EINVAL;
     }
     try {
+        V2<double>* nodeT = reinterpret_cast<V2<double>*>(ctx->jin);
+        V2<double>* cellT = nodeT + (size_t)S * ctx->grids[0].N;
         launch_jacobian<double, double>(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], phi,
                                         K, p, c, reinterpret_cast<B4<double>*>(J), nullptr,
-                                        nullptr, nullptr, 0, S, (cudaStream_t)stream);
+                                        nullptr, cellT, nodeT, nullptr, 0, S,
+                                        (cudaStream_t)stream);
         CKL();
     } catch (const Fail& f) {
         return set_error(ctx, f);

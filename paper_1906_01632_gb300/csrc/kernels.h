@@ -10,9 +10,36 @@ struct KScal {
     double rho, rho_old, alpha, omega;
     double bn2, rn2;
     double best_rn2;             // smallest ||r||^2 seen (x = 0 counts)
+    double beta;                 // (rho/rho_old)(alpha/omega) of the next p update
+    float alpha_f, omega_f, beta_f, pad_f;  // FP32 copies for the FP32 vector updates
     int active, iters, status;
     int improved;                // the last iteration lowered best_rn2
 };
+
+// BiCGStab scalars in the vector type: the FP32 solver reads the FP32
+// copies, so that its vector kernels issue no FP64 instruction per element.
+template <class T> __device__ __forceinline__ T ks_alpha(const KScal& k);
+template <> __device__ __forceinline__ float ks_alpha<float>(const KScal& k) { return k.alpha_f; }
+template <> __device__ __forceinline__ double ks_alpha<double>(const KScal& k) { return k.alpha; }
+template <class T> __device__ __forceinline__ T ks_omega(const KScal& k);
+template <> __device__ __forceinline__ float ks_omega<float>(const KScal& k) { return k.omega_f; }
+template <> __device__ __forceinline__ double ks_omega<double>(const KScal& k) { return k.omega; }
+template <class T> __device__ __forceinline__ T ks_beta(const KScal& k);
+template <> __device__ __forceinline__ float ks_beta<float>(const KScal& k) { return k.beta_f; }
+template <> __device__ __forceinline__ double ks_beta<double>(const KScal& k) { return k.beta; }
+
+// Per-node contribution a.p b.p + a.c b.c to an FP64 inner product: FP64
+// products for the FP64 solver; for the FP32 solver the two products are
+// summed in FP32 and the sum is accumulated in FP64 (the vectors themselves
+// carry FP32 rounding).
+__device__ __forceinline__ double dot2(double ap, double ac, double bp, double bc)
+{
+    return ap * bp + ac * bc;
+}
+__device__ __forceinline__ double dot2(float ap, float ac, float bp, float bc)
+{
+    return (double)fmaf(ap, bp, ac * bc);
+}
 
 // Per-sample Newton state (Section 2.3: Newton with line search).
 struct NScal {
@@ -53,12 +80,13 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      double* act, const int* mask, int mask_stride, int S,
                      cudaStream_t st, E4* edge);
 // Jacobian rows as T (JT) and/or as the multigrid type M (JM), and the inverse
-// interior diagonal blocks (Dinv); null outputs are skipped.
+// interior diagonal blocks (Dinv); null outputs are skipped.  cellT [S][C]
+// and nodeT [S][N] are scratch for the inputs converted to T.
 template <class T, class M>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* phi, const double* K, const double* p,
-                     const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv,
-                     const int* mask, int mask_stride, int S, cudaStream_t st);
+                     const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv, V2<T>* cellT,
+                     V2<T>* nodeT, const int* mask, int mask_stride, int S, cudaStream_t st);
 void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
                    const double* cf, double* pc, double* cc, const int* mask,
                    int mask_stride, int S, cudaStream_t st);

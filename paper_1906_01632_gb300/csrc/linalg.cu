@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(kMaxBS)
         y[n] = V2<T>{yp, yc};
         if (MODE == 1 || MODE == 2) {
             const V2<T> av = a[on_ + n];
-            d0 = (double)av.p * (double)yp + (double)av.c * (double)yc;
+            d0 = dot2(av.p, av.c, yp, yc);
         }
-        if (MODE == 2) d1 = (double)yp * (double)yp + (double)yc * (double)yc;
+        if (MODE == 2) d1 = dot2(yp, yc, yp, yc);
     }
     // One partial per warp of 32 nodes, so the sums do not depend on the
     // (tuned) block size: the inner products are bitwise reproducible.
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(kBS)
         v[q] = z;
         r[q] = bv;
         rh[q] = bv;
-        d = (double)bv.p * (double)bv.p + (double)bv.c * (double)bv.c;
+        d = dot2(bv.p, bv.c, bv.p, bv.c);
     }
     const double t = block_sum(d, red);
     if (threadIdx.x == 0) partial[((size_t)s * 2) * gridDim.x + blockIdx.x] = t;
@@ -594,8 +594,7 @@ __global__ void __launch_bounds__(kBS)
     if (!k.active) return;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const double beta = (k.rho / k.rho_old) * (k.alpha / k.omega);
-    const T b = T(beta), w = T(k.omega);
+    const T b = ks_beta<T>(k), w = ks_omega<T>(k);
     const size_t q = (size_t)s * N + n;
     const V2<T> rv = r[q], vv = v[q];
     V2<T> pv = p[q];
@@ -623,7 +622,7 @@ __global__ void __launch_bounds__(kBS)
     if (!k.active) return;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const T a = T(k.alpha);
+    const T a = ks_alpha<T>(k);
     const size_t q = (size_t)s * N + n;
     const V2<T> rv = r[q], vv = v[q];
     sv[q] = V2<T>{rv.p - a * vv.p, rv.c - a * vv.c};
@@ -654,7 +653,7 @@ __global__ void __launch_bounds__(kBS)
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     double d0 = 0.0, d1 = 0.0;
     if (n < N) {
-        const T a = T(k.alpha), w = T(k.omega);
+        const T a = ks_alpha<T>(k), w = ks_omega<T>(k);
         const size_t q = (size_t)s * N + n;
         const V2<T> pv = ph[q], shv = sh[q], svv = sv[q], tv = t[q], rhv = rh[q];
         V2<T> xv = x[q];
@@ -663,8 +662,8 @@ __global__ void __launch_bounds__(kBS)
         x[q] = xv;
         const V2<T> rv{svv.p - w * tv.p, svv.c - w * tv.c};
         r[q] = rv;
-        d0 = (double)rv.p * (double)rv.p + (double)rv.c * (double)rv.c;
-        d1 = (double)rhv.p * (double)rv.p + (double)rhv.c * (double)rv.c;
+        d0 = dot2(rv.p, rv.c, rv.p, rv.c);
+        d1 = dot2(rhv.p, rhv.c, rv.p, rv.c);
     }
     const double t0 = block_sum(d0, red);
     const double t1 = block_sum(d1, red);
@@ -713,6 +712,10 @@ __global__ void k_bicg_finalize(int stage, const double* __restrict__ partial,
         k.status = 0;
         k.best_rn2 = a0;
         k.improved = 0;
+        k.beta = 0.0;  // p = v = 0: the first update sets p = r
+        k.alpha_f = 1.0f;
+        k.omega_f = 1.0f;
+        k.beta_f = 0.0f;
         if (!(a0 > 0.0)) {
             k.active = 0;
             if (!isfinite(a0)) k.status = ELDER_SAMPLE_NONFINITE_;
@@ -723,9 +726,11 @@ __global__ void k_bicg_finalize(int stage, const double* __restrict__ partial,
             k.status = ELDER_SAMPLE_BREAKDOWN_;
         } else {
             k.alpha = k.rho / a0;
+            k.alpha_f = (float)k.alpha;
         }
     } else if (stage == 2) {  // omega = (t, s) / (t, t)
         k.omega = (a1 > 0.0) ? a0 / a1 : 0.0;
+        k.omega_f = (float)k.omega;
     } else {  // end of iteration: ||r||^2 and the next rho = (rh, r)
         k.rn2 = a0;
         k.rho_old = k.rho;
@@ -733,6 +738,9 @@ __global__ void k_bicg_finalize(int stage, const double* __restrict__ partial,
         k.iters += 1;
         k.improved = a0 < k.best_rn2;
         if (k.improved) k.best_rn2 = a0;
+        k.beta = (k.omega != 0.0 && k.rho_old != 0.0) ? (k.rho / k.rho_old) * (k.alpha / k.omega)
+                                                      : 0.0;
+        k.beta_f = (float)k.beta;
         if (!isfinite(a0)) {
             k.active = 0;
             k.status = ELDER_SAMPLE_NONFINITE_;

@@ -141,11 +141,14 @@ def test_config4_adjoint_matches_central_fd(E, I):
     whose 64 perturbed runs go through one batched step loop.
 
     Agreement: 1e-5 relative, plus the round-off of the difference of two
-    FP64 objective values, 100 eps |J| / (2 h theta_e).  The step map is
-    only piecewise smooth (upwinding switches with the sign of each face
-    flux), so the quotient approaches the adjoint roughly linearly in h:
-    at h = 1e-3 cells on the plume path differ by ~1e-3, at 1e-4 by ~6e-5,
-    at 1e-5 by ~1.4e-6; below that the round-off term dominates."""
+    objective values, 1000 eps |J| / (2 h theta_e): each run's state is only
+    determined to the Newton round-off floor, and J of the same sample
+    differs by ~1e-13 |J| (~450 eps |J|) between runs of different batch
+    composition.  The step map is only piecewise smooth (upwinding switches
+    with the sign of each face flux), so the quotient approaches the adjoint
+    roughly linearly in h: at h = 1e-3 cells on the plume path differ by
+    ~1e-3, at 1e-4 by ~6e-5, at 1e-5 by ~1.4e-6; below that the round-off
+    term dominates."""
     P = O.Problem(64, 64, 16)
     Z = I.lognormal_z(P.C, seed=1)
     phi, K = O.fields_lognormal(P, Z)
@@ -189,7 +192,7 @@ def test_config4_adjoint_matches_central_fd(E, I):
         for e in cells:
             fd = (Js[q] - Js[q + 1]) / (2 * rel * base[e])
             q += 2
-            noise = 100 * EPS * abs(J) / (2 * rel * base[e])
+            noise = 1000 * EPS * abs(J) / (2 * rel * base[e])
             assert abs(fd - g[e]) <= 1e-5 * abs(g[e]) + noise, (which, e, fd, g[e], noise)
 
 

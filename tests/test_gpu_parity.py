@@ -273,7 +273,9 @@ def test_moments_match_oracle(E):
 
 def test_grad_matches_oracle_adjoint(E):
     P = O.Problem(8, 8, 4)
-    ctx = _ctx(E, 8, 8, 4)
+    # Newton to round-off, as the oracle: J is compared at 1e-10
+    ctx = _ctx(E, 8, 8, 4, newton_estimate=0, newton_tol_c=1e-13,
+               newton_tol_p=1e-13 * P.rho0 * P.g * P.Lz)
     phi, K = _fields(P, 1, 11)
     p0, c0 = O.initial_state(P)
     dt = YEAR / 12
