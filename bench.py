@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--dt-yr", type=float, default=1.0 / 12.0)
     ap.add_argument("--no-gpc", action="store_true", help="skip the gPC kernel timings")
     ap.add_argument("--smoother", choices=["jacobi", "zline"], default="zline")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the BiCGStab iteration kernels one by one instead of replaying "
+                         "a captured CUDA graph")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps of the profiled pass (per-kernel-class CUDA events)")
     return ap.parse_args()
@@ -251,7 +254,8 @@ def run_ours(a):
     prec = E.ELDER_MIXED if a.precision == "mixed" else E.ELDER_FP64
     smoother = E.ELDER_SMOOTH_ZLINE if a.smoother == "zline" else E.ELDER_SMOOTH_JACOBI
     ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=prec,
-                                                smoother=smoother))
+                                                smoother=smoother,
+                                                use_graphs=0 if a.no_graphs else 1))
     N, C = ctx.N, ctx.C
     xi_all = I.sobol_xi(S * world, seed=0) if a.fields == "sobol" else I.halton_xi(S * world)
     xi = torch.tensor(xi_all[rank * S:(rank + 1) * S].ravel(), dtype=torch.float64, device=dev)

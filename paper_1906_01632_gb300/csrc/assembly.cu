@@ -127,91 +127,128 @@ __host__ __device__ inline CellGeom make_geom(const Grid& G)
 }
 
 // ---------------------------------------------------------------------------
-// Edge-based residual: each face flux computed once.
+// Cell-based residual: each quarter-face flux computed once.
 //
-// k_edge_flux: node n owns the edges to (i+1,j,k), (i,j+1,k), (i,j,k+1); the
-// dual face of an edge consists of the quarter faces of the up to 4 cells
-// around it.  The node writes, per direction, the summed mass and salt flux
-// out of n through that face and the magnitudes of their terms (the
-// round-off scale).  k_edge_residual forms R_n = storage + sum_d (flux_d(n) -
-// flux_d(n - e_d)): the same value is added at one end of an edge and
-// subtracted at the other, so the balance telescopes exactly.
+// k_cell_flux: one thread per cell computes the 12 quarter faces of its
+// sub-control-volume boundary (one per cell edge): the 4 edge differences of
+// p and c and the 4 edge sums of c per direction are formed once and shared
+// by the 4 quarter faces of that direction, which only differ in their Q1
+// weights (9,3,3,1)/16.  Output: [S][12][C] records (mass flux m and salt
+// flux F from the edge's lower end A to its upper end B, and the magnitudes
+// of their terms, the round-off scale).
+// k_cell_residual: node n sums, for each direction, the 4 quarter faces of
+// its forward edge and of its backward edge (always in the same order, from
+// the edge's lower node, so both ends of an edge use the same value and the
+// balance telescopes exactly), then adds storage and Dirichlet rows.
+// Quarter face q = 4 D + 2 u + v of a cell belongs to its direction-D edge at
+// transverse local position (u, v) (see corner_of).
 // ---------------------------------------------------------------------------
 
-// One cell of the edge gather: cell (i+OX, j+OY, k+OZ); this node is its
-// corner (-OX,-OY,-OZ); FX/FY/FZ select the faces of this node's forward
-// x/y/z edges that lie in this cell.
-template <int OX, int OY, int OZ, bool FX, bool FY, bool FZ>
-__device__ __forceinline__ void edge_cell(const Grid& G, const Phys& ph, const CellGeom& cg,
-                                          int i, int j, int k,
-                                          const double* __restrict__ phi,
-                                          const double* __restrict__ K,
-                                          const double* __restrict__ p,
-                                          const double* __restrict__ c, E4 (&acc)[3])
+template <int D>
+__device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const double (&c8)[8],
+                                               const Phys& ph, double invh, double kmuA,
+                                               double dA, QF* __restrict__ out, size_t qs)
 {
-    const int ci = i + OX, cj = j + OY, ck = k + OZ;
-    if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) return;
-    const int e = ci + G.nx * (cj + G.ny * ck);
-    const double phi_e = __ldg(phi + e);
-    const double kmu = __ldg(K + e) / ph.mu;
+    double dp[2][2], dc[2][2], sc[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int A = corner_of(D, u, v, 0), B = corner_of(D, u, v, 1);
+            dp[u][v] = p8[B] - p8[A];
+            dc[u][v] = c8[B] - c8[A];
+            sc[u][v] = c8[A] + c8[B];
+        }
+    const double wh = 0.5625 * invh, wm = 0.1875 * invh, wl = 0.0625 * invh;
+#pragma unroll
+    for (int S_ = 0; S_ < 2; ++S_)
+#pragma unroll
+        for (int T_ = 0; T_ < 2; ++T_) {
+            // weights of the 4 edges for the face of edge (S_, T_)
+            double gp = 0.0, gc = 0.0, ci = 0.0;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const double w = (u == S_) ? (v == T_ ? wh : wm) : (v == T_ ? wm : wl);
+                    const double wc = (u == S_) ? (v == T_ ? 0.28125 : 0.09375)
+                                                : (v == T_ ? 0.09375 : 0.03125);
+                    gp = fma(w, dp[u][v], gp);
+                    gc = fma(w, dc[u][v], gc);
+                    ci = fma(wc, sc[u][v], ci);
+                }
+            const double rho = fma(ph.drho, ci, ph.rho0);
+            const double G = (D == 2) ? fma(ph.g, rho, gp) : gp;
+            const double m = -(rho * kmuA) * G;
+            const double cup =
+                (m >= 0.0) ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
+            const double dif = rho * dA;
+            const double F = fma(cup, m, -dif * gc);
+            // rounding scale: the Darcy flux cancels grad p against rho g
+            const double mm = rho * kmuA * (fabs(gp) + (D == 2 ? ph.g * rho : 0.0));
+            const double Fm = fma(fabs(cup), mm, dif * fabs(gc));
+            out[(size_t)(4 * D + 2 * S_ + T_) * qs] = QF{m, F, (float)mm, (float)Fm};
+        }
+}
+
+__global__ void __launch_bounds__(kBS)
+    k_cell_flux(Grid G, Phys ph, CellGeom cg, const double* __restrict__ phi,
+                const double* __restrict__ K, const double* __restrict__ p,
+                const double* __restrict__ c, QF* __restrict__ qf, const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G.C) return;
+    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
+    const int ci = e % G.nx, cj = (e / G.nx) % G.ny, ck = e / (G.nx * G.ny);
     const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
     const int base = ci + sy * cj + sz * ck;
     double p8[8], c8[8];
 #pragma unroll
     for (int L = 0; L < 8; ++L) {
         const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
-        p8[L] = __ldg(p + base + off);
-        c8[L] = __ldg(c + base + off);
+        p8[L] = __ldg(p + on + base + off);
+        c8[L] = __ldg(c + on + base + off);
     }
-    double m, F, mm, Fm;
-    if (FX) {
-        flux_face<0, -OY, -OZ>(p8, c8, phi_e, kmu, ph, cg.ih[0], cg.area[0], m, F, mm, Fm);
-        acc[0].m += m; acc[0].F += F; acc[0].mm += mm; acc[0].Fm += Fm;
-    }
-    if (FY) {
-        flux_face<1, -OX, -OZ>(p8, c8, phi_e, kmu, ph, cg.ih[1], cg.area[1], m, F, mm, Fm);
-        acc[1].m += m; acc[1].F += F; acc[1].mm += mm; acc[1].Fm += Fm;
-    }
-    if (FZ) {
-        flux_face<2, -OX, -OY>(p8, c8, phi_e, kmu, ph, cg.ih[2], cg.area[2], m, F, mm, Fm);
-        acc[2].m += m; acc[2].F += F; acc[2].mm += mm; acc[2].Fm += Fm;
-    }
+    const double phi_e = __ldg(phi + oc + e);
+    const double kmu = __ldg(K + oc + e) / ph.mu;
+    QF* out = qf + (size_t)s * 12 * G.C + e;
+    const size_t qs = (size_t)G.C;
+    cell_dir_faces<0>(p8, c8, ph, cg.ih[0], kmu * cg.area[0], phi_e * ph.Dm * cg.area[0], out, qs);
+    cell_dir_faces<1>(p8, c8, ph, cg.ih[1], kmu * cg.area[1], phi_e * ph.Dm * cg.area[1], out, qs);
+    cell_dir_faces<2>(p8, c8, ph, cg.ih[2], kmu * cg.area[2], phi_e * ph.Dm * cg.area[2], out, qs);
 }
 
-__global__ void __launch_bounds__(kBS)
-    k_edge_flux(Grid G, Phys ph, CellGeom cg, const double* __restrict__ phi,
-                const double* __restrict__ K, const double* __restrict__ p,
-                const double* __restrict__ c, E4* __restrict__ edge, const int* mask,
-                int mstride)
+// Sum of the up to 4 quarter faces of the direction-D edge whose lower node
+// is (i, j, k) (the edge must exist); fixed order.
+template <int D>
+__device__ __forceinline__ void edge_sum(const Grid& G, const QF* __restrict__ qf, int i, int j,
+                                         int k, double& m, double& F, float& mm, float& Fm)
 {
-    const int s = blockIdx.y;
-    if (!sample_on(mask, mstride, s)) return;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= G.N) return;
-    const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
-    phi += oc; K += oc; p += on; c += on;
-    int i, j, k;
-    node_ijk(G, n, i, j, k);
-    E4 acc[3];
+    m = 0.0; F = 0.0; mm = 0.0f; Fm = 0.0f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) acc[d] = E4{0.0, 0.0, 0.0, 0.0};
-    edge_cell<0, 0, 0, true, true, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    edge_cell<0, -1, 0, true, false, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    edge_cell<0, 0, -1, true, true, false>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    edge_cell<-1, 0, 0, false, true, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    edge_cell<0, -1, -1, true, false, false>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    edge_cell<-1, 0, -1, false, true, false>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    edge_cell<-1, -1, 0, false, false, true>(G, ph, cg, i, j, k, phi, K, p, c, acc);
-    E4* out = edge + (size_t)s * 3 * G.N;
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) out[(size_t)d * G.N + n] = acc[d];
+        for (int b = 0; b < 2; ++b) {
+            int ci, cj, ck;
+            if (D == 0) { ci = i; cj = j - b; ck = k - a; }
+            else if (D == 1) { ci = i - b; cj = j; ck = k - a; }
+            else { ci = i - b; cj = j - a; ck = k; }
+            if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
+            const QF f = qf[(size_t)(4 * D + 2 * b + a) * G.C + ci + G.nx * (cj + G.ny * ck)];
+            m += f.m;
+            F += f.F;
+            mm += f.mm;
+            Fm += f.Fm;
+        }
 }
 
 __global__ void __launch_bounds__(kBS)
-    k_edge_residual(Grid G, Phys ph, const uint8_t* __restrict__ bc,
+    k_cell_residual(Grid G, Phys ph, const uint8_t* __restrict__ bc,
                     const double* __restrict__ cval, const double* __restrict__ phi,
                     const double* __restrict__ p, const double* __restrict__ c,
-                    const double* __restrict__ c_old, const E4* __restrict__ edge,
+                    const double* __restrict__ c_old, const QF* __restrict__ qf,
                     V2<double>* __restrict__ R, double* __restrict__ partial,
                     double* __restrict__ act, const int* mask, int mstride)
 {
@@ -220,30 +257,22 @@ __global__ void __launch_bounds__(kBS)
     if (!sample_on(mask, mstride, s)) return;
     const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
     phi += oc; p += on; c += on; c_old += on; R += on;
-    edge += (size_t)s * 3 * G.N;
+    qf += (size_t)s * 12 * G.C;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0, aq = 0.0;
     if (n < G.N) {
         int i, j, k;
         node_ijk(G, n, i, j, k);
-        const int st[3] = {1, G.nx + 1, (G.nx + 1) * (G.ny + 1)};
-        const bool back[3] = {i > 0, j > 0, k > 0};
-        double Rp = 0.0, Rc = 0.0, Ap = 0.0, Ac = 0.0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const E4 f = edge[(size_t)d * G.N + n];
-            Rp += f.m;
-            Rc += f.F;
-            Ap += f.mm;
-            Ac += f.Fm;
-            if (back[d]) {
-                const E4 b = edge[(size_t)d * G.N + n - st[d]];
-                Rp -= b.m;
-                Rc -= b.F;
-                Ap += b.mm;
-                Ac += b.Fm;
-            }
-        }
+        double Rp = 0.0, Rc = 0.0;
+        float Ap = 0.0f, Ac = 0.0f;
+        double m, F;
+        float mm, Fm;
+        if (i < G.nx) { edge_sum<0>(G, qf, i, j, k, m, F, mm, Fm); Rp += m; Rc += F; Ap += mm; Ac += Fm; }
+        if (i > 0) { edge_sum<0>(G, qf, i - 1, j, k, m, F, mm, Fm); Rp -= m; Rc -= F; Ap += mm; Ac += Fm; }
+        if (j < G.ny) { edge_sum<1>(G, qf, i, j, k, m, F, mm, Fm); Rp += m; Rc += F; Ap += mm; Ac += Fm; }
+        if (j > 0) { edge_sum<1>(G, qf, i, j - 1, k, m, F, mm, Fm); Rp -= m; Rc -= F; Ap += mm; Ac += Fm; }
+        if (k < G.nz) { edge_sum<2>(G, qf, i, j, k, m, F, mm, Fm); Rp += m; Rc += F; Ap += mm; Ac += Fm; }
+        if (k > 0) { edge_sum<2>(G, qf, i, j, k - 1, m, F, mm, Fm); Rp -= m; Rc -= F; Ap += mm; Ac += Fm; }
         double phis = 0.0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -256,14 +285,14 @@ __global__ void __launch_bounds__(kBS)
         const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
         Rp += vdt * (rn - ro);
         Rc += vdt * (rn * cn - ro * co);
-        Ap += vdt * (fabs(rn) + fabs(ro));
-        Ac += vdt * (fabs(rn * cn) + fabs(ro * co));
+        double Apd = (double)Ap + vdt * (fabs(rn) + fabs(ro));
+        double Acd = (double)Ac + vdt * (fabs(rn * cn) + fabs(ro * co));
         const uint8_t b = bc[n];
-        if (b & BC_P) { Rp = p[n]; Ap = 0.0; }
-        if (b & BC_C) { Rc = cn - cval[n]; Ac = 0.0; }
+        if (b & BC_P) { Rp = p[n]; Apd = 0.0; }
+        if (b & BC_C) { Rc = cn - cval[n]; Acd = 0.0; }
         R[n] = V2<double>{Rp, Rc};
         sq = Rp * Rp + Rc * Rc;
-        aq = Ap * Ap + Ac * Ac;
+        aq = Apd * Apd + Acd * Acd;
     }
     if (partial) {
         const double t = block_sum(sq, red);
@@ -280,13 +309,14 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* p, const double* c, const double* p_old,
                      const double* c_old, V2<double>* R, double* partial,
                      double* act, const int* mask, int mstride, int S,
-                     cudaStream_t st, E4* edge)
+                     cudaStream_t st, QF* qf)
 {
     (void)p_old;  // p has no time derivative
     count_launch(2);
+    dim3 gc(nblocks(G.C), S);
+    k_cell_flux<<<gc, kBS, 0, st>>>(G, ph, make_geom(G), phi, K, p, c, qf, mask, mstride);
     dim3 grid(nblocks(G.N), S);
-    k_edge_flux<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), phi, K, p, c, edge, mask, mstride);
-    k_edge_residual<<<grid, kBS, 0, st>>>(G, ph, bc, cval, phi, p, c, c_old, edge, R, partial,
+    k_cell_residual<<<grid, kBS, 0, st>>>(G, ph, bc, cval, phi, p, c, c_old, qf, R, partial,
                                           act, mask, mstride);
 }
 
@@ -433,7 +463,7 @@ __global__ void __launch_bounds__(128)
     k_jacobian(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
                const V2<T>* __restrict__ cellT, const V2<T>* __restrict__ nodeT,
                B4<T>* __restrict__ JT, B4<M>* __restrict__ JM, B4<T>* __restrict__ Dinv,
-               const int* mask, int mstride)
+               T vscale, const int* mask, int mstride)
 {
     const int s = blockIdx.y;
     if (!sample_on(mask, mstride, s)) return;
@@ -459,7 +489,7 @@ __global__ void __launch_bounds__(128)
     jac_cell<T, -1, 0, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     jac_cell<T, 0, 0, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     // lumped storage: d/dc of rho(c) and rho(c) c
-    const T vdt = phis * T(0.125 * G.hx * G.hy * G.hz / ph.dt);
+    const T vdt = phis * vscale;
     const T cn = nodeT[n].c;
     acc[13][1] += vdt * pt.drho;
     acc[13][3] += vdt * (pt.rho0 + T(2) * pt.drho * cn);
@@ -489,11 +519,12 @@ __global__ void __launch_bounds__(128)
                       mg_store<M>(acc[q][3])};
     }
     if (Dinv) {
-        double a = acc[13][0], bb = acc[13][1], cc = acc[13][2], e = acc[13][3];
-        if (b & BC_P) { a = 1.0; bb = 0.0; cc = 0.0; }
-        if (b & BC_C) { e = 1.0; bb = 0.0; cc = 0.0; }
-        const double id = 1.0 / (a * e - bb * cc);
-        Dinv[(size_t)s * G.N + n] = B4<T>{T(e * id), T(-bb * id), T(-cc * id), T(a * id)};
+        // in T: the FP32 entries' determinant is formed without FP64 work
+        T a = acc[13][0], bb = acc[13][1], cc = acc[13][2], e = acc[13][3];
+        if (b & BC_P) { a = T(1); bb = T(0); cc = T(0); }
+        if (b & BC_C) { e = T(1); bb = T(0); cc = T(0); }
+        const T id = T(1) / (a * e - bb * cc);
+        Dinv[(size_t)s * G.N + n] = B4<T>{e * id, -bb * id, -cc * id, a * id};
     }
 }
 
@@ -507,8 +538,10 @@ void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
     dim3 gin(nblocks(std::max(G.N, G.C)), S);
     k_jac_inputs<T><<<gin, kBS, 0, st>>>(G, ph, phi, K, p, c, cellT, nodeT, mask, mstride);
     dim3 grid(nblocks(G.N, 128), S);
+    // lumped storage volume per unit phi over dt: (h^3 / 8) / dt per cell corner
+    const T vscale = T(0.125 * G.hx * G.hy * G.hz / ph.dt);
     k_jacobian<T, M><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, cellT, nodeT, JT, JM, Dinv,
-                                            mask, mstride);
+                                            vscale, mask, mstride);
 }
 template void launch_jacobian<double, double>(const Grid&, const Phys&, const uint8_t*,
                                               const double*, const double*, const double*,

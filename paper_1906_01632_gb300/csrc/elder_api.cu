@@ -196,7 +196,7 @@ struct elder_ctx {
     double* partial2 = nullptr;
     double* partial3 = nullptr;
     double* pk = nullptr;              // packed batch for the FP64 re-solve
-    E4* edge = nullptr;                // [S][3][N] edge fluxes of the residual
+    QF* qf = nullptr;                  // [S][12][C] quarter-face fluxes of the residual
     double* mass = nullptr;            // [S][3] salt-mass balance
     double* h_mass = nullptr;          // pinned
     NScal* ns = nullptr;
@@ -575,7 +575,6 @@ void bicg_iteration(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int m
                     int S, cudaStream_t st)
 {
     const Grid& G = ctx->grids[0];
-    const int nb = ctx->nblk0;
     const int bs_mv = ctx->bs[ELDER_K_SPMV];
     const int nb_mv = nblocks(G.N, 32);  // per-warp partials of the stencil products
     KScal* ks = ctx->ks;
@@ -595,7 +594,7 @@ void bicg_iteration(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int m
     prof_end(ctx, pi, ELDER_K_SPMV, G, sizeof(T), sizeof(T), ctx->n_active_k, st);
     launch_bicg_finalize(2, ctx->partial, nb_mv, ks, rtol, maxit, S, st);
     launch_bicg_xr<T>(G, sv.ph, sv.sh, sv.s, sv.t, sv.rh, sv.x, sv.r, ctx->partial, ks, S, st);
-    launch_bicg_finalize(3, ctx->partial, nb, ks, rtol, maxit, S, st);
+    launch_bicg_finalize(3, ctx->partial, bicg_xr_blocks(G.N), ks, rtol, maxit, S, st);
 }
 
 __global__ void k_arm_krylov(KScal* ks, const NScal* ns, int S)
@@ -750,7 +749,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     CK(cudaMemcpyAsync(ns, ctx->h_ns, sizeof(NScal) * S, cudaMemcpyHostToDevice, st));
     int pi = prof_begin(ctx, st);
     launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, p, c, ctx->p_old, ctx->c_old, ctx->R,
-                    ctx->partial, ctx->partial2, nullptr, 0, S, st, ctx->edge);
+                    ctx->partial, ctx->partial2, nullptr, 0, S, st, ctx->qf);
     prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, 8, S, st);
     launch_norm_finalize(ctx->partial, ctx->partial2, nb, ns, 0, S, st);
     CKL();
@@ -775,7 +774,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
             pi = prof_begin(ctx, st);
             launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
                             ctx->c_old, ctx->Rt, ctx->partial, ctx->partial3, lsmask, NSTRIDE,
-                            S, st, ctx->edge);
+                            S, st, ctx->qf);
             prof_end(ctx, pi, ELDER_K_RESIDUAL, G, 8, 8, ctx->n_active_ls, st);
             launch_norm_finalize(ctx->partial, ctx->partial3, nb, ns, 1, S, st);
             launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, set.ls_max, S, st);
@@ -1122,8 +1121,8 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         ctx->partial = dalloc<double>((size_t)S * 2 * nblocks(G.N, 32));
         ctx->partial2 = dalloc<double>((size_t)S * 2 * ctx->nblk0);
         ctx->partial3 = dalloc<double>((size_t)S * 3 * ctx->nblk0);
-        ctx->edge = dalloc<E4>((size_t)S * 3 * G.N);
-        ctx->mem.add(ctx->edge);
+        ctx->qf = dalloc<QF>((size_t)S * 12 * G.C);
+        ctx->mem.add(ctx->qf);
         // Jacobian inputs in the solver's arithmetic type, reused level by level
         ctx->jin = dalloc<double>((size_t)S * 2 * (G.N + G.C));
         ctx->mem.add(ctx->jin);
@@ -1212,7 +1211,7 @@ int elder_residual(elder_ctx* ctx, int S, const double* phi, const double* K,
     try {
         launch_residual(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], ctx->cval, phi, K,
                         p, c, p_old, c_old, reinterpret_cast<V2<double>*>(R), nullptr, nullptr,
-                        nullptr, 0, S, (cudaStream_t)stream, ctx->edge);
+                        nullptr, 0, S, (cudaStream_t)stream, ctx->qf);
         CKL();
     } catch (const Fail& f) {
         return set_error(ctx, f);

@@ -57,8 +57,11 @@ struct NScal {
 
 // Flux through the dual face of one edge, out of its lower node: mass and
 // salt flux and the magnitudes of their terms.
-struct alignas(32) E4 {
-    double m, F, mm, Fm;
+// One quarter-face record of the residual: mass and salt flux from the
+// edge's lower to its upper end, and the magnitudes of their terms.
+struct alignas(8) QF {
+    double m, F;
+    float mm, Fm;
 };
 
 constexpr int kBS = 256;     // threads per block of the node kernels
@@ -66,6 +69,8 @@ constexpr int kMaxBS = 512;  // largest block of the autotuned stencil kernels
 constexpr int kMinBS = 128;  // smallest block of the autotuned stencil kernels
 
 inline int nblocks(int n, int bs = kBS) { return (n + bs - 1) / bs; }
+// blocks of the BiCGStab x/r update (4 nodes per thread): its partials per sample
+inline int bicg_xr_blocks(int n) { return nblocks((n + 3) / 4); }
 
 // Process-wide count of kernel launches made by this library.
 void count_launch(int n);
@@ -78,7 +83,7 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* p, const double* c, const double* p_old,
                      const double* c_old, V2<double>* R, double* partial,
                      double* act, const int* mask, int mask_stride, int S,
-                     cudaStream_t st, E4* edge);
+                     cudaStream_t st, QF* qf);
 // Jacobian rows as T (JT) and/or as the multigrid type M (JM), and the inverse
 // interior diagonal blocks (Dinv); null outputs are skipped.  cellT [S][C]
 // and nodeT [S][N] are scratch for the inputs converted to T.

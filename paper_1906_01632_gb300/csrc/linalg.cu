@@ -477,19 +477,26 @@ __global__ void __launch_bounds__(kBS)
     int i, j, k;
     node_ijk(Gf, n, i, j, k);
     xc += (size_t)s * Gc.N;
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1),
-            wk = (k & 1) ? T(0.5) : T(1);
-    T sp = T(0), sc = T(0);
-    for (int c = 0; c < nk; ++c)
-        for (int b = 0; b < nj; ++b)
-            for (int a = 0; a < ni; ++a) {
-                const V2<T> v = xc[node_id(Gc, I0 + a, J0 + b, K0 + c)];
-                const T w = wi * wj * wk;
-                sp += w * v.p;
-                sc += w * v.c;
-            }
+    // trilinear interpolation as three nested averages of the 8 coarse
+    // parents; for an even fine index both parents are the same node, whose
+    // average is exact, so no branch depends on the parity
+    const int sxc = Gc.nx + 1, szc = (Gc.nx + 1) * (Gc.ny + 1);
+    const int c0 = (i >> 1) + sxc * (j >> 1) + szc * (k >> 1);
+    const int di = i & 1, dj = (j & 1) * sxc, dk = (k & 1) * szc;
+    V2<T> v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        v[q] = xc[c0 + ((q & 1) ? di : 0) + ((q & 2) ? dj : 0) + ((q & 4) ? dk : 0)];
+    const T h = T(0.5);
+    T ap[4], ac[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ap[q] = h * (v[2 * q].p + v[2 * q + 1].p);
+        ac[q] = h * (v[2 * q].c + v[2 * q + 1].c);
+    }
+    const T bp0 = h * (ap[0] + ap[1]), bp1 = h * (ap[2] + ap[3]);
+    const T bc0 = h * (ac[0] + ac[1]), bc1 = h * (ac[2] + ac[3]);
+    const T sp = h * (bp0 + bp1), sc = h * (bc0 + bc1);
     const uint8_t m = bcf[n];
     V2<T> o = xf[(size_t)s * Gf.N + n];
     o.p = (m & BC_P) ? T(0) : o.p + sp;
@@ -638,6 +645,11 @@ void launch_bicg_s(const Grid& G, const V2<T>* r, const V2<T>* v, V2<T>* s,
     k_bicg_s<T><<<grid, kBS, 0, st>>>(G.N, r, v, s, ks);
 }
 
+// Each thread updates kXrNodes consecutive-stride nodes and sums its own
+// terms of the two inner products before the FP64 block reduction (for the
+// FP32 solver the per-thread sum is FP32, see dot2).
+constexpr int kXrNodes = 4;
+
 template <class T>
 __global__ void __launch_bounds__(kBS)
     k_bicg_xr(int N, const V2<T>* __restrict__ ph, const V2<T>* __restrict__ sh,
@@ -650,23 +662,27 @@ __global__ void __launch_bounds__(kBS)
     const int s = blockIdx.y;
     const KScal k = ks[s];
     if (!k.active) return;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double d0 = 0.0, d1 = 0.0;
-    if (n < N) {
-        const T a = ks_alpha<T>(k), w = ks_omega<T>(k);
-        const size_t q = (size_t)s * N + n;
-        const V2<T> pv = ph[q], shv = sh[q], svv = sv[q], tv = t[q], rhv = rh[q];
-        V2<T> xv = x[q];
-        xv.p += a * pv.p + w * shv.p;
-        xv.c += a * pv.c + w * shv.c;
-        x[q] = xv;
-        const V2<T> rv{svv.p - w * tv.p, svv.c - w * tv.c};
-        r[q] = rv;
-        d0 = dot2(rv.p, rv.c, rv.p, rv.c);
-        d1 = dot2(rhv.p, rhv.c, rv.p, rv.c);
+    const T a = ks_alpha<T>(k), w = ks_omega<T>(k);
+    T l0 = T(0), l1 = T(0);
+    const int stride = gridDim.x * blockDim.x;
+#pragma unroll
+    for (int u = 0; u < kXrNodes; ++u) {
+        const int n = blockIdx.x * blockDim.x + threadIdx.x + u * stride;
+        if (n < N) {
+            const size_t q = (size_t)s * N + n;
+            const V2<T> pv = ph[q], shv = sh[q], svv = sv[q], tv = t[q], rhv = rh[q];
+            V2<T> xv = x[q];
+            xv.p += a * pv.p + w * shv.p;
+            xv.c += a * pv.c + w * shv.c;
+            x[q] = xv;
+            const V2<T> rv{svv.p - w * tv.p, svv.c - w * tv.c};
+            r[q] = rv;
+            l0 += rv.p * rv.p + rv.c * rv.c;
+            l1 += rhv.p * rv.p + rhv.c * rv.c;
+        }
     }
-    const double t0 = block_sum(d0, red);
-    const double t1 = block_sum(d1, red);
+    const double t0 = block_sum((double)l0, red);
+    const double t1 = block_sum((double)l1, red);
     if (threadIdx.x == 0) {
         partial[((size_t)s * 2 + 0) * gridDim.x + blockIdx.x] = t0;
         partial[((size_t)s * 2 + 1) * gridDim.x + blockIdx.x] = t1;
@@ -680,7 +696,7 @@ void launch_bicg_xr(const Grid& G, const V2<T>* ph, const V2<T>* sh,
                     cudaStream_t st)
 {
     count_launch(1);
-    dim3 grid(nblocks(G.N), S);
+    dim3 grid(bicg_xr_blocks(G.N), S);
     k_bicg_xr<T><<<grid, kBS, 0, st>>>(G.N, ph, sh, s, t, rh, x, r, partial, ks);
 }
 
