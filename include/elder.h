@@ -342,9 +342,10 @@ int elder_gpc_project(int M, int T, const int32_t* beta, int maxdeg, int Nq,
 /* Exceedance probability from the surrogate: for each listed node n
  * (nodes[k], or n = k for k < n_pts when nodes is NULL), the fraction of the
  * Ns points theta [Ns][M] at which sum_t coef[t][n] P_{beta_t}(theta) is
- * above threshold.  The surrogate is evaluated in FP32 (coefficients and
- * basis values rounded to FP32, FP32 fused multiply-adds in the order of
- * t); its error is below about 4 T 2^-24 sum_t |coef[t][n]|.  Device arrays:
+ * above threshold.  The surrogate is evaluated in FP32 (coefficients rounded
+ * to FP32, basis values by the FP32 Legendre recurrence, FP32 fused
+ * multiply-adds in the order of t); its error is below about
+ * 16 T 2^-24 sum_t |coef[t][n]| for degrees up to 8.  Device arrays:
  * beta [T][M], coef [T][N] (from elder_gpc_project), nodes [n_pts] int32 or
  * NULL, theta [Ns][M] (the caller draws the points), p_exceed [n_pts]
  * output (used as 64-bit counters until the last kernel converts them).

@@ -339,6 +339,11 @@ template <class T> struct PhysT {
     T rho0, drho, g, Dm;
 };
 
+// Cell geometry in the assembly's arithmetic type (converted on the host).
+template <class T> struct GeomT {
+    T ih[3], area[3];
+};
+
 template <class T, int D, int S_, int T_, int OX, int OY, int OZ>
 __device__ __forceinline__ void jac_face(const T (&p8)[8], const T (&c8)[8],
                                          T phi_e, T kmu, const PhysT<T>& ph,
@@ -400,7 +405,7 @@ __device__ __forceinline__ void jac_face(const T (&p8)[8], const T (&c8)[8],
 
 template <class T, int OX, int OY, int OZ>
 __device__ __forceinline__ void jac_cell(const Grid& G, const PhysT<T>& pt,
-                                         const CellGeom& cg, int i, int j, int k,
+                                         const GeomT<T>& cg, int i, int j, int k,
                                          const V2<T>* __restrict__ cellT,
                                          const V2<T>* __restrict__ nodeT,
                                          T (&acc)[27][4], T& phis)
@@ -422,9 +427,9 @@ __device__ __forceinline__ void jac_cell(const Grid& G, const PhysT<T>& pt,
         c8[L] = u.c;
     }
     constexpr int lx = -OX, ly = -OY, lz = -OZ;
-    jac_face<T, 0, ly, lz, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, T(cg.ih[0]), T(cg.area[0]), acc);
-    jac_face<T, 1, lx, lz, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, T(cg.ih[1]), T(cg.area[1]), acc);
-    jac_face<T, 2, lx, ly, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, T(cg.ih[2]), T(cg.area[2]), acc);
+    jac_face<T, 0, ly, lz, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, cg.ih[0], cg.area[0], acc);
+    jac_face<T, 1, lx, lz, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, cg.ih[1], cg.area[1], acc);
+    jac_face<T, 2, lx, ly, OX, OY, OZ>(p8, c8, fk.p, fk.c, pt, cg.ih[2], cg.area[2], acc);
 }
 
 // Inputs of the Jacobian in its arithmetic type T, converted once per level
@@ -460,7 +465,7 @@ __global__ void k_jac_inputs(Grid G, Phys ph, const double* __restrict__ phi,
 // the three outputs may be null.
 template <class T, class M>
 __global__ void __launch_bounds__(128)
-    k_jacobian(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
+    k_jacobian(Grid G, PhysT<T> pt, GeomT<T> cg, const uint8_t* __restrict__ bc,
                const V2<T>* __restrict__ cellT, const V2<T>* __restrict__ nodeT,
                B4<T>* __restrict__ JT, B4<M>* __restrict__ JM, B4<T>* __restrict__ Dinv,
                T vscale, const int* mask, int mstride)
@@ -471,7 +476,6 @@ __global__ void __launch_bounds__(128)
     if (n >= G.N) return;
     const size_t on = (size_t)s * G.N, oc = (size_t)s * G.C;
     cellT += oc; nodeT += on;
-    PhysT<T> pt{T(ph.rho0), T(ph.drho), T(ph.g), T(ph.Dm)};
     int i, j, k;
     node_ijk(G, n, i, j, k);
     T acc[27][4];
@@ -540,8 +544,15 @@ void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
     dim3 grid(nblocks(G.N, 128), S);
     // lumped storage volume per unit phi over dt: (h^3 / 8) / dt per cell corner
     const T vscale = T(0.125 * G.hx * G.hy * G.hz / ph.dt);
-    k_jacobian<T, M><<<grid, 128, 0, st>>>(G, ph, make_geom(G), bc, cellT, nodeT, JT, JM, Dinv,
-                                            vscale, mask, mstride);
+    const CellGeom cgd = make_geom(G);
+    GeomT<T> cg;
+    for (int d = 0; d < 3; ++d) {
+        cg.ih[d] = T(cgd.ih[d]);
+        cg.area[d] = T(cgd.area[d]);
+    }
+    const PhysT<T> pt{T(ph.rho0), T(ph.drho), T(ph.g), T(ph.Dm)};
+    k_jacobian<T, M><<<grid, 128, 0, st>>>(G, pt, cg, bc, cellT, nodeT, JT, JM, Dinv, vscale,
+                                            mask, mstride);
 }
 template void launch_jacobian<double, double>(const Grid&, const Phys&, const uint8_t*,
                                               const double*, const double*, const double*,

@@ -10,9 +10,9 @@
 //                  shared memory, then each thread streams its node's values
 //                  and keeps one FP64 accumulator per basis function);
 //   k_gpc_exceed   the surrogate at N_s sample points per node and the count
-//                  above a threshold (FP32: coefficients in registers, basis
-//                  values of a chunk of samples broadcast from shared memory,
-//                  samples split across blocks with integer atomics).
+//                  above a threshold (FP32: coefficients in registers, FP32
+//                  basis values of a chunk of samples broadcast from shared
+//                  memory, samples split across blocks with integer atomics).
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -38,13 +38,23 @@ __host__ __device__ inline void legendre_all(int n, double x, double* P)
     for (int k = 1; k < n; ++k) P[k + 1] = ((2 * k + 1) * x * P[k] - k * P[k - 1]) / (k + 1);
 }
 
+// FP32 recurrence for the surrogate evaluation (its sums are FP32 anyway;
+// on GB300 FP64 runs at 1/64 of the FP32 rate).
+__device__ inline void legendre_all_f(int n, float x, float* P)
+{
+    P[0] = 1.0f;
+    if (n >= 1) P[1] = x;
+    for (int k = 1; k < n; ++k) P[k + 1] = ((2 * k + 1) * x * P[k] - k * P[k - 1]) / (k + 1);
+}
+
 // P_beta(theta) for one point; beta is [T][M], P1 scratch [M][maxdeg+1].
 // (beta entries outside [0, maxdeg] are clamped: a caller error gives wrong
 // values, never an out-of-range read)
-__device__ inline double basis_value(const int32_t* beta, int t, int M, const double* P1,
-                                     int stride, int maxdeg)
+template <class R>
+__device__ inline R basis_value(const int32_t* beta, int t, int M, const R* P1, int stride,
+                                int maxdeg)
 {
-    double v = 1.0;
+    R v = R(1);
     for (int j = 0; j < M; ++j) v *= P1[j * stride + min(max((int)beta[t * M + j], 0), maxdeg)];
     return v;
 }
@@ -125,12 +135,13 @@ __global__ void __launch_bounds__(kGpcBS)
         if (threadIdx.x < kGpcChunk) {
             const int j = threadIdx.x;
             if (j < nc) {
-                double P1[kGpcMaxM * (kGpcMaxDeg + 1)];
+                float P1[kGpcMaxM * (kGpcMaxDeg + 1)];
                 for (int m = 0; m < M; ++m)
-                    legendre_all(maxdeg, theta[(size_t)(c0 + j) * M + m],
-                                 P1 + m * (kGpcMaxDeg + 1));
+                    legendre_all_f(maxdeg, (float)theta[(size_t)(c0 + j) * M + m],
+                                   P1 + m * (kGpcMaxDeg + 1));
                 for (int t = 0; t < TP; ++t)
-                    Bs[j][t] = t < T ? (float)basis_value(beta, t, M, P1, kGpcMaxDeg + 1, maxdeg) : 0.f;
+                    Bs[j][t] = t < T ? basis_value<float>(beta, t, M, P1, kGpcMaxDeg + 1, maxdeg)
+                                     : 0.f;
             }
         }
         __syncthreads();

@@ -286,21 +286,36 @@ __global__ void __launch_bounds__(kLineBS)
     V2<T> gp{T(0), T(0)};
     uint8_t bc_prev = 0;
     uint8_t mk = bc[col];
-    for (int k = 0; k <= G.nz; ++k) {
+    // the loads of node k + 1 are issued before the arithmetic of node k
+    // (each thread walks its line serially and few warps fit an SM)
+    struct In {
+        V2<T> b;
+        B4<T> di;
+        B4<M> qL, qU;
+        uint8_t bcn;
+    };
+    auto load = [&](int k, In& in) {
         const int n = col + k * sz;
-        const uint8_t bc_next = (k < G.nz) ? bc[n + sz] : uint8_t(0);
-        const V2<T> bv = b[on_ + n];
-        T rp = bv.p, rc = bv.c;
-        B4<M> qL{}, qU{};
+        in.bcn = (k < G.nz) ? bc[n + sz] : uint8_t(0);
+        in.b = b[on_ + n];
+        in.di = Dinv[on_ + n];
         if (k > 0)
-            qL = !TRANS ? Js[(size_t)slot27(0, 0, -1) * G.N + n]
-                        : Js[(size_t)slot27(0, 0, 1) * G.N + n - sz];
+            in.qL = !TRANS ? Js[(size_t)slot27(0, 0, -1) * G.N + n]
+                           : Js[(size_t)slot27(0, 0, 1) * G.N + n - sz];
         if (k < G.nz)
-            qU = !TRANS ? Js[(size_t)slot27(0, 0, 1) * G.N + n]
-                        : Js[(size_t)slot27(0, 0, -1) * G.N + n + sz];
+            in.qU = !TRANS ? Js[(size_t)slot27(0, 0, 1) * G.N + n]
+                           : Js[(size_t)slot27(0, 0, -1) * G.N + n + sz];
+    };
+    In cur, nxt;
+    load(0, cur);
+    for (int k = 0; k <= G.nz; ++k) {
+        if (k < G.nz) load(k + 1, nxt);
+        const uint8_t bc_next = cur.bcn;
+        T rp = cur.b.p, rc = cur.b.c;
+        const B4<M> qL = cur.qL, qU = cur.qU;
         if (mk & BC_P) rp = T(0);
         if (mk & BC_C) rc = T(0);
-        B4<T> di = Dinv[on_ + n];
+        B4<T> di = cur.di;
         if (TRANS) di = B4<T>{di.pp, di.cp, di.pc, di.cc};
         B4<T> Mk = inv2(di);
         if (k > 0) {
@@ -320,6 +335,7 @@ __global__ void __launch_bounds__(kLineBS)
         gs[(size_t)k * bsz + tx] = gp;
         bc_prev = mk;
         mk = bc_next;
+        cur = nxt;
     }
     V2<T> d = gp;
     for (int k = G.nz;; --k) {
