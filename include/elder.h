@@ -88,12 +88,14 @@ typedef struct {
     int ls_max;               /* step halvings before the sample's line
                                  search fails (status LINESEARCH)           */
     /* BiCGStab (Section 5.1) */
-    double lin_rtol;          /* relative residual target per Newton solve  */
+    double lin_rtol;          /* relative residual target per Newton solve
+                                 (default 3e-3: inexact Newton)             */
     int lin_maxit;            /* iteration cap                              */
     /* geometric multigrid V-cycle (Section 5.1) */
     int mg_levels;            /* 0 = coarsen as far as the grid allows      */
     int nu1, nu2;             /* pre/post smoothing sweeps                  */
-    double omega;             /* damping of the block-Jacobi smoother       */
+    double omega;             /* damping of the point block-Jacobi smoother
+                                 (default 0.5)                              */
     int coarse_K_harmonic;    /* 0 arithmetic, 1 harmonic mean of K         */
     int use_graphs;           /* capture the Krylov iteration in CUDA graphs*/
     int autotune;             /* time threads-per-block candidates of the
@@ -107,7 +109,9 @@ typedef struct {
                                  tridiagonal solve per line, nz <= 128;
                                  the default).  The robust re-solve of
                                  failed samples always uses the z-line
-                                 smoother.                                  */
+                                 smoother (damping 0.5).                    */
+    double omega_line;        /* damping of the z-line smoother (default
+                                 0.75)                                      */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */

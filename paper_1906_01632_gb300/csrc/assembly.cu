@@ -629,9 +629,9 @@ void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
 // partial pivoting, FP64), one block per sample.  work: [S][n][2n].
 // ---------------------------------------------------------------------------
 
-template <class M>
+template <class M, class R>
 __global__ void k_coarse_build(Grid G, const uint8_t* __restrict__ bc,
-                               const B4<M>* __restrict__ J, double* __restrict__ W,
+                               const B4<M>* __restrict__ J, R* __restrict__ W,
                                const int* mask, int mstride)
 {
     const int s = blockIdx.y;
@@ -639,9 +639,9 @@ __global__ void k_coarse_build(Grid G, const uint8_t* __restrict__ bc,
     const int node = blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= G.N) return;
     const int n2 = 2 * G.N;
-    double* row0 = W + (size_t)s * n2 * 2 * n2 + (size_t)(2 * node) * 2 * n2;
-    double* row1 = row0 + 2 * n2;
-    for (int q = 0; q < 2 * n2; ++q) { row0[q] = 0.0; row1[q] = 0.0; }
+    R* row0 = W + (size_t)s * n2 * 2 * n2 + (size_t)(2 * node) * 2 * n2;
+    R* row1 = row0 + 2 * n2;
+    for (int q = 0; q < 2 * n2; ++q) { row0[q] = R(0); row1[q] = R(0); }
     int i, j, k;
     node_ijk(G, node, i, j, k);
     const uint8_t mr = bc[node];
@@ -655,49 +655,63 @@ __global__ void k_coarse_build(Grid G, const uint8_t* __restrict__ bc,
                 const uint8_t mc = bc[m];
                 const B4<M> B = J[((size_t)s * 27 + slot27(dx, dy, dz)) * G.N + node];
                 if (!(mr & BC_P)) {
-                    if (!(mc & BC_P)) row0[2 * m] = mg_load<double>(B.pp);
-                    if (!(mc & BC_C)) row0[2 * m + 1] = mg_load<double>(B.pc);
+                    if (!(mc & BC_P)) row0[2 * m] = mg_load<R>(B.pp);
+                    if (!(mc & BC_C)) row0[2 * m + 1] = mg_load<R>(B.pc);
                 }
                 if (!(mr & BC_C)) {
-                    if (!(mc & BC_P)) row1[2 * m] = mg_load<double>(B.cp);
-                    if (!(mc & BC_C)) row1[2 * m + 1] = mg_load<double>(B.cc);
+                    if (!(mc & BC_P)) row1[2 * m] = mg_load<R>(B.cp);
+                    if (!(mc & BC_C)) row1[2 * m + 1] = mg_load<R>(B.cc);
                 }
             }
-    if (mr & BC_P) row0[2 * node] = 1.0;
-    if (mr & BC_C) row1[2 * node + 1] = 1.0;
-    row0[n2 + 2 * node] = 1.0;
-    row1[n2 + 2 * node + 1] = 1.0;
+    if (mr & BC_P) row0[2 * node] = R(1);
+    if (mr & BC_C) row1[2 * node + 1] = R(1);
+    row0[n2 + 2 * node] = R(1);
+    row1[n2 + 2 * node + 1] = R(1);
 }
 
-__global__ void k_gauss_jordan(int n, double* __restrict__ W,
-                               double* __restrict__ Ainv, const int* mask,
+// Gauss-Jordan with partial pivoting on [A | I] of one sample per block, in
+// arithmetic R (FP32 for the mixed solver, whose coarse matrix is stored in
+// bfloat16 and is only a preconditioner; FP64 otherwise).  SMEM: the
+// augmented matrix is copied into shared memory first (it fits for the
+// 100-unknown 4x4x1 coarsest grid), which keeps the n elimination sweeps
+// off L2; otherwise it is eliminated in place in global memory.  Each warp
+// updates whole rows, columns k..2n-1 only.
+template <bool SMEM, class R>
+__global__ void k_gauss_jordan(int n, R* __restrict__ W, R* __restrict__ Ainv, const int* mask,
                                int mstride)
 {
-    extern __shared__ double sh[];  // n factors + reduction scratch
-    __shared__ double rv[32];
+    extern __shared__ __align__(16) unsigned char gj_smem[];
+    __shared__ R rv[32];
     __shared__ int ri[32];
     const int s = blockIdx.x;
     if (!sample_on(mask, mstride, s)) return;
     const int w2 = 2 * n;
-    double* A = W + (size_t)s * n * w2;
-    double* f = sh;
+    R* f = reinterpret_cast<R*>(gj_smem);
+    R* A = W + (size_t)s * n * w2;
+    if (SMEM) {
+        R* As = f + n;
+        for (int q = threadIdx.x; q < n * w2; q += blockDim.x) As[q] = A[q];
+        A = As;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = 0; k < n; ++k) {
-        // pivot: argmax |A[r][k]| over r >= k
-        double best = -1.0;
+        // pivot: argmax |A[r][k]| over r >= k (ties to the lower row)
+        R best = R(-1);
         int bi = k;
         for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-            const double a = fabs(A[(size_t)r * w2 + k]);
+            const R a = fabs(A[(size_t)r * w2 + k]);
             if (a > best) { best = a; bi = r; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+        if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            for (int q = 1; q < nw; ++q)
                 if (rv[q] > rv[0] || (rv[q] == rv[0] && ri[q] < ri[0])) { rv[0] = rv[q]; ri[0] = ri[q]; }
         }
         __syncthreads();
@@ -705,24 +719,25 @@ __global__ void k_gauss_jordan(int n, double* __restrict__ W,
         __syncthreads();
         if (piv != k)
             for (int q = threadIdx.x; q < w2; q += blockDim.x) {
-                const double t = A[(size_t)k * w2 + q];
+                const R t = A[(size_t)k * w2 + q];
                 A[(size_t)k * w2 + q] = A[(size_t)piv * w2 + q];
                 A[(size_t)piv * w2 + q] = t;
             }
         __syncthreads();
-        const double inv = 1.0 / A[(size_t)k * w2 + k];
+        const R inv = R(1) / A[(size_t)k * w2 + k];
         __syncthreads();
         for (int q = threadIdx.x; q < w2; q += blockDim.x) A[(size_t)k * w2 + q] *= inv;
         for (int r = threadIdx.x; r < n; r += blockDim.x) f[r] = A[(size_t)r * w2 + k];
         __syncthreads();
-        for (int idx = threadIdx.x; idx < n * w2; idx += blockDim.x) {
-            const int r = idx / w2, q = idx - r * w2;
-            if (r == k || q < k) continue;
-            A[(size_t)r * w2 + q] -= f[r] * A[(size_t)k * w2 + q];
+        for (int r = warp; r < n; r += nw) {
+            if (r == k) continue;
+            const R fr = f[r];
+            for (int q = k + lane; q < w2; q += 32)
+                A[(size_t)r * w2 + q] -= fr * A[(size_t)k * w2 + q];
         }
         __syncthreads();
     }
-    double* out = Ainv + (size_t)s * n * n;
+    R* out = Ainv + (size_t)s * n * n;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int r = idx / n, q = idx - r * n;
         out[idx] = A[(size_t)r * w2 + n + q];
@@ -734,12 +749,25 @@ void launch_coarse_inverse(const Grid& G, const uint8_t* bc, const B4<M>* J,
                            double* work, double* Ainv, const int* mask,
                            int mstride, int S, cudaStream_t st)
 {
-    count_launch(1);
+    using R = typename CoarseType<M>::type;
+    count_launch(2);
     dim3 grid(nblocks(G.N, 64), S);
-    k_coarse_build<M><<<grid, 64, 0, st>>>(G, bc, J, work, mask, mstride);
+    R* W = reinterpret_cast<R*>(work);
+    k_coarse_build<M, R><<<grid, 64, 0, st>>>(G, bc, J, W, mask, mstride);
     const int n = 2 * G.N;
-    count_launch(1);
-    k_gauss_jordan<<<S, 256, sizeof(double) * n, st>>>(n, work, Ainv, mask, mstride);
+    R* Ai = reinterpret_cast<R*>(Ainv);
+    const size_t smem = sizeof(R) * ((size_t)n + (size_t)2 * n * n);
+    if (smem <= 200 * 1024) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_gauss_jordan<true, R>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        k_gauss_jordan<true, R><<<S, 256, smem, st>>>(n, W, Ai, mask, mstride);
+    } else {
+        k_gauss_jordan<false, R><<<S, 256, sizeof(R) * n, st>>>(n, W, Ai, mask, mstride);
+    }
 }
 template void launch_coarse_inverse<double>(const Grid&, const uint8_t*,
                                             const B4<double>*, double*,

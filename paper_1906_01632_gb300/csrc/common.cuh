@@ -52,6 +52,11 @@ template <class T> struct alignas(4 * sizeof(T)) B4 { T pp, pc, cp, cc; };
 template <class T> struct MgType { using type = T; };
 template <> struct MgType<float> { using type = __nv_bfloat16; };
 
+// Arithmetic of the dense coarsest-grid inverse: FP32 under bfloat16
+// multigrid matrices (mixed solver), FP64 otherwise.
+template <class M> struct CoarseType { using type = double; };
+template <> struct CoarseType<__nv_bfloat16> { using type = float; };
+
 template <class T> __device__ __forceinline__ T mg_load(__nv_bfloat16 v)
 {
     return T(__bfloat162float(v));

@@ -211,6 +211,7 @@ struct elder_ctx {
     // threads per block of the autotuned kernel classes (indexed by ELDER_K_*)
     int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, kBS};
     int smoother_now = ELDER_SMOOTH_JACOBI;  // smoother of the solve in progress
+    double omega_now = 0.5;                  // its damping
     double* jin = nullptr;  // Jacobian input scratch, [S][N] + [S][C] pairs
     bool tuned[2] = {false, false};    // per precision (FP64, FP32)
     float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
@@ -242,6 +243,12 @@ Phys make_phys(const elder_config& c, double dt)
 // Algorithmic DRAM bytes and flops per node of one launch (every array the
 // kernel must touch, read or written once; neighbour reuse of x is free).
 // T = bytes of the solver type.  J row: 27 blocks of 4; vectors: 2 values.
+// Damping of the configured smoother.
+double configured_omega(const elder_config& cf)
+{
+    return cf.smoother == ELDER_SMOOTH_ZLINE ? cf.omega_line : cf.omega;
+}
+
 double model_bytes(int cls, int T, int Mz, const Grid& G, bool line)
 {
     // T: bytes of a vector / Dinv entry; Mz: bytes of a stored matrix entry
@@ -477,16 +484,16 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     auto sweep = [&](const V2<T>* xin, V2<T>* xout) {
         if (line && xin == nullptr) {
             launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout,
-                                      cf.omega, trans, mask, KSTRIDE, S, st, 1);
+                                      ctx->omega_now, trans, mask, KSTRIDE, S, st, 1);
         } else if (line) {
             // residual at full stream rate into the level's residual vector
             // (free once the restriction has been made), then the line solves
             launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, xin, sv.mr[l], trans, mask,
                                      KSTRIDE, S, st, bs_mr);
             launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], sv.mr[l], xin, xout,
-                                      cf.omega, trans, mask, KSTRIDE, S, st, 2);
+                                      ctx->omega_now, trans, mask, KSTRIDE, S, st, 2);
         } else
-            launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout, cf.omega,
+            launch_smooth<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout, ctx->omega_now,
                                 trans, mask, KSTRIDE, S, st, bs_sm);
     };
     int pi = prof_begin(ctx, st);
@@ -640,7 +647,8 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
     // bypassed while per-launch events are recorded.
     const bool use_exec = ctx->cfg.use_graphs != 0 && !ctx->prof.on &&
                           rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit &&
-                          ctx->smoother_now == ctx->cfg.smoother;
+                          ctx->smoother_now == ctx->cfg.smoother &&
+                          ctx->omega_now == configured_omega(ctx->cfg);
     cudaGraphExec_t exec = nullptr;
     long long per_replay = 0;
     if (use_exec) {
@@ -685,13 +693,19 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
 struct NewtonSettings {
     double lin_rtol;
     int lin_maxit, ls_max, newton_maxit, estimate, keep_best, smoother;
+    double omega;
 };
 
 NewtonSettings configured_settings(const elder_config& cf)
 {
     return NewtonSettings{cf.lin_rtol, cf.lin_maxit, cf.ls_max, cf.newton_maxit,
-                          cf.newton_estimate, 0, cf.smoother};
+                          cf.newton_estimate, 0, cf.smoother, configured_omega(cf)};
 }
+
+// Damping of the robust re-solve's z-line smoother: on the steepest first
+// steps of rough fields 0.5 converges where larger values need more
+// iterations or stall.
+constexpr double kRobustOmega = 0.5;
 
 // Settings of the last re-solve of a failed sample: the z-line smoother, a
 // tighter and longer Krylov solve that returns its best iterate, more step
@@ -702,6 +716,7 @@ NewtonSettings robust_settings(const elder_config& cf)
 {
     NewtonSettings r = configured_settings(cf);
     r.smoother = ELDER_SMOOTH_ZLINE;
+    r.omega = kRobustOmega;
     r.lin_rtol = std::min(cf.lin_rtol, 1e-6);
     r.lin_maxit = std::max(20 * cf.lin_maxit, 2000);
     r.ls_max = std::max(cf.ls_max, 16);
@@ -767,8 +782,10 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         if (it == 0) autotune<T>(ctx, sv, S, st);
         launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
         ctx->smoother_now = set.smoother;
+        ctx->omega_now = set.omega;
         bicgstab<T>(ctx, sv, 0, set.lin_rtol, set.lin_maxit, ns, S, st, set.keep_best);
         ctx->smoother_now = cf.smoother;
+        ctx->omega_now = configured_omega(cf);
         for (int ls = 0; ls <= set.ls_max; ++ls) {
             launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
             pi = prof_begin(ctx, st);
@@ -1017,12 +1034,13 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->newton_tol_c = 1e-11;
     cfg->newton_tol_p = 1e-11 * 1000.0 * 9.81 * 150.0;
     cfg->ls_max = 6;
-    cfg->lin_rtol = 1e-4;
+    cfg->lin_rtol = 3e-3;
     cfg->lin_maxit = 100;
     cfg->mg_levels = 0;
     cfg->nu1 = 1;
     cfg->nu2 = 1;
     cfg->omega = 0.5;
+    cfg->omega_line = 0.75;
     cfg->coarse_K_harmonic = 0;
     cfg->use_graphs = 1;
     cfg->autotune = 1;
@@ -1049,7 +1067,8 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         !(c.Ly > 0) || !(c.Lz > 0) || !(c.mu > 0) || c.bc_mode < 0 || c.bc_mode > 3 ||
         (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
         c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0 ||
-        (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE)) {
+        (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE) ||
+        !(c.omega > 0) || !(c.omega_line > 0)) {
         g_create_error = "invalid elder_config";
         return ELDER_EINVAL;
     }
@@ -1064,6 +1083,7 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
     std::unique_ptr<elder_ctx> ctx(new elder_ctx());
     ctx->cfg = c;
     ctx->smoother_now = c.smoother;
+    ctx->omega_now = configured_omega(c);
     try {
         CK(cudaGetDevice(&ctx->device));
         // hierarchy: halve while all three counts are even (and the top square
@@ -1454,9 +1474,11 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
                     // the transposed system of a step on a steep front: again
                     // with the z-line smoother and a longer solve
                     ctx->smoother_now = ELDER_SMOOTH_ZLINE;
+                    ctx->omega_now = kRobustOmega;
                     bicgstab<double>(ctx, sv, 1, 1e-12, std::max(20 * ctx->cfg.lin_maxit, 4000),
                                      nullptr, 1, st, 1);
                     ctx->smoother_now = ctx->cfg.smoother;
+                    ctx->omega_now = configured_omega(ctx->cfg);
                     if (!krylov_converged(ctx, st)) {
                         rc_all = ELDER_ENOTCONV;
                         ctx->err = "elder_grad: adjoint solve of step " + std::to_string(n) +

@@ -118,26 +118,33 @@ __global__ void __launch_bounds__(kGpcBS)
                  unsigned long long* __restrict__ cnt)
 {
     __shared__ __align__(16) float Bs[kGpcChunk][TP];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = k < n_pts;
-    const int n = live ? (nodes ? nodes[k] : k) : 0;
-    float c[TP];
+    // two listed nodes per thread (k0, k0 + blockDim.x): each basis value
+    // read from shared memory feeds two FMA chains
+    const int k0 = blockIdx.x * 2 * blockDim.x + threadIdx.x;
+    const int k1 = k0 + blockDim.x;
+    const bool live0 = k0 < n_pts, live1 = k1 < n_pts;
+    const int n0 = live0 ? (nodes ? nodes[k0] : k0) : 0;
+    const int n1 = live1 ? (nodes ? nodes[k1] : k1) : 0;
+    float c0v[TP], c1v[TP];
 #pragma unroll
-    for (int t = 0; t < TP; ++t) c[t] = (live && t < T) ? (float)coef[(size_t)t * N + n] : 0.f;
+    for (int t = 0; t < TP; ++t) {
+        c0v[t] = (live0 && t < T) ? (float)coef[(size_t)t * N + n0] : 0.f;
+        c1v[t] = (live1 && t < T) ? (float)coef[(size_t)t * N + n1] : 0.f;
+    }
     // this block's slice of the samples
     const int per = (Ns + gridDim.y - 1) / gridDim.y;
     const int s0 = blockIdx.y * per;
     const int s1 = min(Ns, s0 + per);
-    unsigned int count = 0;
-    for (int c0 = s0; c0 < s1; c0 += kGpcChunk) {
-        const int nc = min(kGpcChunk, s1 - c0);
+    unsigned int count0 = 0, count1 = 0;
+    for (int cs = s0; cs < s1; cs += kGpcChunk) {
+        const int nc = min(kGpcChunk, s1 - cs);
         __syncthreads();
         if (threadIdx.x < kGpcChunk) {
             const int j = threadIdx.x;
             if (j < nc) {
                 float P1[kGpcMaxM * (kGpcMaxDeg + 1)];
                 for (int m = 0; m < M; ++m)
-                    legendre_all_f(maxdeg, (float)theta[(size_t)(c0 + j) * M + m],
+                    legendre_all_f(maxdeg, (float)theta[(size_t)(cs + j) * M + m],
                                    P1 + m * (kGpcMaxDeg + 1));
                 for (int t = 0; t < TP; ++t)
                     Bs[j][t] = t < T ? basis_value<float>(beta, t, M, P1, kGpcMaxDeg + 1, maxdeg)
@@ -145,20 +152,32 @@ __global__ void __launch_bounds__(kGpcBS)
             }
         }
         __syncthreads();
-        for (int j = 0; j < nc; ++j) {
-            float a = 0.f;
+        // two samples at a time for each of the two nodes: four independent
+        // FMA chains (each sum still runs over t in order); rows at or past nc
+        // (the tail of the last chunk; kGpcChunk is even) are evaluated but
+        // not counted
+        for (int j = 0; j < nc; j += 2) {
+            float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
 #pragma unroll
             for (int t = 0; t < TP; t += 4) {
-                const float4 b = *reinterpret_cast<const float4*>(&Bs[j][t]);
-                a = fmaf(c[t], b.x, a);
-                a = fmaf(c[t + 1], b.y, a);
-                a = fmaf(c[t + 2], b.z, a);
-                a = fmaf(c[t + 3], b.w, a);
+                const float4 b0 = *reinterpret_cast<const float4*>(&Bs[j][t]);
+                const float4 b1 = *reinterpret_cast<const float4*>(&Bs[j + 1][t]);
+                a00 = fmaf(c0v[t], b0.x, a00); a00 = fmaf(c0v[t + 1], b0.y, a00);
+                a00 = fmaf(c0v[t + 2], b0.z, a00); a00 = fmaf(c0v[t + 3], b0.w, a00);
+                a01 = fmaf(c0v[t], b1.x, a01); a01 = fmaf(c0v[t + 1], b1.y, a01);
+                a01 = fmaf(c0v[t + 2], b1.z, a01); a01 = fmaf(c0v[t + 3], b1.w, a01);
+                a10 = fmaf(c1v[t], b0.x, a10); a10 = fmaf(c1v[t + 1], b0.y, a10);
+                a10 = fmaf(c1v[t + 2], b0.z, a10); a10 = fmaf(c1v[t + 3], b0.w, a10);
+                a11 = fmaf(c1v[t], b1.x, a11); a11 = fmaf(c1v[t + 1], b1.y, a11);
+                a11 = fmaf(c1v[t + 2], b1.z, a11); a11 = fmaf(c1v[t + 3], b1.w, a11);
             }
-            count += (a > thr) ? 1u : 0u;
+            const bool v1 = j + 1 < nc;
+            count0 += (a00 > thr ? 1u : 0u) + ((v1 && a01 > thr) ? 1u : 0u);
+            count1 += (a10 > thr ? 1u : 0u) + ((v1 && a11 > thr) ? 1u : 0u);
         }
     }
-    if (live && count) atomicAdd(cnt + k, (unsigned long long)count);
+    if (live0 && count0) atomicAdd(cnt + k0, (unsigned long long)count0);
+    if (live1 && count1) atomicAdd(cnt + k1, (unsigned long long)count1);
 }
 
 __global__ void k_gpc_counts_to_fraction(int n_pts, int Ns, double* p)
@@ -318,7 +337,7 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int gx = (n_pts + kGpcBS - 1) / kGpcBS;
+    const int gx = (n_pts + 2 * kGpcBS - 1) / (2 * kGpcBS);  // two nodes per thread
     // enough sample slices to give every SM several blocks, at least one
     // chunk per slice
     int gy = std::max(1, (8 * sms + gx - 1) / gx);

@@ -532,25 +532,26 @@ void launch_prolong_add(const Grid& Gf, const Grid& Gc, const uint8_t* bcf,
 
 // x = A_c^{-1} b on the coarsest grid (FP64 inverse), one block per sample.
 template <class T>
-__global__ void k_coarse_apply(int n, const double* __restrict__ Ainv,
+__global__ void k_coarse_apply(int n, const T* __restrict__ Ainv,
                                const V2<T>* __restrict__ b, V2<T>* __restrict__ x,
                                int trans, const int* mask, int mstride)
 {
-    extern __shared__ double bs[];
+    extern __shared__ __align__(16) unsigned char ca_smem[];
+    T* bs = reinterpret_cast<T*>(ca_smem);
     const int s = blockIdx.x;
     if (!on(mask, mstride, s)) return;
     const T* bb = reinterpret_cast<const T*>(b + (size_t)s * (n / 2));
-    for (int q = threadIdx.x; q < n; q += blockDim.x) bs[q] = (double)bb[q];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) bs[q] = bb[q];
     __syncthreads();
-    const double* A = Ainv + (size_t)s * n * n;
+    const T* A = Ainv + (size_t)s * n * n;
     T* xx = reinterpret_cast<T*>(x + (size_t)s * (n / 2));
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
-        double acc = 0.0;
+        T acc = T(0);
         if (!trans)
             for (int q = 0; q < n; ++q) acc = fma(A[(size_t)r * n + q], bs[q], acc);
         else
             for (int q = 0; q < n; ++q) acc = fma(A[(size_t)q * n + r], bs[q], acc);
-        xx[r] = T(acc);
+        xx[r] = acc;
     }
 }
 
@@ -561,7 +562,10 @@ void launch_coarse_apply(const Grid& G, const double* Ainv, const V2<T>* b,
 {
     count_launch(1);
     const int n = 2 * G.N;
-    k_coarse_apply<T><<<S, 128, sizeof(double) * n, st>>>(n, Ainv, b, x, trans, mask, mstride);
+    // the inverse is stored in the solver's arithmetic (CoarseType of its
+    // multigrid storage type: FP32 for the mixed solver, FP64 otherwise)
+    k_coarse_apply<T><<<S, 128, sizeof(T) * n, st>>>(n, reinterpret_cast<const T*>(Ainv), b, x,
+                                                     trans, mask, mstride);
 }
 
 // ---------------------------------------------------------------------------

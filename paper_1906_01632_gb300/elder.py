@@ -43,7 +43,7 @@ class elder_config(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("newton_estimate", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("omega_line", ctypes.c_double)]
 
 
 class elder_stats(ctypes.Structure):

@@ -66,3 +66,23 @@ def test_config_default_without_gpu():
     assert cfg.Dm == 3.565e-6
     with pytest.raises(AttributeError):
         E.elder_config_default(4, 4, 2, no_such_field=1)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=6),                       # top square edges off the nodes (bc_mode 0)
+    dict(nz=129),                     # z-line smoother: lines of at most 129 nodes
+    dict(smoother=7), dict(precision=5), dict(omega_line=0.0), dict(omega=-1.0),
+    dict(max_samples=0), dict(nu1=0), dict(bc_mode=9), dict(mu=0.0),
+])
+def test_create_rejects_invalid_config_before_touching_a_device(bad):
+    """elder_create validates the configuration on the host and returns
+    ELDER_EINVAL with a message before any CUDA call (this runs without a
+    GPU)."""
+    import ctypes
+    from paper_1906_01632_gb300 import elder as E
+    grid = {k: bad.pop(k) for k in ("nx", "nz") if k in bad}
+    cfg = E.elder_config_default(grid.get("nx", 8), 8, grid.get("nz", 4), **bad)
+    h = ctypes.c_void_p()
+    rc = E.lib().elder_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert rc == E.ELDER_EINVAL and not h.value
+    assert E.lib().elder_last_error(None)

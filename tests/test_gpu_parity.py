@@ -327,3 +327,38 @@ def test_paper_parallelepiped_workload_steps_match_oracle(E):
         for n in range(steps):
             assert np.abs(traj[n][1][s] - ref[n][1]).max() <= 1e-10, (s, n)
             assert np.abs(traj[n][0][s] - ref[n][0]).max() <= 1e-9 * P.rho0 * P.g * P.Lz, (s, n)
+
+
+def test_step_argument_errors(E):
+    """S outside [1, max_samples] and a non-positive dt are rejected with
+    ELDER_EINVAL before anything is launched; the state is left untouched."""
+    P = O.Problem(8, 8, 4)
+    ctx = _ctx(E, 8, 8, 4, S=2)
+    phi, K = _fields(P, 2, 31)
+    p0, c0 = O.initial_state(P)
+    pt, ct = T(np.tile(p0, (2, 1))), T(np.tile(c0, (2, 1)))
+    for S, dt in ((0, YEAR / 12), (3, YEAR / 12), (2, 0.0), (2, -1.0)):
+        with pytest.raises(E.ElderError) as ei:
+            ctx.step(S, T(phi), T(K), pt, ct, dt, raise_on_fail=True)
+        assert ei.value.code == E.ELDER_EINVAL
+    assert np.array_equal(H(pt), np.tile(p0, 2)) and np.array_equal(H(ct), np.tile(c0, 2))
+
+
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_odd_grid_single_level_matches_oracle(E, smoother):
+    """An odd grid (6x10x3, the diffusion-column boundary set) cannot be
+    coarsened: the hierarchy is the grid itself and the dense inverse is the
+    whole preconditioner.  Ragged node and cell counts against every block
+    size; steps against the oracle."""
+    P = O.Problem(6, 10, 3, bc_mode=2)
+    S = 2
+    phi, K = _fields(P, S, 41)
+    p0, c0 = O.initial_state(P)
+    dt = YEAR / 12
+    traj, _ = _run_gpu(E, P, phi, K, np.tile(p0, (S, 1)), np.tile(c0, (S, 1)), 3, dt,
+                       bc_mode=2, smoother=smoother)
+    for s in range(S):
+        ref = _oracle_traj(P, phi[s], K[s], p0, c0, 3, dt)
+        for n in range(3):
+            assert np.abs(traj[n][1][s] - ref[n][1]).max() <= 1e-10, (s, n)
+            assert np.abs(traj[n][0][s] - ref[n][0]).max() <= 1e-9 * P.rho0 * P.g * P.Lz, (s, n)
