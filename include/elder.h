@@ -205,6 +205,19 @@ int elder_step(elder_ctx* ctx, int S, const double* phi, const double* K,
                double* p, double* c, double dt, int32_t* status,
                elder_stats* stats, void* stream);
 
+/* elder_step starting Newton from the linear extrapolation 2 u^n - u^{n-1}
+ * (c clipped to [0, 1], Dirichlet values imposed) instead of u^n: the same
+ * implicit Euler step (Sections 2.3 and 5.1) to the same Newton tolerance,
+ * usually with one Newton iteration fewer when the solution evolves
+ * smoothly.  p_prev, c_prev: [S][N] in: u^{n-1} (pass u^n on the first
+ * step), out: u^n, so that repeated calls with the same four buffers march
+ * in time.  p, c: in u^n, out u^{n+1}.  Re-solves of failed samples start
+ * from u^n; a failed sample keeps u^n.  Other arguments as elder_step. */
+int elder_step_extrapolated(elder_ctx* ctx, int S, const double* phi, const double* K,
+                            double* p_prev, double* c_prev, double* p, double* c,
+                            double dt, int32_t* status, elder_stats* stats,
+                            void* stream);
+
 /* Linearises at (p, c) and solves J x = rhs (transpose=0) or J^T x = rhs
  * (transpose=1) with the multigrid-preconditioned BiCGStab of elder_step,
  * to the relative residual rtol.  rhs, x: [S][N][2] device; x is output

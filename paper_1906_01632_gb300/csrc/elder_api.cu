@@ -737,7 +737,7 @@ bool krylov_converged(elder_ctx* ctx, cudaStream_t st)
 template <class T>
 int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st,
-              const NewtonSettings& set)
+              const NewtonSettings& set, double* p_prev = nullptr, double* c_prev = nullptr)
 {
     Solver<T>& sv = solver_reserve<T>(ctx, S);
     const elder_config& cf = ctx->cfg;
@@ -751,6 +751,13 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
 
     CK(cudaMemcpyAsync(ctx->p_old, p, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ctx->c_old, c, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    if (p_prev) {
+        // Newton starts from 2 u^n - u^{n-1}; the caller's u^{n-1} buffers
+        // receive u^n for the next call
+        launch_extrapolate(G, ctx->p_old, ctx->c_old, p_prev, c_prev, p, c, S, st);
+        CK(cudaMemcpyAsync(p_prev, ctx->p_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c_prev, ctx->c_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    }
     launch_impose_dirichlet(G, ctx->bc[0], ctx->cval, p, c, S, st);
     average_coefficients(ctx, S, phi, K, st);
     for (int s = 0; s < S; ++s) {
@@ -903,16 +910,21 @@ void resolve_fp64(elder_ctx* ctx, const std::vector<int>& idx, const double* phi
 // again from u^n in FP64 (tier 1); samples that still fail (in either
 // precision) get a last FP64 solve with robust settings (tier 2).
 int step_tiers(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
-               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st)
+               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st,
+               double* p_prev = nullptr, double* c_prev = nullptr)
 {
     std::vector<int32_t> st1(S);
     std::vector<elder_stats> sts(S);
     const NewtonSettings conf = configured_settings(ctx->cfg);
     const bool mixed = ctx->cfg.precision == ELDER_MIXED;
+    // (re-solves of failed samples start again from u^n, which a failed
+    // sample holds)
     if (mixed)
-        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf);
+        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, p_prev,
+                         c_prev);
     else
-        step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf);
+        step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, p_prev,
+                          c_prev);
     auto failed = [&]() {
         std::vector<int> f;
         for (int s = 0; s < S; ++s)
@@ -1273,6 +1285,24 @@ int elder_step(elder_ctx* ctx, int S, const double* phi, const double* K, double
     }
     try {
         return step_tiers(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream);
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+}
+
+int elder_step_extrapolated(elder_ctx* ctx, int S, const double* phi, const double* K,
+                            double* p_prev, double* c_prev, double* p, double* c, double dt,
+                            int32_t* status, elder_stats* stats, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !p_prev || !c_prev || !(dt > 0)) {
+        ctx->err = "elder_step_extrapolated: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        return step_tiers(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream, p_prev,
+                          c_prev);
     } catch (const Fail& f) {
         return set_error(ctx, f);
     }

@@ -1063,6 +1063,28 @@ void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
     k_newton_check<<<nblocks(S, 128), 128, 0, st>>>(ns, ks, tol_p, tol_c, maxit, estimate, S);
 }
 
+// Newton's starting point 2 u^n - u^{n-1}, the salt fraction clipped to
+// [0, 1] (Dirichlet values are imposed afterwards).
+__global__ void k_extrapolate(int N, const double* __restrict__ p_n,
+                              const double* __restrict__ c_n, const double* __restrict__ p_m,
+                              const double* __restrict__ c_m, double* __restrict__ p,
+                              double* __restrict__ c)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const size_t q = (size_t)blockIdx.y * N + n;
+    p[q] = 2.0 * p_n[q] - p_m[q];
+    c[q] = fmin(1.0, fmax(0.0, 2.0 * c_n[q] - c_m[q]));
+}
+
+void launch_extrapolate(const Grid& G, const double* p_n, const double* c_n, const double* p_m,
+                        const double* c_m, double* p, double* c, int S, cudaStream_t st)
+{
+    count_launch(1);
+    dim3 grid(nblocks(G.N), S);
+    k_extrapolate<<<grid, kBS, 0, st>>>(G.N, p_n, c_n, p_m, c_m, p, c);
+}
+
 __global__ void k_newton_restore_failed(int N, double* __restrict__ p,
                                         double* __restrict__ c,
                                         const double* __restrict__ p_old,

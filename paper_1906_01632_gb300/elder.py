@@ -80,6 +80,9 @@ def _load():
     lib.elder_jacobian.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, vp, vp]
     lib.elder_step.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double,
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(elder_stats), vp]
+    lib.elder_step_extrapolated.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(elder_stats), vp]
     lib.elder_solve.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, vp, vp,
                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int32), vp]
     lib.elder_moments.argtypes = [vp, ip, vp, vp, ctypes.c_double, vp, vp, vp, vp]
@@ -147,6 +150,13 @@ def elder_config_default(nx, ny, nz, **overrides) -> elder_config:
             raise AttributeError(f"elder_config has no field {k}")
         setattr(cfg, k, v)
     return cfg
+
+
+def _stats_list(stats):
+    return [{"status": s.status, "newton_iters": s.newton_iters,
+             "krylov_iters": s.krylov_iters, "ls_cuts": s.ls_cuts, "res0": s.res0,
+             "res": s.res, "fp64_retry": s.fp64_retry, "salt_mass0": s.salt_mass0,
+             "salt_mass": s.salt_mass, "salt_inflow": s.salt_inflow} for s in stats]
 
 
 class Elder:
@@ -238,11 +248,21 @@ class Elder:
                              _ptr(c, "c"), dt, status, stats, _stream(stream))
         self._check(rc, allow_notconv=not raise_on_fail)
         st = np.frombuffer(status, dtype=np.int32).copy()
-        info = [{"status": s.status, "newton_iters": s.newton_iters,
-                 "krylov_iters": s.krylov_iters, "ls_cuts": s.ls_cuts, "res0": s.res0,
-                 "res": s.res, "fp64_retry": s.fp64_retry, "salt_mass0": s.salt_mass0,
-                 "salt_mass": s.salt_mass, "salt_inflow": s.salt_inflow} for s in stats]
-        return st, info
+        return st, _stats_list(stats)
+
+    def step_extrapolated(self, S, phi, K, p_prev, c_prev, p, c, dt, stream=None,
+                          raise_on_fail=False):
+        """One implicit Euler step started from 2 u^n - u^{n-1}: p_prev, c_prev
+        hold u^{n-1} on entry and u^n on return; p, c hold u^n on entry and
+        u^{n+1} on return.  Returns (status[S], stats list) as step."""
+        status = (ctypes.c_int32 * S)()
+        stats = (elder_stats * S)()
+        rc = _lib.elder_step_extrapolated(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"),
+                                          _ptr(p_prev, "p_prev"), _ptr(c_prev, "c_prev"),
+                                          _ptr(p, "p"), _ptr(c, "c"), dt, status, stats,
+                                          _stream(stream))
+        self._check(rc, allow_notconv=not raise_on_fail)
+        return np.frombuffer(status, dtype=np.int32).copy(), _stats_list(stats)
 
     def solve(self, S, phi, K, p, c, dt, rhs, transpose=False, rtol=1e-10, x=None, stream=None):
         x = x if x is not None else torch.empty_like(rhs)
@@ -396,6 +416,10 @@ def elder_destroy(ctx: Elder):
 
 def elder_step(ctx: Elder, *a, **k):
     return ctx.step(*a, **k)
+
+
+def elder_step_extrapolated(ctx: Elder, *a, **k):
+    return ctx.step_extrapolated(*a, **k)
 
 
 def elder_solve(ctx: Elder, *a, **k):

@@ -362,3 +362,31 @@ def test_odd_grid_single_level_matches_oracle(E, smoother):
         for n in range(3):
             assert np.abs(traj[n][1][s] - ref[n][1]).max() <= 1e-10, (s, n)
             assert np.abs(traj[n][0][s] - ref[n][0]).max() <= 1e-9 * P.rho0 * P.g * P.Lz, (s, n)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+def test_extrapolated_start_marches_to_the_oracle_states(E, precision, tol):
+    """elder_step_extrapolated starts Newton from 2 u^n - u^{n-1} but solves
+    the same implicit step: a 5-step march matches the oracle's states (which
+    start each Newton iteration from u^n), and the history buffers return
+    u^n."""
+    P = O.Problem(16, 16, 4)
+    S = 2
+    phi, K = _fields(P, S, 51)
+    p0, c0 = O.initial_state(P)
+    ctx = _ctx(E, 16, 16, 4, S=S, precision=precision)
+    pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+    pm, cm = pt.clone(), ct.clone()
+    phit, Kt = T(phi), T(K)
+    dt = YEAR / 12
+    refs = [_oracle_traj(P, phi[s], K[s], p0, c0, 5, dt) for s in range(S)]
+    for n in range(5):
+        p_before, c_before = H(pt).copy(), H(ct).copy()
+        st, _ = ctx.step_extrapolated(S, phit, Kt, pm, cm, pt, ct, dt)
+        assert (st == 0).all()
+        assert np.array_equal(H(pm), p_before) and np.array_equal(H(cm), c_before)
+        for s in range(S):
+            c1 = H(ct).reshape(S, -1)[s]
+            p1 = H(pt).reshape(S, -1)[s]
+            assert np.abs(c1 - refs[s][n][1]).max() <= tol, (s, n)
+            assert np.abs(p1 - refs[s][n][0]).max() <= max(tol, 1e-9) * P.rho0 * P.g * P.Lz, (s, n)
