@@ -144,12 +144,66 @@ __host__ __device__ inline CellGeom make_geom(const Grid& G)
 // transverse local position (u, v) (see corner_of).
 // ---------------------------------------------------------------------------
 
-template <int D>
-__device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const double (&c8)[8],
-                                               const Phys& ph, double invh, double kmuA,
-                                               double dA, QF* __restrict__ out, size_t qs)
+// Constants of the cell-based residual, formed on the host.  The Q1 weights
+// (9,3,3,1)/16 of a quarter face are applied as two passes of (3,1) sums
+// (kron31: 16x the weights, additions only), and 1/(16 h_d) is folded into
+// the per-direction coefficients:
+//   m = -(rho K kA_d) (g16_d + [d=z] g16h rho),  F = c_up m - rho phi dA_d gc16_d,
+//   rho = rho0 + drho32 sc16,
+// with g16, gc16, sc16 the 16x-weighted sums of the edge differences of p and
+// c and of the edge sums of c.
+struct FluxConst {
+    double kA[3];   // A_d / (16 h_d mu)
+    double dA[3];   // Dm A_d / (16 h_d)
+    double g16h;    // 16 h_z g
+    double drho32;  // drho / 32 (sc16 = 32 c_ip)
+    // FP32 copies for the round-off scale (a magnitude)
+    float kAf[3], dAf[3], g16hf, drho32f, rho0f;
+};
+
+static FluxConst make_flux_const(const Grid& G, const Phys& ph)
 {
-    double dp[2][2], dc[2][2], sc[2][2];
+    const CellGeom cg = make_geom(G);
+    const double h[3] = {G.hx, G.hy, G.hz};
+    FluxConst f;
+    for (int d = 0; d < 3; ++d) {
+        f.kA[d] = cg.area[d] / (16.0 * h[d] * ph.mu);
+        f.dA[d] = ph.Dm * cg.area[d] / (16.0 * h[d]);
+        f.kAf[d] = (float)f.kA[d];
+        f.dAf[d] = (float)f.dA[d];
+    }
+    f.g16h = 16.0 * G.hz * ph.g;
+    f.drho32 = ph.drho / 32.0;
+    f.g16hf = (float)f.g16h;
+    f.drho32f = (float)f.drho32;
+    f.rho0f = (float)ph.rho0;
+    return f;
+}
+
+// y[S][T] = sum_{u,v} (u == S ? 3 : 1) (v == T ? 3 : 1) x[u][v]
+template <class R>
+__device__ __forceinline__ void kron31(const R (&x)[2][2], R (&y)[2][2])
+{
+    R t[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const R a = x[u][0] + x[u][1];
+        t[u][0] = R(2) * x[u][0] + a;
+        t[u][1] = R(2) * x[u][1] + a;
+    }
+#pragma unroll
+    for (int T_ = 0; T_ < 2; ++T_) {
+        const R a = t[0][T_] + t[1][T_];
+        y[0][T_] = R(2) * t[0][T_] + a;
+        y[1][T_] = R(2) * t[1][T_] + a;
+    }
+}
+
+template <class R, int D>
+__device__ __forceinline__ void dir_sums(const R (&p8)[8], const R (&c8)[8], R (&gp)[2][2],
+                                         R (&gc)[2][2], R (&sc)[2][2])
+{
+    R dp[2][2], dc[2][2], cs[2][2];
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -157,42 +211,49 @@ __device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const doub
             const int A = corner_of(D, u, v, 0), B = corner_of(D, u, v, 1);
             dp[u][v] = p8[B] - p8[A];
             dc[u][v] = c8[B] - c8[A];
-            sc[u][v] = c8[A] + c8[B];
+            cs[u][v] = c8[A] + c8[B];
         }
-    const double wh = 0.5625 * invh, wm = 0.1875 * invh, wl = 0.0625 * invh;
+    kron31(dp, gp);
+    kron31(dc, gc);
+    kron31(cs, sc);
+}
+
+template <int D>
+__device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const double (&c8)[8],
+                                               const float (&pf)[8], const float (&cf)[8],
+                                               const Phys& ph, const FluxConst& fc, double Ke,
+                                               double phie, float Kf, float phif,
+                                               QF* __restrict__ out, size_t qs)
+{
+    double gp[2][2], gc[2][2], sc[2][2];
+    dir_sums<double, D>(p8, c8, gp, gc, sc);
+    float gpf[2][2], gcf[2][2], scf[2][2];
+    dir_sums<float, D>(pf, cf, gpf, gcf, scf);
+    const double kmuA = Ke * fc.kA[D], dA = phie * fc.dA[D];
+    const float kmuAf = Kf * fc.kAf[D], dAf = phif * fc.dAf[D];
 #pragma unroll
     for (int S_ = 0; S_ < 2; ++S_)
 #pragma unroll
         for (int T_ = 0; T_ < 2; ++T_) {
-            // weights of the 4 edges for the face of edge (S_, T_)
-            double gp = 0.0, gc = 0.0, ci = 0.0;
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    const double w = (u == S_) ? (v == T_ ? wh : wm) : (v == T_ ? wm : wl);
-                    const double wc = (u == S_) ? (v == T_ ? 0.28125 : 0.09375)
-                                                : (v == T_ ? 0.09375 : 0.03125);
-                    gp = fma(w, dp[u][v], gp);
-                    gc = fma(w, dc[u][v], gc);
-                    ci = fma(wc, sc[u][v], ci);
-                }
-            const double rho = fma(ph.drho, ci, ph.rho0);
-            const double G = (D == 2) ? fma(ph.g, rho, gp) : gp;
+            const double rho = fma(fc.drho32, sc[S_][T_], ph.rho0);
+            const double G = (D == 2) ? fma(fc.g16h, rho, gp[S_][T_]) : gp[S_][T_];
             const double m = -(rho * kmuA) * G;
-            const double cup =
-                (m >= 0.0) ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
-            const double dif = rho * dA;
-            const double F = fma(cup, m, -dif * gc);
-            // rounding scale: the Darcy flux cancels grad p against rho g
-            const double mm = rho * kmuA * (fabs(gp) + (D == 2 ? ph.g * rho : 0.0));
-            const double Fm = fma(fabs(cup), mm, dif * fabs(gc));
-            out[(size_t)(4 * D + 2 * S_ + T_) * qs] = QF{m, F, (float)mm, (float)Fm};
+            // upwind end from the sign bit (an integer test)
+            const bool upA = __double2hiint(m) >= 0;
+            const double cup = upA ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
+            const double F = fma(cup, m, -(rho * dA) * gc[S_][T_]);
+            // rounding scale in FP32: the Darcy flux cancels grad p against rho g
+            const float rhof = fmaf(fc.drho32f, scf[S_][T_], fc.rho0f);
+            const float mm = rhof * kmuAf *
+                             (fabsf(gpf[S_][T_]) + (D == 2 ? fc.g16hf * rhof : 0.0f));
+            const float cupf = upA ? cf[corner_of(D, S_, T_, 0)] : cf[corner_of(D, S_, T_, 1)];
+            const float Fm = fmaf(fabsf(cupf), mm, rhof * dAf * fabsf(gcf[S_][T_]));
+            out[(size_t)(4 * D + 2 * S_ + T_) * qs] = QF{m, F, mm, Fm};
         }
 }
 
 __global__ void __launch_bounds__(kBS)
-    k_cell_flux(Grid G, Phys ph, CellGeom cg, const double* __restrict__ phi,
+    k_cell_flux(Grid G, Phys ph, FluxConst fc, const double* __restrict__ phi,
                 const double* __restrict__ K, const double* __restrict__ p,
                 const double* __restrict__ c, QF* __restrict__ qf, const int* mask, int mstride)
 {
@@ -205,28 +266,32 @@ __global__ void __launch_bounds__(kBS)
     const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
     const int base = ci + sy * cj + sz * ck;
     double p8[8], c8[8];
+    float pf[8], cf[8];
 #pragma unroll
     for (int L = 0; L < 8; ++L) {
         const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
         p8[L] = __ldg(p + on + base + off);
         c8[L] = __ldg(c + on + base + off);
+        pf[L] = (float)p8[L];
+        cf[L] = (float)c8[L];
     }
-    const double phi_e = __ldg(phi + oc + e);
-    const double kmu = __ldg(K + oc + e) / ph.mu;
+    const double phie = __ldg(phi + oc + e);
+    const double Ke = __ldg(K + oc + e);
+    const float phif = (float)phie, Kf = (float)Ke;
     QF* out = qf + (size_t)s * 12 * G.C + e;
     const size_t qs = (size_t)G.C;
-    cell_dir_faces<0>(p8, c8, ph, cg.ih[0], kmu * cg.area[0], phi_e * ph.Dm * cg.area[0], out, qs);
-    cell_dir_faces<1>(p8, c8, ph, cg.ih[1], kmu * cg.area[1], phi_e * ph.Dm * cg.area[1], out, qs);
-    cell_dir_faces<2>(p8, c8, ph, cg.ih[2], kmu * cg.area[2], phi_e * ph.Dm * cg.area[2], out, qs);
+    cell_dir_faces<0>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
+    cell_dir_faces<1>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
+    cell_dir_faces<2>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
 }
 
 // Sum of the up to 4 quarter faces of the direction-D edge whose lower node
-// is (i, j, k) (the edge must exist); fixed order.
+// is (i, j, k) (the edge must exist); fixed order, missing cells read as 0.
 template <int D>
 __device__ __forceinline__ void edge_sum(const Grid& G, const QF* __restrict__ qf, int i, int j,
                                          int k, double& m, double& F, float& mm, float& Fm)
 {
-    m = 0.0; F = 0.0; mm = 0.0f; Fm = 0.0f;
+    QF f[4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -235,17 +300,20 @@ __device__ __forceinline__ void edge_sum(const Grid& G, const QF* __restrict__ q
             if (D == 0) { ci = i; cj = j - b; ck = k - a; }
             else if (D == 1) { ci = i - b; cj = j; ck = k - a; }
             else { ci = i - b; cj = j - a; ck = k; }
-            if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
-            const QF f = qf[(size_t)(4 * D + 2 * b + a) * G.C + ci + G.nx * (cj + G.ny * ck)];
-            m += f.m;
-            F += f.F;
-            mm += f.mm;
-            Fm += f.Fm;
+            const bool ok = ci >= 0 && ci < G.nx && cj >= 0 && cj < G.ny && ck >= 0 && ck < G.nz;
+            f[2 * a + b] = ok ? qf[(size_t)(4 * D + 2 * b + a) * G.C + ci + G.nx * (cj + G.ny * ck)]
+                              : QF{0.0, 0.0, 0.0f, 0.0f};
         }
+    m = ((f[0].m + f[1].m) + f[2].m) + f[3].m;
+    F = ((f[0].F + f[1].F) + f[2].F) + f[3].F;
+    mm = (f[0].mm + f[1].mm) + (f[2].mm + f[3].mm);
+    Fm = (f[0].Fm + f[1].Fm) + (f[2].Fm + f[3].Fm);
 }
 
+// vsc = |scv| / dt = hx hy hz / (8 dt); the rounding scale (Ap, Ac and the
+// per-block partials of its square) is carried in FP32.
 __global__ void __launch_bounds__(kBS)
-    k_cell_residual(Grid G, Phys ph, const uint8_t* __restrict__ bc,
+    k_cell_residual(Grid G, Phys ph, double vsc, const uint8_t* __restrict__ bc,
                     const double* __restrict__ cval, const double* __restrict__ phi,
                     const double* __restrict__ p, const double* __restrict__ c,
                     const double* __restrict__ c_old, const QF* __restrict__ qf,
@@ -259,7 +327,8 @@ __global__ void __launch_bounds__(kBS)
     phi += oc; p += on; c += on; c_old += on; R += on;
     qf += (size_t)s * 12 * G.C;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double sq = 0.0, aq = 0.0;
+    double sq = 0.0;
+    float aq = 0.0f;
     if (n < G.N) {
         int i, j, k;
         node_ijk(G, n, i, j, k);
@@ -267,7 +336,7 @@ __global__ void __launch_bounds__(kBS)
         float Ap = 0.0f, Ac = 0.0f;
         double m, F;
         float mm, Fm;
-        if (i < G.nx) { edge_sum<0>(G, qf, i, j, k, m, F, mm, Fm); Rp += m; Rc += F; Ap += mm; Ac += Fm; }
+        if (i < G.nx) { edge_sum<0>(G, qf, i, j, k, m, F, mm, Fm); Rp = m; Rc = F; Ap = mm; Ac = Fm; }
         if (i > 0) { edge_sum<0>(G, qf, i - 1, j, k, m, F, mm, Fm); Rp -= m; Rc -= F; Ap += mm; Ac += Fm; }
         if (j < G.ny) { edge_sum<1>(G, qf, i, j, k, m, F, mm, Fm); Rp += m; Rc += F; Ap += mm; Ac += Fm; }
         if (j > 0) { edge_sum<1>(G, qf, i, j - 1, k, m, F, mm, Fm); Rp -= m; Rc -= F; Ap += mm; Ac += Fm; }
@@ -280,27 +349,30 @@ __global__ void __launch_bounds__(kBS)
             if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) continue;
             phis += __ldg(phi + ci + G.nx * (cj + G.ny * ck));
         }
-        const double vdt = phis * 0.125 * G.hx * G.hy * G.hz / ph.dt;
+        const double vdt = phis * vsc;
         const double cn = c[n], co = c_old[n];
         const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
         Rp += vdt * (rn - ro);
         Rc += vdt * (rn * cn - ro * co);
-        double Apd = (double)Ap + vdt * (fabs(rn) + fabs(ro));
-        double Acd = (double)Ac + vdt * (fabs(rn * cn) + fabs(ro * co));
+        const float vdtf = (float)vdt, cnf = (float)cn, cof = (float)co;
+        const float rnf = fmaf((float)ph.drho, cnf, (float)ph.rho0);
+        const float rof = fmaf((float)ph.drho, cof, (float)ph.rho0);
+        Ap = fmaf(vdtf, fabsf(rnf) + fabsf(rof), Ap);
+        Ac = fmaf(vdtf, fabsf(rnf * cnf) + fabsf(rof * cof), Ac);
         const uint8_t b = bc[n];
-        if (b & BC_P) { Rp = p[n]; Apd = 0.0; }
-        if (b & BC_C) { Rc = cn - cval[n]; Acd = 0.0; }
+        if (b & BC_P) { Rp = p[n]; Ap = 0.0f; }
+        if (b & BC_C) { Rc = cn - cval[n]; Ac = 0.0f; }
         R[n] = V2<double>{Rp, Rc};
         sq = Rp * Rp + Rc * Rc;
-        aq = Apd * Apd + Acd * Acd;
+        aq = fmaf(Ap, Ap, Ac * Ac);
     }
     if (partial) {
         const double t = block_sum(sq, red);
         if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = t;
     }
     if (act) {
-        const double t = block_sum(aq, red);
-        if (threadIdx.x == 0) act[(size_t)s * gridDim.x + blockIdx.x] = t;
+        const float t = block_sum(aq, reinterpret_cast<float*>(red));
+        if (threadIdx.x == 0) act[(size_t)s * gridDim.x + blockIdx.x] = (double)t;
     }
 }
 
@@ -314,10 +386,12 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
     (void)p_old;  // p has no time derivative
     count_launch(2);
     dim3 gc(nblocks(G.C), S);
-    k_cell_flux<<<gc, kBS, 0, st>>>(G, ph, make_geom(G), phi, K, p, c, qf, mask, mstride);
+    k_cell_flux<<<gc, kBS, 0, st>>>(G, ph, make_flux_const(G, ph), phi, K, p, c, qf, mask,
+                                    mstride);
     dim3 grid(nblocks(G.N), S);
-    k_cell_residual<<<grid, kBS, 0, st>>>(G, ph, bc, cval, phi, p, c, c_old, qf, R, partial,
-                                          act, mask, mstride);
+    const double vsc = G.hx * G.hy * G.hz / (8.0 * ph.dt);
+    k_cell_residual<<<grid, kBS, 0, st>>>(G, ph, vsc, bc, cval, phi, p, c, c_old, qf, R,
+                                          partial, act, mask, mstride);
 }
 
 // ---------------------------------------------------------------------------

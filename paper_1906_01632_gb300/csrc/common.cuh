@@ -84,12 +84,30 @@ __device__ __forceinline__ void node_ijk(const Grid& G, int n, int& i, int& j,
     i = r - j * nx1;
 }
 
-// Block-wide sum of one double per thread (blockDim.x a multiple of 32,
-// at most 1024); every thread receives the result.
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Block-wide sum of one value per thread (blockDim.x a multiple of 32,
+// at most 1024); every thread receives the result.
+__device__ __forceinline__ float block_sum(float v, float* smem32)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem32[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    float t = (threadIdx.x < nw) ? smem32[threadIdx.x] : 0.0f;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) smem32[0] = t;
+    __syncthreads();
+    float r = smem32[0];
+    __syncthreads();
+    return r;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* smem32)

@@ -271,14 +271,22 @@ double model_bytes(int cls, int T, int Mz, const Grid& G, bool line)
     return 0.0;
 }
 
-double model_flops(int cls)
+double model_flops(int cls, const Grid& G)
 {
+    const double cells_per_node = (double)G.C / G.N;
     switch (cls) {
     case ELDER_K_SMOOTH: return 216 + 8 + 4 + 4;
     case ELDER_K_SMOOTH0: return 8 + 2;
     case ELDER_K_SPMV: return 216 + 8;
     case ELDER_K_MGRES: return 216 + 2;
-    case ELDER_K_RESIDUAL: return 12 * 54 + 40;   // 12 face fluxes per node + storage
+    case ELDER_K_RESIDUAL:
+        // FP64 flops (FMA = 2) of the quarter-face form.  Per cell and
+        // direction: 12 edge differences and sums, three (3,1) weight passes
+        // of 20, and per quarter face 8 (+2 on vertical edges) for rho, m, F;
+        // plus 6 per cell for the coefficients: 326.  Per node: 36 edge sums,
+        // 10 edge accumulations, 8 porosity sums and 21 for storage and the
+        // squared norm: 75.
+        return 326 * cells_per_node + 75;
     case ELDER_K_JACOBIAN: return 24 * (54 + 66) + 10;
     }
     return 0.0;
@@ -312,7 +320,7 @@ void prof_end(elder_ctx* ctx, int idx, int cls, const Grid& G, int T, int Mz, in
     r.cls = cls;
     const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
     r.bytes = model_bytes(cls, T, Mz, G, line) * G.N * samples;
-    r.flops = model_flops(cls) * G.N * samples;
+    r.flops = model_flops(cls, G) * G.N * samples;
 }
 
 // after a stream synchronisation: accumulate and recycle the events
