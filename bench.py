@@ -82,6 +82,8 @@ def workload_config(a):
         "dt_yr": a.dt_yr,
         "precision": a.precision,
         "smoother": a.smoother,
+        "solver": "inexact Newton (Krylov rtol 1e-2), BiCGStab + V(1,0) multigrid, " +
+                  ("z-line damping 0.95" if a.smoother == "zline" else "point block Jacobi damping 0.5"),
         "newton_start": "u^n" if a.no_extrapolate else "2u^n - u^(n-1)",
         "fields": fields,
         "l2": "no flush: per-step working set (Jacobians of all levels, vectors) ~10 GB >> 129 MB L2",

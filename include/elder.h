@@ -89,11 +89,13 @@ typedef struct {
                                  search fails (status LINESEARCH)           */
     /* BiCGStab (Section 5.1) */
     double lin_rtol;          /* relative residual target per Newton solve
-                                 (default 3e-3: inexact Newton)             */
+                                 (default 1e-2: inexact Newton)             */
     int lin_maxit;            /* iteration cap                              */
     /* geometric multigrid V-cycle (Section 5.1) */
     int mg_levels;            /* 0 = coarsen as far as the grid allows      */
-    int nu1, nu2;             /* pre/post smoothing sweeps                  */
+    int nu1, nu2;             /* pre/post smoothing sweeps (default 1, 0:
+                                 V(1,0); the robust re-solve of failed
+                                 samples uses at least one post-sweep)      */
     double omega;             /* damping of the point block-Jacobi smoother
                                  (default 0.5)                              */
     int coarse_K_harmonic;    /* 0 arithmetic, 1 harmonic mean of K         */
@@ -111,7 +113,7 @@ typedef struct {
                                  failed samples always uses the z-line
                                  smoother (damping 0.5).                    */
     double omega_line;        /* damping of the z-line smoother (default
-                                 0.75)                                      */
+                                 0.95)                                      */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */

@@ -212,6 +212,7 @@ struct elder_ctx {
     int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, kBS};
     int smoother_now = ELDER_SMOOTH_JACOBI;  // smoother of the solve in progress
     double omega_now = 0.5;                  // its damping
+    int nu2_now = 1;                         // its post-smoothing sweeps
     double* jin = nullptr;  // Jacobian input scratch, [S][N] + [S][C] pairs
     bool tuned[2] = {false, false};    // per precision (FP64, FP32)
     float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
@@ -478,7 +479,7 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
         return;
     }
     const elder_config& cf = ctx->cfg;
-    const int nu1 = std::max(1, cf.nu1), nu2 = std::max(0, cf.nu2);
+    const int nu1 = std::max(1, cf.nu1), nu2 = std::max(0, ctx->nu2_now);
     const int sweeps = nu1 + nu2;
     V2<T>* bufA = out;
     V2<T>* bufB = sv.mx2[l];
@@ -656,7 +657,8 @@ void bicgstab(elder_ctx* ctx, Solver<T>& sv, int trans, double rtol, int maxit,
     const bool use_exec = ctx->cfg.use_graphs != 0 && !ctx->prof.on &&
                           rtol == ctx->cfg.lin_rtol && maxit == ctx->cfg.lin_maxit &&
                           ctx->smoother_now == ctx->cfg.smoother &&
-                          ctx->omega_now == configured_omega(ctx->cfg);
+                          ctx->omega_now == configured_omega(ctx->cfg) &&
+                          ctx->nu2_now == ctx->cfg.nu2;
     cudaGraphExec_t exec = nullptr;
     long long per_replay = 0;
     if (use_exec) {
@@ -702,12 +704,13 @@ struct NewtonSettings {
     double lin_rtol;
     int lin_maxit, ls_max, newton_maxit, estimate, keep_best, smoother;
     double omega;
+    int nu2;  // post-smoothing sweeps of the V-cycle
 };
 
 NewtonSettings configured_settings(const elder_config& cf)
 {
     return NewtonSettings{cf.lin_rtol, cf.lin_maxit, cf.ls_max, cf.newton_maxit,
-                          cf.newton_estimate, 0, cf.smoother, configured_omega(cf)};
+                          cf.newton_estimate, 0, cf.smoother, configured_omega(cf), cf.nu2};
 }
 
 // Damping of the robust re-solve's z-line smoother: on the steepest first
@@ -725,6 +728,7 @@ NewtonSettings robust_settings(const elder_config& cf)
     NewtonSettings r = configured_settings(cf);
     r.smoother = ELDER_SMOOTH_ZLINE;
     r.omega = kRobustOmega;
+    r.nu2 = std::max(cf.nu2, 1);
     r.lin_rtol = std::min(cf.lin_rtol, 1e-6);
     r.lin_maxit = std::max(20 * cf.lin_maxit, 2000);
     r.ls_max = std::max(cf.ls_max, 16);
@@ -798,9 +802,11 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, st);
         ctx->smoother_now = set.smoother;
         ctx->omega_now = set.omega;
+        ctx->nu2_now = set.nu2;
         bicgstab<T>(ctx, sv, 0, set.lin_rtol, set.lin_maxit, ns, S, st, set.keep_best);
         ctx->smoother_now = cf.smoother;
         ctx->omega_now = configured_omega(cf);
+        ctx->nu2_now = cf.nu2;
         for (int ls = 0; ls <= set.ls_max; ++ls) {
             launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
             pi = prof_begin(ctx, st);
@@ -1054,13 +1060,13 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->newton_tol_c = 1e-11;
     cfg->newton_tol_p = 1e-11 * 1000.0 * 9.81 * 150.0;
     cfg->ls_max = 6;
-    cfg->lin_rtol = 3e-3;
+    cfg->lin_rtol = 1e-2;
     cfg->lin_maxit = 100;
     cfg->mg_levels = 0;
     cfg->nu1 = 1;
-    cfg->nu2 = 1;
+    cfg->nu2 = 0;
     cfg->omega = 0.5;
-    cfg->omega_line = 0.75;
+    cfg->omega_line = 0.95;
     cfg->coarse_K_harmonic = 0;
     cfg->use_graphs = 1;
     cfg->autotune = 1;
@@ -1104,6 +1110,7 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
     ctx->cfg = c;
     ctx->smoother_now = c.smoother;
     ctx->omega_now = configured_omega(c);
+    ctx->nu2_now = c.nu2;
     try {
         CK(cudaGetDevice(&ctx->device));
         // hierarchy: halve while all three counts are even (and the top square
@@ -1513,10 +1520,12 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
                     // with the z-line smoother and a longer solve
                     ctx->smoother_now = ELDER_SMOOTH_ZLINE;
                     ctx->omega_now = kRobustOmega;
+                    ctx->nu2_now = std::max(ctx->cfg.nu2, 1);
                     bicgstab<double>(ctx, sv, 1, 1e-12, std::max(20 * ctx->cfg.lin_maxit, 4000),
                                      nullptr, 1, st, 1);
                     ctx->smoother_now = ctx->cfg.smoother;
                     ctx->omega_now = configured_omega(ctx->cfg);
+                    ctx->nu2_now = ctx->cfg.nu2;
                     if (!krylov_converged(ctx, st)) {
                         rc_all = ELDER_ENOTCONV;
                         ctx->err = "elder_grad: adjoint solve of step " + std::to_string(n) +
