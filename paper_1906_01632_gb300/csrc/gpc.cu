@@ -28,7 +28,7 @@ namespace {
 constexpr int kGpcMaxM = 8;      // stochastic dimensions
 constexpr int kGpcMaxDeg = 16;   // largest degree in one variable
 constexpr int kGpcBS = 128;      // threads per block
-constexpr int kGpcChunk = 64;    // samples per shared-memory chunk
+constexpr int kGpcChunk = 128;   // samples per shared-memory chunk (even)
 
 // P_0..P_n at x by (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} (Appendix A).
 __host__ __device__ inline void legendre_all(int n, double x, double* P)
@@ -110,74 +110,95 @@ __global__ void __launch_bounds__(kGpcBS)
 
 // Surrogate at Ns points for the listed nodes; counts of values above the
 // threshold accumulate in cnt (64-bit, one per listed node).
-template <int TP>
+//
+// Per chunk of kGpcChunk samples the block first tabulates, with all its
+// threads, the FP32 Legendre values P_k(theta_m) of every sample (Ps) and
+// then the basis values P_beta(theta) = prod_m P_{beta_m}(theta_m) (Bs, the
+// product over m in order).  Each thread keeps the FP32 coefficients of NPT
+// listed nodes (k0 + r blockDim.x) in registers, so every basis value read
+// from shared memory feeds NPT FMA chains; two samples are evaluated at a
+// time.  Each sum runs over t in order.
+// Dynamic shared memory: Bs [kGpcChunk][TP] floats, Ps [kGpcChunk][M][maxdeg+1]
+// floats, the clamped multi-indices [T][M] ints.
+template <int TP, int NPT>
 __global__ void __launch_bounds__(kGpcBS)
     k_gpc_exceed(int M, int T, const int32_t* __restrict__ beta, int N,
                  const double* __restrict__ coef, int n_pts, const int32_t* __restrict__ nodes,
                  int Ns, const double* __restrict__ theta, float thr, int maxdeg,
                  unsigned long long* __restrict__ cnt)
 {
-    __shared__ __align__(16) float Bs[kGpcChunk][TP];
-    // two listed nodes per thread (k0, k0 + blockDim.x): each basis value
-    // read from shared memory feeds two FMA chains
-    const int k0 = blockIdx.x * 2 * blockDim.x + threadIdx.x;
-    const int k1 = k0 + blockDim.x;
-    const bool live0 = k0 < n_pts, live1 = k1 < n_pts;
-    const int n0 = live0 ? (nodes ? nodes[k0] : k0) : 0;
-    const int n1 = live1 ? (nodes ? nodes[k1] : k1) : 0;
-    float c0v[TP], c1v[TP];
+    extern __shared__ __align__(16) unsigned char gx_smem[];
+    float* Bs = reinterpret_cast<float*>(gx_smem);          // [kGpcChunk][TP]
+    const int D1 = maxdeg + 1;
+    float* Ps = Bs + kGpcChunk * TP;                         // [kGpcChunk][M][D1]
+    int* bs = reinterpret_cast<int*>(Ps + kGpcChunk * M * D1);  // [T][M]
+    for (int e = threadIdx.x; e < T * M; e += blockDim.x)
+        bs[e] = min(max((int)beta[e], 0), maxdeg);
+    int kk[NPT];
+    bool live[NPT];
+    float cv[NPT][TP];
 #pragma unroll
-    for (int t = 0; t < TP; ++t) {
-        c0v[t] = (live0 && t < T) ? (float)coef[(size_t)t * N + n0] : 0.f;
-        c1v[t] = (live1 && t < T) ? (float)coef[(size_t)t * N + n1] : 0.f;
+    for (int r = 0; r < NPT; ++r) {
+        kk[r] = blockIdx.x * NPT * blockDim.x + r * blockDim.x + threadIdx.x;
+        live[r] = kk[r] < n_pts;
+        const int n = live[r] ? (nodes ? nodes[kk[r]] : kk[r]) : 0;
+#pragma unroll
+        for (int t = 0; t < TP; ++t)
+            cv[r][t] = (live[r] && t < T) ? (float)coef[(size_t)t * N + n] : 0.f;
     }
     // this block's slice of the samples
     const int per = (Ns + gridDim.y - 1) / gridDim.y;
     const int s0 = blockIdx.y * per;
     const int s1 = min(Ns, s0 + per);
-    unsigned int count0 = 0, count1 = 0;
+    unsigned int count[NPT];
+#pragma unroll
+    for (int r = 0; r < NPT; ++r) count[r] = 0;
     for (int cs = s0; cs < s1; cs += kGpcChunk) {
         const int nc = min(kGpcChunk, s1 - cs);
         __syncthreads();
-        if (threadIdx.x < kGpcChunk) {
-            const int j = threadIdx.x;
-            if (j < nc) {
-                float P1[kGpcMaxM * (kGpcMaxDeg + 1)];
-                for (int m = 0; m < M; ++m)
-                    legendre_all_f(maxdeg, (float)theta[(size_t)(cs + j) * M + m],
-                                   P1 + m * (kGpcMaxDeg + 1));
-                for (int t = 0; t < TP; ++t)
-                    Bs[j][t] = t < T ? basis_value<float>(beta, t, M, P1, kGpcMaxDeg + 1, maxdeg)
-                                     : 0.f;
-            }
+        for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
+            const int j = e / M, m = e - j * M;
+            legendre_all_f(maxdeg, (float)theta[(size_t)(cs + j) * M + m], Ps + e * D1);
         }
         __syncthreads();
-        // two samples at a time for each of the two nodes: four independent
-        // FMA chains (each sum still runs over t in order); rows at or past nc
-        // (the tail of the last chunk; kGpcChunk is even) are evaluated but
-        // not counted
+        // rows at or past nc (the tail of the last chunk) are zero
+        for (int e = threadIdx.x; e < kGpcChunk * TP; e += blockDim.x) {
+            const int j = e / TP, t = e - j * TP;
+            float v = 0.f;
+            if (j < nc && t < T) {
+                v = 1.f;
+                for (int m = 0; m < M; ++m) v *= Ps[(j * M + m) * D1 + bs[t * M + m]];
+            }
+            Bs[e] = v;
+        }
+        __syncthreads();
+        // two samples at a time (kGpcChunk is even): 2 NPT independent FMA
+        // chains; the second sample of the last pair may be a zero row past nc
         for (int j = 0; j < nc; j += 2) {
-            float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+            float a0[NPT], a1[NPT];
+#pragma unroll
+            for (int r = 0; r < NPT; ++r) { a0[r] = 0.f; a1[r] = 0.f; }
 #pragma unroll
             for (int t = 0; t < TP; t += 4) {
-                const float4 b0 = *reinterpret_cast<const float4*>(&Bs[j][t]);
-                const float4 b1 = *reinterpret_cast<const float4*>(&Bs[j + 1][t]);
-                a00 = fmaf(c0v[t], b0.x, a00); a00 = fmaf(c0v[t + 1], b0.y, a00);
-                a00 = fmaf(c0v[t + 2], b0.z, a00); a00 = fmaf(c0v[t + 3], b0.w, a00);
-                a01 = fmaf(c0v[t], b1.x, a01); a01 = fmaf(c0v[t + 1], b1.y, a01);
-                a01 = fmaf(c0v[t + 2], b1.z, a01); a01 = fmaf(c0v[t + 3], b1.w, a01);
-                a10 = fmaf(c1v[t], b0.x, a10); a10 = fmaf(c1v[t + 1], b0.y, a10);
-                a10 = fmaf(c1v[t + 2], b0.z, a10); a10 = fmaf(c1v[t + 3], b0.w, a10);
-                a11 = fmaf(c1v[t], b1.x, a11); a11 = fmaf(c1v[t + 1], b1.y, a11);
-                a11 = fmaf(c1v[t + 2], b1.z, a11); a11 = fmaf(c1v[t + 3], b1.w, a11);
+                const float4 b0 = *reinterpret_cast<const float4*>(Bs + j * TP + t);
+                const float4 b1 = *reinterpret_cast<const float4*>(Bs + (j + 1) * TP + t);
+#pragma unroll
+                for (int r = 0; r < NPT; ++r) {
+                    a0[r] = fmaf(cv[r][t], b0.x, a0[r]); a0[r] = fmaf(cv[r][t + 1], b0.y, a0[r]);
+                    a0[r] = fmaf(cv[r][t + 2], b0.z, a0[r]); a0[r] = fmaf(cv[r][t + 3], b0.w, a0[r]);
+                    a1[r] = fmaf(cv[r][t], b1.x, a1[r]); a1[r] = fmaf(cv[r][t + 1], b1.y, a1[r]);
+                    a1[r] = fmaf(cv[r][t + 2], b1.z, a1[r]); a1[r] = fmaf(cv[r][t + 3], b1.w, a1[r]);
+                }
             }
             const bool v1 = j + 1 < nc;
-            count0 += (a00 > thr ? 1u : 0u) + ((v1 && a01 > thr) ? 1u : 0u);
-            count1 += (a10 > thr ? 1u : 0u) + ((v1 && a11 > thr) ? 1u : 0u);
+#pragma unroll
+            for (int r = 0; r < NPT; ++r)
+                count[r] += (a0[r] > thr ? 1u : 0u) + ((v1 && a1[r] > thr) ? 1u : 0u);
         }
     }
-    if (live0 && count0) atomicAdd(cnt + k0, (unsigned long long)count0);
-    if (live1 && count1) atomicAdd(cnt + k1, (unsigned long long)count1);
+#pragma unroll
+    for (int r = 0; r < NPT; ++r)
+        if (live[r] && count[r]) atomicAdd(cnt + kk[r], (unsigned long long)count[r]);
 }
 
 __global__ void k_gpc_counts_to_fraction(int n_pts, int Ns, double* p)
@@ -337,7 +358,9 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int gx = (n_pts + 2 * kGpcBS - 1) / (2 * kGpcBS);  // two nodes per thread
+    const int TP = (T + 3) / 4 * 4;       // terms padded to a multiple of 4
+    const int NPT = TP <= 36 ? 4 : 2;     // listed nodes per thread
+    const int gx = (n_pts + NPT * kGpcBS - 1) / (NPT * kGpcBS);
     // enough sample slices to give every SM several blocks, at least one
     // chunk per slice
     int gy = std::max(1, (8 * sms + gx - 1) / gx);
@@ -345,19 +368,32 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const
     gy = std::min(gy, 65535);
     dim3 grid(gx, gy);
     const float thr = (float)threshold;
-    const int TP = round_tp(T);
-#define ELDER_GPC_EXC(TPV)                                                                \
-    k_gpc_exceed<TPV><<<grid, kGpcBS, 0, st>>>(M, T, beta, N, coef, n_pts, nodes, Ns, theta, \
-                                               thr, maxdeg, cnt)
+    const size_t smem = sizeof(float) * ((size_t)kGpcChunk * TP + (size_t)kGpcChunk * M * (maxdeg + 1)) +
+                        sizeof(int) * (size_t)T * M;
+#define ELDER_GPC_EXC(TPV, NPTV)                                                                   \
+    do {                                                                                           \
+        cudaFuncSetAttribute(k_gpc_exceed<TPV, NPTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                           \
+        k_gpc_exceed<TPV, NPTV><<<grid, kGpcBS, smem, st>>>(M, T, beta, N, coef, n_pts, nodes, Ns, \
+                                                            theta, thr, maxdeg, cnt);              \
+    } while (0)
     switch (TP) {
-        case 8: ELDER_GPC_EXC(8); break;
-        case 16: ELDER_GPC_EXC(16); break;
-        case 24: ELDER_GPC_EXC(24); break;
-        case 32: ELDER_GPC_EXC(32); break;
-        case 40: ELDER_GPC_EXC(40); break;
-        case 48: ELDER_GPC_EXC(48); break;
-        case 56: ELDER_GPC_EXC(56); break;
-        default: ELDER_GPC_EXC(64); break;
+        case 4: ELDER_GPC_EXC(4, 4); break;
+        case 8: ELDER_GPC_EXC(8, 4); break;
+        case 12: ELDER_GPC_EXC(12, 4); break;
+        case 16: ELDER_GPC_EXC(16, 4); break;
+        case 20: ELDER_GPC_EXC(20, 4); break;
+        case 24: ELDER_GPC_EXC(24, 4); break;
+        case 28: ELDER_GPC_EXC(28, 4); break;
+        case 32: ELDER_GPC_EXC(32, 4); break;
+        case 36: ELDER_GPC_EXC(36, 4); break;
+        case 40: ELDER_GPC_EXC(40, 2); break;
+        case 44: ELDER_GPC_EXC(44, 2); break;
+        case 48: ELDER_GPC_EXC(48, 2); break;
+        case 52: ELDER_GPC_EXC(52, 2); break;
+        case 56: ELDER_GPC_EXC(56, 2); break;
+        case 60: ELDER_GPC_EXC(60, 2); break;
+        default: ELDER_GPC_EXC(64, 2); break;
     }
 #undef ELDER_GPC_EXC
     k_gpc_counts_to_fraction<<<(n_pts + 255) / 256, 256, 0, st>>>(n_pts, Ns, p_exceed);
