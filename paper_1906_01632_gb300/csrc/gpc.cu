@@ -116,11 +116,11 @@ __global__ void __launch_bounds__(kGpcBS)
 // then the basis values P_beta(theta) = prod_m P_{beta_m}(theta_m) (Bs, the
 // product over m in order).  Each thread keeps the FP32 coefficients of NPT
 // listed nodes (k0 + r blockDim.x) in registers, so every basis value read
-// from shared memory feeds NPT FMA chains; two samples are evaluated at a
+// from shared memory feeds NPT FMA chains; SPT samples are evaluated at a
 // time.  Each sum runs over t in order.
 // Dynamic shared memory: Bs [kGpcChunk][TP] floats, Ps [kGpcChunk][M][maxdeg+1]
 // floats, the clamped multi-indices [T][M] ints.
-template <int TP, int NPT>
+template <int TP, int NPT, int SPT>
 __global__ void __launch_bounds__(kGpcBS)
     k_gpc_exceed(int M, int T, const int32_t* __restrict__ beta, int N,
                  const double* __restrict__ coef, int n_pts, const int32_t* __restrict__ nodes,
@@ -172,28 +172,35 @@ __global__ void __launch_bounds__(kGpcBS)
             Bs[e] = v;
         }
         __syncthreads();
-        // two samples at a time (kGpcChunk is even): 2 NPT independent FMA
-        // chains; the second sample of the last pair may be a zero row past nc
-        for (int j = 0; j < nc; j += 2) {
-            float a0[NPT], a1[NPT];
+        // SPT samples at a time (kGpcChunk is a multiple of SPT): SPT NPT
+        // independent FMA chains; the last group may run into zero rows
+        // past nc, which are not counted
+        for (int j = 0; j < nc; j += SPT) {
+            float a[SPT][NPT];
 #pragma unroll
-            for (int r = 0; r < NPT; ++r) { a0[r] = 0.f; a1[r] = 0.f; }
+            for (int q = 0; q < SPT; ++q)
+#pragma unroll
+                for (int r = 0; r < NPT; ++r) a[q][r] = 0.f;
 #pragma unroll
             for (int t = 0; t < TP; t += 4) {
-                const float4 b0 = *reinterpret_cast<const float4*>(Bs + j * TP + t);
-                const float4 b1 = *reinterpret_cast<const float4*>(Bs + (j + 1) * TP + t);
 #pragma unroll
-                for (int r = 0; r < NPT; ++r) {
-                    a0[r] = fmaf(cv[r][t], b0.x, a0[r]); a0[r] = fmaf(cv[r][t + 1], b0.y, a0[r]);
-                    a0[r] = fmaf(cv[r][t + 2], b0.z, a0[r]); a0[r] = fmaf(cv[r][t + 3], b0.w, a0[r]);
-                    a1[r] = fmaf(cv[r][t], b1.x, a1[r]); a1[r] = fmaf(cv[r][t + 1], b1.y, a1[r]);
-                    a1[r] = fmaf(cv[r][t + 2], b1.z, a1[r]); a1[r] = fmaf(cv[r][t + 3], b1.w, a1[r]);
+                for (int q = 0; q < SPT; ++q) {
+                    const float4 b = *reinterpret_cast<const float4*>(Bs + (j + q) * TP + t);
+#pragma unroll
+                    for (int r = 0; r < NPT; ++r) {
+                        a[q][r] = fmaf(cv[r][t], b.x, a[q][r]);
+                        a[q][r] = fmaf(cv[r][t + 1], b.y, a[q][r]);
+                        a[q][r] = fmaf(cv[r][t + 2], b.z, a[q][r]);
+                        a[q][r] = fmaf(cv[r][t + 3], b.w, a[q][r]);
+                    }
                 }
             }
-            const bool v1 = j + 1 < nc;
 #pragma unroll
-            for (int r = 0; r < NPT; ++r)
-                count[r] += (a0[r] > thr ? 1u : 0u) + ((v1 && a1[r] > thr) ? 1u : 0u);
+            for (int q = 0; q < SPT; ++q) {
+                const bool vq = j + q < nc;
+#pragma unroll
+                for (int r = 0; r < NPT; ++r) count[r] += (vq && a[q][r] > thr) ? 1u : 0u;
+            }
         }
     }
 #pragma unroll
@@ -372,9 +379,9 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const
                         sizeof(int) * (size_t)T * M;
 #define ELDER_GPC_EXC(TPV, NPTV)                                                                   \
     do {                                                                                           \
-        cudaFuncSetAttribute(k_gpc_exceed<TPV, NPTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+        cudaFuncSetAttribute(k_gpc_exceed<TPV, NPTV, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)smem);                                                           \
-        k_gpc_exceed<TPV, NPTV><<<grid, kGpcBS, smem, st>>>(M, T, beta, N, coef, n_pts, nodes, Ns, \
+        k_gpc_exceed<TPV, NPTV, 4><<<grid, kGpcBS, smem, st>>>(M, T, beta, N, coef, n_pts, nodes, Ns, \
                                                             theta, thr, maxdeg, cnt);              \
     } while (0)
     switch (TP) {
