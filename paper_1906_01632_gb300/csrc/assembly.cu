@@ -1281,7 +1281,6 @@ extern "C" int elder_residual_norms_static(const elder_config* cfg, int S, const
     G.hy = f.Ly / f.ny;
     G.hz = f.Lz / f.nz;
     G.Lz = f.Lz;
-    grid_divisors(G);
     const int nblk = nblocks(G.N);
     if ((size_t)S * (size_t)nblk > kStaticScratchDoubles) {
         set_static_error("elder_residual_norms_static: S * ceil(N/256) exceeds the static "

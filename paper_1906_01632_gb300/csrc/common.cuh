@@ -17,30 +17,7 @@ struct Grid {
     int N, C;         // nodes, cells
     double hx, hy, hz;
     double Lz;
-    // exact division multipliers (see fast_div) by the nodes per row and
-    // per plane
-    unsigned long long mdx, mdxy;
 };
-
-// floor(n / d) for 0 <= n < 2^31 and 2 <= d < 2^32 with M = floor((2^64-1)/d)
-// + 1: n M / 2^64 = n/d + n e/2^64 with 0 <= e <= 1, and n e/2^64 < 2^-32 <=
-// 1/d leaves the integer part unchanged.
-__host__ __device__ inline unsigned long long div_multiplier(unsigned d)
-{
-    return ~0ull / d + 1ull;
-}
-
-__device__ __forceinline__ int fast_div(int n, unsigned long long M)
-{
-    return (int)__umul64hi((unsigned long long)(unsigned)n, M);
-}
-
-// Fills the division multipliers of a grid whose nx, ny, nz are set.
-inline void grid_divisors(Grid& G)
-{
-    G.mdx = div_multiplier((unsigned)(G.nx + 1));
-    G.mdxy = div_multiplier((unsigned)((G.nx + 1) * (G.ny + 1)));
-}
 
 // Constants of Table 1 / eq. e_lin_density and the time step.
 struct Phys {
@@ -100,10 +77,10 @@ __host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
 __device__ __forceinline__ void node_ijk(const Grid& G, int n, int& i, int& j,
                                          int& k)
 {
-    const int nx1 = G.nx + 1, ny1 = G.ny + 1;
-    k = fast_div(n, G.mdxy);
-    const int r = n - k * nx1 * ny1;
-    j = fast_div(r, G.mdx);
+    int nx1 = G.nx + 1, ny1 = G.ny + 1;
+    k = n / (nx1 * ny1);
+    int r = n - k * nx1 * ny1;
+    j = r / nx1;
     i = r - j * nx1;
 }
 
