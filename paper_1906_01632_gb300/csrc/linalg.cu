@@ -12,6 +12,8 @@
 //
 // Solver vectors hold the unknowns of the interior system: Dirichlet
 // components are kept at 0 by masking every kernel's output.
+#include <cuda_pipeline.h>
+
 #include "kernels.h"
 
 namespace elder {
@@ -254,9 +256,29 @@ __device__ __forceinline__ B4<T> mask_block(B4<T> a, uint8_t row_bc, uint8_t col
     return a;
 }
 
+// Depth of the per-thread ring of line inputs in shared memory.
+constexpr int kZlRing = 4;
+
+// Asynchronous copy of one element (8, 16 or 32 bytes, naturally aligned)
+// from global to shared memory.
+template <class X>
+__device__ __forceinline__ void async_copy(X* dst, const X* src)
+{
+    static_assert(sizeof(X) % 8 == 0 && sizeof(X) <= 32, "element size");
+    constexpr int step = (sizeof(X) % 16 == 0) ? 16 : 8;
+#pragma unroll
+    for (int o = 0; o < (int)sizeof(X); o += step)
+        __pipeline_memcpy_async(reinterpret_cast<char*>(dst) + o,
+                                reinterpret_cast<const char*>(src) + o, step);
+}
+
 // The Thomas factors C_k = M_k^{-1} U_k and g_k of the forward sweep live in
 // shared memory, [k][thread], for the backward sweep; the forward recursion
-// carries C_{k-1} and g_{k-1} in registers.
+// carries C_{k-1} and g_{k-1} in registers.  The inputs of node k (rhs,
+// inverse diagonal block, the two vertical line blocks) reach a per-thread
+// ring of kZlRing slots in shared memory by asynchronous copies issued
+// kZlRing nodes ahead: each thread walks its line serially, and the ring
+// keeps several nodes' loads in flight per thread.
 // MODE 1: x = 0, x_out = omega L^{-1} b;
 // MODE 2: b holds the residual b - A x (masked), x_out = x + omega L^{-1} b.
 // A sweep from a nonzero x is the multigrid residual kernel (all nodes in
@@ -274,48 +296,56 @@ __global__ void __launch_bounds__(kLineBS)
     const int s = blockIdx.y;
     if (!on(mask, mstride, s)) return;
     const int bsz = blockDim.x, tx = threadIdx.x;
-    B4<T>* Cs = reinterpret_cast<B4<T>*>(zl_smem);               // [nz][bsz]
-    V2<T>* gs = reinterpret_cast<V2<T>*>(Cs + (size_t)G.nz * bsz); // [nz+1][bsz]
+    B4<T>* Cs = reinterpret_cast<B4<T>*>(zl_smem);                  // [nz][bsz]
+    V2<T>* gs = reinterpret_cast<V2<T>*>(Cs + (size_t)G.nz * bsz);   // [nz+1][bsz]
+    B4<T>* Rdi = reinterpret_cast<B4<T>*>(gs + (size_t)(G.nz + 1) * bsz);  // [ring][bsz]
+    V2<T>* Rb = reinterpret_cast<V2<T>*>(Rdi + (size_t)kZlRing * bsz);
+    B4<M>* RL = reinterpret_cast<B4<M>*>(Rb + (size_t)kZlRing * bsz);
+    B4<M>* RU = RL + (size_t)kZlRing * bsz;
     const int sz = (G.nx + 1) * (G.ny + 1);
     const int col = blockIdx.x * bsz + tx;
     if (col >= sz) return;
     const size_t on_ = (size_t)s * G.N;
     const B4<M>* Js = J + (size_t)s * 27 * G.N;
     const V2<T>* xs = (MODE == 1) ? nullptr : x + on_;
+    // copies of node k into ring slot k % kZlRing (one commit group per node,
+    // empty past the end of the line)
+    auto issue = [&](int k) {
+        if (k <= G.nz) {
+            const int n = col + k * sz;
+            const int q = (k % kZlRing) * bsz + tx;
+            async_copy(Rb + q, b + on_ + n);
+            async_copy(Rdi + q, Dinv + on_ + n);
+            if (k > 0)
+                async_copy(RL + q, !TRANS ? Js + (size_t)slot27(0, 0, -1) * G.N + n
+                                          : Js + (size_t)slot27(0, 0, 1) * G.N + n - sz);
+            if (k < G.nz)
+                async_copy(RU + q, !TRANS ? Js + (size_t)slot27(0, 0, 1) * G.N + n
+                                          : Js + (size_t)slot27(0, 0, -1) * G.N + n + sz);
+        }
+        __pipeline_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < kZlRing; ++k) issue(k);
     B4<T> Cp{T(0), T(0), T(0), T(0)};
     V2<T> gp{T(0), T(0)};
     uint8_t bc_prev = 0;
     uint8_t mk = bc[col];
-    // the loads of node k + 1 are issued before the arithmetic of node k
-    // (each thread walks its line serially and few warps fit an SM)
-    struct In {
-        V2<T> b;
-        B4<T> di;
-        B4<M> qL, qU;
-        uint8_t bcn;
-    };
-    auto load = [&](int k, In& in) {
-        const int n = col + k * sz;
-        in.bcn = (k < G.nz) ? bc[n + sz] : uint8_t(0);
-        in.b = b[on_ + n];
-        in.di = Dinv[on_ + n];
-        if (k > 0)
-            in.qL = !TRANS ? Js[(size_t)slot27(0, 0, -1) * G.N + n]
-                           : Js[(size_t)slot27(0, 0, 1) * G.N + n - sz];
-        if (k < G.nz)
-            in.qU = !TRANS ? Js[(size_t)slot27(0, 0, 1) * G.N + n]
-                           : Js[(size_t)slot27(0, 0, -1) * G.N + n + sz];
-    };
-    In cur, nxt;
-    load(0, cur);
+    uint8_t bnext = (G.nz >= 1) ? bc[col + sz] : uint8_t(0);
     for (int k = 0; k <= G.nz; ++k) {
-        if (k < G.nz) load(k + 1, nxt);
-        const uint8_t bc_next = cur.bcn;
-        T rp = cur.b.p, rc = cur.b.c;
-        const B4<M> qL = cur.qL, qU = cur.qU;
+        const uint8_t bc_next = bnext;
+        bnext = (k + 2 <= G.nz) ? bc[col + (k + 2) * sz] : uint8_t(0);
+        // node k's group is complete once at most kZlRing - 1 newer ones pend
+        __pipeline_wait_prior(kZlRing - 1);
+        const int q = (k % kZlRing) * bsz + tx;
+        const V2<T> bv = Rb[q];
+        B4<T> di = Rdi[q];
+        B4<M> qL{}, qU{};
+        if (k > 0) qL = RL[q];
+        if (k < G.nz) qU = RU[q];
+        T rp = bv.p, rc = bv.c;
         if (mk & BC_P) rp = T(0);
         if (mk & BC_C) rc = T(0);
-        B4<T> di = cur.di;
         if (TRANS) di = B4<T>{di.pp, di.cp, di.pc, di.cc};
         B4<T> Mk = inv2(di);
         if (k > 0) {
@@ -335,8 +365,10 @@ __global__ void __launch_bounds__(kLineBS)
         gs[(size_t)k * bsz + tx] = gp;
         bc_prev = mk;
         mk = bc_next;
-        cur = nxt;
+        // every value of slot q is in registers and used above: refill it
+        issue(k + kZlRing);
     }
+    __pipeline_wait_prior(0);
     V2<T> d = gp;
     for (int k = G.nz;; --k) {
         const int n = col + k * sz;
@@ -357,11 +389,13 @@ __global__ void __launch_bounds__(kLineBS)
 }
 
 // Threads per block of the z-line sweep: as many as fit the per-thread
-// Thomas storage in 96 KiB of shared memory (at least one warp).
-template <class T>
+// Thomas storage and input ring in 96 KiB of shared memory (at least one
+// warp).
+template <class T, class M>
 inline int zline_block(const Grid& G, size_t* smem)
 {
-    const size_t per = (size_t)G.nz * sizeof(B4<T>) + (size_t)(G.nz + 1) * sizeof(V2<T>);
+    const size_t per = (size_t)G.nz * sizeof(B4<T>) + (size_t)(G.nz + 1) * sizeof(V2<T>) +
+                       (size_t)kZlRing * (sizeof(B4<T>) + sizeof(V2<T>) + 2 * sizeof(B4<M>));
     int bs = (int)std::min<size_t>(kLineBS, (96 * 1024 / per) / 32 * 32);
     if (bs < 32) bs = 32;
     *smem = per * bs;
@@ -376,7 +410,7 @@ void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const
     if (G.nz + 1 > kMaxLine) return;  // callers check the line limit first
     count_launch(1);
     size_t smem = 0;
-    const int bs = zline_block<T>(G, &smem);
+    const int bs = zline_block<T, M>(G, &smem);
     dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), bs), S);
     const T w = T(omega);
 #define ELDER_ZL(TR, MO)                                                                       \
@@ -384,7 +418,7 @@ void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const
         static bool attr_set = false;                                                          \
         if (!attr_set) {                                                                       \
             cudaFuncSetAttribute(k_smooth_zline<T, M, TR, MO>,                                 \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);     \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);     \
             attr_set = true;                                                                   \
         }                                                                                      \
         k_smooth_zline<T, M, TR, MO><<<grid, bs, smem, st>>>(G, J, Dinv, bc, b, x, xo, w, mask, \
