@@ -60,15 +60,19 @@ def parse():
     ap.add_argument("--gpc-samples", type=int, default=1_000_000,
                     help="surrogate sample points per node of the exceedance timing")
     ap.add_argument("--smoother", choices=["jacobi", "zline"], default="zline")
-    ap.add_argument("--no-extrapolate", action="store_true",
-                    help="start each Newton iteration from u^n (elder_step) instead of "
-                         "2 u^n - u^{n-1} (elder_step_extrapolated)")
+    ap.add_argument("--predictor", type=int, choices=[0, 1, 2], default=2,
+                    help="Newton's starting point: 0 u^n (elder_step), 1 2u^n - u^{n-1}, "
+                         "2 3u^n - 3u^{n-1} + u^{n-2} (elder_step_predicted)")
+    ap.add_argument("--no-extrapolate", action="store_true", help="the same as --predictor 0")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the BiCGStab iteration kernels one by one instead of replaying "
                          "a captured CUDA graph")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps of the profiled pass (per-kernel-class CUDA events)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.no_extrapolate:
+        a.predictor = 0
+    return a
 
 
 def workload_config(a):
@@ -88,7 +92,7 @@ def workload_config(a):
         "smoother": a.smoother,
         "solver": "inexact Newton (Krylov rtol 1e-2), BiCGStab + V(1,0) multigrid, " +
                   ("z-line damping 0.95" if a.smoother == "zline" else "point block Jacobi damping 0.5"),
-        "newton_start": "u^n" if a.no_extrapolate else "2u^n - u^(n-1)",
+        "newton_start": ["u^n", "2u^n - u^(n-1)", "3u^n - 3u^(n-1) + u^(n-2)"][a.predictor],
         "fields": fields,
         "l2": "no flush: per-step working set (Jacobians of all levels, vectors) ~10 GB >> 129 MB L2",
         "parallelism": f"samples sharded, dp{a.gpus}",
@@ -281,16 +285,17 @@ def run_ours(a):
         ctx.destroy()
         return
 
-    # u^{n-1} for the extrapolated Newton start (u^n on the first step)
-    p_prev, c_prev = p.clone(), c.clone()
+    # history levels (u^{n-1}[, u^{n-2}]) of the extrapolated Newton start,
+    # u^n in every level on the first step
+    order = a.predictor
+    p_hist = p.repeat(max(order, 1))
+    c_hist = c.repeat(max(order, 1))
 
-    def bench_step(p_, c_, pm=None, cm=None):
-        pm = p_prev if pm is None else pm
-        cm = c_prev if cm is None else cm
-        if a.no_extrapolate:
+    def bench_step(p_, c_):
+        if order == 0:
             st, info = ctx.step(S, phi, K, p_, c_, dt)
         else:
-            st, info = ctx.step_extrapolated(S, phi, K, pm, cm, p_, c_, dt)
+            st, info = ctx.step_predicted(S, phi, K, order, p_hist, c_hist, p_, c_, dt)
         mom = ctx.moments(S, c_)
         return st, info, mom
 
@@ -392,8 +397,9 @@ def run_ours(a):
     if not a.no_e2e:
         hp = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
         hc = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
-        hpm = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
-        hcm = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
+        # host history levels, newest first
+        hph = [torch.empty(S * N, dtype=torch.float64, pin_memory=True) for _ in range(order)]
+        hch = [torch.empty(S * N, dtype=torch.float64, pin_memory=True) for _ in range(order)]
         hphi = torch.empty(S * C, dtype=torch.float64, pin_memory=True)
         hK = torch.empty(S * C, dtype=torch.float64, pin_memory=True)
         hmom = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
@@ -402,11 +408,13 @@ def run_ours(a):
         hphi.copy_(phi)
         hK.copy_(K)
         dp_, dc_ = torch.empty_like(p), torch.empty_like(c)
-        dpm, dcm = torch.empty_like(p), torch.empty_like(c)
+        dph = torch.empty(max(order, 1) * S * N, dtype=torch.float64, device=dev)
+        dch = torch.empty_like(dph)
         dphi, dK = torch.empty_like(phi), torch.empty_like(K)
         bench_step(p, c)  # keep the state moving as in the timed run
-        hpm.copy_(p_prev)
-        hcm.copy_(c_prev)
+        for q in range(order):
+            hph[q].copy_(p_hist[q * S * N:(q + 1) * S * N])
+            hch[q].copy_(c_hist[q * S * N:(q + 1) * S * N])
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -415,16 +423,17 @@ def run_ours(a):
             dc_.copy_(hc, non_blocking=True)
             dphi.copy_(hphi, non_blocking=True)
             dK.copy_(hK, non_blocking=True)
-            if a.no_extrapolate:
+            if order == 0:
                 ctx.step(S, dphi, dK, dp_, dc_, dt)
             else:
-                dpm.copy_(hpm, non_blocking=True)
-                dcm.copy_(hcm, non_blocking=True)
-                ctx.step_extrapolated(S, dphi, dK, dpm, dcm, dp_, dc_, dt)
-                # the host keeps u^n as the next step's u^{n-1}: swap the
-                # buffers, u^{n+1} lands in the old u^{n-1} buffer below
-                hpm, hp = hp, hpm
-                hcm, hc = hc, hcm
+                for q in range(order):
+                    dph[q * S * N:(q + 1) * S * N].copy_(hph[q], non_blocking=True)
+                    dch[q * S * N:(q + 1) * S * N].copy_(hch[q], non_blocking=True)
+                ctx.step_predicted(S, dphi, dK, order, dph, dch, dp_, dc_, dt)
+                # the host history shifts by one level (u^n becomes the
+                # newest); u^{n+1} lands in the buffer of the dropped level
+                hp, hph = hph[-1], [hp] + hph[:-1]
+                hc, hch = hch[-1], [hc] + hch[:-1]
             m, v, pe = ctx.moments(S, dc_)
             hp.copy_(dp_, non_blocking=True)
             hc.copy_(dc_, non_blocking=True)
@@ -438,7 +447,7 @@ def run_ours(a):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
         e2e = {"value": S * world * a.steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": 8 * S * ((2 if a.no_extrapolate else 4) * N + 2 * C),
+               "h2d_bytes_per_step": 8 * S * ((2 + 2 * order) * N + 2 * C),
                "d2h_bytes_per_step": 8 * (S * 2 * N + 3 * N)}
 
     # ---- FP64 path on the same workload and state ---------------------------

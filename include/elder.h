@@ -220,6 +220,21 @@ int elder_step_extrapolated(elder_ctx* ctx, int S, const double* phi, const doub
                             double dt, int32_t* status, elder_stats* stats,
                             void* stream);
 
+/* elder_step starting Newton from a polynomial extrapolation of the last
+ * states (c clipped to [0, 1], Dirichlet values imposed): order 1 the linear
+ * 2 u^n - u^{n-1} (as elder_step_extrapolated), order 2 the quadratic
+ * 3 u^n - 3 u^{n-1} + u^{n-2}.  The same implicit Euler step (Sections 2.3
+ * and 5.1) to the same Newton tolerance.
+ *  p_hist, c_hist: [order][S][N] history levels, in: (u^{n-1}[, u^{n-2}])
+ *  (pass u^n in every level on the first step), out: (u^n[, u^{n-1}]), so
+ *  that repeated calls with the same buffers march in time.  p, c: in u^n,
+ *  out u^{n+1}.  Re-solves of failed samples start from u^n; a failed
+ *  sample keeps u^n.  Other arguments as elder_step; order outside {1, 2}
+ *  returns ELDER_EINVAL. */
+int elder_step_predicted(elder_ctx* ctx, int S, const double* phi, const double* K, int order,
+                         double* p_hist, double* c_hist, double* p, double* c, double dt,
+                         int32_t* status, elder_stats* stats, void* stream);
+
 /* Linearises at (p, c) and solves J x = rhs (transpose=0) or J^T x = rhs
  * (transpose=1) with the multigrid-preconditioned BiCGStab of elder_step,
  * to the relative residual rtol.  rhs, x: [S][N][2] device; x is output

@@ -749,7 +749,8 @@ bool krylov_converged(elder_ctx* ctx, cudaStream_t st)
 template <class T>
 int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st,
-              const NewtonSettings& set, double* p_prev = nullptr, double* c_prev = nullptr)
+              const NewtonSettings& set, int order = 0, double* p_hist = nullptr,
+              double* c_hist = nullptr)
 {
     Solver<T>& sv = solver_reserve<T>(ctx, S);
     const elder_config& cf = ctx->cfg;
@@ -763,12 +764,21 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
 
     CK(cudaMemcpyAsync(ctx->p_old, p, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ctx->c_old, c, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
-    if (p_prev) {
-        // Newton starts from 2 u^n - u^{n-1}; the caller's u^{n-1} buffers
-        // receive u^n for the next call
-        launch_extrapolate(G, ctx->p_old, ctx->c_old, p_prev, c_prev, p, c, S, st);
-        CK(cudaMemcpyAsync(p_prev, ctx->p_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(c_prev, ctx->c_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    if (p_hist) {
+        // Newton starts from the extrapolation of u^n and the order history
+        // levels (u^{n-1}[, u^{n-2}]); the history shifts by one level and
+        // its first level receives u^n for the next call
+        launch_extrapolate(G, order, ctx->p_old, ctx->c_old, p_hist, c_hist,
+                           order == 2 ? p_hist + nN : nullptr, order == 2 ? c_hist + nN : nullptr,
+                           p, c, S, st);
+        if (order == 2) {
+            CK(cudaMemcpyAsync(p_hist + nN, p_hist, sizeof(double) * nN, cudaMemcpyDeviceToDevice,
+                               st));
+            CK(cudaMemcpyAsync(c_hist + nN, c_hist, sizeof(double) * nN, cudaMemcpyDeviceToDevice,
+                               st));
+        }
+        CK(cudaMemcpyAsync(p_hist, ctx->p_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c_hist, ctx->c_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     }
     launch_impose_dirichlet(G, ctx->bc[0], ctx->cval, p, c, S, st);
     average_coefficients(ctx, S, phi, K, st);
@@ -925,7 +935,7 @@ void resolve_fp64(elder_ctx* ctx, const std::vector<int>& idx, const double* phi
 // precision) get a last FP64 solve with robust settings (tier 2).
 int step_tiers(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
                double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st,
-               double* p_prev = nullptr, double* c_prev = nullptr)
+               int order = 0, double* p_hist = nullptr, double* c_hist = nullptr)
 {
     std::vector<int32_t> st1(S);
     std::vector<elder_stats> sts(S);
@@ -934,11 +944,11 @@ int step_tiers(elder_ctx* ctx, int S, const double* phi, const double* K, double
     // (re-solves of failed samples start again from u^n, which a failed
     // sample holds)
     if (mixed)
-        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, p_prev,
-                         c_prev);
+        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, order,
+                         p_hist, c_hist);
     else
-        step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, p_prev,
-                          c_prev);
+        step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, order,
+                          p_hist, c_hist);
     auto failed = [&]() {
         std::vector<int> f;
         for (int s = 0; s < S; ++s)
@@ -1316,8 +1326,26 @@ int elder_step_extrapolated(elder_ctx* ctx, int S, const double* phi, const doub
         return ELDER_EINVAL;
     }
     try {
-        return step_tiers(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream, p_prev,
+        return step_tiers(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream, 1, p_prev,
                           c_prev);
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+}
+
+int elder_step_predicted(elder_ctx* ctx, int S, const double* phi, const double* K, int order,
+                         double* p_hist, double* c_hist, double* p, double* c, double dt,
+                         int32_t* status, elder_stats* stats, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !p_hist || !c_hist || !(dt > 0) || order < 1 || order > 2) {
+        ctx->err = "elder_step_predicted: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        return step_tiers(ctx, S, phi, K, p, c, dt, status, stats, (cudaStream_t)stream, order,
+                          p_hist, c_hist);
     } catch (const Fail& f) {
         return set_error(ctx, f);
     }

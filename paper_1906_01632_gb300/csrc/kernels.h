@@ -206,8 +206,9 @@ void launch_bicg_keep(const Grid& G, V2<T>* x, V2<T>* xbest, const KScal* ks, in
                       cudaStream_t st);
 void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
                          double tol_c, int maxit, int estimate, int S, cudaStream_t st);
-void launch_extrapolate(const Grid& G, const double* p_n, const double* c_n, const double* p_m,
-                        const double* c_m, double* p, double* c, int S, cudaStream_t st);
+void launch_extrapolate(const Grid& G, int order, const double* p_n, const double* c_n,
+                        const double* p1, const double* c1, const double* p2, const double* c2,
+                        double* p, double* c, int S, cudaStream_t st);
 void launch_newton_restore_failed(const Grid& G, double* p, double* c,
                                   const double* p_old, const double* c_old,
                                   const NScal* ns, int S, cudaStream_t st);

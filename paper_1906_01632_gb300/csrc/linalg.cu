@@ -1097,26 +1097,38 @@ void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
     k_newton_check<<<nblocks(S, 128), 128, 0, st>>>(ns, ks, tol_p, tol_c, maxit, estimate, S);
 }
 
-// Newton's starting point 2 u^n - u^{n-1}, the salt fraction clipped to
-// [0, 1] (Dirichlet values are imposed afterwards).
-__global__ void k_extrapolate(int N, const double* __restrict__ p_n,
-                              const double* __restrict__ c_n, const double* __restrict__ p_m,
-                              const double* __restrict__ c_m, double* __restrict__ p,
+// Newton's starting point from the last states: order 1 the linear
+// extrapolation 2 u^n - u^{n-1}, order 2 the quadratic 3 u^n - 3 u^{n-1} +
+// u^{n-2}; the salt fraction clipped to [0, 1] (Dirichlet values are imposed
+// afterwards).  h1, h2 hold u^{n-1}, u^{n-2}.
+__global__ void k_extrapolate(int N, int order, const double* __restrict__ p_n,
+                              const double* __restrict__ c_n, const double* __restrict__ p1,
+                              const double* __restrict__ c1, const double* __restrict__ p2,
+                              const double* __restrict__ c2, double* __restrict__ p,
                               double* __restrict__ c)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const size_t q = (size_t)blockIdx.y * N + n;
-    p[q] = 2.0 * p_n[q] - p_m[q];
-    c[q] = fmin(1.0, fmax(0.0, 2.0 * c_n[q] - c_m[q]));
+    double pe, ce;
+    if (order == 2) {
+        pe = 3.0 * (p_n[q] - p1[q]) + p2[q];
+        ce = 3.0 * (c_n[q] - c1[q]) + c2[q];
+    } else {
+        pe = 2.0 * p_n[q] - p1[q];
+        ce = 2.0 * c_n[q] - c1[q];
+    }
+    p[q] = pe;
+    c[q] = fmin(1.0, fmax(0.0, ce));
 }
 
-void launch_extrapolate(const Grid& G, const double* p_n, const double* c_n, const double* p_m,
-                        const double* c_m, double* p, double* c, int S, cudaStream_t st)
+void launch_extrapolate(const Grid& G, int order, const double* p_n, const double* c_n,
+                        const double* p1, const double* c1, const double* p2, const double* c2,
+                        double* p, double* c, int S, cudaStream_t st)
 {
     count_launch(1);
     dim3 grid(nblocks(G.N), S);
-    k_extrapolate<<<grid, kBS, 0, st>>>(G.N, p_n, c_n, p_m, c_m, p, c);
+    k_extrapolate<<<grid, kBS, 0, st>>>(G.N, order, p_n, c_n, p1, c1, p2, c2, p, c);
 }
 
 __global__ void k_newton_restore_failed(int N, double* __restrict__ p,

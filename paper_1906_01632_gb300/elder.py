@@ -83,6 +83,9 @@ def _load():
     lib.elder_step_extrapolated.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(elder_stats), vp]
+    lib.elder_step_predicted.argtypes = [vp, ip, vp, vp, ip, vp, vp, vp, vp, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(elder_stats), vp]
     lib.elder_solve.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, vp, vp,
                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int32), vp]
     lib.elder_moments.argtypes = [vp, ip, vp, vp, ctypes.c_double, vp, vp, vp, vp]
@@ -264,6 +267,25 @@ class Elder:
         self._check(rc, allow_notconv=not raise_on_fail)
         return np.frombuffer(status, dtype=np.int32).copy(), _stats_list(stats)
 
+    def step_predicted(self, S, phi, K, order, p_hist, c_hist, p, c, dt, stream=None,
+                       raise_on_fail=False):
+        """One implicit Euler step started from the order-1 (2 u^n - u^{n-1}) or
+        order-2 (3 u^n - 3 u^{n-1} + u^{n-2}) extrapolation: p_hist, c_hist
+        [order][S][N] hold (u^{n-1}[, u^{n-2}]) on entry and (u^n[, u^{n-1}]) on
+        return; p, c hold u^n on entry and u^{n+1} on return.  Returns
+        (status[S], stats list) as step."""
+        for h, what in ((p_hist, "p_hist"), (c_hist, "c_hist")):
+            if isinstance(h, torch.Tensor) and h.numel() < int(order) * S * self.N:
+                raise ValueError(f"{what}: needs order * S * N = {int(order) * S * self.N} values")
+        status = (ctypes.c_int32 * S)()
+        stats = (elder_stats * S)()
+        rc = _lib.elder_step_predicted(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"), int(order),
+                                       _ptr(p_hist, "p_hist"), _ptr(c_hist, "c_hist"),
+                                       _ptr(p, "p"), _ptr(c, "c"), dt, status, stats,
+                                       _stream(stream))
+        self._check(rc, allow_notconv=not raise_on_fail)
+        return np.frombuffer(status, dtype=np.int32).copy(), _stats_list(stats)
+
     def solve(self, S, phi, K, p, c, dt, rhs, transpose=False, rtol=1e-10, x=None, stream=None):
         x = x if x is not None else torch.empty_like(rhs)
         status = (ctypes.c_int32 * S)()
@@ -420,6 +442,10 @@ def elder_step(ctx: Elder, *a, **k):
 
 def elder_step_extrapolated(ctx: Elder, *a, **k):
     return ctx.step_extrapolated(*a, **k)
+
+
+def elder_step_predicted(ctx: Elder, *a, **k):
+    return ctx.step_predicted(*a, **k)
 
 
 def elder_solve(ctx: Elder, *a, **k):

@@ -390,3 +390,49 @@ def test_extrapolated_start_marches_to_the_oracle_states(E, precision, tol):
             p1 = H(pt).reshape(S, -1)[s]
             assert np.abs(c1 - refs[s][n][1]).max() <= tol, (s, n)
             assert np.abs(p1 - refs[s][n][0]).max() <= max(tol, 1e-9) * P.rho0 * P.g * P.Lz, (s, n)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+def test_quadratic_predictor_marches_to_the_oracle_states(E, precision, tol):
+    """elder_step_predicted with order 2 starts Newton from 3 u^n - 3 u^{n-1} +
+    u^{n-2} and solves the same implicit step: a 5-step march matches the
+    oracle's states, and the two history levels shift by one level per call."""
+    P = O.Problem(16, 16, 4)
+    S = 2
+    phi, K = _fields(P, S, 52)
+    p0, c0 = O.initial_state(P)
+    ctx = _ctx(E, 16, 16, 4, S=S, precision=precision)
+    pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+    ph, ch = pt.repeat(2), ct.repeat(2)
+    phit, Kt = T(phi), T(K)
+    dt = YEAR / 12
+    nN = S * P.N
+    refs = [_oracle_traj(P, phi[s], K[s], p0, c0, 5, dt) for s in range(S)]
+    for n in range(5):
+        p_before, c_before = H(pt).copy(), H(ct).copy()
+        p_lvl0, c_lvl0 = H(ph)[:nN].copy(), H(ch)[:nN].copy()
+        st, _ = ctx.step_predicted(S, phit, Kt, 2, ph, ch, pt, ct, dt)
+        assert (st == 0).all()
+        assert np.array_equal(H(ph)[:nN], p_before) and np.array_equal(H(ch)[:nN], c_before)
+        assert np.array_equal(H(ph)[nN:], p_lvl0) and np.array_equal(H(ch)[nN:], c_lvl0)
+        for s in range(S):
+            c1 = H(ct).reshape(S, -1)[s]
+            p1 = H(pt).reshape(S, -1)[s]
+            assert np.abs(c1 - refs[s][n][1]).max() <= tol, (s, n)
+            assert np.abs(p1 - refs[s][n][0]).max() <= max(tol, 1e-9) * P.rho0 * P.g * P.Lz, (s, n)
+
+
+def test_predicted_step_rejects_bad_orders_and_short_history(E):
+    P = O.Problem(8, 8, 2)
+    ctx = _ctx(E, 8, 8, 2, S=1)
+    phi, K = _fields(P, 1, 53)
+    p0, c0 = O.initial_state(P)
+    pt, ct = T(p0), T(c0)
+    # the library rejects orders outside {1, 2} (history long enough for 3)
+    for order in (0, 3):
+        with pytest.raises(Exception):
+            ctx.step_predicted(1, T(phi), T(K), order, pt.repeat(3), ct.repeat(3), pt, ct,
+                               YEAR / 12)
+    # the binding rejects a history shorter than order * S * N
+    with pytest.raises(ValueError):
+        ctx.step_predicted(1, T(phi), T(K), 2, pt.clone(), ct.clone(), pt, ct, YEAR / 12)
