@@ -558,10 +558,34 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[q][r] = T(0);
     T phis = T(0);
+    const uint8_t b = bc[n];
+    if (JT) JT += (size_t)s * 27 * G.N;
+    if (JM) JM += (size_t)s * 27 * G.N;
+    // Dirichlet rows are identity rows: zero a block's p row / c row (the
+    // diagonal block gets its 1 after storage), then store it
+    auto finish = [&](int q) {
+        if (b & BC_P) { acc[q][0] = T(0); acc[q][1] = T(0); }
+        if (b & BC_C) { acc[q][2] = T(0); acc[q][3] = T(0); }
+        if (q == 13) {
+            if (b & BC_P) acc[13][0] = T(1);
+            if (b & BC_C) acc[13][3] = T(1);
+        }
+        if (JT) JT[(size_t)q * G.N + n] = B4<T>{acc[q][0], acc[q][1], acc[q][2], acc[q][3]};
+        if (JM)
+            JM[(size_t)q * G.N + n] =
+                B4<M>{mg_store<M>(acc[q][0]), mg_store<M>(acc[q][1]), mg_store<M>(acc[q][2]),
+                      mg_store<M>(acc[q][3])};
+    };
+    // the 4 cells below the node touch only the blocks of offsets dz = -1
+    // and dz = 0, the 4 above only dz = 0 and dz = +1: the dz = -1 blocks
+    // are complete (and stored) before the upper cells, so at most 18 of the
+    // 27 blocks are live at a time
     jac_cell<T, -1, -1, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     jac_cell<T, 0, -1, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     jac_cell<T, -1, 0, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     jac_cell<T, 0, 0, -1>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) finish(q);
     jac_cell<T, -1, -1, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     jac_cell<T, 0, -1, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
     jac_cell<T, -1, 0, 0>(G, pt, cg, i, j, k, cellT, nodeT, acc, phis);
@@ -571,34 +595,13 @@ __global__ void __launch_bounds__(128)
     const T cn = nodeT[n].c;
     acc[13][1] += vdt * pt.drho;
     acc[13][3] += vdt * (pt.rho0 + T(2) * pt.drho * cn);
-    const uint8_t b = bc[n];
-    if (b & BC_P) {
+    // the diagonal block's Dirichlet-free entries for Dinv
+    const T a0 = acc[13][0], b0 = acc[13][1], c0 = acc[13][2], e0 = acc[13][3];
 #pragma unroll
-        for (int q = 0; q < 27; ++q) { acc[q][0] = T(0); acc[q][1] = T(0); }
-        acc[13][0] = T(1);
-    }
-    if (b & BC_C) {
-#pragma unroll
-        for (int q = 0; q < 27; ++q) { acc[q][2] = T(0); acc[q][3] = T(0); }
-        acc[13][3] = T(1);
-    }
-    if (JT) {
-        JT += (size_t)s * 27 * G.N;
-#pragma unroll
-        for (int q = 0; q < 27; ++q)
-            JT[(size_t)q * G.N + n] = B4<T>{acc[q][0], acc[q][1], acc[q][2], acc[q][3]};
-    }
-    if (JM) {
-        JM += (size_t)s * 27 * G.N;
-#pragma unroll
-        for (int q = 0; q < 27; ++q)
-            JM[(size_t)q * G.N + n] =
-                B4<M>{mg_store<M>(acc[q][0]), mg_store<M>(acc[q][1]), mg_store<M>(acc[q][2]),
-                      mg_store<M>(acc[q][3])};
-    }
+    for (int q = 9; q < 27; ++q) finish(q);
     if (Dinv) {
         // in T: the FP32 entries' determinant is formed without FP64 work
-        T a = acc[13][0], bb = acc[13][1], cc = acc[13][2], e = acc[13][3];
+        T a = a0, bb = b0, cc = c0, e = e0;
         if (b & BC_P) { a = T(1); bb = T(0); cc = T(0); }
         if (b & BC_C) { e = T(1); bb = T(0); cc = T(0); }
         const T id = T(1) / (a * e - bb * cc);
