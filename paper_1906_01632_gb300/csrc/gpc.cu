@@ -47,18 +47,6 @@ __device__ inline void legendre_all_f(int n, float x, float* P)
     for (int k = 1; k < n; ++k) P[k + 1] = ((2 * k + 1) * x * P[k] - k * P[k - 1]) / (k + 1);
 }
 
-// P_beta(theta) for one point; beta is [T][M], P1 scratch [M][maxdeg+1].
-// (beta entries outside [0, maxdeg] are clamped: a caller error gives wrong
-// values, never an out-of-range read)
-template <class R>
-__device__ inline R basis_value(const int32_t* beta, int t, int M, const R* P1, int stride,
-                                int maxdeg)
-{
-    R v = R(1);
-    for (int j = 0; j < M; ++j) v *= P1[j * stride + min(max((int)beta[t * M + j], 0), maxdeg)];
-    return v;
-}
-
 // coef[t][n] = sum_i Bq[t][i] u[i][n] with Bq = 0.5^M w_i P_t(theta_i) / Q_t
 // (eq. PCEcoef); TP >= T accumulators per thread.
 template <int TP>
@@ -132,6 +120,8 @@ __global__ void __launch_bounds__(kGpcBS)
     const int D1 = maxdeg + 1;
     float* Ps = Bs + kGpcChunk * TP;                         // [kGpcChunk][M][D1]
     int* bs = reinterpret_cast<int*>(Ps + kGpcChunk * M * D1);  // [T][M]
+    // multi-index entries outside [0, maxdeg] are clamped: a caller error
+    // gives wrong values, never an out-of-range read
     for (int e = threadIdx.x; e < T * M; e += blockDim.x)
         bs[e] = min(max((int)beta[e], 0), maxdeg);
     int kk[NPT];
