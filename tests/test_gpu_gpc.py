@@ -65,10 +65,12 @@ def _bracket_check(E, beta, coef, theta, thr, nodes=None):
     return got, lo, hi
 
 
-def test_exceedance_brackets_oracle(E):
-    M, p = 3, 4
+# (3, 4): 35 terms (the bench's surrogate, padded to 36, 4 nodes per thread);
+# (3, 3): 20 terms; (3, 5) and (5, 3): 56 terms (2 nodes per thread)
+@pytest.mark.parametrize("M,p", [(3, 4), (3, 3), (3, 5), (5, 3)])
+def test_exceedance_brackets_oracle(E, M, p):
     beta = G.multi_indices(M, p)
-    rng = np.random.default_rng(7)
+    rng = np.random.default_rng(7 + 10 * M + p)
     N = 300
     # coefficients of smooth responses: decaying with degree, mean near the threshold
     deg = beta.sum(1)
