@@ -123,7 +123,11 @@ typedef struct {
     int32_t krylov_iters;     /* summed over the Newton iterations          */
     int32_t ls_cuts;          /* step halvings                              */
     double res0;              /* ||R(u^n)||_2 with Dirichlet data imposed   */
-    double res;               /* ||R(u^{n+1})||_2                           */
+    double res;               /* ||R||_2 of the last iterate whose residual
+                                 was evaluated: u^{n+1}, or its predecessor
+                                 when Newton stopped on the size of the
+                                 last full correction (whose residual is
+                                 then not evaluated)                        */
     int32_t fp64_retry;       /* 0: solved by the configured solver; 1: the
                                  ELDER_MIXED solve failed and the step was
                                  solved again from u^n with the FP64 solver;

@@ -819,6 +819,20 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         ctx->nu2_now = cf.nu2;
         for (int ls = 0; ls <= set.ls_max; ++ls) {
             launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, st);
+            // full step: samples whose correction meets the stop need no
+            // trial residual (they drop out of its mask)
+            if (ls == 0) {
+                launch_newton_predict(ctx->partial2, nb, ns, cf.newton_tol_p, cf.newton_tol_c,
+                                      set.estimate, S, st);
+                if (ctx->prof.on) {  // the residual's work counts only the samples left
+                    CK(cudaMemcpyAsync(ctx->h_ns, ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost,
+                                       st));
+                    CK(cudaStreamSynchronize(st));
+                    int nls = 0;
+                    for (int s = 0; s < S; ++s) nls += ctx->h_ns[s].ls_active ? 1 : 0;
+                    ctx->n_active_ls = nls;
+                }
+            }
             pi = prof_begin(ctx, st);
             launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
                             ctx->c_old, ctx->Rt, ctx->partial, ctx->partial3, lsmask, NSTRIDE,

@@ -48,7 +48,8 @@ struct NScal {
     double dmax_p, dmax_c;       // max |lambda * delta| of the last step
     double rfloor, rfloor_t;     // round-off level of ||R(u)||, ||R(u_trial)||
     double dprev_p, dprev_c;     // max |delta| of the previous Newton step
-    int full_prev, pad0;         // previous step was a full (lambda = 1) step
+    int full_prev;               // previous step was a full (lambda = 1) step
+    int skip_res;                // this full step meets the stop: no trial residual
     int active;                  // still iterating
     int ls_active;               // line search still running
     int accepted;                // trial accepted in this Newton iteration
@@ -206,6 +207,10 @@ void launch_bicg_keep(const Grid& G, V2<T>* x, V2<T>* xbest, const KScal* ks, in
                       cudaStream_t st);
 void launch_newton_check(NScal* ns, const KScal* ks, double tol_p,
                          double tol_c, int maxit, int estimate, int S, cudaStream_t st);
+// Before the trial residual of a full step: a sample whose correction
+// already meets the stop of launch_newton_check is accepted without it.
+void launch_newton_predict(const double* partial_max, int nblk, NScal* ns, double tol_p,
+                           double tol_c, int estimate, int S, cudaStream_t st);
 void launch_extrapolate(const Grid& G, int order, const double* p_n, const double* c_n,
                         const double* p1, const double* c1, const double* p2, const double* c2,
                         double* p, double* c, int S, cudaStream_t st);

@@ -1033,7 +1033,7 @@ __global__ void __launch_bounds__(kBS)
     const size_t q = (size_t)s * N + n;
     p[q] = pt[q];
     c[q] = ct[q];
-    R[q] = Rt[q];
+    if (!ns[s].skip_res) R[q] = Rt[q];  // else R stays that of the last evaluated iterate
 }
 
 void launch_newton_accept(const Grid& G, double* p, double* c,
@@ -1046,6 +1046,62 @@ void launch_newton_accept(const Grid& G, double* p, double* c,
     k_newton_accept<<<grid, kBS, 0, st>>>(G.N, p, c, pt, ct, R, Rt, ns);
 }
 
+// With inexact linear solves Newton converges linearly: from two
+// consecutive full steps the contraction is theta = |d_k| / |d_{k-1}| and
+// the remaining error about theta / (1 - theta) |d_k|.  A full step stops
+// the iteration when that estimate, or the last correction itself, is
+// within tolerance.
+__device__ __forceinline__ bool newton_small(const NScal& k, double tol_p, double tol_c,
+                                             int estimate)
+{
+    if (k.lambda != 1.0) return false;
+    if (k.dmax_c <= tol_c && k.dmax_p <= tol_p) return true;
+    if (estimate && k.full_prev && k.dprev_c > 0.0 && k.dprev_p > 0.0) {
+        const double th = fmax(k.dmax_c / k.dprev_c, k.dmax_p / k.dprev_p);
+        if (th < 0.5) {
+            const double f = th / (1.0 - th);
+            return f * k.dmax_c <= tol_c && f * k.dmax_p <= tol_p;
+        }
+    }
+    return false;
+}
+
+// Before the trial residual of a full step (lambda = 1): the sizes of the
+// correction (per-block maxima of k_newton_trial) decide the stop already,
+// and a sample that meets it is accepted without its trial residual (its
+// Armijo test would only compare a converged iterate).
+__global__ void k_newton_predict(const double* __restrict__ pmax, int nblk, NScal* ns,
+                                 double tol_p, double tol_c, int estimate)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    if (!ns[s].ls_active || ns[s].lambda != 1.0) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+        a0 = fmax(a0, pmax[((size_t)s * 2 + 0) * nblk + q]);
+        a1 = fmax(a1, pmax[((size_t)s * 2 + 1) * nblk + q]);
+    }
+    a0 = block_max(a0, red);
+    a1 = block_max(a1, red);
+    if (threadIdx.x != 0) return;
+    NScal k = ns[s];
+    k.dmax_p = a0;
+    k.dmax_c = a1;
+    if (newton_small(k, tol_p, tol_c, estimate)) {
+        k.ls_active = 0;
+        k.accepted = 1;
+        k.skip_res = 1;
+        ns[s] = k;
+    }
+}
+
+void launch_newton_predict(const double* partial_max, int nblk, NScal* ns, double tol_p,
+                           double tol_c, int estimate, int S, cudaStream_t st)
+{
+    count_launch(1);
+    k_newton_predict<<<S, 128, 0, st>>>(partial_max, nblk, ns, tol_p, tol_c, estimate);
+}
+
 __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
                                double tol_c, int maxit, int estimate, int S)
 {
@@ -1055,34 +1111,30 @@ __global__ void k_newton_check(NScal* ns, const KScal* ks, double tol_p,
     if (!k.active) return;
     k.kiters += ks[s].iters;
     if (k.accepted) {
-        k.rn = k.rt;
-        k.rfloor = k.rfloor_t;
         k.iters += 1;
-        // With inexact linear solves Newton converges linearly: from two
-        // consecutive full steps the contraction is theta = |d_k| / |d_{k-1}|
-        // and the remaining error about theta / (1 - theta) |d_k|.  The
-        // iterate is accepted when that estimate, or the last correction
-        // itself, is within tolerance (or R is at its round-off floor).
-        bool small = k.lambda == 1.0 && k.dmax_c <= tol_c && k.dmax_p <= tol_p;
-        if (estimate && !small && k.lambda == 1.0 && k.full_prev && k.dprev_c > 0.0 &&
-            k.dprev_p > 0.0) {
-            const double th = fmax(k.dmax_c / k.dprev_c, k.dmax_p / k.dprev_p);
-            if (th < 0.5) {
-                const double f = th / (1.0 - th);
-                small = f * k.dmax_c <= tol_c && f * k.dmax_p <= tol_p;
-            }
-        }
-        k.full_prev = (k.lambda == 1.0);
-        k.dprev_c = k.dmax_c;
-        k.dprev_p = k.dmax_p;
-        if (small || k.rn <= k.rfloor) {
+        if (k.skip_res) {
+            // accepted by k_newton_predict: its correction met the stop (rn
+            // stays the norm of the last evaluated iterate)
             k.active = 0;
             k.status = 0;
-        } else if (k.iters >= maxit) {
-            k.active = 0;
-            k.status = ELDER_SAMPLE_NEWTON_MAXIT_;
+        } else {
+            k.rn = k.rt;
+            k.rfloor = k.rfloor_t;
+            // the correction-size stop (or R at its round-off floor)
+            const bool small = newton_small(k, tol_p, tol_c, estimate);
+            k.full_prev = (k.lambda == 1.0);
+            k.dprev_c = k.dmax_c;
+            k.dprev_p = k.dmax_p;
+            if (small || k.rn <= k.rfloor) {
+                k.active = 0;
+                k.status = 0;
+            } else if (k.iters >= maxit) {
+                k.active = 0;
+                k.status = ELDER_SAMPLE_NEWTON_MAXIT_;
+            }
         }
     }
+    k.skip_res = 0;
     k.accepted = 0;
     k.ls_count = 0;
     k.lambda = 1.0;
