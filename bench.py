@@ -193,7 +193,12 @@ def run_reference(a):
     if rank != 0:
         return
     cfg = workload_config(a)
+    # the same workload; the solver keys describe the oracle's own method
     cfg["precision"] = "fp64"
+    cfg["smoother"] = "block Jacobi (oracle)"
+    cfg["solver"] = ("Newton (tolerance 1e-12) with dense LU up to 1200 unknowns, else BiCGStab + "
+                     "damped block-Jacobi V(1,1) multigrid (oracle)")
+    cfg["newton_start"] = "u^n"
     steps = []
     for i in range(a.warmup + a.steps):
         r = cpu_baseline(a)
