@@ -5,10 +5,12 @@ Workload: the batched qMC ensemble at 64x64x16 cells (71,825 nodes, 143,650
 unknowns per sample), 256 samples of scrambled-Sobol porosity fields
 phi = 0.1*(1 + 0.3*(xi1 cos(pi x/600) + xi2 cos(pi y/600) + xi3 sin(2 pi
 z/150))/3) with normalised Kozeny-Carman permeability, dt = 1/12 yr, mixed
-precision (FP32 multigrid and Krylov storage inside FP64 Newton with FP64
-residual and inner products).  One bench step = one implicit Euler step of
-every sample (elder_step) plus the ensemble moments of that step
-(elder_moments).  Metric: sample-timesteps/s, higher is better.
+precision (bfloat16 multigrid matrices, FP32 Krylov operator and vectors
+inside FP64 Newton with FP64 residual and inner products).  One bench step =
+one implicit Euler step of every sample (elder_step_predicted: Newton from
+the quadratic extrapolation of the last states; --predictor 0 uses
+elder_step) plus the ensemble moments of that step (elder_moments).
+Metric: sample-timesteps/s, higher is better.
 
 Under torchrun each rank takes its own 256 samples (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
