@@ -148,9 +148,11 @@ typedef struct {
 
 typedef struct elder_ctx elder_ctx;
 
-/* Fills *cfg with the benchmark problem of Table 1 (Dm = 3.565e-6, see the
- * design notes on the printed 0.565e-6) on an nx*ny*nz grid and default
- * solver settings.  Returns ELDER_EINVAL for a NULL cfg. */
+/* Fills *cfg with the benchmark problem of Table 1 on an nx*ny*nz grid and
+ * default solver settings.  Dm = 3.565e-6 m^2/s, the classic Elder value:
+ * Table 1 prints 0.565e-6, read as a dropped leading digit (both densities,
+ * the viscosity, K and phi of the table are the classic Elder values too).
+ * Returns ELDER_EINVAL for a NULL cfg. */
 int elder_config_default(elder_config* cfg, int nx, int ny, int nz);
 
 /* Creates a context: validates the grid, builds the multigrid hierarchy and
@@ -296,9 +298,19 @@ enum {
 int elder_profile(elder_ctx* ctx, int on);
 
 /* Totals since elder_profile(ctx, 1) for one class: launches, summed event
- * time [ms], algorithmic DRAM bytes and FP64/FP32 flops of those launches
- * (per-node model x nodes x active samples; see the design notes).  Any
- * output pointer may be NULL.  Host outputs. */
+ * time [ms], algorithmic DRAM bytes and FP64/FP32 flops of those launches.
+ * Bytes = per-node model x nodes x samples active in the launch; the model
+ * counts every array the kernel must touch once (neighbour reuse of a
+ * vector is free).  Per node, with T the vector entry size (8 FP64, 4
+ * mixed) and Mz the multigrid matrix entry size (8 FP64, 2 mixed):
+ *   SMOOTH  108 Mz + 10 T + 1    SMOOTH0  8 T + 1 (+ 8 Mz z-line)
+ *   SPMV    108 T  + 6 T + 1     MGRES    108 Mz + 6 T + 1
+ *   RESIDUAL 49 + 16 C/N         JACOBIAN 108 T + 108 Mz + 4 T + 17 + 16 C/N
+ * (the Jacobian writes the Krylov and the multigrid copies of J and the
+ * inverse diagonal blocks; the residual reads p, c, c_old, phi, K and writes
+ * R).  Flops: the FP64 residual counts 326 C/N + 75 of its factored face
+ * form, the stencil products 216 + their vector terms.  Any output pointer
+ * may be NULL.  Host outputs. */
 int elder_profile_read(const elder_ctx* ctx, int kernel_class,
                        int64_t* launches, double* ms, double* bytes,
                        double* flops);
@@ -331,9 +343,15 @@ int elder_autotune_result(const elder_ctx* ctx, int* bs_smooth, int* bs_spmv,
  * Scratch: the per-block partial sums live in a file-scope device array of
  * 262144 doubles (2 MiB), which every GPU that loads the library holds until
  * the process exits.  S * ceil(N/256) must not exceed 262144, otherwise
- * ELDER_EINVAL is returned before anything is launched.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * ELDER_EINVAL is returned before anything is launched, as it is for
+ * S > 65535 (samples run along the launch grid's y dimension).  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  With CUDA's lazy module
+ * loading (the default since CUDA 12.2) that first lookup is also what
+ * loads the library's device code and reserves the 2 MiB array on that
+ * device, i.e. it may allocate device memory once.  So make the first call
+ * on each device early: before another runtime takes the device's memory
+ * and before any stream capture.  Later calls allocate nothing.
  * Every call shares the array and overwrites the entries it uses (nothing
  * in it has to start at zero); calls that overlap on the GPU race on it.
  * Errors: elder_last_error(NULL). */

@@ -1285,6 +1285,10 @@ extern "C" int elder_residual_norms_static(const elder_config* cfg, int S, const
     G.hz = f.Lz / f.nz;
     G.Lz = f.Lz;
     const int nblk = nblocks(G.N);
+    if (S > 65535) {  // samples run along grid.y
+        set_static_error("elder_residual_norms_static: S exceeds 65535 samples per call");
+        return ELDER_EINVAL;
+    }
     if ((size_t)S * (size_t)nblk > kStaticScratchDoubles) {
         set_static_error("elder_residual_norms_static: S * ceil(N/256) exceeds the static "
                          "scratch capacity (262144 partial sums)");
@@ -1316,8 +1320,13 @@ extern "C" int elder_residual_norms_static(const elder_config* cfg, int S, const
                                                      c, p_old, c_old,
                                                      reinterpret_cast<V2<double>*>(R),
                                                      g_scratch_addr[dev]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {  // the norms are not formed from stale partial sums
+        set_static_error(cudaGetErrorString(e));
+        return ELDER_ECUDA;
+    }
     k_norms_static<<<S, 128, 0, st>>>(nblk, g_scratch_addr[dev], norms);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_static_error(cudaGetErrorString(e));
         return ELDER_ECUDA;

@@ -952,8 +952,10 @@ __global__ void __launch_bounds__(kBS)
         const double dp = lam * (double)d.p, dc = lam * (double)d.c;
         pt[q] = p[q] + dp;
         ct[q] = c[q] + dc;
-        mp = fabs(dp);
-        mc = fabs(dc);
+        // a non-finite correction must never meet the Newton stop: block_max
+        // (fmax) would drop a NaN, so it enters the maxima as +inf
+        mp = isfinite(dp) ? fabs(dp) : INFINITY;
+        mc = isfinite(dc) ? fabs(dc) : INFINITY;
     }
     const double t0 = block_max(mp, red);
     const double t1 = block_max(mc, red);

@@ -330,12 +330,20 @@ def elder_residual_norms_static(cfg: elder_config, S, phi, K, p, c, p_old, c_old
     allocation inside the library (its scratch is a fixed 2 MiB device
     array).  R and norms are allocated here by torch unless passed in."""
     N = (cfg.nx + 1) * (cfg.ny + 1) * (cfg.nz + 1)
-    R = R if R is not None else torch.empty(S * N * 2, dtype=torch.float64, device=p.device)
-    norms = norms if norms is not None else torch.empty(S, dtype=torch.float64, device=p.device)
-    rc = _lib.elder_residual_norms_static(ctypes.byref(cfg), S, _ptr(phi, "phi"), _ptr(K, "K"),
-                                          _ptr(p, "p"), _ptr(c, "c"), _ptr(p_old, "p_old"),
-                                          _ptr(c_old, "c_old"), dt, _ptr(R, "R"),
-                                          _ptr(norms, "norms"), _stream(stream))
+    dev = p.device
+    R = R if R is not None else torch.empty(S * N * 2, dtype=torch.float64, device=dev)
+    norms = norms if norms is not None else torch.empty(S, dtype=torch.float64, device=dev)
+    for name, t in (("phi", phi), ("K", K), ("c", c), ("p_old", p_old), ("c_old", c_old),
+                    ("R", R), ("norms", norms)):
+        if isinstance(t, torch.Tensor) and t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, p on {dev}: all tensors must share a device")
+    # the library launches on the current device: make it the tensors' one
+    with torch.cuda.device(dev):
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        rc = _lib.elder_residual_norms_static(ctypes.byref(cfg), S, _ptr(phi, "phi"),
+                                              _ptr(K, "K"), _ptr(p, "p"), _ptr(c, "c"),
+                                              _ptr(p_old, "p_old"), _ptr(c_old, "c_old"), dt,
+                                              _ptr(R, "R"), _ptr(norms, "norms"), _stream(st))
     if rc != ELDER_OK:
         raise ElderError(rc, _lib.elder_last_error(None).decode())
     return R, norms

@@ -442,3 +442,155 @@ def test_adjoint_gradient_matches_central_fd():
                 fd = (J_of(phi, up) - J_of(phi, dn)) / (2 * h)
             scale = np.abs(g).max()
             assert abs(fd - g[e]) <= 1e-5 * max(abs(g[e]), 1e-3 * scale), (which, e, fd, g[e])
+
+
+# --------------------------------------------------------------------------
+# the paper's parallelepiped porosity field (Section 5.3, eq. poro-paral3RVS)
+# --------------------------------------------------------------------------
+
+def _kc(phi, K_mean=4.845e-13):
+    return K_mean * (phi ** 3 / (1 - phi) ** 2) / (0.1 ** 3 / 0.9 ** 2)
+
+
+def test_paper3rv_field_closed_forms():
+    """eq. poro-paral3RVS: phi = 0.1 + 0.01 (xi1 sx + xi2 sy + xi3 sz + xi1 sx sy
+    + xi2 sx sz) with sx = sin(pi x/600), sy = sin(pi y/600), sz = sin(pi
+    z/150) at the cell centre.  On a 6x6x2 grid the centres sit at x, y in
+    {50, 150, ..., 550} and z in {37.5, 112.5}, where the sines have closed
+    forms: sin(pi/12) = (sqrt6 - sqrt2)/4, sin(pi/4) = sqrt2/2, sin(5pi/12) =
+    (sqrt6 + sqrt2)/4, and sz = sqrt2/2 in both layers.  Expected values are
+    written from those surds, not from the oracle's expression."""
+    P = O.Problem(6, 6, 2)
+    r2, r6 = math.sqrt(2.0), math.sqrt(6.0)
+    s = {0: (r6 - r2) / 4, 1: r2 / 2, 2: (r6 + r2) / 4}  # sin of the centre of cell i (i<=2)
+
+    def cell(i, j, k):
+        return i + P.nx * (j + P.ny * k)
+
+    phi0, K0 = O.fields_paper3rv(P, [0.0, 0.0, 0.0])
+    assert np.all(phi0 == 0.1)
+    np.testing.assert_allclose(K0, 4.845e-13, rtol=1e-15)
+    sz = r2 / 2
+    cases = [  # (xi, cell (i, j, k), expected phi)
+        ((1.0, 0.0, 0.0), (1, 0, 0), 0.1 + 0.01 * (s[1] + s[1] * s[0])),
+        ((1.0, 0.0, 0.0), (0, 2, 1), 0.1 + 0.01 * (s[0] + s[0] * s[2])),
+        ((0.0, 1.0, 0.0), (2, 0, 0), 0.1 + 0.01 * (s[0] + s[2] * sz)),
+        ((0.0, 1.0, 0.0), (0, 1, 1), 0.1 + 0.01 * (s[1] + s[0] * sz)),
+        ((0.0, 0.0, 1.0), (2, 1, 0), 0.1 + 0.01 * sz),
+        ((-1.0, 0.5, 1.0), (1, 2, 1),
+         0.1 + 0.01 * (-s[1] + 0.5 * s[2] + sz - s[1] * s[2] + 0.5 * s[1] * sz)),
+    ]
+    for xi, (i, j, k), want in cases:
+        phi, K = O.fields_paper3rv(P, list(xi))
+        assert abs(phi[cell(i, j, k)] - want) <= 1e-16, (xi, (i, j, k), phi[cell(i, j, k)], want)
+        assert abs(K[cell(i, j, k)] - _kc(want)) <= 1e-14 * _kc(want)
+
+
+def test_paper3rv_field_mirror_symmetries():
+    """All three sines are symmetric under x -> 600 - x, y -> 600 - y and
+    z -> 150 - z (sin(pi - a) = sin a), so the field is too, for every xi;
+    the cross terms are not symmetric under x <-> y (xi2 multiplies sx sz, not
+    sy sz), which a swapped argument would make them."""
+    P = O.Problem(8, 12, 4)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        phi, _ = O.fields_paper3rv(P, rng.uniform(-1, 1, 3))
+        a = phi.reshape(P.nz, P.ny, P.nx)
+        np.testing.assert_allclose(a, a[:, :, ::-1], rtol=0, atol=1e-16)
+        np.testing.assert_allclose(a, a[:, ::-1, :], rtol=0, atol=1e-16)
+        np.testing.assert_allclose(a, a[::-1, :, :], rtol=0, atol=1e-16)
+    Q = O.Problem(8, 8, 4)
+    phi, _ = O.fields_paper3rv(Q, [0.0, 1.0, 0.0])
+    a = phi.reshape(Q.nz, Q.ny, Q.nx)
+    assert np.abs(a - a.transpose(0, 2, 1)).max() > 1e-4
+
+
+# --------------------------------------------------------------------------
+# the plume functional (salt mass below mid-depth)
+# --------------------------------------------------------------------------
+
+def test_objective_closed_forms():
+    """J = sum over the cells whose centre lies below Lz/2 of sum over their
+    8 corners of phi_e |scv| rho(c) c, |scv| = hx hy hz / 8.  Closed forms on
+    an even nz (the mid-plane is a grid plane):
+      c = 1 everywhere:   J = rho1 phi Lx Ly Lz / 2;
+      c = 0.5 everywhere: J = rho(0.5) 0.5 phi Lx Ly Lz / 2;
+      c = 0 everywhere:   J = 0;
+      c = 1 on nodes with z > Lz/2 only: J = 0 (no lower cell has such a corner);
+      c = 1 on nodes with z >= Lz/2: only the upper corners of the top lower
+        layer count, 4 per cell: J = rho1 phi Lx Ly hz / 2;
+    and with phi different per layer only the lower layers count."""
+    P = O.Problem(8, 6, 4)
+    phi = np.full(P.C, 0.13)
+    x, y, z, i, j, k = _node_xyz(P)
+    V = P.Lx * P.Ly * P.Lz
+    hz = P.Lz / P.nz
+    rho = lambda cc: P.rho0 + (P.rho1 - P.rho0) * cc  # noqa: E731
+    tol = 1e-13
+    assert abs(O.objective(P, phi, np.ones(P.N)) - P.rho1 * 0.13 * V / 2) <= tol * P.rho1 * V
+    assert abs(O.objective(P, phi, np.full(P.N, 0.5)) - rho(0.5) * 0.5 * 0.13 * V / 2) \
+        <= tol * P.rho1 * V
+    assert O.objective(P, phi, np.zeros(P.N)) == 0.0
+    assert O.objective(P, phi, (z > P.Lz / 2).astype(float)) == 0.0
+    want = P.rho1 * 0.13 * P.Lx * P.Ly * hz / 2
+    assert abs(O.objective(P, phi, (z >= P.Lz / 2 - 1e-9).astype(float)) - want) <= tol * want
+    # layered porosity: layers k = 0, 1 (below) weigh in, layers 2, 3 do not
+    lay = np.array([0.05, 0.07, 0.11, 0.19])
+    phil = np.repeat(lay, P.nx * P.ny)
+    want = P.rho1 * (lay[0] + lay[1]) * P.Lx * P.Ly * hz
+    assert abs(O.objective(P, phil, np.ones(P.N)) - want) <= tol * want
+
+
+# --------------------------------------------------------------------------
+# boundary sets (Section 2.1 and the caption of Fig. 1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(8, 8, 4), (12, 16, 2), (4, 8, 3)])
+def test_dirichlet_sets_counts(dims):
+    """Paper variant (bc_mode 1): p = 0 on the four top edges, i.e. 2(nx+1) +
+    2(ny+1) - 4 nodes; c prescribed on every top and every bottom node and
+    nowhere else, with c = 1 on the closed square [Lx/4, 3Lx/4] x [Ly/4,
+    3Ly/4] of the top, (nx/2 + 1)(ny/2 + 1) nodes, and c = 0 on the rest.
+    Benchmark (bc_mode 0): p = 0 at the four top corners only; c prescribed
+    on the square and on the bottom only."""
+    nx, ny, nz = dims
+    for mode in (0, 1):
+        P = O.Problem(nx, ny, nz, bc_mode=mode)
+        pm, cm, cv = O.dirichlet(P)
+        x, y, z, i, j, k = _node_xyz(P)
+        top, bottom = k == nz, k == 0
+        sq = top & (4 * i >= nx) & (4 * i <= 3 * nx) & (4 * j >= ny) & (4 * j <= 3 * ny)
+        assert sq.sum() == (nx // 2 + 1) * (ny // 2 + 1)
+        edge = top & ((i == 0) | (i == nx) | (j == 0) | (j == ny))
+        corner = top & ((i == 0) | (i == nx)) & ((j == 0) | (j == ny))
+        if mode == 1:
+            assert pm.sum() == 2 * (nx + 1) + 2 * (ny + 1) - 4
+            assert np.array_equal(pm, edge)
+            assert np.array_equal(cm, top | bottom)
+        else:
+            assert pm.sum() == 4 and np.array_equal(pm, corner)
+            assert np.array_equal(cm, sq | bottom)
+        assert np.array_equal(cv == 1.0, sq)
+        assert np.all(cv[~sq] == 0.0)
+
+
+def test_mirror_symmetry_paper_boundary_variant():
+    """bc_mode 1 is invariant under x -> Lx - x, y -> Ly - y and x <-> y as
+    well, so the solution is too (uniform phi, K)."""
+    P = O.Problem(8, 8, 4, bc_mode=1)
+    phi, K = _uniform(P)
+    p, c = O.initial_state(P)
+    for _ in range(3):
+        p, c, info = O.newton_step(P, phi, K, p, c, YEAR / 12)
+        assert info["status"] == 0
+    for f in (p, c):
+        a = f.reshape(P.nz + 1, P.ny + 1, P.nx + 1)
+        tol = 1e-12 * max(1.0, np.abs(a).max())
+        assert np.max(np.abs(a - a[:, :, ::-1])) <= tol
+        assert np.max(np.abs(a - a[:, ::-1, :])) <= tol
+        assert np.max(np.abs(a - a.transpose(0, 2, 1))) <= tol
+    # Dirichlet rows (R = u - u_D) hold c at its prescribed values: 1 on the
+    # square, 0 on the rest of the top and on the bottom
+    pm, cm, cv = O.dirichlet(P)
+    assert np.abs(c[cm] - cv[cm]).max() <= 1e-15
+    assert np.abs(p[pm]).max() <= 1e-9
