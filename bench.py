@@ -12,6 +12,12 @@ the quadratic extrapolation of the last states; --predictor 0 uses
 elder_step) plus the ensemble moments of that step (elder_moments).
 Metric: sample-timesteps/s, higher is better.
 
+Timed window: the K timed steps are steps 1..K of the run from the initial
+state (t = 0); the W warm-up steps (autotuning, CUDA-graph capture) run on a
+discarded copy of the initial state first.  Beside it the line carries the
+whole 60-step run of the configuration from t = 0 (`full_run`) and the FP64
+solver over the same steps 1..K with the same Newton start (`fp64_path`).
+
 Under torchrun each rank takes its own 256 samples (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
 
@@ -43,7 +49,7 @@ FP64_NOMINAL_GFLOPS = 1250.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
@@ -72,6 +78,9 @@ def parse():
                          "a captured CUDA graph")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps of the profiled pass (per-kernel-class CUDA events)")
+    ap.add_argument("--run-steps", type=int, default=60,
+                    help="steps of the configuration's whole run from t = 0, timed beside the "
+                         "K bench steps (0: skip)")
     a = ap.parse_args()
     if a.no_extrapolate:
         a.predictor = 0
@@ -99,6 +108,10 @@ def workload_config(a):
         "fields": fields,
         "l2": "no flush: per-step working set (Jacobians of all levels, vectors) ~10 GB >> 129 MB L2",
         "parallelism": f"samples sharded, dp{a.gpus}",
+        "timed_steps": f"1-{a.steps} of the run from t = 0 (warm-up on a discarded copy)",
+        "precision_detail": ("FP64 Newton residual, inner products and state; FP32 Krylov vectors "
+                             "and level-0 Krylov operator; bfloat16 multigrid matrices"
+                             if a.precision == "mixed" else "FP64 throughout"),
     }
 
 
@@ -300,54 +313,68 @@ def run_ours(a):
     # history levels (u^{n-1}[, u^{n-2}]) of the extrapolated Newton start,
     # u^n in every level on the first step
     order = a.predictor
-    p_hist = p.repeat(max(order, 1))
-    c_hist = c.repeat(max(order, 1))
+    p_init, c_init = p, c
 
-    def bench_step(p_, c_):
+    def fresh():
+        """The initial state (t = 0) and its history levels, as new tensors."""
+        return (p_init.clone(), c_init.clone(), p_init.repeat(max(order, 1)),
+                c_init.repeat(max(order, 1)))
+
+    def bench_step(ctx_, state):
+        p_, c_, ph_, ch_ = state
         if order == 0:
-            st, info = ctx.step(S, phi, K, p_, c_, dt)
+            st, info = ctx_.step(S, phi, K, p_, c_, dt)
         else:
-            st, info = ctx.step_predicted(S, phi, K, order, p_hist, c_hist, p_, c_, dt)
-        mom = ctx.moments(S, c_)
+            st, info = ctx_.step_predicted(S, phi, K, order, ph_, ch_, p_, c_, dt)
+        mom = ctx_.moments(S, c_)
         return st, info, mom
 
-    stats_log = []
+    def timed_run(ctx_, steps, log=None):
+        """steps bench steps from t = 0 between CUDA events on the launching
+        stream; returns (ms, final state)."""
+        state = fresh()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            st, info, _ = bench_step(ctx_, state)
+            if log is not None:
+                log.append((st, info))
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return t0.elapsed_time(t1), state
+
+    # warm-up (autotuning, CUDA-graph capture) on a discarded copy of t = 0
+    warm = fresh()
     for _ in range(a.warmup):
-        st, info, _ = bench_step(p, c)
-        stats_log.append(info)
+        bench_step(ctx, warm)
+    del warm
     torch.cuda.synchronize()
 
-    # ---- device-timed region ------------------------------------------------
+    # ---- device-timed region: steps 1..K from t = 0 -------------------------
     # (no per-launch events here: they force a host synchronisation per Krylov
     # iteration and bypass the captured CUDA graphs; the per-kernel-class
     # events are taken in a separate profiled pass right after)
     clocks = Clocks(local)
     clocks.start()
     l0 = E.elder_launch_count()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    log = []
     # the ncu launch list is taken with --profile-from-start off: only the
     # timed steps are captured
     torch.cuda.profiler.start()
-    e0.record(stream)
-    fails = 0
-    retries = 0
-    newton, krylov = [], []
-    for _ in range(a.steps):
-        st, info, _ = bench_step(p, c)
-        fails += int((st != 0).sum())
-        retries += sum(1 for x in info if x["fp64_retry"])
-        newton.append(np.mean([x["newton_iters"] for x in info]))
-        krylov.append(np.mean([x["krylov_iters"] for x in info]))
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, state = timed_run(ctx, a.steps, log)
     torch.cuda.profiler.stop()
-    barrier()
-    ms = e0.elapsed_time(e1)
     launches = E.elder_launch_count() - l0
     clk = clocks.stop()
+    fails = sum(int((st != 0).sum()) for st, _ in log)
+    retries = sum(1 for _, info in log for x in info if x["fp64_retry"])
+    newton = [np.mean([x["newton_iters"] for x in info]) for _, info in log]
+    krylov = [np.mean([x["krylov_iters"] for x in info]) for _, info in log]
+    p, c, p_hist, c_hist = state
+    c_mixed_K = c.clone()
 
     # ---- profiled pass: CUDA events around every launch of the stencil,
     # residual and assembly kernel classes, on the launching stream ----------
@@ -356,8 +383,8 @@ def run_ours(a):
     q0 = torch.cuda.Event(enable_timing=True)
     q1 = torch.cuda.Event(enable_timing=True)
     q0.record(stream)
-    for _ in range(a.profile_steps):
-        bench_step(p, c)
+    for _ in range(a.profile_steps):  # continues the run: steps K+1, ...
+        bench_step(ctx, state)
     q1.record(stream)
     torch.cuda.synchronize()
     prof_step_ms = q0.elapsed_time(q1) / max(a.profile_steps, 1)
@@ -404,7 +431,22 @@ def run_ours(a):
                    "GFLOP/s": round((v["flops"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None}
                for k, v in prof.items()}
 
-    # ---- end to end through host buffers -------------------------------------
+    # ---- the configuration's whole run from t = 0 -----------------------------
+    full_run = None
+    if a.run_steps > 0:
+        if a.run_steps == a.steps:
+            ms_run = ms
+        else:
+            ms_run, _ = timed_run(ctx, a.run_steps)
+            if world > 1:
+                t = torch.tensor([ms_run], dtype=torch.float64, device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ms_run = float(t.item())
+        full_run = {"value": S * world * a.run_steps / (ms_run / 1000.0), "unit": UNIT,
+                    "steps": f"1-{a.run_steps} from t = 0", "ms": ms_run,
+                    "timing": "CUDA events on the launching stream, as value"}
+
+    # ---- end to end through host buffers: steps 1..K from t = 0 ---------------
     e2e = None
     if not a.no_e2e:
         hp = torch.empty(S * N, dtype=torch.float64, pin_memory=True)
@@ -415,18 +457,17 @@ def run_ours(a):
         hphi = torch.empty(S * C, dtype=torch.float64, pin_memory=True)
         hK = torch.empty(S * C, dtype=torch.float64, pin_memory=True)
         hmom = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
-        hp.copy_(p)
-        hc.copy_(c)
+        hp.copy_(p_init)
+        hc.copy_(c_init)
+        for q in range(order):
+            hph[q].copy_(p_init)
+            hch[q].copy_(c_init)
         hphi.copy_(phi)
         hK.copy_(K)
         dp_, dc_ = torch.empty_like(p), torch.empty_like(c)
         dph = torch.empty(max(order, 1) * S * N, dtype=torch.float64, device=dev)
         dch = torch.empty_like(dph)
         dphi, dK = torch.empty_like(phi), torch.empty_like(K)
-        bench_step(p, c)  # keep the state moving as in the timed run
-        for q in range(order):
-            hph[q].copy_(p_hist[q * S * N:(q + 1) * S * N])
-            hch[q].copy_(c_hist[q * S * N:(q + 1) * S * N])
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -460,31 +501,34 @@ def run_ours(a):
             el = float(t.item())
         e2e = {"value": S * world * a.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": 8 * S * ((2 + 2 * order) * N + 2 * C),
-               "d2h_bytes_per_step": 8 * (S * 2 * N + 3 * N)}
+               "d2h_bytes_per_step": 8 * (S * 2 * N + 3 * N),
+               "steps": f"1-{a.steps} from t = 0", "timing": "host wall clock (perf_counter)"}
 
-    # ---- FP64 path on the same workload and state ---------------------------
+    # ---- FP64 solver over the same steps 1..K, same Newton start -------------
     fp64 = None
     if not a.no_fp64 and a.precision == "mixed":
         ctx64 = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S,
                                                       precision=E.ELDER_FP64, smoother=smoother))
-        p64, c64 = p.clone(), c.clone()
-        pm, cm = p.clone(), c.clone()
-        ctx64.step(S, phi, K, p64, c64, dt)  # warm-up (graph capture) from the same state
-        ctx.step(S, phi, K, pm, cm, dt)
-        diff = float((c64 - cm).abs().max().item())
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        k64 = max(1, min(a.steps, 2))
-        f0.record(stream)
-        for _ in range(k64):
-            ctx64.step(S, phi, K, p64, c64, dt)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        fp64 = {"value": S * world * k64 / (ms64 / 1000.0), "unit": UNIT, "steps": k64,
-                "ms_per_step": ms64 / k64,
-                "mixed_vs_fp64_max_abs_c_same_state": diff}
+        warm = fresh()
+        bench_step(ctx64, warm)  # warm-up (autotuning, graph capture) on a discarded copy
+        del warm
+        log64 = []
+        ms64, state64 = timed_run(ctx64, a.steps, log64)
+        if world > 1:
+            t = torch.tensor([ms64], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms64 = float(t.item())
+        diff = float((state64[1] - c_mixed_K).abs().max().item())
+        fp64 = {"value": S * world * a.steps / (ms64 / 1000.0), "unit": UNIT,
+                "steps": f"1-{a.steps} from t = 0", "ms_per_step": ms64 / a.steps,
+                "newton_start": workload_config(a)["newton_start"],
+                "newton_per_step": float(np.mean([np.mean([x["newton_iters"] for x in info])
+                                                  for _, info in log64])),
+                "krylov_per_step": float(np.mean([np.mean([x["krylov_iters"] for x in info])
+                                                  for _, info in log64])),
+                "mixed_vs_fp64_max_abs_c_after_K_steps": diff,
+                "mixed_speedup": (S * world * a.steps / (ms / 1000.0)) /
+                                 (S * world * a.steps / (ms64 / 1000.0))}
         ctx64.destroy()
 
     gpc = None
@@ -499,10 +543,10 @@ def run_ours(a):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64+f32" if a.precision == "mixed" else "f64",
+                "dtype": "f64+f32+bf16" if a.precision == "mixed" else "f64",
                 "data": "synthetic", "config": workload_config(a), "clocks": clk,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-                "fp64_path": fp64, "gpc": gpc, "kernel_classes": classes,
+                "full_run": full_run, "fp64_path": fp64, "gpc": gpc, "kernel_classes": classes,
                 "iterations": {"newton_per_step": float(np.mean(newton)),
                                "krylov_per_step": float(np.mean(krylov)), "failed_samples": fails,
                                "fp64_retries": retries},

@@ -1,0 +1,85 @@
+"""Writes tests/golden/longrun_moments_<nx>x<ny>x<nz>.npz: the oracle's sample
+mean, variance and exceedance probability P(c > 0.5) per node (Section 3,
+eqs. pdestat and numer_var with w_i = 1/S, and the exceedance estimate) after
+60 implicit Euler steps of dt = 1/12 yr from the initial state, over the
+first S scrambled-Sobol samples of the qMC ensemble (porosity
+phi = 0.1 (1 + 0.3 (xi1 cos(pi x/600) + xi2 cos(pi y/600) + xi3 sin(2 pi
+z/150))/3), normalised Kozeny-Carman K, benchmark boundary sets).
+
+Cases: 32 samples at 32x32x8 and 16 samples at 64x64x16 (the first 16
+points of the 256-point ensemble).  Calls only the oracle (and the seeded
+Sobol draws); one sample per spawned worker process.  Command (from the
+repository root; about 2 h of CPU on 6 cores):
+
+    python tests/golden/make_longrun_moments.py [--workers 6] [--case 32|64]
+
+Stored: xi [S][3]; mean, var, pexc [N]; amb [N] uint8, the number of samples
+whose c lies within AMB_BAND of the threshold (there the decision c > 0.5 is
+not fixed by the oracle's accuracy and may flip); c_idx and c_smp [S][len]:
+c of every sample at a few sampled nodes (diagnostics of per-sample drift).
+"""
+import argparse
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+STEPS = 60
+THRESH = 0.5
+AMB_BAND = 1e-6
+N_SAMPLED = 512
+CASES = {"32": (32, 32, 8, 32), "64": (64, 64, 16, 16)}
+
+
+def _run(args):
+    nx, ny, nz, xi = args
+    import oracle as O
+    P = O.Problem(nx, ny, nz)
+    phi, K = O.fields_sobol(P, xi)
+    p, c = O.initial_state(P)
+    dt = O.SECONDS_PER_YEAR / 12
+    t = time.time()
+    for n in range(STEPS):
+        p, c, info = O.newton_step(P, phi, K, p, c, dt)
+        if info["status"] != 0:
+            raise RuntimeError(f"oracle step {n + 1} failed: {info}")
+    return c, time.time() - t
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workers", type=int, default=6)
+    ap.add_argument("--case", choices=sorted(CASES), nargs="*", default=sorted(CASES))
+    a = ap.parse_args()
+    import oracle as O
+    from paper_1906_01632_gb300 import inputs as I
+    O.build()
+    for case in a.case:
+        nx, ny, nz, S = CASES[case]
+        xi = I.sobol_xi(256, seed=0)[:S]
+        t0 = time.time()
+        with mp.get_context("spawn").Pool(a.workers) as pool:
+            res = pool.map(_run, [(nx, ny, nz, xi[s]) for s in range(S)], chunksize=1)
+        cs = np.stack([r[0] for r in res])
+        mean, var, pexc = O.moments(cs, threshold=THRESH)
+        amb = (np.abs(cs - THRESH) <= AMB_BAND).sum(0).astype(np.uint8)
+        rng = np.random.default_rng(7)
+        c_idx = np.sort(rng.choice(cs.shape[1], N_SAMPLED, replace=False)).astype(np.int32)
+        out = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                           f"longrun_moments_{nx}x{ny}x{nz}.npz")
+        np.savez_compressed(out, xi=xi, mean=mean, var=var, pexc=pexc, amb=amb,
+                            c_idx=c_idx, c_smp=cs[:, c_idx], steps=np.array(STEPS),
+                            threshold=np.array(THRESH), amb_band=np.array(AMB_BAND))
+        print(f"{case}: {S} samples x {STEPS} steps in {time.time() - t0:.0f} s "
+              f"(per sample {[round(r[1]) for r in res]}); wrote {out} "
+              f"({os.path.getsize(out)} bytes); max var {var.max():.4f}, "
+              f"nodes with an ambiguous sample {(amb > 0).sum()}", flush=True)
+
+
+if __name__ == "__main__":
+    main()

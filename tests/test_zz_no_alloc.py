@@ -42,10 +42,13 @@ def _inputs(nx, ny, nz, S, seed):
     return [T(a) for a in (phi, K, p, c, po, co)]
 
 
-def test_static_scratch_residual_matches_context_residual(E):
+@pytest.mark.parametrize("bc_mode", [0, 1, 2, 3])
+def test_static_scratch_residual_matches_context_residual(E, bc_mode):
+    """Every boundary set: the entry point evaluates the Dirichlet sets from
+    the node indices itself, the context from its stored masks."""
     dt = 365.25 * 86400.0 / 12
-    for (nx, ny, nz, S, seed) in ((16, 16, 4, 3, 1), (32, 32, 8, 2, 2)):
-        cfg = E.elder_config_default(nx, ny, nz, max_samples=S)
+    for (nx, ny, nz, S, seed) in ((16, 16, 4, 3, 1 + bc_mode), (32, 32, 8, 2, 2 + bc_mode)):
+        cfg = E.elder_config_default(nx, ny, nz, max_samples=S, bc_mode=bc_mode)
         ctx = E.elder_create(cfg)
         phi, K, p, c, po, co = _inputs(nx, ny, nz, S, seed)
         R_ref = ctx.residual(S, phi, K, p, c, po, co, dt)
@@ -71,3 +74,18 @@ def test_static_scratch_rejects_oversized_batch(E):
                                       norms=torch.empty(1, dtype=torch.float64, device="cuda:0"))
     assert ei.value.code == E.ELDER_EINVAL
     assert "capacity" in str(ei.value)
+
+
+def test_static_scratch_rejects_more_samples_than_the_launch_grid_holds(E):
+    """On a grid of at most 256 nodes one partial sum per sample fits the
+    scratch for up to 262,144 samples, but a call takes at most 65,535 (the
+    samples run along the launch grid's y dimension): refused before any
+    launch."""
+    cfg = E.elder_config_default(4, 4, 2, max_samples=1)
+    phi, K, p, c, po, co = _inputs(4, 4, 2, 1, 0)  # never read: the call is refused first
+    with pytest.raises(E.ElderError) as ei:
+        E.elder_residual_norms_static(cfg, 65536, phi, K, p, c, po, co, 1.0,
+                                      R=torch.empty(1, dtype=torch.float64, device="cuda:0"),
+                                      norms=torch.empty(1, dtype=torch.float64, device="cuda:0"))
+    assert ei.value.code == E.ELDER_EINVAL
+    assert "65535" in str(ei.value)
