@@ -78,6 +78,10 @@ def parse():
                          "a captured CUDA graph")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps of the profiled pass (per-kernel-class CUDA events)")
+    ap.add_argument("--workload", choices=["qmc", "uneven"], default="qmc",
+                    help="qmc: the batched 64x64x16 ensemble (the headline); uneven: 48 samples "
+                         "at 128x128x32 plus 16 at 256x256x64, dt = 1/24 yr, one context per grid "
+                         "size, samples shared out longest-processing-time first across ranks")
     ap.add_argument("--run-steps", type=int, default=60,
                     help="steps of the configuration's whole run from t = 0, timed beside the "
                          "K bench steps (0: skip)")
@@ -626,10 +630,154 @@ def E_model_bytes(cls, tsize, nx, ny, nz, line=True):
             "jacobian": 108 * tsize + 108 * mz + 4 * tsize + 17 + 16 * cpn}[cls]
 
 
+# --------------------------------------------------------------------------
+# the uneven ensemble: two grid sizes in one run
+# --------------------------------------------------------------------------
+
+UNEVEN = ((128, 128, 32, 48), (256, 256, 64, 16))
+
+
+def uneven_plan(world: int, rank: int, sizes=UNEVEN):
+    """The samples of the uneven ensemble that ``rank`` owns, per grid size:
+    {(nx, ny, nz): [global sample indices]}.  Samples are numbered in the
+    order of ``sizes`` and shared out longest-processing-time first with a
+    cost proportional to the sample's node count."""
+    from paper_1906_01632_gb300.ensemble import lpt_assign
+    grids = [(nx, ny, nz) for nx, ny, nz, count in sizes for _ in range(count)]
+    costs = [(nx + 1) * (ny + 1) * (nz + 1) for nx, ny, nz in grids]
+    mine = lpt_assign(costs, world)[rank]
+    plan: dict = {}
+    for i in mine:
+        plan.setdefault(grids[i], []).append(i)
+    return plan
+
+
+def run_uneven(a):
+    """Sample-timesteps/s of the uneven ensemble: 64 scrambled-Sobol samples
+    (seed 0), the first 48 at 128x128x32 and the last 16 at 256x256x64,
+    dt = 1/24 yr, mixed precision, Newton from the quadratic extrapolation.
+    One context per grid size; each bench step advances every grid's batch
+    by one implicit step (converged samples masked out within a batch).
+    Steps 1..K from t = 0 are timed, after W warm-up steps on discarded
+    copies of the initial state."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1906_01632_gb300 import build as B
+    B.build()
+    from paper_1906_01632_gb300 import elder as E
+    from paper_1906_01632_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    total = sum(cnt for *_, cnt in UNEVEN)
+    xi_all = I.sobol_xi(total, seed=0)
+    dt = YEAR / 24.0
+    order = a.predictor
+    stream = torch.cuda.current_stream()
+    runs = []
+    for (nx, ny, nz), ids in sorted(uneven_plan(world, rank).items()):
+        S = len(ids)
+        ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S,
+                                                    precision=E.ELDER_MIXED))
+        xi = torch.tensor(xi_all[ids].ravel(), dtype=torch.float64, device=dev)
+        phi, K = ctx.fields(S, 0, xi)
+        p0, c0 = ctx.initial_state(S, device=dev)
+        runs.append({"grid": (nx, ny, nz), "S": S, "ctx": ctx, "phi": phi, "K": K,
+                     "p0": p0, "c0": c0, "newton": [], "krylov": [], "fails": 0,
+                     "retries": 0})
+
+    def fresh(r):
+        return (r["p0"].clone(), r["c0"].clone(), r["p0"].repeat(max(order, 1)),
+                r["c0"].repeat(max(order, 1)))
+
+    def step(r, state, log):
+        p_, c_, ph_, ch_ = state
+        if order == 0:
+            st, info = r["ctx"].step(r["S"], r["phi"], r["K"], p_, c_, dt)
+        else:
+            st, info = r["ctx"].step_predicted(r["S"], r["phi"], r["K"], order, ph_, ch_, p_,
+                                               c_, dt)
+        if log:
+            r["fails"] += int((st != 0).sum())
+            r["retries"] += sum(1 for x in info if x["fp64_retry"])
+            r["newton"].append(float(np.mean([x["newton_iters"] for x in info])))
+            r["krylov"].append(float(np.mean([x["krylov_iters"] for x in info])))
+
+    for r in runs:  # warm-up: autotuning and graph capture on discarded copies
+        warm = fresh(r)
+        for _ in range(a.warmup):
+            step(r, warm, False)
+    torch.cuda.synchronize()
+    states = [fresh(r) for r in runs]
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = E.elder_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        for r, stt in zip(runs, states):
+            step(r, stt, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = E.elder_launch_count() - l0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = total * a.steps / (ms / 1000.0)
+    per_grid = {f"{r['grid'][0]}x{r['grid'][1]}x{r['grid'][2]}": {
+        "samples": r["S"], "nodes_per_sample": (r["grid"][0] + 1) * (r["grid"][1] + 1) *
+        (r["grid"][2] + 1), "newton_per_step": float(np.mean(r["newton"])),
+        "krylov_per_step": float(np.mean(r["krylov"])), "failed_samples": r["fails"],
+        "fp64_retries": r["retries"], "autotune": r["ctx"].autotune_result()}
+        for r in runs}
+    if rank == 0:
+        line = {"metric": "sample-timesteps/s, uneven ensemble 48 @ 128x128x32 + 16 @ 256x256x64",
+                "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64+f32+bf16",
+                "data": "synthetic",
+                "config": {"workload": "elder3d-box-uneven-48x128x128x32+16x256x256x64-qmc64",
+                           "dt_yr": 1.0 / 24.0, "precision": "mixed",
+                           "newton_start": ["u^n", "2u^n - u^(n-1)",
+                                            "3u^n - 3u^(n-1) + u^(n-2)"][order],
+                           "fields": "scrambled Sobol (torch SobolEngine seed 0), first 48 "
+                                     "points at 128x128x32, last 16 at 256x256x64",
+                           "timed_steps": f"1-{a.steps} of the run from t = 0",
+                           "schedule": "one context per grid size, batches stepped in turn "
+                                       "on one stream; ranks get samples by LPT on node count",
+                           "l2": "no flush: working set ~100 GB >> 129 MB L2",
+                           "parallelism": f"samples sharded (LPT), dp{world}"},
+                "clocks": clk, "gpu_launches": launches, "per_grid": per_grid,
+                "timing": "CUDA events on the launching stream around the K timed steps"}
+        print(json.dumps(line), flush=True)
+    for r in runs:
+        r["ctx"].destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "uneven":
+        run_uneven(a)
     else:
         run_ours(a)
 

@@ -204,7 +204,8 @@ int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
  * multigrid-preconditioned BiCGStab (FP64, or FP32 multigrid and Krylov
  * storage with FP64 inner products in ELDER_MIXED).  In ELDER_MIXED a
  * sample whose Newton iteration fails is solved again from u^n with the
- * FP64 solver (packed into batches of at most 32 samples).
+ * FP64 solver (packed into batches of at most 32 samples and at most 2^25
+ * node-samples).
  *  phi, K: [S][C] inputs.  p, c: [S][N] in: u^n, out: u^{n+1}.
  *  dt: time step [s].  status, stats: HOST arrays of S entries (stats may
  *  be NULL), written after the stream is synchronised.  A failed sample

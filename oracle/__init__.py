@@ -64,7 +64,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("tol_c", ctypes.c_double),
                 ("tol_p", ctypes.c_double), ("lin_rtol", ctypes.c_double),
                 ("lin_maxit", ctypes.c_int), ("ls_max", ctypes.c_int),
-                ("dense_max", ctypes.c_int)]
+                ("dense_max", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -112,10 +112,11 @@ class NewtonOpts:
     lin_maxit: int = 2000
     ls_max: int = 6
     dense_max: int = 1200
+    smoother: int = 0  # 0 point block Jacobi, 1 vertical-line block Jacobi
 
     def _c(self) -> _Opts:
         return _Opts(self.maxit, self.tol_c, self.tol_p, self.lin_rtol,
-                     self.lin_maxit, self.ls_max, self.dense_max)
+                     self.lin_maxit, self.ls_max, self.dense_max, self.smoother)
 
 
 def lib():

@@ -738,6 +738,10 @@ typedef struct {
     int* piv;
     int nu1, nu2;
     double omega;
+    int line;                     /* vertical-line smoother (else point)      */
+    double* Lb[ORC_MAXLEV];       /* [N][4] line blocks A(n, n-below)         */
+    double* Db[ORC_MAXLEV];       /* [N][4] diagonal blocks A(n, n)           */
+    double* Ub[ORC_MAXLEV];       /* [N][4] line blocks A(n, n-above)         */
 } orc_mg;
 
 static int mg_can_coarsen(const orc_problem* P)
@@ -754,6 +758,7 @@ static void mg_free(orc_mg* mg)
     for (int l = 0; l < mg->nlev; ++l) {
         free(mg->rp[l]); free(mg->ci[l]); free(mg->A[l]); free(mg->Dinv[l]);
         free(mg->dm[l]); free(mg->b[l]); free(mg->x[l]); free(mg->r[l]);
+        free(mg->Lb[l]); free(mg->Db[l]); free(mg->Ub[l]);
     }
     free(mg->LU);
     free(mg->piv);
@@ -767,17 +772,31 @@ static double csr_get(const int* rp, const int* ci, const double* A, int r,
     return 0.0;
 }
 
+/* the 2x2 block of rows (2r, 2r+1) and columns (2q, 2q+1), row-major */
+static void csr_block(const int* rp, const int* ci, const double* A, int r, int q,
+                      double* B)
+{
+    B[0] = csr_get(rp, ci, A, 2 * r, 2 * q);
+    B[1] = csr_get(rp, ci, A, 2 * r, 2 * q + 1);
+    B[2] = csr_get(rp, ci, A, 2 * r + 1, 2 * q);
+    B[3] = csr_get(rp, ci, A, 2 * r + 1, 2 * q + 1);
+}
+
 static int mg_setup(orc_mg* mg, const orc_problem* P0, const double* phi0,
                     const double* K0, const double* p0, const double* c0,
-                    double dt, int transpose)
+                    double dt, int transpose, int line)
 {
     memset(mg, 0, sizeof(*mg));
-    /* damping 0.5: at dt = 1/12 yr the pressure/salt coupling next to the
-     * salt source makes block Jacobi with damping 0.7 diverge on some
-     * permeability fields */
+    /* point smoother, damping 0.5: at dt = 1/12 yr the pressure/salt
+     * coupling next to the salt source makes block Jacobi with damping 0.7
+     * diverge on some permeability fields.  Line smoother, damping 0.7: the
+     * vertical coupling (gravity, the salt front) is solved exactly per
+     * line, which keeps the V-cycle's contraction nearly independent of the
+     * grid size where point Jacobi slows down. */
     mg->nu1 = 1;
     mg->nu2 = 1;
-    mg->omega = 0.5;
+    mg->line = line;
+    mg->omega = line ? 0.7 : 0.5;
     orc_problem P = *P0;
     double *phi = (double*)phi0, *K = (double*)K0, *p = (double*)p0,
            *c = (double*)c0;
@@ -827,6 +846,19 @@ static int mg_setup(orc_mg* mg, const orc_problem* P0, const double* phi0,
             Dinv[4 * n + 1] = -b / det;
             Dinv[4 * n + 2] = -cc / det;
             Dinv[4 * n + 3] = a / det;
+        }
+        if (line) {
+            double* Lb = calloc(4 * (size_t)N, sizeof(double));
+            double* Db = calloc(4 * (size_t)N, sizeof(double));
+            double* Ub = calloc(4 * (size_t)N, sizeof(double));
+            int sz = (P.nx + 1) * (P.ny + 1);
+            for (int n = 0; n < N; ++n) {
+                int k = n / sz;
+                csr_block(rp, ci, A, n, n, Db + 4 * n);
+                if (k > 0) csr_block(rp, ci, A, n, n - sz, Lb + 4 * n);
+                if (k < P.nz) csr_block(rp, ci, A, n, n + sz, Ub + 4 * n);
+            }
+            mg->Lb[l] = Lb; mg->Db[l] = Db; mg->Ub[l] = Ub;
         }
         mg->rp[l] = rp; mg->ci[l] = ci; mg->A[l] = A; mg->Dinv[l] = Dinv;
         mg->dm[l] = dm;
@@ -922,11 +954,80 @@ static void mg_zero_dirichlet(const orc_mg* mg, int l, double* v)
         if (mg->dm[l][i]) v[i] = 0.0;
 }
 
+static void inv2x2(const double* M, double* Mi)
+{
+    double det = M[0] * M[3] - M[1] * M[2];
+    Mi[0] = M[3] / det;
+    Mi[1] = -M[1] / det;
+    Mi[2] = -M[2] / det;
+    Mi[3] = M[0] / det;
+}
+
+/* one damped line sweep: x += omega T^{-1} (b - A x), T the block-tridiagonal
+ * part of A along each vertical grid line (i, j fixed), solved by block
+ * Gaussian elimination (Thomas algorithm with 2x2 blocks) */
+static void mg_smooth_line(const orc_mg* mg, int l, const double* b, double* x,
+                           double* tmp)
+{
+    const orc_problem* P = &mg->P[l];
+    int n = mg->n[l], nz = P->nz, sz = (P->nx + 1) * (P->ny + 1);
+    csr_matvec(n, mg->rp[l], mg->ci[l], mg->A[l], x, tmp);
+    double* C = malloc(sizeof(double) * 4 * (size_t)(nz + 1));
+    double* g = malloc(sizeof(double) * 2 * (size_t)(nz + 1));
+    for (int col = 0; col < sz; ++col) {
+        for (int k = 0; k <= nz; ++k) {        /* forward elimination */
+            int node = col + k * sz;
+            double M[4], r[2], Mi[4];
+            const double* D = mg->Db[l] + 4 * node;
+            M[0] = D[0]; M[1] = D[1]; M[2] = D[2]; M[3] = D[3];
+            r[0] = b[2 * node] - tmp[2 * node];
+            r[1] = b[2 * node + 1] - tmp[2 * node + 1];
+            if (k > 0) {                       /* M -= L C_{k-1}, r -= L g_{k-1} */
+                const double* L = mg->Lb[l] + 4 * node;
+                const double* Cp = C + 4 * (k - 1);
+                const double* gp = g + 2 * (k - 1);
+                M[0] -= L[0] * Cp[0] + L[1] * Cp[2];
+                M[1] -= L[0] * Cp[1] + L[1] * Cp[3];
+                M[2] -= L[2] * Cp[0] + L[3] * Cp[2];
+                M[3] -= L[2] * Cp[1] + L[3] * Cp[3];
+                r[0] -= L[0] * gp[0] + L[1] * gp[1];
+                r[1] -= L[2] * gp[0] + L[3] * gp[1];
+            }
+            inv2x2(M, Mi);
+            if (k < nz) {                      /* C_k = M^{-1} U_k */
+                const double* U = mg->Ub[l] + 4 * node;
+                C[4 * k + 0] = Mi[0] * U[0] + Mi[1] * U[2];
+                C[4 * k + 1] = Mi[0] * U[1] + Mi[1] * U[3];
+                C[4 * k + 2] = Mi[2] * U[0] + Mi[3] * U[2];
+                C[4 * k + 3] = Mi[2] * U[1] + Mi[3] * U[3];
+            }
+            g[2 * k + 0] = Mi[0] * r[0] + Mi[1] * r[1];
+            g[2 * k + 1] = Mi[2] * r[0] + Mi[3] * r[1];
+        }
+        for (int k = nz - 1; k >= 0; --k) {    /* back substitution */
+            g[2 * k + 0] -= C[4 * k + 0] * g[2 * k + 2] + C[4 * k + 1] * g[2 * k + 3];
+            g[2 * k + 1] -= C[4 * k + 2] * g[2 * k + 2] + C[4 * k + 3] * g[2 * k + 3];
+        }
+        for (int k = 0; k <= nz; ++k) {
+            int node = col + k * sz;
+            x[2 * node] += mg->omega * g[2 * k];
+            x[2 * node + 1] += mg->omega * g[2 * k + 1];
+        }
+    }
+    free(C);
+    free(g);
+    mg_zero_dirichlet(mg, l, x);
+}
+
 /* one damped block-Jacobi sweep: x += omega D^{-1} (b - A x) */
 static void mg_smooth(const orc_mg* mg, int l, const double* b, double* x,
                       double* tmp)
 {
     int n = mg->n[l];
+    if (mg->line) {
+        mg_smooth_line(mg, l, b, x, tmp);
+        return;
+    }
     csr_matvec(n, mg->rp[l], mg->ci[l], mg->A[l], x, tmp);
     for (int node = 0; node < n / 2; ++node) {
         double rp = b[2 * node] - tmp[2 * node];
@@ -1017,7 +1118,7 @@ static int solve_at_state(const orc_problem* P, const double* phi,
     int n = 2 * orc_num_nodes(P);
     if (n <= o->dense_max) return orc_linear_solve(n, rowptr, col, val, b, x, o, iters);
     orc_mg mg;
-    int rc = mg_setup(&mg, P, phi, K, p, c, dt, transpose);
+    int rc = mg_setup(&mg, P, phi, K, p, c, dt, transpose, o->smoother == 1);
     if (rc == 0) {
         for (int i = 0; i < n; ++i) x[i] = 0.0;
         double rr;

@@ -49,6 +49,11 @@ typedef struct {
     int lin_maxit;      /* BiCGStab iteration cap                          */
     int ls_max;         /* maximum number of step halvings                 */
     int dense_max;      /* use dense LU when 2N <= dense_max               */
+    int smoother;       /* multigrid smoother of the iterative solve:
+                           0 damped 2x2-block Jacobi, 1 damped block Jacobi
+                           over vertical grid lines (block-tridiagonal
+                           solve per line); the converged step does not
+                           depend on it                                    */
 } orc_newton_opts;
 
 typedef struct {

@@ -897,7 +897,8 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
 }
 
 // Solves the step again from u^n, in FP64 with the settings `set`, for the
-// samples listed in `idx` (packed into batches of at most 32 samples).  Their
+// samples listed in `idx` (packed into batches of at most 32 samples and 2^25
+// node-samples).  Their
 // entries of st1 and sts are replaced; the iteration counts accumulate and
 // fp64_retry records `tier`.
 void resolve_fp64(elder_ctx* ctx, const std::vector<int>& idx, const double* phi,
@@ -907,7 +908,10 @@ void resolve_fp64(elder_ctx* ctx, const std::vector<int>& idx, const double* phi
 {
     const Grid& G = ctx->grids[0];
     const size_t N = G.N, C = G.C;
-    const int chunk = std::min(32, ctx->cfg.max_samples);
+    // at most 32 samples, and at most 2^25 node-samples per batch (the FP64
+    // solver's workspace is ~1.3 KB per node: ~44 GB at that bound)
+    const int chunk = std::max(
+        1, std::min({32, ctx->cfg.max_samples, (int)((size_t(1) << 25) / N)}));
     if (!ctx->pk) {
         ctx->pk = dalloc<double>((size_t)chunk * (2 * N + 2 * C));
         ctx->mem.add(ctx->pk);

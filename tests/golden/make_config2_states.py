@@ -4,7 +4,13 @@ the first 5 implicit Euler steps of the 128x128x32 box (the paper's
 with phi = 0.1 and K = 4.845e-13 (Table 1), dt = 1/12 yr, benchmark boundary
 sets, from the initial state.
 
-Calls only the oracle.  Command (from the repository root, ~1 h on one core):
+Calls only the oracle.  Its Newton iteration runs to the oracle's default
+tolerances; the linear solves use the oracle's vertical-line multigrid
+smoother to a relative residual of 1e-10 (the converged step does not depend
+on the solver: with the point smoother the first step at 64x64x16 agrees to
+3e-15, but at this size the point smoother needs hundreds of Krylov
+iterations per Newton step).  Command (from the repository root, about
+30 min on one core):
 
     python tests/golden/make_config2_states.py
 
@@ -43,7 +49,7 @@ def main():
            "grid": np.array([P.nx, P.ny, P.nz], np.int32)}
     for n in range(1, STEPS + 1):
         t = time.time()
-        p, c, info = O.newton_step(P, phi, K, p, c, dt)
+        p, c, info = O.newton_step(P, phi, K, p, c, dt, O.NewtonOpts(smoother=1, lin_rtol=1e-10))
         assert info["status"] == 0, info
         keep = np.nonzero(np.abs(c) > C_FLOOR)[0].astype(np.int32)
         out[f"c{n}_idx"] = keep

@@ -45,3 +45,21 @@ def test_traffic_lines_of_the_committed_profiles():
     assert bench.ncu_traffic("mg_residual", "mixed") == pytest.approx(229.8)
     assert bench.ncu_traffic("residual", "fp64") == pytest.approx(302.0)
     assert bench.ncu_traffic("no_such_class", "mixed") is None
+
+
+def test_uneven_plan_covers_the_ensemble_once():
+    """48 samples at 128x128x32 and 16 at 256x256x64: on one rank all of them,
+    grouped by grid; on 4 ranks every sample exactly once, each rank's node
+    count within 4/3 of the balanced share (the LPT bound)."""
+    plan = bench.uneven_plan(1, 0)
+    assert sorted(plan) == [(128, 128, 32), (256, 256, 64)]
+    assert plan[(128, 128, 32)] == list(range(48)) and plan[(256, 256, 64)] == list(range(48, 64))
+    nodes = {(128, 128, 32): 129 * 129 * 33, (256, 256, 64): 257 * 257 * 65}
+    seen, loads = [], []
+    for r in range(4):
+        pl = bench.uneven_plan(4, r)
+        loads.append(sum(nodes[g] * len(ids) for g, ids in pl.items()))
+        seen += [i for ids in pl.values() for i in ids]
+    assert sorted(seen) == list(range(64))
+    total = 48 * nodes[(128, 128, 32)] + 16 * nodes[(256, 256, 64)]
+    assert max(loads) <= 4 / 3 * total / 4

@@ -594,3 +594,33 @@ def test_mirror_symmetry_paper_boundary_variant():
     pm, cm, cv = O.dirichlet(P)
     assert np.abs(c[cm] - cv[cm]).max() <= 1e-15
     assert np.abs(p[pm]).max() <= 1e-9
+
+
+def test_line_smoother_reaches_the_same_step():
+    """The oracle's two multigrid smoothers only change the path of the
+    linear solves: the converged implicit step (and a transposed solve) agree
+    to round-off.  16x16x4 has 2890 unknowns, above the dense-LU limit."""
+    P = O.Problem(16, 16, 4)
+    rng = np.random.default_rng(17)
+    phi, K = O.fields_lognormal(P, rng.standard_normal(P.C))
+    p0, c0 = O.initial_state(P)
+    dt = YEAR / 12
+    out = []
+    for sm in (0, 1):
+        p, c, info = O.newton_step(P, phi, K, p0, c0, dt, O.NewtonOpts(smoother=sm))
+        assert info["status"] == 0
+        out.append((p, c, info["lin_iters"]))
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-13
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-9 * P.rho0 * P.g * P.Lz
+    # the adjoint's transposed multigrid solves (two steps)
+    g = []
+    for sm in (0, 1):
+        J, gphi, gK, rc = O.adjoint_gradient(P, phi, K, p0, c0, dt, 2, O.NewtonOpts(smoother=sm))
+        assert rc == 0
+        g.append((J, gphi, gK))
+    assert abs(g[0][0] - g[1][0]) <= 1e-13 * abs(g[0][0])
+    # the gradients go through the states' Jacobians, so they inherit the
+    # states' round-off differences amplified by the solves: 1e-6 of the
+    # largest entry (the FD pins hold the adjoint to 1e-5)
+    for q in (1, 2):
+        np.testing.assert_allclose(g[1][q], g[0][q], rtol=0, atol=1e-6 * np.abs(g[0][q]).max())
