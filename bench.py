@@ -245,6 +245,19 @@ def run_reference(a):
 # the CUDA path
 # --------------------------------------------------------------------------
 
+def alu_peaks(E):
+    """FMA peaks of this GPU measured by the library's FMA-chain probe
+    (elder_measure_peak), with the nominal figures as fallback."""
+    out = {}
+    for kind, nominal in (("fp64", FP64_NOMINAL_GFLOPS), ("fp32", FP32_NOMINAL_GFLOPS)):
+        try:
+            out[kind] = (E.elder_measure_peak(kind), f"measured {kind.upper()} FMA-chain probe "
+                         "(elder_measure_peak)")
+        except Exception as ex:  # noqa: BLE001
+            out[kind] = (nominal, f"nominal {kind.upper()} ({ex})")
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -409,12 +422,14 @@ def run_ours(a):
     per_launch_ms = pk["ms"] / max(pk["launches"], 1)
     bytes_per_launch = pk["bytes"] / max(pk["launches"], 1)
     tr = ncu_traffic(top, a.precision)
+    apk = alu_peaks(E)
+    alu = apk["fp64"]
     if top == "residual" or (top == "jacobian" and a.precision == "fp64"):
-        # FP64-ALU bound (FP64 pipe ~85% busy under ncu); GB300 FP64 is a
-        # nominal 1.25 TFLOP/s and no FP64 peak is measured on this machine
+        # FP64-ALU bound (FP64 pipe ~85% busy under ncu): rated against the
+        # FP64 FMA peak measured on this GPU
         achieved = (pk["flops"] / 1e9) / (pk["ms"] / 1e3) if pk["ms"] > 0 else None
-        bound, peak, unit, src = "alu", FP64_NOMINAL_GFLOPS, "GFLOP/s", \
-            "nominal FP64 1.25 TFLOP/s (profiling recipe); flops from the per-node model"
+        bound, peak, unit = "alu", alu[0], "GFLOP/s"
+        src = alu[1] + "; flops from the per-node model"
     else:
         achieved = (pk["bytes"] / 1e9) / (pk["ms"] / 1e3) if pk["ms"] > 0 else None
         bound, peak, unit = "hbm", hbm_peak, "GB/s"
@@ -434,6 +449,11 @@ def run_ours(a):
                    "GB/s": round((v["bytes"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None,
                    "GFLOP/s": round((v["flops"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None}
                for k, v in prof.items()}
+    for k, v in classes.items():  # fraction of the class's own bound
+        if k == "residual":
+            v["bound"], v["frac"] = "fp64 alu", (v["GFLOP/s"] / alu[0] if v["GFLOP/s"] else None)
+        else:
+            v["bound"], v["frac"] = "hbm", (v["GB/s"] / hbm_peak if v["GB/s"] else None)
 
     # ---- the configuration's whole run from t = 0 -----------------------------
     full_run = None
@@ -537,7 +557,7 @@ def run_ours(a):
 
     gpc = None
     if rank == 0 and not a.no_gpc and S >= 1:
-        gpc = gpc_timings(E, torch, c.reshape(S, N), stream, a.gpc_samples)
+        gpc = gpc_timings(E, torch, c.reshape(S, N), stream, a.gpc_samples, apk)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -569,7 +589,7 @@ def run_ours(a):
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x FMA x max SM clock (GHz)
 
 
-def gpc_timings(E, torch, cfield, stream, Ns=1_000_000):
+def gpc_timings(E, torch, cfield, stream, Ns=1_000_000, apk=None):
     """Kernel timings of the gPC surrogate (Section 3) on this GPU: FP64
     projection of 125 fields (the 5^3 Gauss-Legendre points, total degree
     <= 4, 35 terms) onto every node, and the FP32 surrogate evaluated
@@ -577,6 +597,7 @@ def gpc_timings(E, torch, cfield, stream, Ns=1_000_000):
     concentration fields stand in for the quadrature-point fields (the
     kernels' cost does not depend on the values)."""
     S, N = cfield.shape
+    apk = apk or alu_peaks(E)
     M, p, q = 3, 4, 5
     x, w1 = E.elder_gauss_legendre(q)
     import numpy as np
@@ -597,9 +618,9 @@ def gpc_timings(E, torch, cfield, stream, Ns=1_000_000):
     res = {}
     for name, fn, flops, unit_peak in (
             ("project", lambda: E.elder_gpc_project(beta, theta_q, wt, u, coef, mean, var),
-             2.0 * T * Nq * N, ("FP64 nominal", FP64_NOMINAL_GFLOPS)),
+             2.0 * T * Nq * N, (apk["fp64"][1], apk["fp64"][0])),
             ("exceed", lambda: E.elder_gpc_exceed(beta, coef, theta_s, 0.5, out=out),
-             2.0 * T * Ns * N, ("FP32 nominal", FP32_NOMINAL_GFLOPS))):
+             2.0 * T * Ns * N, (apk["fp32"][1], apk["fp32"][0]))):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         reps = 3

@@ -114,6 +114,11 @@ typedef struct {
                                  smoother (damping 0.5).                    */
     double omega_line;        /* damping of the z-line smoother (default
                                  0.95)                                      */
+    int mixed_newton_maxit;   /* Newton iteration cap of the ELDER_MIXED
+                                 solve only (0: newton_maxit).  A sample that
+                                 reaches it is solved again in FP64 with
+                                 newton_maxit; a cap of 1 forces that FP64
+                                 re-solve from the host (failure-tier test) */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */
@@ -327,6 +332,14 @@ int elder_launch_count(int64_t* launches);
  * may be NULL. */
 int elder_autotune_result(const elder_ctx* ctx, int* bs_smooth, int* bs_spmv,
                           int* bs_mgres, float* ms);
+
+/* Measured arithmetic peak of the current device: kind 0 FP64 fused
+ * multiply-adds, kind 1 FP32 fused multiply-adds.  A kernel of 8
+ * independent FMA chains per thread on 8 resident blocks of 256 threads per
+ * SM is timed with CUDA events on `stream` (best of 3 launches after a
+ * warm-up); *gflops receives 2 x FMAs / time in GFLOP/s (host output).
+ * Allocates and frees one small device buffer; synchronises the stream. */
+int elder_measure_peak(int kind, double* gflops, void* stream);
 
 /* ---- allocation-free entry point (no counterpart in the paper) -------- */
 

@@ -961,9 +961,12 @@ int step_tiers(elder_ctx* ctx, int S, const double* phi, const double* K, double
     const bool mixed = ctx->cfg.precision == ELDER_MIXED;
     // (re-solves of failed samples start again from u^n, which a failed
     // sample holds)
-    if (mixed)
-        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, order,
+    if (mixed) {
+        NewtonSettings mset = conf;
+        if (ctx->cfg.mixed_newton_maxit > 0) mset.newton_maxit = ctx->cfg.mixed_newton_maxit;
+        step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, mset, order,
                          p_hist, c_hist);
+    }
     else
         step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, order,
                           p_hist, c_hist);
@@ -1060,6 +1063,63 @@ int set_error(elder_ctx* ctx, const Fail& f)
 
 }  // namespace
 
+namespace {
+
+// FMA-chain probe of the arithmetic peak: 8 independent chains per thread
+// keep every FMA pipe busy; the sum is stored only if it equals a value it
+// never takes, so that the chains are not optimised away.
+template <class F>
+__global__ void __launch_bounds__(256) k_fma_peak(const F* __restrict__ in, F* __restrict__ out,
+                                                 int iters)
+{
+    const F b = in[1], c = in[2];
+    F a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = in[0] + F(threadIdx.x + q);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = fma(a[q], b, c);
+    }
+    F sum = F(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += a[q];
+    if (sum == in[3]) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+template <class F> double fma_peak_gflops(int iters, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;
+    DevFree mem;
+    F* buf = dalloc<F>(4 + (size_t)blocks * threads);
+    mem.add(buf);
+    const F h[4] = {F(1), F(0.999999), F(1e-7), F(-12345.0)};
+    CK(cudaMemcpyAsync(buf, h, sizeof h, cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {  // launch 0 warms up
+        CK(cudaEventRecord(e0, st));
+        k_fma_peak<F><<<blocks, threads, 0, st>>>(buf, buf + 4, iters);
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) best = std::min(best, ms);
+    }
+    count_launch(4);
+    CK(cudaEventDestroy(e0));
+    CK(cudaEventDestroy(e1));
+    CKL();
+    const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+    return flops / (best * 1e-3) / 1e9;
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1100,6 +1160,7 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->autotune = 1;
     cfg->newton_estimate = 1;
     cfg->smoother = ELDER_SMOOTH_ZLINE;
+    cfg->mixed_newton_maxit = 0;
     return ELDER_OK;
 }
 
@@ -1122,7 +1183,7 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
         c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0 ||
         (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE) ||
-        !(c.omega > 0) || !(c.omega_line > 0)) {
+        !(c.omega > 0) || !(c.omega_line > 0) || c.mixed_newton_maxit < 0) {
         g_create_error = "invalid elder_config";
         return ELDER_EINVAL;
     }
@@ -1449,6 +1510,22 @@ int elder_autotune_result(const elder_ctx* ctx, int* bs_smooth, int* bs_spmv, in
     if (ms)
         for (int c = 0; c < 3; ++c)
             for (int q = 0; q < 3; ++q) ms[3 * c + q] = ctx->tune_ms[c][q];
+    return ELDER_OK;
+}
+
+int elder_measure_peak(int kind, double* gflops, void* stream)
+{
+    if (!gflops || kind < 0 || kind > 1) {
+        g_create_error = "elder_measure_peak: bad argument";
+        return ELDER_EINVAL;
+    }
+    try {
+        *gflops = kind == 0 ? fma_peak_gflops<double>(4000, (cudaStream_t)stream)
+                            : fma_peak_gflops<float>(200000, (cudaStream_t)stream);
+    } catch (const Fail& f) {
+        g_create_error = f.msg;
+        return f.code;
+    }
     return ELDER_OK;
 }
 

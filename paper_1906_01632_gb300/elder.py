@@ -43,7 +43,8 @@ class elder_config(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("newton_estimate", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("omega_line", ctypes.c_double)]
+                ("smoother", ctypes.c_int), ("omega_line", ctypes.c_double),
+                ("mixed_newton_maxit", ctypes.c_int)]
 
 
 class elder_stats(ctypes.Structure):
@@ -94,6 +95,7 @@ def _load():
     lib.elder_profile.argtypes = [vp, ip]
     lib.elder_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
     lib.elder_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    lib.elder_measure_peak.argtypes = [ip, dp, vp]
     lib.elder_autotune_result.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int),
@@ -322,6 +324,15 @@ def elder_launch_count() -> int:
     n = ctypes.c_int64()
     _lib.elder_launch_count(ctypes.byref(n))
     return n.value
+
+
+def elder_measure_peak(kind: str = "fp64", stream=None) -> float:
+    """Measured FMA peak of the current device in GFLOP/s ("fp64" or "fp32")."""
+    g = ctypes.c_double(0.0)
+    rc = _lib.elder_measure_peak({"fp64": 0, "fp32": 1}[kind], ctypes.byref(g), _stream(stream))
+    if rc != ELDER_OK:
+        raise ElderError(rc, _lib.elder_last_error(None).decode())
+    return g.value
 
 
 def elder_residual_norms_static(cfg: elder_config, S, phi, K, p, c, p_old, c_old, dt,

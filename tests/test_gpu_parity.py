@@ -436,3 +436,41 @@ def test_predicted_step_rejects_bad_orders_and_short_history(E):
     # the binding rejects a history shorter than order * S * N
     with pytest.raises(ValueError):
         ctx.step_predicted(1, T(phi), T(K), 2, pt.clone(), ct.clone(), pt, ct, YEAR / 12)
+
+
+@pytest.mark.parametrize("knob,tier", [(dict(mixed_newton_maxit=1), 1),
+                                       (dict(newton_maxit=1), 2)])
+def test_failure_tiers_resolve_to_the_oracle_state(E, knob, tier):
+    """Failures forced from the host: a Newton cap of 1 on the mixed solve
+    alone fails every sample there, and the FP64 re-solve with the
+    configured settings succeeds (fp64_retry 1); a cap of 1 on every solve
+    fails the FP64 re-solve too, and the last robust FP64 solve succeeds
+    (fp64_retry 2).  Either way the returned state is the implicit step's
+    solution: the oracle's within 1e-10 in c."""
+    P = O.Problem(16, 16, 4)
+    S = 3
+    phi, K = _fields(P, S, 41)
+    p0, c0 = O.initial_state(P)
+    dt = YEAR / 12
+    ctx = _ctx(E, 16, 16, 4, S, precision=E.ELDER_MIXED, **knob)
+    pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+    st, info = ctx.step(S, T(phi), T(K), pt, ct, dt)
+    assert (st == 0).all(), info
+    assert [i["fp64_retry"] for i in info] == [tier] * S
+    pg, cg = H(pt).reshape(S, -1), H(ct).reshape(S, -1)
+    for s in range(S):
+        pr, cr, oi = O.newton_step(P, phi[s], K[s], p0, c0, dt)
+        assert oi["status"] == 0
+        assert np.abs(cg[s] - cr).max() <= 1e-10
+        assert np.abs(pg[s] - pr).max() <= 1e-9 * P.rho0 * P.g * P.Lz
+    ctx.destroy()
+
+
+def test_measured_fma_peaks(E):
+    """The FMA-chain probe that rates the FP64 residual and the FP32
+    surrogate evaluation: finite, positive, and FP32 well above FP64 (GB300
+    issues FP64 at a small fraction of the FP32 rate)."""
+    f64 = E.elder_measure_peak("fp64")
+    f32 = E.elder_measure_peak("fp32")
+    print(f"FP64 {f64:.0f} GFLOP/s, FP32 {f32:.0f} GFLOP/s")
+    assert 0 < f64 < f32 and np.isfinite(f32)
