@@ -73,21 +73,28 @@ def parse():
                     help="Newton's starting point: 0 u^n (elder_step), 1 2u^n - u^{n-1}, "
                          "2 3u^n - 3u^{n-1} + u^{n-2} (elder_step_predicted)")
     ap.add_argument("--no-extrapolate", action="store_true", help="the same as --predictor 0")
-    ap.add_argument("--no-graphs", action="store_true",
-                    help="launch the BiCGStab iteration kernels one by one instead of replaying "
-                         "a captured CUDA graph")
+    ap.add_argument("--graphs", type=int, choices=[0, 1, 2], default=2,
+                    help="0: every kernel launched from the host; 1: the BiCGStab iteration "
+                         "replayed as a CUDA graph, the host polling convergence flags; 2: the "
+                         "whole step one graph with device-driven Newton/Krylov/line-search "
+                         "loops (conditional while nodes)")
+    ap.add_argument("--no-graphs", action="store_true", help="the same as --graphs 0")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps of the profiled pass (per-kernel-class CUDA events)")
-    ap.add_argument("--workload", choices=["qmc", "uneven"], default="qmc",
+    ap.add_argument("--workload", choices=["qmc", "uneven", "config2"], default="qmc",
                     help="qmc: the batched 64x64x16 ensemble (the headline); uneven: 48 samples "
                          "at 128x128x32 plus 16 at 256x256x64, dt = 1/24 yr, one context per grid "
-                         "size, samples shared out longest-processing-time first across ranks")
+                         "size, samples shared out longest-processing-time first across ranks; "
+                         "config2: one sample at 128x128x32 for --run-steps steps with the FP64 "
+                         "and the mixed solver, their states compared along the run")
     ap.add_argument("--run-steps", type=int, default=60,
                     help="steps of the configuration's whole run from t = 0, timed beside the "
                          "K bench steps (0: skip)")
     a = ap.parse_args()
     if a.no_extrapolate:
         a.predictor = 0
+    if a.no_graphs:
+        a.graphs = 0
     return a
 
 
@@ -311,7 +318,7 @@ def run_ours(a):
     smoother = E.ELDER_SMOOTH_ZLINE if a.smoother == "zline" else E.ELDER_SMOOTH_JACOBI
     ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=prec,
                                                 smoother=smoother,
-                                                use_graphs=0 if a.no_graphs else 1))
+                                                use_graphs=a.graphs))
     N, C = ctx.N, ctx.C
     xi_all = I.sobol_xi(S * world, seed=0) if a.fields == "sobol" else I.halton_xi(S * world)
     xi = torch.tensor(xi_all[rank * S:(rank + 1) * S].ravel(), dtype=torch.float64, device=dev)
@@ -793,12 +800,84 @@ def run_uneven(a):
         dist.destroy_process_group()
 
 
+def run_config2(a):
+    """The paper's box mesh (128x128x32, 1,098,306 unknowns), one sample with
+    phi = 0.1 and K = 4.845e-13, dt = 1/12 yr, --run-steps steps (default
+    120) from t = 0 with the FP64 solver and with the mixed solver, each
+    timed with CUDA events; along the run, max |c_mixed - c_fp64| and the
+    salt masses of both runs.  Newton from the quadratic extrapolation."""
+    import numpy as np
+    import torch
+
+    from paper_1906_01632_gb300 import build as B
+    B.build()
+    from paper_1906_01632_gb300 import elder as E
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nx, ny, nz = 128, 128, 32
+    steps = a.run_steps or 120
+    dt = YEAR / 12
+    stream = torch.cuda.current_stream()
+    runs = {}
+    for name, prec in (("fp64", E.ELDER_FP64), ("mixed", E.ELDER_MIXED)):
+        ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=1, precision=prec))
+        C = ctx.C
+        phi = torch.full((C,), 0.1, dtype=torch.float64, device=dev)
+        K = torch.full((C,), 4.845e-13, dtype=torch.float64, device=dev)
+        p0, c0 = ctx.initial_state(1, device=dev)
+        warm = (p0.clone(), c0.clone(), p0.repeat(2), c0.repeat(2))
+        for _ in range(max(a.warmup, 2)):  # tuning and graph capture on a discarded copy
+            ctx.step_predicted(1, phi, K, 2, warm[2], warm[3], warm[0], warm[1], dt)
+        p, c, ph, ch = p0.clone(), c0.clone(), p0.repeat(2), c0.repeat(2)
+        states, info_log, ms = [], [], 0.0
+        for n in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = ctx.step_predicted(1, phi, K, 2, ph, ch, p, c, dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            info_log.append(info[0])
+            states.append(c.clone())
+        runs[name] = {"ms": ms, "states": states, "info": info_log}
+        ctx.destroy()
+    drift = {}
+    for n in (1, 2, 5, 10, 30, 60, steps):
+        if n <= steps:
+            d = float((runs["mixed"]["states"][n - 1] - runs["fp64"]["states"][n - 1]).abs().max())
+            m64 = runs["fp64"]["info"][n - 1]["salt_mass"]
+            m32 = runs["mixed"]["info"][n - 1]["salt_mass"]
+            drift[str(n)] = {"max_abs_dc": d, "salt_mass_fp64": m64,
+                             "salt_mass_rel_diff": abs(m32 - m64) / abs(m64)}
+    line = {"metric": "sample-timesteps/s, 128x128x32 single sample, mixed vs FP64 solver",
+            "value": steps / (runs["mixed"]["ms"] / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": max(a.warmup, 2), "higher_is_better": True,
+            "dtype": "f64+f32+bf16", "data": "synthetic",
+            "config": {"workload": "elder3d-box-128x128x32-single", "dt_yr": 1.0 / 12.0,
+                       "fields": "phi = 0.1, K = 4.845e-13 (Table 1)",
+                       "newton_start": "3u^n - 3u^(n-1) + u^(n-2)",
+                       "timed_steps": f"1-{steps} from t = 0"},
+            "fp64_value": steps / (runs["fp64"]["ms"] / 1000.0),
+            "newton_per_step": {k: float(np.mean([i["newton_iters"] for i in r["info"]]))
+                                for k, r in runs.items()},
+            "krylov_per_step": {k: float(np.mean([i["krylov_iters"] for i in r["info"]]))
+                                for k, r in runs.items()},
+            "failed": {k: sum(1 for i in r["info"] if i["status"]) for k, r in runs.items()},
+            "mixed_vs_fp64": drift,
+            "timing": "CUDA events around each step on the launching stream"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "uneven":
         run_uneven(a)
+    elif a.workload == "config2":
+        run_config2(a)
     else:
         run_ours(a)
 

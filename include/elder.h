@@ -99,7 +99,20 @@ typedef struct {
     double omega;             /* damping of the point block-Jacobi smoother
                                  (default 0.5)                              */
     int coarse_K_harmonic;    /* 0 arithmetic, 1 harmonic mean of K         */
-    int use_graphs;           /* capture the Krylov iteration in CUDA graphs*/
+    int use_graphs;           /* 0: every kernel launched from the host;
+                                 1: the BiCGStab iteration replayed as a
+                                 captured CUDA graph, the host polling the
+                                 per-sample flags between iterations;
+                                 2 (default): the whole step is one captured
+                                 graph whose Newton, BiCGStab and line-search
+                                 loops are conditional while nodes driven by
+                                 the per-sample flags on the device (the
+                                 host launches it and reads the results
+                                 once); used from a context's second step
+                                 on (the first tunes block sizes), for the
+                                 configured settings, outside profiling, and
+                                 cached for the 4 most recent argument sets
+                                 (array pointers, S, dt, Newton start)      */
     int autotune;             /* time threads-per-block candidates of the
                                  stencil kernels on the first step          */
     int newton_estimate;      /* also accept when the linear-convergence
@@ -322,8 +335,16 @@ int elder_profile_read(const elder_ctx* ctx, int kernel_class,
                        double* flops);
 
 /* Number of kernels this library has launched in the process (graph
- * replays count every kernel node).  Host output. */
+ * replays count every kernel node, the loop bodies of a device-controlled
+ * step as often as they ran).  Host output. */
 int elder_launch_count(int64_t* launches);
+
+/* Device-controlled steps of ctx (use_graphs = 2): *cached receives the
+ * number of captured step graphs held, *replays the steps run through them
+ * since the context was created, and *note (may be NULL) the reason the
+ * context fell back to host-driven steps ("" while it has not).  Host
+ * outputs; the note stays valid until the next call on ctx. */
+int elder_graph_status(const elder_ctx* ctx, int* cached, int64_t* replays, const char** note);
 
 /* Threads per block chosen by the autotuner for the smoother, the Krylov
  * stencil product and the multigrid residual (256 until the first step has

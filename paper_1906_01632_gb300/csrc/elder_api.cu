@@ -179,6 +179,28 @@ struct Prof {
     }
 };
 
+// Key of a captured step: everything the graph bakes in.
+struct StepKey {
+    int S, order, prec, newton_maxit, lin_maxit, ls_max, estimate, smoother, nu2;
+    double lin_rtol, omega, dt;
+    const void* ptr[6];  // phi, K, p, c, p_hist, c_hist
+    bool operator==(const StepKey& o) const
+    {
+        return std::memcmp(this, &o, sizeof(StepKey)) == 0;
+    }
+};
+
+// One captured implicit step: the prologue, a while node over the Newton
+// iterations whose body holds while nodes over the Krylov iterations and
+// over the line search, and the epilogue.  k_*: kernels per prologue,
+// Newton body (outside the inner loops), Krylov body, line-search body and
+// epilogue, for the launch count of a replay.
+struct StepGraph {
+    StepKey key;
+    cudaGraphExec_t exec = nullptr;
+    long long k_pro = 0, k_nb = 0, k_kb = 0, k_lb = 0, k_epi = 0;
+};
+
 struct elder_ctx {
     elder_config cfg;
     int device = 0;
@@ -216,8 +238,18 @@ struct elder_ctx {
     double* jin = nullptr;  // Jacobian input scratch, [S][N] + [S][C] pairs
     bool tuned[2] = {false, false};    // per precision (FP64, FP32)
     float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
+    // device-controlled steps (use_graphs = 2): captured step graphs, most
+    // recent last; loop counters [0..2] and bodies run per loop [3..5]
+    std::vector<StepGraph> step_graphs;
+    bool step_graph_ok = true;
+    std::string step_graph_note;
+    long long step_graph_replays = 0;
+    int* loopc = nullptr;
+    int* h_loopc = nullptr;            // pinned
     ~elder_ctx()
     {
+        for (auto& g : step_graphs) cudaGraphExecDestroy(g.exec);
+        if (h_loopc) cudaFreeHost(h_loopc);
         s64.reset();
         s32.reset();
         if (h_ns) cudaFreeHost(h_ns);
@@ -746,13 +778,315 @@ bool krylov_converged(elder_ctx* ctx, cudaStream_t st)
     return ctx->h_ks[0].status == 0 && !ctx->h_ks[0].active;
 }
 
+int finish_step(elder_ctx* ctx, int S, int32_t* status, elder_stats* stats);
+
+// ---------------------------------------------------------------------------
+// Device-controlled step (use_graphs = 2): the whole implicit step is one
+// captured CUDA graph.  Its Newton iterations, the BiCGStab iterations of
+// each Newton system and the line search are while nodes whose conditions
+// kernels set on the device from the per-sample flags (any sample still
+// iterating, and an iteration cap); the host launches the graph and reads
+// the per-sample results once.
+// ---------------------------------------------------------------------------
+
+// Condition of a while node: some sample's flag (flags[s * stride]) is set
+// and fewer than `limit` bodies have run.  first = 1 (before the loop) resets
+// the loop's counter; otherwise one more body has run, which is also added
+// to the step's running total for that loop (the launch count of a replay).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* __restrict__ flags,
+                            int stride, int S, int* counter, int* total, int limit, int first)
+{
+    int any = 0;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) any |= flags[(size_t)s * stride];
+    any = __syncthreads_or(any);
+    if (threadIdx.x != 0) return;
+    const int c = first ? 0 : *counter + 1;
+    *counter = c;
+    if (!first) *total += 1;
+    cudaGraphSetConditional(h, (any && c < limit) ? 1u : 0u);
+}
+
+void launch_loop_cond(cudaGraphConditionalHandle h, const int* flags, int stride, int S,
+                      int* counter, int* total, int limit, int first, cudaStream_t st)
+{
+    count_launch(1);
+    k_loop_cond<<<1, 256, 0, st>>>(h, flags, stride, S, counter, total, limit, first);
+}
+
+// Newton scalars at the start of a step: every sample iterating, full step.
+__global__ void k_newton_init(NScal* ns, int S)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    NScal z{};
+    z.active = 1;
+    z.ls_active = 1;
+    z.lambda = 1.0;
+    ns[s] = z;
+}
+
+// A sample still iterating after the Newton loop's cap has run out of
+// Newton iterations.
+__global__ void k_newton_cap(NScal* ns, int S)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || !ns[s].active) return;
+    ns[s].active = 0;
+    ns[s].status = ELDER_SAMPLE_NEWTON_MAXIT;
+}
+
+// Appends a while node after the current dependencies of the capture on
+// `cs` (handle created on the capturing graph), makes it the capture's only
+// dependency and returns its body graph.
+cudaGraph_t append_while(cudaStream_t cs, cudaGraphConditionalHandle h)
+{
+    cudaStreamCaptureStatus stt;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &g, &deps, &ed, &nd));
+    // zeroed storage: the struct's union has no default constructor
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof raw);
+    cudaGraphNodeParams& prm = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, ed, nd, &prm));
+    CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                           cudaStreamSetCaptureDependencies));
+    return prm.conditional.phGraph_out[0];
+}
+
+// Captures the step (the same launches, in the same order, as the
+// host-driven loop of step_impl) into out.exec.  Returns false, with the
+// reason in ctx->step_graph_note, when the capture fails; the caller then
+// runs the host-driven loop.
+template <class T>
+bool build_step_graph(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi, const double* K,
+                      double* p, double* c, double dt, const NewtonSettings& set, int order,
+                      double* p_hist, double* c_hist, StepGraph& out)
+{
+    const elder_config& cf = ctx->cfg;
+    const Grid& G = ctx->grids[0];
+    const Phys ph = make_phys(cf, dt);
+    const size_t nN = (size_t)S * G.N;
+    const int nb = ctx->nblk0;
+    NScal* ns = ctx->ns;
+    KScal* ks = ctx->ks;
+    const int* nmask = &ns[0].active;
+    const int* lsmask = &ns[0].ls_active;
+    const int* kmask = &ks[0].active;
+    int* cnt = ctx->loopc;      // loop counters: Newton, Krylov, line search
+    int* tot = ctx->loopc + 3;  // bodies run in this step, per loop
+    const auto mode = cudaStreamCaptureModeThreadLocal;
+    cudaStream_t cs = nullptr, cb1 = nullptr, cb2 = nullptr;
+    cudaGraph_t g = nullptr;
+    const long long launches0 = g_launches.load();
+    try {
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&cb1, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&cb2, cudaStreamNonBlocking));
+        CK(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle hN, hK, hL;
+        CK(cudaGraphConditionalHandleCreate(&hN, g, 0, 0));
+        // ---- prologue ----
+        CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode));
+        long long k0 = g_launches.load();
+        CK(cudaMemsetAsync(tot, 0, 3 * sizeof(int), cs));
+        CK(cudaMemcpyAsync(ctx->p_old, p, sizeof(double) * nN, cudaMemcpyDeviceToDevice, cs));
+        CK(cudaMemcpyAsync(ctx->c_old, c, sizeof(double) * nN, cudaMemcpyDeviceToDevice, cs));
+        if (p_hist) {
+            launch_extrapolate(G, order, ctx->p_old, ctx->c_old, p_hist, c_hist,
+                               order == 2 ? p_hist + nN : nullptr,
+                               order == 2 ? c_hist + nN : nullptr, p, c, S, cs);
+            if (order == 2) {
+                CK(cudaMemcpyAsync(p_hist + nN, p_hist, sizeof(double) * nN,
+                                   cudaMemcpyDeviceToDevice, cs));
+                CK(cudaMemcpyAsync(c_hist + nN, c_hist, sizeof(double) * nN,
+                                   cudaMemcpyDeviceToDevice, cs));
+            }
+            CK(cudaMemcpyAsync(p_hist, ctx->p_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice,
+                               cs));
+            CK(cudaMemcpyAsync(c_hist, ctx->c_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice,
+                               cs));
+        }
+        launch_impose_dirichlet(G, ctx->bc[0], ctx->cval, p, c, S, cs);
+        average_coefficients(ctx, S, phi, K, cs);
+        k_newton_init<<<nblocks(S, 128), 128, 0, cs>>>(ns, S);
+        count_launch(1);
+        launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, p, c, ctx->p_old, ctx->c_old,
+                        ctx->R, ctx->partial, ctx->partial2, nullptr, 0, S, cs, ctx->qf);
+        launch_norm_finalize(ctx->partial, ctx->partial2, nb, ns, 0, S, cs);
+        launch_loop_cond(hN, nmask, NSTRIDE, S, cnt + 0, tot + 0, set.newton_maxit, 1, cs);
+        CKL();
+        out.k_pro = g_launches.load() - k0;
+        // ---- Newton iteration ----
+        cudaGraph_t bN = append_while(cs, hN);
+        CK(cudaGraphConditionalHandleCreate(&hK, bN, 0, 0));
+        CK(cudaGraphConditionalHandleCreate(&hL, bN, 0, 0));
+        CK(cudaStreamBeginCaptureToGraph(cb1, bN, nullptr, nullptr, 0, mode));
+        k0 = g_launches.load();
+        assemble<T>(ctx, sv, S, phi, K, p, c, ph, nmask, NSTRIDE, S, cb1);
+        launch_newton_rhs<T>(G, ctx->R, sv.b, ns, S, cb1);
+        ctx->smoother_now = set.smoother;
+        ctx->omega_now = set.omega;
+        ctx->nu2_now = set.nu2;
+        k_arm_krylov<<<nblocks(S, 128), 128, 0, cb1>>>(ks, ns, S);
+        count_launch(1);
+        launch_bicg_init<T>(G, ctx->bc[0], sv.b, sv.x, sv.r, sv.rh, sv.p, sv.v, ctx->partial, ks,
+                            S, cb1);
+        launch_bicg_finalize(0, ctx->partial, nb, ks, set.lin_rtol, set.lin_maxit, S, cb1);
+        launch_loop_cond(hK, kmask, KSTRIDE, S, cnt + 1, tot + 1, set.lin_maxit, 1, cb1);
+        // BiCGStab iterations
+        cudaGraph_t bK = append_while(cb1, hK);
+        CK(cudaStreamBeginCaptureToGraph(cb2, bK, nullptr, nullptr, 0, mode));
+        long long k1 = g_launches.load();
+        bicg_iteration<T>(ctx, sv, 0, set.lin_rtol, set.lin_maxit, S, cb2);
+        launch_loop_cond(hK, kmask, KSTRIDE, S, cnt + 1, tot + 1, set.lin_maxit, 0, cb2);
+        CKL();
+        out.k_kb = g_launches.load() - k1;
+        CK(cudaStreamEndCapture(cb2, &bK));
+        ctx->smoother_now = cf.smoother;
+        ctx->omega_now = configured_omega(cf);
+        ctx->nu2_now = cf.nu2;
+        // line search: the full step, the stop test on its correction, then
+        // trial residuals and halvings while any sample's search runs
+        launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, cb1);
+        launch_newton_predict(ctx->partial2, nb, ns, cf.newton_tol_p, cf.newton_tol_c,
+                              set.estimate, S, cb1);
+        launch_loop_cond(hL, lsmask, NSTRIDE, S, cnt + 2, tot + 2, set.ls_max + 1, 1, cb1);
+        cudaGraph_t bL = append_while(cb1, hL);
+        CK(cudaStreamBeginCaptureToGraph(cb2, bL, nullptr, nullptr, 0, mode));
+        k1 = g_launches.load();
+        launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, ctx->pt, ctx->ct, ctx->p_old,
+                        ctx->c_old, ctx->Rt, ctx->partial, ctx->partial3, lsmask, NSTRIDE, S, cb2,
+                        ctx->qf);
+        launch_norm_finalize(ctx->partial, ctx->partial3, nb, ns, 1, S, cb2);
+        launch_newton_ls_finalize(nullptr, ctx->partial2, nb, ns, set.ls_max, S, cb2);
+        launch_newton_trial<T>(G, p, c, sv.x, ctx->pt, ctx->ct, ctx->partial2, ns, S, cb2);
+        launch_loop_cond(hL, lsmask, NSTRIDE, S, cnt + 2, tot + 2, set.ls_max + 1, 0, cb2);
+        CKL();
+        out.k_lb = g_launches.load() - k1;
+        CK(cudaStreamEndCapture(cb2, &bL));
+        launch_newton_accept(G, p, c, ctx->pt, ctx->ct, ctx->R, ctx->Rt, ns, S, cb1);
+        launch_newton_check(ns, ks, cf.newton_tol_p, cf.newton_tol_c, set.newton_maxit,
+                            set.estimate, S, cb1);
+        launch_loop_cond(hN, nmask, NSTRIDE, S, cnt + 0, tot + 0, set.newton_maxit, 0, cb1);
+        CKL();
+        out.k_nb = g_launches.load() - k0 - out.k_kb - out.k_lb;
+        CK(cudaStreamEndCapture(cb1, &bN));
+        // ---- epilogue ----
+        k0 = g_launches.load();
+        k_newton_cap<<<nblocks(S, 128), 128, 0, cs>>>(ns, S);
+        count_launch(1);
+        launch_newton_restore_failed(G, p, c, ctx->p_old, ctx->c_old, ns, S, cs);
+        launch_mass_balance(G, ph, ctx->bc[0], phi, K, p, c, ctx->c_old, ctx->partial3, S, cs);
+        launch_sum_partials(ctx->partial3, nb, ctx->mass, 3 * S, cs);
+        CKL();
+        out.k_epi = g_launches.load() - k0;
+        CK(cudaStreamEndCapture(cs, &g));
+        CK(cudaGraphInstantiate(&out.exec, g, 0));
+        CK(cudaGraphDestroy(g));
+        g = nullptr;
+        for (cudaStream_t q : {cs, cb1, cb2}) cudaStreamDestroy(q);
+        g_launches.store(launches0);  // captured, not launched
+        return true;
+    } catch (const Fail& f) {
+        ctx->step_graph_note = f.msg;
+        for (cudaStream_t q : {cb2, cb1, cs}) {
+            if (!q) continue;
+            cudaStreamCaptureStatus cst;
+            if (cudaStreamIsCapturing(q, &cst) == cudaSuccess &&
+                cst != cudaStreamCaptureStatusNone) {
+                cudaGraph_t dropped = nullptr;
+                cudaStreamEndCapture(q, &dropped);
+                if (dropped && dropped != g) cudaGraphDestroy(dropped);
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+        for (cudaStream_t q : {cs, cb1, cb2})
+            if (q) cudaStreamDestroy(q);
+        cudaGetLastError();
+        ctx->smoother_now = cf.smoother;
+        ctx->omega_now = configured_omega(cf);
+        ctx->nu2_now = cf.nu2;
+        g_launches.store(launches0);
+        return false;
+    }
+}
+
+// Replays (capturing on first use) the step graph of these arguments.
+// Returns false when no graph could be built; the step has then not run.
+template <class T>
+bool step_graph(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi, const double* K,
+                double* p, double* c, double dt, cudaStream_t st, const NewtonSettings& set,
+                int order, double* p_hist, double* c_hist)
+{
+    StepKey key;
+    std::memset(&key, 0, sizeof key);
+    key.S = S;
+    key.order = p_hist ? order : 0;
+    key.prec = (int)sizeof(T);
+    key.newton_maxit = set.newton_maxit;
+    key.lin_maxit = set.lin_maxit;
+    key.ls_max = set.ls_max;
+    key.estimate = set.estimate;
+    key.smoother = set.smoother;
+    key.nu2 = set.nu2;
+    key.lin_rtol = set.lin_rtol;
+    key.omega = set.omega;
+    key.dt = dt;
+    const void* ptrs[6] = {phi, K, p, c, p_hist, c_hist};
+    for (int q = 0; q < 6; ++q) key.ptr[q] = ptrs[q];
+    auto& cache = ctx->step_graphs;
+    StepGraph sg;
+    auto it = std::find_if(cache.begin(), cache.end(),
+                           [&](const StepGraph& x) { return x.key == key; });
+    if (it != cache.end()) {
+        sg = *it;
+        cache.erase(it);
+    } else {
+        sg.key = key;
+        if (!build_step_graph<T>(ctx, sv, S, phi, K, p, c, dt, set, order, p_hist, c_hist, sg)) {
+            ctx->step_graph_ok = false;
+            return false;
+        }
+        if (cache.size() >= 4) {  // keep the four most recent argument sets
+            cudaGraphExecDestroy(cache.front().exec);
+            cache.erase(cache.begin());
+        }
+    }
+    cache.push_back(sg);  // most recent last
+    CK(cudaGraphLaunch(sg.exec, st));
+    ctx->step_graph_replays += 1;
+    CK(cudaMemcpyAsync(ctx->h_ns, ctx->ns, sizeof(NScal) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_mass, ctx->mass, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaMemcpyAsync(ctx->h_loopc, ctx->loopc, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    count_launch((int)(sg.k_pro + sg.k_epi + ctx->h_loopc[3] * sg.k_nb +
+                       ctx->h_loopc[4] * sg.k_kb + ctx->h_loopc[5] * sg.k_lb));
+    return true;
+}
+
 template <class T>
 int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double* p,
               double* c, double dt, int32_t* status, elder_stats* stats, cudaStream_t st,
               const NewtonSettings& set, int order = 0, double* p_hist = nullptr,
-              double* c_hist = nullptr)
+              double* c_hist = nullptr, bool allow_graph = false)
 {
     Solver<T>& sv = solver_reserve<T>(ctx, S);
+    // the device-controlled step once the context is tuned, for the
+    // configured (not the robust) settings and outside profiling
+    const int tidx = std::is_same<T, float>::value ? 1 : 0;
+    if (allow_graph && ctx->cfg.use_graphs == 2 && ctx->step_graph_ok && !ctx->prof.on &&
+        !set.keep_best && (ctx->tuned[tidx] || !ctx->cfg.autotune) &&
+        step_graph<T>(ctx, sv, S, phi, K, p, c, dt, st, set, order, p_hist, c_hist))
+        return finish_step(ctx, S, status, stats);
     const elder_config& cf = ctx->cfg;
     const Grid& G = ctx->grids[0];
     const Phys ph = make_phys(cf, dt);
@@ -874,6 +1208,13 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
     CKL();
     CK(cudaStreamSynchronize(st));
     prof_drain(ctx);
+    return finish_step(ctx, S, status, stats);
+}
+
+// Per-sample status and statistics of a finished step from the host copies
+// of the Newton scalars and the salt-mass balance.
+int finish_step(elder_ctx* ctx, int S, int32_t* status, elder_stats* stats)
+{
     int rc = ELDER_OK;
     for (int s = 0; s < S; ++s) {
         const NScal& k = ctx->h_ns[s];
@@ -965,11 +1306,11 @@ int step_tiers(elder_ctx* ctx, int S, const double* phi, const double* K, double
         NewtonSettings mset = conf;
         if (ctx->cfg.mixed_newton_maxit > 0) mset.newton_maxit = ctx->cfg.mixed_newton_maxit;
         step_impl<float>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, mset, order,
-                         p_hist, c_hist);
+                         p_hist, c_hist, true);
     }
     else
         step_impl<double>(ctx, S, phi, K, p, c, dt, st1.data(), sts.data(), st, conf, order,
-                          p_hist, c_hist);
+                          p_hist, c_hist, true);
     auto failed = [&]() {
         std::vector<int> f;
         for (int s = 0; s < S; ++s)
@@ -1156,7 +1497,7 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->omega = 0.5;
     cfg->omega_line = 0.95;
     cfg->coarse_K_harmonic = 0;
-    cfg->use_graphs = 1;
+    cfg->use_graphs = 2;
     cfg->autotune = 1;
     cfg->newton_estimate = 1;
     cfg->smoother = ELDER_SMOOTH_ZLINE;
@@ -1183,7 +1524,8 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
         c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0 ||
         (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE) ||
-        !(c.omega > 0) || !(c.omega_line > 0) || c.mixed_newton_maxit < 0) {
+        !(c.omega > 0) || !(c.omega_line > 0) || c.mixed_newton_maxit < 0 ||
+        c.use_graphs < 0 || c.use_graphs > 2) {
         g_create_error = "invalid elder_config";
         return ELDER_EINVAL;
     }
@@ -1276,6 +1618,10 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         CK(cudaMallocHost((void**)&ctx->h_ns, sizeof(NScal) * S));
         CK(cudaMallocHost((void**)&ctx->h_ks, sizeof(KScal) * S));
         CK(cudaMallocHost((void**)&ctx->h_scalar, sizeof(double) * 64));
+        ctx->loopc = dalloc<int>(8);
+        ctx->mem.add(ctx->loopc);
+        CK(cudaMemset(ctx->loopc, 0, 8 * sizeof(int)));
+        CK(cudaMallocHost((void**)&ctx->h_loopc, sizeof(int) * 8));
         // solver workspace up front when the grid supports the solver (grids
         // that do not still serve the residual, Jacobian and moment calls)
         if (2 * ctx->grids.back().N <= MAX_COARSE_UNKNOWNS) {
@@ -1526,6 +1872,15 @@ int elder_measure_peak(int kind, double* gflops, void* stream)
         g_create_error = f.msg;
         return f.code;
     }
+    return ELDER_OK;
+}
+
+int elder_graph_status(const elder_ctx* ctx, int* cached, int64_t* replays, const char** note)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (cached) *cached = (int)ctx->step_graphs.size();
+    if (replays) *replays = ctx->step_graph_replays;
+    if (note) *note = ctx->step_graph_note.c_str();
     return ELDER_OK;
 }
 

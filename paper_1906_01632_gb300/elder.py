@@ -96,6 +96,9 @@ def _load():
     lib.elder_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
     lib.elder_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     lib.elder_measure_peak.argtypes = [ip, dp, vp]
+    lib.elder_graph_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_char_p)]
     lib.elder_autotune_result.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int),
@@ -213,6 +216,15 @@ class Elder:
         return {"threads_per_block": dict(zip(names, (x.value for x in b))),
                 "ms_per_launch": {n: dict(zip(cand, [round(ms[3 * i + q], 4) for q in range(3)]))
                                   for i, n in enumerate(names)}}
+
+    def graph_status(self):
+        """Device-controlled steps: (cached step graphs, replays, fallback note)."""
+        n = ctypes.c_int()
+        r = ctypes.c_int64()
+        note = ctypes.c_char_p()
+        self._check(_lib.elder_graph_status(self._h, ctypes.byref(n), ctypes.byref(r),
+                                            ctypes.byref(note)))
+        return n.value, r.value, (note.value or b"").decode()
 
     def profile(self, on: bool):
         self._check(_lib.elder_profile(self._h, 1 if on else 0))

@@ -15,8 +15,10 @@ iterations per Newton step).  Command (from the repository root, about
     python tests/golden/make_config2_states.py
 
 Stored per step n (1..5):
-  c{n}_idx, c{n}_val: every node with |c| > C_FLOOR (int32 index, FP64
-      value); every other node has |c| <= C_FLOOR;
+  c{n}_idx, c{n}_val: at the last step every node with |c| > C_FLOOR (every
+      other node has |c| <= C_FLOOR); at steps 1-4 C_NODES of those nodes
+      drawn at random (int32 index, FP64 value), with c{n}_count the number
+      of nodes above the floor;
   p{n}_val: FP64 p at the P_NODES sampled node indices (p_idx);
   info{n}: Newton iterations, linear iterations, ||R|| before and after.
 """
@@ -32,6 +34,7 @@ sys.path.insert(0, ROOT)
 import oracle as O  # noqa: E402
 
 C_FLOOR = 1e-13
+C_NODES = 16384
 P_NODES = 4096
 STEPS = 5
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "config2_states.npz")
@@ -52,6 +55,9 @@ def main():
         p, c, info = O.newton_step(P, phi, K, p, c, dt, O.NewtonOpts(smoother=1, lin_rtol=1e-10))
         assert info["status"] == 0, info
         keep = np.nonzero(np.abs(c) > C_FLOOR)[0].astype(np.int32)
+        out[f"c{n}_count"] = np.array(keep.size)
+        if n < STEPS:
+            keep = np.sort(rng.choice(keep, min(C_NODES, keep.size), replace=False))
         out[f"c{n}_idx"] = keep
         out[f"c{n}_val"] = c[keep]
         out[f"p{n}_val"] = p[p_idx]

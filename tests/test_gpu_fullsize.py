@@ -73,37 +73,55 @@ def _check_solved(P, phi, K, p1, c1, p0, c0, dt, slack=10.0):
 
 
 def test_config2_128x128x32_fp64_and_mixed(E):
-    """128x128x32 (1,098,306 unknowns, the paper's box mesh), one sample,
-    the first steps: both paths solve the implicit step and agree."""
+    """128x128x32 (1,098,306 unknowns, the paper's box mesh of Section 2.1),
+    one sample, the first 5 steps of dt = 1/12 yr from the initial state,
+    FP64 path and mixed path each against the oracle's own states
+    (tests/golden/config2_states.npz, written by the oracle): c within 1e-10
+    (FP64) and 1e-6 (mixed) at 16,384 sampled nodes after steps 1-4 and at
+    every node after step 5 (every node the oracle left below 1e-13 too);
+    p at 4,096 sampled nodes; the oracle residual at every FP64 state at its
+    round-off floor; the salt balance of every step."""
+    import os as _os
+    path = _os.path.join(_os.path.dirname(__file__), "golden", "config2_states.npz")
+    if not _os.path.exists(path):
+        pytest.skip("config2_states.npz not generated (tests/golden/make_config2_states.py)")
+    g = np.load(path)
     P = O.Problem(128, 128, 32)
     phi = np.full(P.C, 0.1)
     K = np.full(P.C, 4.845e-13)
     p0, c0 = O.initial_state(P)
-    dt = YEAR / 12
-    states = {}
-    for prec in (0, 1):
+    dt = float(g["dt"])
+    assert abs(dt - YEAR / 12) <= 1e-9
+    floor = float(g["c_floor"])
+    pscale = P.rho0 * P.g * P.Lz
+    for prec, tol_c, tol_p in ((0, 1e-10, 1e-9), (1, 1e-6, 1e-6)):
         ctx = E.elder_create(E.elder_config_default(128, 128, 32, max_samples=1, precision=prec))
         pt, ct = T(p0), T(c0)
-        traj = []
-        for _ in range(2):
+        pp, cp = p0, c0
+        for n in range(1, 6):
             st, info = ctx.step(1, T(phi), T(K), pt, ct, dt)
             assert st[0] == 0, info
-            traj.append((H(pt).copy(), H(ct).copy(), info[0]))
-        states[prec] = traj
+            p1, c1 = H(pt).copy(), H(ct).copy()
+            idx = g[f"c{n}_idx"]
+            dc = np.abs(c1[idx] - g[f"c{n}_val"]).max()
+            assert dc <= tol_c, (prec, n, dc)
+            if n == 5:
+                rest = np.ones(P.N, bool)
+                rest[idx] = False
+                assert np.abs(c1[rest]).max() <= floor + tol_c
+            dp = np.abs(p1[g["p_idx"]] - g[f"p{n}_val"]).max()
+            assert dp <= tol_p * pscale, (prec, n, dp)
+            if prec == 0:
+                _check_solved(P, phi, K, p1, c1, pp, cp, dt)
+            m0, m1 = _masses(P, phi, cp), _masses(P, phi, c1)
+            assert abs(info[0]["salt_mass0"] - m0) <= 1e-12 * max(m0, 1.0)
+            assert abs(info[0]["salt_mass"] - m1) <= 1e-12 * m1
+            assert abs(info[0]["salt_mass"] - info[0]["salt_mass0"] - info[0]["salt_inflow"]) \
+                <= 1e-9 * m1
+            print(f"precision {prec} step {n}: max |c - c_oracle| {dc:.2e}, "
+                  f"max |p - p_oracle| {dp:.2e} Pa")
+            pp, cp = p1, c1
         ctx.destroy()
-    pp, cp = p0, c0
-    for n in range(2):
-        p1, c1, info = states[0][n]
-        _check_solved(P, phi, K, p1, c1, pp, cp, dt)
-        pm, cm, _ = states[1][n]
-        assert np.abs(cm - c1).max() <= 1e-8
-        assert np.abs(pm - p1).max() <= 1e-8 * P.rho0 * P.g * P.Lz
-        # salt-mass balance of the step (FP64 accumulation on the device)
-        m0, m1 = _masses(P, phi, cp), _masses(P, phi, c1)
-        assert abs(info["salt_mass0"] - m0) <= 1e-12 * max(m0, 1.0)
-        assert abs(info["salt_mass"] - m1) <= 1e-12 * m1
-        assert abs(info["salt_mass"] - info["salt_mass0"] - info["salt_inflow"]) <= 1e-9 * m1
-        pp, cp = p1, c1
 
 
 def _oracle_trajectory(args):
@@ -321,14 +339,14 @@ def test_autograd_rollout_matches_elder_grad_and_a_forward_run(E):
     J = E.ElderRollout.apply(phi, K, T(p0), T(c0), ctx, steps, dt)
     (3.0 * J).backward()
     Jr, gphi, gK = ctx.grad(steps, T(phi_np), T(K_np), T(p0), T(c0), dt)
-    assert float(J) == Jr
+    assert float(J.detach()) == Jr
     torch.testing.assert_close(phi.grad, 3.0 * gphi, rtol=0, atol=0)
     torch.testing.assert_close(K.grad, 3.0 * gK, rtol=0, atol=0)
     pt, ct = T(p0), T(c0)
     for _ in range(steps):
         st, _ = ctx.step(1, T(phi_np), T(K_np), pt, ct, dt)
         assert st[0] == 0
-    assert abs(O.objective(P, phi_np, H(ct)) - float(J)) <= 1e-12 * abs(float(J))
+    assert abs(O.objective(P, phi_np, H(ct)) - Jr) <= 1e-12 * abs(Jr)
     # chain rule through a torch Kozeny-Carman map
     ph = T(phi_np).requires_grad_(True)
     Kc = 4.845e-13 * (ph ** 3 / (1 - ph) ** 2) / (0.1 ** 3 / 0.9 ** 2)

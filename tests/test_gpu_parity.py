@@ -474,3 +474,52 @@ def test_measured_fma_peaks(E):
     f32 = E.elder_measure_peak("fp32")
     print(f"FP64 {f64:.0f} GFLOP/s, FP32 {f32:.0f} GFLOP/s")
     assert 0 < f64 < f32 and np.isfinite(f32)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_device_controlled_step_matches_host_driven_step(E, precision):
+    """use_graphs = 2 (the whole step one CUDA graph, its Newton, BiCGStab
+    and line-search loops while nodes driven by the per-sample flags on the
+    device) runs the same kernels in the same order as the host-driven loop
+    (use_graphs = 1): states and iteration counts are bitwise equal over 4
+    steps with the quadratic Newton start, and the graph is really used from
+    the second step on.  Pointers that change between calls get their own
+    captured graph."""
+    P = O.Problem(16, 16, 4)
+    S = 4
+    phi, K = _fields(P, S, 51)
+    p0, c0 = O.initial_state(P)
+    dt = YEAR / 12
+    out = {}
+    for mode in (1, 2):
+        ctx = _ctx(E, 16, 16, 4, S, precision=precision, use_graphs=mode)
+        ph_t, K_t = T(phi), T(K)
+        pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+        hp, hc = pt.repeat(2), ct.repeat(2)
+        traj = []
+        for n in range(4):
+            st, info = ctx.step_predicted(S, ph_t, K_t, 2, hp, hc, pt, ct, dt)
+            assert (st == 0).all()
+            traj.append((H(pt).copy(), H(ct).copy(),
+                         [(i["newton_iters"], i["krylov_iters"], i["ls_cuts"]) for i in info]))
+        # a second state buffer: a new argument set, a new graph
+        p2, c2 = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+        st, _ = ctx.step(S, ph_t, K_t, p2, c2, dt)
+        assert (st == 0).all()
+        traj.append((H(p2).copy(), H(c2).copy(), None))
+        cached, replays, note = ctx.graph_status()
+        if mode == 2:
+            assert note == "" and replays == 4 and cached == 2, (cached, replays, note)
+        else:
+            assert replays == 0
+        out[mode] = traj
+        ctx.destroy()
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert a[2] == b[2]
+    # and the marched states are the oracle's
+    p, c = p0, c0
+    for n in range(4):
+        p, c, oi = O.newton_step(P, phi[0], K[0], p, c, dt)
+        tol = 1e-10 if precision == 0 else 1e-6
+        assert np.abs(out[2][n][1].reshape(S, -1)[0] - c).max() <= tol
