@@ -503,6 +503,10 @@ def elder_jacobian(ctx: Elder, *a, **k):
     return ctx.jacobian(*a, **k)
 
 
+def elder_graph_status(ctx: Elder):
+    return ctx.graph_status()
+
+
 class ElderRollout(torch.autograd.Function):
     """Salt mass below mid-depth after n_steps implicit steps of one sample,
     differentiable w.r.t. the per-cell porosity and permeability through the
