@@ -647,15 +647,19 @@ def gpc_timings(E, torch, cfield, stream, Ns=1_000_000, apk=None):
 
 def E_model_bytes(cls, tsize, nx, ny, nz, line=True):
     """Algorithmic bytes per node of one launch (mirrors the library's model);
-    the mixed path stores the multigrid matrices in bfloat16; the z-line
-    sweep from x = 0 also reads the two vertical line blocks."""
+    the mixed path stores the multigrid matrices in bfloat16.  With the z-line
+    smoother the sweep from x = 0 reads the assembly's line factors (zMi, zC),
+    the lower line block, b and writes x; the assembly also forms those
+    factors (reading Dinv and both line blocks)."""
     N = (nx + 1) * (ny + 1) * (nz + 1)
     cpn = nx * ny * nz / N
     mz = 2 if tsize == 4 else 8
-    return {"smooth": 108 * mz + 10 * tsize + 1, "smooth0": 8 * tsize + 1 + (8 * mz if line else 0),
+    return {"smooth": 108 * mz + 10 * tsize + 1,
+            "smooth0": (12 * tsize + 4 * mz + 1) if line else 8 * tsize + 1,
             "spmv": 108 * tsize + 6 * tsize + 1, "mg_residual": 108 * mz + 6 * tsize + 1,
             "residual": 49 + 16 * cpn,
-            "jacobian": 108 * tsize + 108 * mz + 4 * tsize + 17 + 16 * cpn}[cls]
+            "jacobian": 108 * tsize + 108 * mz + 4 * tsize + 17 + 16 * cpn +
+                        ((12 * tsize + 8 * mz + 1) if line else 0)}[cls]
 
 
 # --------------------------------------------------------------------------

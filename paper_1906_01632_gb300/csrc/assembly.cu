@@ -533,6 +533,47 @@ __global__ void k_jac_inputs(Grid G, Phys ph, const double* __restrict__ phi,
     }
 }
 
+// The node part of k_jac_inputs alone (a Newton iterate changes the state
+// only; the cell coefficients are converted once per step).
+template <class T>
+__global__ void k_node_inputs(Grid G, double rho0g, const double* __restrict__ p,
+                              const double* __restrict__ c, V2<T>* __restrict__ nodeT,
+                              const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!sample_on(mask, mstride, s)) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= G.N) return;
+    const size_t o = (size_t)s * G.N + q;
+    int i, j, k;
+    node_ijk(G, q, i, j, k);
+    const double z = k * G.hz;
+    nodeT[o] = V2<T>{T(fma(rho0g, z - G.Lz, p[o])), T(c[o])};
+}
+
+// The cell part of k_jac_inputs alone: (phi, K / mu) in T.
+template <class T>
+__global__ void k_cell_inputs(int C, double mu, const double* __restrict__ phi,
+                              const double* __restrict__ K, V2<T>* __restrict__ cellT)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= C) return;
+    const size_t o = (size_t)blockIdx.y * C + q;
+    cellT[o] = V2<T>{T(phi[o]), T(K[o] / mu)};
+}
+
+template <class T>
+void launch_cell_inputs(const Grid& G, double mu, const double* phi, const double* K,
+                        V2<T>* cellT, int S, cudaStream_t st)
+{
+    count_launch(1);
+    k_cell_inputs<T><<<dim3(nblocks(G.C), S), kBS, 0, st>>>(G.C, mu, phi, K, cellT);
+}
+template void launch_cell_inputs<float>(const Grid&, double, const double*, const double*,
+                                        V2<float>*, int, cudaStream_t);
+template void launch_cell_inputs<double>(const Grid&, double, const double*, const double*,
+                                         V2<double>*, int, cudaStream_t);
+
 // Writes the row blocks as T (JT, the Krylov operator) and/or as the
 // multigrid storage type M (JM), and the inverse of the interior diagonal
 // block (Dinv, Dirichlet rows and columns replaced by the identity); any of
@@ -613,11 +654,19 @@ template <class T, class M>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* phi, const double* K, const double* p,
                      const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv, V2<T>* cellT,
-                     V2<T>* nodeT, const int* mask, int mstride, int S, cudaStream_t st)
+                     V2<T>* nodeT, const int* mask, int mstride, int S, cudaStream_t st,
+                     int inputs)
 {
-    count_launch(2);
-    dim3 gin(nblocks(std::max(G.N, G.C)), S);
-    k_jac_inputs<T><<<gin, kBS, 0, st>>>(G, ph, phi, K, p, c, cellT, nodeT, mask, mstride);
+    count_launch(1);
+    if (inputs == 0) {  // convert the state and the coefficients
+        count_launch(1);
+        dim3 gin(nblocks(std::max(G.N, G.C)), S);
+        k_jac_inputs<T><<<gin, kBS, 0, st>>>(G, ph, phi, K, p, c, cellT, nodeT, mask, mstride);
+    } else if (inputs == 1) {  // the coefficients are converted already
+        count_launch(1);
+        k_node_inputs<T><<<dim3(nblocks(G.N), S), kBS, 0, st>>>(G, ph.rho0 * ph.g, p, c, nodeT,
+                                                                mask, mstride);
+    }
     dim3 grid(nblocks(G.N, 128), S);
     // lumped storage volume per unit phi over dt: (h^3 / 8) / dt per cell corner
     const T vscale = T(0.125 * G.hx * G.hy * G.hz / ph.dt);
@@ -635,21 +684,25 @@ template void launch_jacobian<double, double>(const Grid&, const Phys&, const ui
                                               const double*, const double*, const double*,
                                               const double*, B4<double>*, B4<double>*,
                                               B4<double>*, V2<double>*, V2<double>*, const int*,
-                                              int, int, cudaStream_t);
+                                              int, int, cudaStream_t, int);
 template void launch_jacobian<float, __nv_bfloat16>(const Grid&, const Phys&, const uint8_t*,
                                                     const double*, const double*,
                                                     const double*, const double*, B4<float>*,
                                                     B4<__nv_bfloat16>*, B4<float>*, V2<float>*,
                                                     V2<float>*, const int*, int, int,
-                                                    cudaStream_t);
+                                                    cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // hierarchy: state injection, cell averaging, block-diagonal inverse
 // ---------------------------------------------------------------------------
 
+// State injection to the coarse grid; with nodeT also the coarse Jacobian's
+// node inputs (p - rho0 g (Lz - z), c) in T, as k_jac_inputs forms them.
+template <class T>
 __global__ void k_inject(Grid Gf, Grid Gc, const double* __restrict__ pf,
                          const double* __restrict__ cf, double* __restrict__ pc,
-                         double* __restrict__ cc, const int* mask, int mstride)
+                         double* __restrict__ cc, V2<T>* __restrict__ nodeT, double rho0g,
+                         const int* mask, int mstride)
 {
     const int s = blockIdx.y;
     if (!sample_on(mask, mstride, s)) return;
@@ -658,18 +711,31 @@ __global__ void k_inject(Grid Gf, Grid Gc, const double* __restrict__ pf,
     int I, J, K;
     node_ijk(Gc, n, I, J, K);
     const int f = node_id(Gf, 2 * I, 2 * J, 2 * K);
-    pc[(size_t)s * Gc.N + n] = pf[(size_t)s * Gf.N + f];
-    cc[(size_t)s * Gc.N + n] = cf[(size_t)s * Gf.N + f];
+    const size_t o = (size_t)s * Gc.N + n;
+    const double pv = pf[(size_t)s * Gf.N + f], cv = cf[(size_t)s * Gf.N + f];
+    pc[o] = pv;
+    cc[o] = cv;
+    if (nodeT) {
+        const double z = K * Gc.hz;
+        nodeT[o] = V2<T>{T(fma(rho0g, z - Gc.Lz, pv)), T(cv)};
+    }
 }
 
-void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
-                   const double* cf, double* pc, double* cc, const int* mask,
+template <class T>
+void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf, const double* cf,
+                   double* pc, double* cc, V2<T>* nodeT, double rho0g, const int* mask,
                    int mstride, int S, cudaStream_t st)
 {
     count_launch(1);
     dim3 grid(nblocks(Gc.N), S);
-    k_inject<<<grid, kBS, 0, st>>>(Gf, Gc, pf, cf, pc, cc, mask, mstride);
+    k_inject<T><<<grid, kBS, 0, st>>>(Gf, Gc, pf, cf, pc, cc, nodeT, rho0g, mask, mstride);
 }
+template void launch_inject<float>(const Grid&, const Grid&, const double*, const double*,
+                                   double*, double*, V2<float>*, double, const int*, int, int,
+                                   cudaStream_t);
+template void launch_inject<double>(const Grid&, const Grid&, const double*, const double*,
+                                    double*, double*, V2<double>*, double, const int*, int, int,
+                                    cudaStream_t);
 
 __global__ void k_average_cells(Grid Gf, Grid Gc, const double* __restrict__ phif,
                                 const double* __restrict__ Kf,

@@ -145,6 +145,7 @@ template <class T> struct Solver : SolverBase {
     B4<T>* J0 = nullptr;           // level-0 Krylov operator (T)
     std::vector<B4<M>*> Jm;        // multigrid matrices per level (M)
     std::vector<B4<T>*> Dinv;      // inverse interior diagonal blocks per level
+    std::vector<B4<T>*> zMi, zC;   // block-LU factors of the vertical lines per level
     std::vector<V2<T>*> mb, mx, mx2, mr;  // multigrid vectors per level
     V2<T> *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr,
           *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr,
@@ -235,7 +236,9 @@ struct elder_ctx {
     int smoother_now = ELDER_SMOOTH_JACOBI;  // smoother of the solve in progress
     double omega_now = 0.5;                  // its damping
     int nu2_now = 1;                         // its post-smoothing sweeps
-    double* jin = nullptr;  // Jacobian input scratch, [S][N] + [S][C] pairs
+    // Jacobian inputs per level in the assembly's arithmetic type (room for
+    // FP64 pairs): node (p - rho0 g (Lz - z), c) [S][N], cell (phi, K/mu) [S][C]
+    std::vector<double*> jn, jc;
     bool tuned[2] = {false, false};    // per precision (FP64, FP32)
     float tune_ms[3][3] = {};          // [class smooth/spmv/mgres][bs 128/256/512]
     // device-controlled steps (use_graphs = 2): captured step graphs, most
@@ -282,24 +285,29 @@ double configured_omega(const elder_config& cf)
     return cf.smoother == ELDER_SMOOTH_ZLINE ? cf.omega_line : cf.omega;
 }
 
-double model_bytes(int cls, int T, int Mz, const Grid& G, bool line)
+double model_bytes(int cls, int T, int Mz, const Grid& G, int line)
 {
     // T: bytes of a vector / Dinv entry; Mz: bytes of a stored matrix entry
     // (for the Jacobian class: Mz of the multigrid copy, T of the Krylov copy
-    // or 0 when the level has none).  line: the z-line smoother, whose sweep
-    // from x = 0 also reads the two vertical line blocks of J (its sweep from
-    // a nonzero x reads all of J anyway).
+    // or 0 when the level has none).  line (SMOOTH0): 1 the z-line sweep that
+    // factors as it goes, reading the two vertical line blocks of J besides
+    // Dinv; 2 the sweep with the assembly's line factors (zMi, zC and the
+    // lower line block).  line (JACOBIAN): 1 with the line factorisation.
     const double cells_per_node = (double)G.C / G.N;
+    const int Td = T ? T : Mz;
     switch (cls) {
     case ELDER_K_SMOOTH: return 108 * Mz + (4 + 2 + 2 + 2) * T + 1;  // J, Dinv, b, x, xo, bc
-    case ELDER_K_SMOOTH0:                                            // Dinv, b, xo, bc (+ L, U)
-        return (4 + 2 + 2) * T + 1 + (line ? 8 * Mz : 0);
+    case ELDER_K_SMOOTH0:
+        if (line == 2) return (4 + 4 + 2 + 2) * T + 4 * Mz + 1;    // zMi, zC, b, xo, L, bc
+        return (4 + 2 + 2) * T + 1 + (line ? 8 * Mz : 0);          // Dinv, b, xo, bc (+ L, U)
     case ELDER_K_SPMV: return 108 * Mz + (2 + 2 + 2) * T + 1;        // J, x, y, a, bc
     case ELDER_K_MGRES: return 108 * Mz + (2 + 2 + 2) * T + 1;       // J, x, b, r, bc
     case ELDER_K_RESIDUAL:  // p, c, c_old, R, cval, bc, phi, K
         return 3 * 8 + 16 + 8 + 1 + 16 * cells_per_node;
-    case ELDER_K_JACOBIAN:  // J written (Krylov + multigrid copies), Dinv; p, c, bc, phi, K
-        return 108 * T + 108 * Mz + 4 * (T ? T : Mz) + 16 + 1 + 16 * cells_per_node;
+    case ELDER_K_JACOBIAN:  // J written (Krylov + multigrid copies), Dinv; p, c, bc, phi, K;
+                            // line factors: Dinv, L, U, bc read, zMi, zC written
+        return 108 * T + 108 * Mz + 4 * Td + 16 + 1 + 16 * cells_per_node +
+               (line ? 12 * Td + 8 * Mz + 1 : 0);
     }
     return 0.0;
 }
@@ -344,14 +352,17 @@ int prof_begin(elder_ctx* ctx, cudaStream_t st)
     return (int)P.pending.size() - 1;
 }
 
+// variant: for SMOOTH0 -1 = by the smoother in use, 2 = the factored z-line
+// sweep; for JACOBIAN 1 = with the line factorisation
 void prof_end(elder_ctx* ctx, int idx, int cls, const Grid& G, int T, int Mz, int samples,
-              cudaStream_t st)
+              cudaStream_t st, int variant = -1)
 {
     if (idx < 0) return;
     ProfRec& r = ctx->prof.pending[idx];
     CK(cudaEventRecord(r.b, st));
     r.cls = cls;
-    const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
+    int line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine ? 1 : 0;
+    if (variant >= 0) line = variant;
     r.bytes = model_bytes(cls, T, Mz, G, line) * G.N * samples;
     r.flops = model_flops(cls, G) * G.N * samples;
 }
@@ -429,6 +440,15 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap)
         }
         sv.Dinv.push_back(dalloc<B4<T>>(nN));
         sv.mem.add(sv.Dinv.back());
+        if (G.nz + 1 <= kMaxLine) {
+            sv.zMi.push_back(dalloc<B4<T>>(nN));
+            sv.mem.add(sv.zMi.back());
+            sv.zC.push_back(dalloc<B4<T>>(nN));
+            sv.mem.add(sv.zC.back());
+        } else {
+            sv.zMi.push_back(nullptr);
+            sv.zC.push_back(nullptr);
+        }
         for (auto* vec : {&sv.mb, &sv.mx, &sv.mx2, &sv.mr}) {
             vec->push_back(dalloc<V2<T>>(nN));
             sv.mem.add(vec->back());
@@ -464,21 +484,28 @@ void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
         const double* K = l == 0 ? K0 : ctx->K[l];
         const double* p = l == 0 ? p0 : ctx->pl[l];
         const double* c = l == 0 ? c0 : ctx->cl[l];
+        V2<T>* nodeT = reinterpret_cast<V2<T>*>(ctx->jn[l]);
+        V2<T>* cellT = reinterpret_cast<V2<T>*>(ctx->jc[l]);
         if (l > 0) {
             const double* pf = l == 1 ? p0 : ctx->pl[l - 1];
             const double* cf = l == 1 ? c0 : ctx->cl[l - 1];
-            launch_inject(ctx->grids[l - 1], G, pf, cf, ctx->pl[l], ctx->cl[l], mask,
-                          mstride, S, st);
+            launch_inject<T>(ctx->grids[l - 1], G, pf, cf, ctx->pl[l], ctx->cl[l], nodeT,
+                             ph.rho0 * ph.g, mask, mstride, S, st);
         }
         const int pi = prof_begin(ctx, st);
         using M = typename Solver<T>::M;
         B4<T>* JT = (l == 0 && !std::is_same<T, M>::value) ? sv.J0 : nullptr;
-        V2<T>* nodeT = reinterpret_cast<V2<T>*>(ctx->jin);
-        V2<T>* cellT = nodeT + (size_t)S * G.N;
+        // the cell inputs of every level were converted once for the step
+        // (average_coefficients); the coarse node inputs came with the
+        // injection, the finest level's are converted here
         launch_jacobian<T, M>(G, ph, ctx->bc[l], phi, K, p, c, JT, sv.Jm[l], sv.Dinv[l], cellT,
-                              nodeT, mask, mstride, S, st);
+                              nodeT, mask, mstride, S, st, l == 0 ? 1 : 2);
+        // the vertical lines' block-LU factors for the z-line sweeps
+        if (sv.zMi[l])
+            launch_zline_factor<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], sv.zMi[l], sv.zC[l],
+                                      mask, mstride, S, st);
         prof_end(ctx, pi, ELDER_K_JACOBIAN, G, JT ? (int)sizeof(T) : 0, (int)sizeof(M), n_active,
-                 st);
+                 st, sv.zMi[l] ? 1 : 0);
     }
     launch_coarse_inverse<typename Solver<T>::M>(ctx->grids.back(), ctx->bc.back(), sv.Jm.back(),
                                                  sv.work,
@@ -486,6 +513,9 @@ void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
     CKL();
 }
 
+// Coefficients of the coarse grids (cell averages) and the cell inputs of
+// every level's Jacobian in the assembly type T, once per step.
+template <class T>
 void average_coefficients(elder_ctx* ctx, int S, const double* phi0,
                           const double* K0, cudaStream_t st)
 {
@@ -495,6 +525,10 @@ void average_coefficients(elder_ctx* ctx, int S, const double* phi0,
         launch_average_cells(ctx->grids[l - 1], ctx->grids[l], pf, kf, ctx->phi[l],
                              ctx->K[l], ctx->cfg.coarse_K_harmonic, S, st);
     }
+    for (size_t l = 0; l < ctx->grids.size(); ++l)
+        launch_cell_inputs<T>(ctx->grids[l], ctx->cfg.mu, l == 0 ? phi0 : ctx->phi[l],
+                              l == 0 ? K0 : ctx->K[l], reinterpret_cast<V2<T>*>(ctx->jc[l]),
+                              S, st);
     CKL();
 }
 
@@ -522,8 +556,19 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     const int na = ctx->n_active_k;
     const int bs_sm = ctx->bs[ELDER_K_SMOOTH], bs_mr = ctx->bs[ELDER_K_MGRES];
     const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
+    // the non-transposed z-line sweep substitutes with the line factors of
+    // the assembly; the transposed one (adjoint solves) factors as it goes
+    const bool fact = line && !trans && sv.zMi[l];
     auto sweep = [&](const V2<T>* xin, V2<T>* xout) {
-        if (line && xin == nullptr) {
+        if (fact && xin == nullptr) {
+            launch_zline_apply<T, M>(G, sv.Jm[l], sv.zMi[l], sv.zC[l], ctx->bc[l], b, nullptr,
+                                     xout, ctx->omega_now, mask, KSTRIDE, S, st, 1);
+        } else if (fact) {
+            launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, xin, sv.mr[l], trans, mask,
+                                     KSTRIDE, S, st, bs_mr);
+            launch_zline_apply<T, M>(G, sv.Jm[l], sv.zMi[l], sv.zC[l], ctx->bc[l], sv.mr[l], xin,
+                                     xout, ctx->omega_now, mask, KSTRIDE, S, st, 2);
+        } else if (line && xin == nullptr) {
             launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout,
                                       ctx->omega_now, trans, mask, KSTRIDE, S, st, 1);
         } else if (line) {
@@ -539,7 +584,7 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     };
     int pi = prof_begin(ctx, st);
     sweep(nullptr, cur);
-    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), sizeof(M), na, st);
+    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), sizeof(M), na, st, fact ? 2 : -1);
     for (int q = 1; q < nu1; ++q) {
         pi = prof_begin(ctx, st);
         sweep(cur, oth);
@@ -915,7 +960,7 @@ bool build_step_graph(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi, c
                                cs));
         }
         launch_impose_dirichlet(G, ctx->bc[0], ctx->cval, p, c, S, cs);
-        average_coefficients(ctx, S, phi, K, cs);
+        average_coefficients<T>(ctx, S, phi, K, cs);
         k_newton_init<<<nblocks(S, 128), 128, 0, cs>>>(ns, S);
         count_launch(1);
         launch_residual(G, ph, ctx->bc[0], ctx->cval, phi, K, p, c, ctx->p_old, ctx->c_old,
@@ -1115,7 +1160,7 @@ int step_impl(elder_ctx* ctx, int S, const double* phi, const double* K, double*
         CK(cudaMemcpyAsync(c_hist, ctx->c_old, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     }
     launch_impose_dirichlet(G, ctx->bc[0], ctx->cval, p, c, S, st);
-    average_coefficients(ctx, S, phi, K, st);
+    average_coefficients<T>(ctx, S, phi, K, st);
     for (int s = 0; s < S; ++s) {
         NScal z;
         std::memset(&z, 0, sizeof(z));
@@ -1342,7 +1387,7 @@ int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const 
     const Grid& G = ctx->grids[0];
     const Phys ph = make_phys(ctx->cfg, dt);
     const size_t nN = (size_t)S * G.N;
-    average_coefficients(ctx, S, phi, K, st);
+    average_coefficients<T>(ctx, S, phi, K, st);
     assemble<T>(ctx, sv, S, phi, K, p, c, ph, nullptr, 0, S, st);
     const V2<double>* rhs2 = reinterpret_cast<const V2<double>*>(rhs);
     V2<double>* x2 = reinterpret_cast<V2<double>*>(x);
@@ -1602,8 +1647,12 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         ctx->qf = dalloc<QF>((size_t)S * 12 * G.C);
         ctx->mem.add(ctx->qf);
         // Jacobian inputs in the solver's arithmetic type, reused level by level
-        ctx->jin = dalloc<double>((size_t)S * 2 * (G.N + G.C));
-        ctx->mem.add(ctx->jin);
+        for (const Grid& Gl : ctx->grids) {
+            ctx->jn.push_back(dalloc<double>((size_t)S * 2 * Gl.N));
+            ctx->mem.add(ctx->jn.back());
+            ctx->jc.push_back(dalloc<double>((size_t)S * 2 * Gl.C));
+            ctx->mem.add(ctx->jc.back());
+        }
         ctx->mass = dalloc<double>((size_t)3 * S);
         ctx->mem.add(ctx->mass);
         CK(cudaMallocHost((void**)&ctx->h_mass, sizeof(double) * 3 * S));
@@ -1711,8 +1760,8 @@ int elder_jacobian(elder_ctx* ctx, int S, const double* phi, const double* K,
         return ELDER_EINVAL;
     }
     try {
-        V2<double>* nodeT = reinterpret_cast<V2<double>*>(ctx->jin);
-        V2<double>* cellT = nodeT + (size_t)S * ctx->grids[0].N;
+        V2<double>* nodeT = reinterpret_cast<V2<double>*>(ctx->jn[0]);
+        V2<double>* cellT = reinterpret_cast<V2<double>*>(ctx->jc[0]);
         launch_jacobian<double, double>(ctx->grids[0], make_phys(ctx->cfg, dt), ctx->bc[0], phi,
                                         K, p, c, reinterpret_cast<B4<double>*>(J), nullptr,
                                         nullptr, cellT, nodeT, nullptr, 0, S,
@@ -1987,7 +2036,7 @@ int elder_grad(elder_ctx* ctx, int n_steps, const double* phi, const double* K,
                 const double* uo = seg + 2 * N * (n - k0 - 1);
                 // J_n^T lambda_n = rhs (interior part; the Dirichlet rows of R_n
                 // neither depend on theta nor on u_{n-1}, so lambda_D is not needed)
-                average_coefficients(ctx, 1, phi, K, st);
+                average_coefficients<double>(ctx, 1, phi, K, st);
                 assemble<double>(ctx, sv, 1, phi, K, un, un + N, ph, nullptr, 0, 1, st);
                 CK(cudaMemcpyAsync(sv.b, rhs, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice,
                                    st));

@@ -88,13 +88,24 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
 // Jacobian rows as T (JT) and/or as the multigrid type M (JM), and the inverse
 // interior diagonal blocks (Dinv); null outputs are skipped.  cellT [S][C]
 // and nodeT [S][N] are scratch for the inputs converted to T.
+// inputs: 0 converts phi, K, p, c into cellT, nodeT first; 1 converts p, c
+// only (cellT holds the step's coefficients); 2 converts nothing (nodeT
+// written by launch_inject as well).
 template <class T, class M>
 void launch_jacobian(const Grid& G, const Phys& ph, const uint8_t* bc,
                      const double* phi, const double* K, const double* p,
                      const double* c, B4<T>* JT, B4<M>* JM, B4<T>* Dinv, V2<T>* cellT,
-                     V2<T>* nodeT, const int* mask, int mask_stride, int S, cudaStream_t st);
-void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf,
-                   const double* cf, double* pc, double* cc, const int* mask,
+                     V2<T>* nodeT, const int* mask, int mask_stride, int S, cudaStream_t st,
+                     int inputs = 0);
+// (phi, K / mu) in T for every cell of S samples
+template <class T>
+void launch_cell_inputs(const Grid& G, double mu, const double* phi, const double* K,
+                        V2<T>* cellT, int S, cudaStream_t st);
+// coarse state by injection; nodeT (nullable) receives the coarse Jacobian's
+// node inputs in T
+template <class T>
+void launch_inject(const Grid& Gf, const Grid& Gc, const double* pf, const double* cf,
+                   double* pc, double* cc, V2<T>* nodeT, double rho0g, const int* mask,
                    int mask_stride, int S, cudaStream_t st);
 void launch_average_cells(const Grid& Gf, const Grid& Gc, const double* phif,
                           const double* Kf, double* phic, double* Kc,
@@ -198,6 +209,20 @@ template <class T, class M>
 void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
                          const V2<T>* b, const V2<T>* x, V2<T>* xo, double omega, int trans,
                          const int* mask, int mstride, int S, cudaStream_t st, int mode);
+
+// Block-LU factors of the vertical lines of a level's (non-transposed)
+// operator, zMi and zC [S][N], and the line sweep that substitutes with
+// them (mode 1: x = 0; mode 2: r is the masked residual of x).  Lines of at
+// most kMaxLine nodes.
+template <class T, class M>
+void launch_zline_factor(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
+                         B4<T>* zMi, B4<T>* zC, const int* mask, int mstride, int S,
+                         cudaStream_t st);
+template <class T, class M>
+void launch_zline_apply(const Grid& G, const B4<M>* J, const B4<T>* zMi, const B4<T>* zC,
+                        const uint8_t* bc, const V2<T>* r, const V2<T>* x, V2<T>* xo,
+                        double omega, const int* mask, int mstride, int S, cudaStream_t st,
+                        int mode);
 
 // Keeps the iterate of smallest residual: copies x into xbest for the
 // samples whose last iteration improved it (keep == 1), or x <- xbest for

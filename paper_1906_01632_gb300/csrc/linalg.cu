@@ -434,6 +434,141 @@ void launch_smooth_zline(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const
 #undef ELDER_ZL
 }
 
+// Block-LU factors of the vertical lines of a level's operator, once per
+// assembly: for node k of a line, with M_0 = D_0 and M_k = D_k - L_k C_{k-1},
+// zMi = M_k^{-1} and zC = C_k = M_k^{-1} U_k (D the diagonal block, formed
+// as the inverse of the stored inverse Dinv exactly as the line sweep of
+// k_smooth_zline does; L, U the masked vertical line blocks).  Each line
+// sweep then only substitutes: the forward elimination and the inversions
+// leave the per-sweep work.
+template <class T, class M>
+__global__ void __launch_bounds__(kBS)
+    k_zline_factor(Grid G, const B4<M>* __restrict__ J, const B4<T>* __restrict__ Dinv,
+                   const uint8_t* __restrict__ bc, B4<T>* __restrict__ zMi,
+                   B4<T>* __restrict__ zC, const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int sz = (G.nx + 1) * (G.ny + 1);
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= sz) return;
+    const size_t on_ = (size_t)s * G.N;
+    const B4<M>* Js = J + (size_t)s * 27 * G.N;
+    const B4<M>* Jl = Js + (size_t)slot27(0, 0, -1) * G.N;
+    const B4<M>* Ju = Js + (size_t)slot27(0, 0, 1) * G.N;
+    B4<T> Cp{T(0), T(0), T(0), T(0)};
+    uint8_t bc_prev = 0;
+    for (int k = 0; k <= G.nz; ++k) {
+        const int n = col + k * sz;
+        const uint8_t mk = bc[n];
+        B4<T> Mk = inv2(Dinv[on_ + n]);
+        if (k > 0) {
+            const B4<T> L = mask_block(raw_line_block<T, M, false>(Jl[n]), mk, bc_prev);
+            const B4<T> LC = mul2(L, Cp);
+            Mk.pp -= LC.pp; Mk.pc -= LC.pc; Mk.cp -= LC.cp; Mk.cc -= LC.cc;
+        }
+        const B4<T> Mi = inv2(Mk);
+        zMi[on_ + n] = Mi;
+        if (k < G.nz) {
+            const uint8_t bn = bc[n + sz];
+            const B4<T> U = mask_block(raw_line_block<T, M, false>(Ju[n]), mk, bn);
+            Cp = mul2(Mi, U);
+            zC[on_ + n] = Cp;
+        }
+        bc_prev = mk;
+    }
+}
+
+template <class T, class M>
+void launch_zline_factor(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
+                         B4<T>* zMi, B4<T>* zC, const int* mask, int mstride, int S,
+                         cudaStream_t st)
+{
+    count_launch(1);
+    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1)), S);
+    k_zline_factor<T, M><<<grid, kBS, 0, st>>>(G, J, Dinv, bc, zMi, zC, mask, mstride);
+}
+
+// One damped z-line sweep with the factors of k_zline_factor (the
+// non-transposed operator): forward substitution g_k = zMi_k (r_k - L_k
+// g_{k-1}), g kept in x_out, then back substitution d_k = g_k - zC_k d_{k+1}
+// and x_out = x + omega d (x = 0 in MODE 1; in MODE 2 r is the masked
+// residual b - A x).  One thread per line; the loads of a node do not depend
+// on the recursion, so unrolled iterations keep several nodes in flight.
+template <class T, class M, int MODE>
+__global__ void __launch_bounds__(kBS)
+    k_zline_apply(Grid G, const B4<M>* __restrict__ J, const B4<T>* __restrict__ zMi,
+                  const B4<T>* __restrict__ zC, const uint8_t* __restrict__ bc,
+                  const V2<T>* __restrict__ r, const V2<T>* __restrict__ x, V2<T>* xo, T omega,
+                  const int* mask, int mstride)
+{
+    const int s = blockIdx.y;
+    if (!on(mask, mstride, s)) return;
+    const int sz = (G.nx + 1) * (G.ny + 1);
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= sz) return;
+    const size_t on_ = (size_t)s * G.N;
+    const B4<M>* Jl = J + (size_t)s * 27 * G.N + (size_t)slot27(0, 0, -1) * G.N;
+    r += on_;
+    zMi += on_;
+    zC += on_;
+    xo += on_;
+    V2<T> gp{T(0), T(0)};
+    uint8_t bc_prev = 0;
+#pragma unroll 4
+    for (int k = 0; k <= G.nz; ++k) {
+        const int n = col + k * sz;
+        const uint8_t mk = bc[n];
+        const V2<T> bv = r[n];
+        const B4<M> qL = Jl[k > 0 ? n : col];
+        const B4<T> Mi = zMi[n];
+        T rp = (mk & BC_P) ? T(0) : bv.p;
+        T rc = (mk & BC_C) ? T(0) : bv.c;
+        if (k > 0) {
+            const B4<T> L = mask_block(raw_line_block<T, M, false>(qL), mk, bc_prev);
+            rp -= L.pp * gp.p + L.pc * gp.c;
+            rc -= L.cp * gp.p + L.cc * gp.c;
+        }
+        gp = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
+        xo[n] = gp;
+        bc_prev = mk;
+    }
+    V2<T> d = gp;
+    const V2<T>* xs = (MODE == 1) ? nullptr : x + on_;
+#pragma unroll 4
+    for (int k = G.nz; k >= 0; --k) {
+        const int n = col + k * sz;
+        if (k < G.nz) {
+            const B4<T> C = zC[n];
+            const V2<T> g = xo[n];
+            d = V2<T>{g.p - (C.pp * d.p + C.pc * d.c), g.c - (C.cp * d.p + C.cc * d.c)};
+        }
+        V2<T> xn{T(0), T(0)};
+        if (MODE != 1) xn = xs[n];
+        T op = xn.p + omega * d.p, oc = xn.c + omega * d.c;
+        const uint8_t m = bc[n];
+        if (m & BC_P) op = T(0);
+        if (m & BC_C) oc = T(0);
+        xo[n] = V2<T>{op, oc};
+    }
+}
+
+template <class T, class M>
+void launch_zline_apply(const Grid& G, const B4<M>* J, const B4<T>* zMi, const B4<T>* zC,
+                        const uint8_t* bc, const V2<T>* r, const V2<T>* x, V2<T>* xo,
+                        double omega, const int* mask, int mstride, int S, cudaStream_t st,
+                        int mode)
+{
+    count_launch(1);
+    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), 128), S);
+    if (mode == 1)
+        k_zline_apply<T, M, 1><<<grid, 128, 0, st>>>(G, J, zMi, zC, bc, r, x, xo, T(omega), mask,
+                                                      mstride);
+    else
+        k_zline_apply<T, M, 2><<<grid, 128, 0, st>>>(G, J, zMi, zC, bc, r, x, xo, T(omega), mask,
+                                                      mstride);
+}
+
 template <class T, class M, bool TRANS>
 __global__ void __launch_bounds__(kMaxBS)
     k_mg_residual(Grid G, const B4<M>* __restrict__ J, const uint8_t* __restrict__ bc,
@@ -1370,6 +1505,13 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
     template void launch_smooth_zline<T, typename MgType<T>::type>(                      \
         const Grid&, const B4<typename MgType<T>::type>*, const B4<T>*, const uint8_t*,  \
         const V2<T>*, const V2<T>*, V2<T>*, double, int, const int*, int, int,           \
+        cudaStream_t, int);                                                              \
+    template void launch_zline_factor<T, typename MgType<T>::type>(                      \
+        const Grid&, const B4<typename MgType<T>::type>*, const B4<T>*, const uint8_t*,  \
+        B4<T>*, B4<T>*, const int*, int, int, cudaStream_t);                             \
+    template void launch_zline_apply<T, typename MgType<T>::type>(                       \
+        const Grid&, const B4<typename MgType<T>::type>*, const B4<T>*, const B4<T>*,    \
+        const uint8_t*, const V2<T>*, const V2<T>*, V2<T>*, double, const int*, int, int,\
         cudaStream_t, int);
 ELDER_INST(double)
 ELDER_INST(float)

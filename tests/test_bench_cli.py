@@ -35,7 +35,9 @@ def test_byte_model_matches_the_stored_formats():
     # mixed: bfloat16 multigrid matrices (108 entries x 2 B), FP32 vectors
     assert bench.E_model_bytes("mg_residual", 4, 64, 64, 16) == 108 * 2 + 6 * 4 + 1
     assert bench.E_model_bytes("spmv", 4, 64, 64, 16) == 108 * 4 + 6 * 4 + 1
-    assert bench.E_model_bytes("smooth0", 4, 64, 64, 16) == 8 * 4 + 1 + 8 * 2
+    # z-line sweep from x = 0 with the assembly's line factors: zMi, zC, b, x
+    # (FP32) and the lower line block (bfloat16)
+    assert bench.E_model_bytes("smooth0", 4, 64, 64, 16) == 12 * 4 + 4 * 2 + 1
     # FP64: every stored entry 8 B
     assert bench.E_model_bytes("spmv", 8, 64, 64, 16) == 108 * 8 + 6 * 8 + 1
 
