@@ -1350,6 +1350,7 @@ extern "C" int elder_residual_norms_static(const elder_config* cfg, int S, const
     G.hy = f.Ly / f.ny;
     G.hz = f.Lz / f.nz;
     G.Lz = f.Lz;
+    grid_set_divisors(G);
     const int nblk = nblocks(G.N);
     if (S > 65535) {  // samples run along grid.y
         set_static_error("elder_residual_norms_static: S exceeds 65535 samples per call");

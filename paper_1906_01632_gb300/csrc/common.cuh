@@ -12,12 +12,38 @@
 
 namespace elder {
 
+// Division of a 32-bit unsigned dividend by a fixed divisor d through a
+// multiply-high and two shifts (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Figure 4.1): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, the quotient is
+// (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n), exact for
+// every n < 2^32.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{(unsigned)m, l < 1 ? l : 1, l > 1 ? l - 1 : 0};
+}
+
 struct Grid {
     int nx, ny, nz;   // cells per direction
     int N, C;         // nodes, cells
     double hx, hy, hz;
     double Lz;
+    FastDiv d_row, d_plane;  // division by nx+1 and by (nx+1)(ny+1)
 };
+
+inline void grid_set_divisors(Grid& G)
+{
+    G.d_row = make_fastdiv((unsigned)(G.nx + 1));
+    G.d_plane = make_fastdiv((unsigned)((G.nx + 1) * (G.ny + 1)));
+}
 
 // Constants of Table 1 / eq. e_lin_density and the time step.
 struct Phys {
@@ -72,6 +98,23 @@ template <> __device__ __forceinline__ __nv_bfloat16 mg_store<__nv_bfloat16>(dou
 __host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
 {
     return i + (G.nx + 1) * (j + (G.ny + 1) * k);
+}
+
+__device__ __forceinline__ unsigned fastdiv(unsigned n, const FastDiv& f)
+{
+    const unsigned t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// node_ijk by the grid's multiply-high divisors (for the instruction-bound
+// transfer kernels)
+__device__ __forceinline__ void node_ijk_fast(const Grid& G, int n, int& i, int& j, int& k)
+{
+    const int nx1 = G.nx + 1;
+    k = (int)fastdiv((unsigned)n, G.d_plane);
+    const int r = n - k * nx1 * (G.ny + 1);
+    j = (int)fastdiv((unsigned)r, G.d_row);
+    i = r - j * nx1;
 }
 
 __device__ __forceinline__ void node_ijk(const Grid& G, int n, int& i, int& j,

@@ -126,6 +126,7 @@ Grid make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz)
     G.hy = Ly / ny;
     G.hz = Lz / nz;
     G.Lz = Lz;
+    grid_set_divisors(G);
     return G;
 }
 

@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kBS)
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= Gc.N) return;
     int I, J, K;
-    node_ijk(Gc, n, I, J, K);
+    node_ijk_fast(Gc, n, I, J, K);
     rf += (size_t)s * Gf.N;
     T sp = T(0), sc = T(0);
 #pragma unroll
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kBS)
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= Gf.N) return;
     int i, j, k;
-    node_ijk(Gf, n, i, j, k);
+    node_ijk_fast(Gf, n, i, j, k);
     xc += (size_t)s * Gc.N;
     // trilinear interpolation as three nested averages of the 8 coarse
     // parents; for an even fine index both parents are the same node, whose
