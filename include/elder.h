@@ -434,7 +434,9 @@ int elder_gpc_project(int M, int T, const int32_t* beta, int maxdeg, int Nq,
 /* Exceedance probability from the surrogate: for each listed node n
  * (nodes[k], or n = k for k < n_pts when nodes is NULL), the fraction of the
  * Ns points theta [Ns][M] at which sum_t coef[t][n] P_{beta_t}(theta) is
- * above threshold.  The surrogate is evaluated in FP32 (coefficients rounded
+ * above threshold.  On the tensor cores where the sizes allow it (see
+ * elder_gpc_exceed_engine), else on the CUDA cores: the surrogate evaluated
+ * in FP32 (coefficients rounded
  * to FP32, basis values by the FP32 Legendre recurrence, FP32 fused
  * multiply-adds in the order of t); its error is below about
  * 16 T 2^-24 sum_t |coef[t][n]| for degrees up to 8.  Device arrays:
@@ -446,6 +448,24 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N,
                      const double* coef, int n_pts, const int32_t* nodes, int Ns,
                      const double* theta, double threshold, double* p_exceed,
                      void* stream);
+
+/* elder_gpc_exceed with a choice of engine for the surrogate evaluation:
+ *  1: the FP32 evaluation described above (CUDA cores);
+ *  2: the tensor cores (M <= 4, maxdeg <= 8, T <= 36, else ELDER_EINVAL): the
+ *     values of a tile of 128 nodes at a chunk of 128 points are one TF32
+ *     matrix product (tcgen05) of the coefficients and the basis values, each
+ *     FP32 factor split as hi + lo with hi exact in TF32 and the product
+ *     formed as hi*hi + hi*lo + lo*hi with FP32 accumulation; its error stays
+ *     below the FP32 engine's bound 16 T 2^-24 sum_t |coef[t][n]| for
+ *     degrees up to 8.  Every internal wait of the kernel is bounded; if one
+ *     gives up, every p_exceed entry of the call is NaN (one error flag per
+ *     device: calls of this engine that overlap on the GPU race on it);
+ *  0: engine 2 where it applies, else engine 1 (what elder_gpc_exceed does).
+ * Other arguments as elder_gpc_exceed. */
+int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int maxdeg, int N,
+                            const double* coef, int n_pts, const int32_t* nodes, int Ns,
+                            const double* theta, double threshold, double* p_exceed,
+                            void* stream);
 
 #ifdef __cplusplus
 }

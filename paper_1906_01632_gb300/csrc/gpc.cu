@@ -198,13 +198,339 @@ __global__ void __launch_bounds__(kGpcBS)
         if (live[r] && count[r]) atomicAdd(cnt + kk[r], (unsigned long long)count[r]);
 }
 
-__global__ void k_gpc_counts_to_fraction(int n_pts, int Ns, double* p)
+// ---------------------------------------------------------------------------
+// Tensor-core evaluation of the surrogate count (sm_103a tcgen05).
+//
+// The surrogate values of a tile of 128 listed nodes at a chunk of 128
+// samples form the product U = C B of the node tile's coefficients C
+// (128 x T) and the chunk's basis values B (T x 128): a dense contraction,
+// run as a TF32 matrix product on the tensor cores with FP32 accumulators in
+// tensor memory.  Each FP32 factor x is split as x = x_hi + x_lo with x_hi
+// exactly representable in TF32 (the low 13 mantissa bits cleared), and the
+// three products C_hi B_hi + C_hi B_lo + C_lo B_hi are one product over the
+// stacked inner dimension K' = 3 TP (padded to a multiple of 8):
+//   A' = [C_hi | C_hi | C_lo] (128 x K'),  B' = [B_hi ; B_lo ; B_hi] (K' x 128).
+// The dropped C_lo B_lo and the TF32 rounding of the lo parts leave at most
+// 3 2^-20 |c| |P| per term; with the FP32 accumulation of the K'/8 partial
+// products the error stays below the FP32 path's bound 16 T 2^-24 sum |c|.
+//
+// One CTA: one node tile (A' in shared memory, loaded once) and a slice of
+// the samples in chunks of 128.  Warps 0-3 count (each thread owns one node
+// row of the accumulator and compares its 128 columns with the threshold
+// after a tcgen05.ld), warps 4-7 write each chunk's B' into one of two
+// shared-memory buffers, warp 8 issues the MMAs (one thread) into one of two
+// TMEM accumulators.  mbarriers hand the buffers over; every wait gives up
+// after a bounded number of polls, sets the error flag and lets the kernel
+// finish.
+//
+// Shared-memory operands use the no-swizzle K-major layout of 8-row x 16-byte
+// core matrices: element (row, k) at ((row / 8) * (K' / 4) + k / 4) * 128 +
+// (row % 8) * 16 + (k % 4) * 4 bytes; the stride between core matrices along
+// K is 128 B, along the rows K' / 4 * 128 B.
+// ---------------------------------------------------------------------------
+
+constexpr int kTcRows = 128;      // node rows per tile (MMA M)
+constexpr int kTcCols = 128;      // samples per chunk (MMA N)
+constexpr int kTcKp = 112;        // stacked inner dimension K' (3 x 36 + pad)
+constexpr int kTcTP = 36;         // terms per part (T <= 36)
+constexpr int kTcMaxM = 4;        // stochastic dimensions of the tensor-core path
+constexpr int kTcMaxDeg = 8;      // largest degree of the tensor-core path
+constexpr int kTcTileBytes = kTcRows * kTcKp * 4;  // 57344
+constexpr unsigned kTcPolls = 1u << 26;            // bound of every mbarrier wait
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+                 : "memory");
+}
+
+// Polls the barrier's phase of the given parity; false when it gave up (the
+// error flag is then set) or another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int* err,
+                                          volatile int* abort_flag)
+{
+    for (unsigned it = 0; it < kTcPolls; ++it) {
+        unsigned done = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 1023u) == 1023u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start, leading-dimension
+// (K-direction core-matrix stride) and stride-dimension (row-group stride)
+// byte offsets, each in 16-byte units, and the descriptor version bits.
+__device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, N = 128,
+// M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
+                              ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(unsigned d_tmem, uint64_t a, uint64_t b, unsigned acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes, one row per
+// thread.
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tc_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// x = hi + lo with hi exactly representable in TF32 (10 mantissa bits)
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo)
+{
+    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    lo = x - hi;
+}
+
+// byte offset of element (row, k) in the no-swizzle K-major operand layout
+__device__ __forceinline__ int tc_off(int row, int k)
+{
+    return ((row >> 3) * (kTcKp / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__global__ void __launch_bounds__(288, 1)
+    k_gpc_exceed_tc(int M, int T, const int32_t* __restrict__ beta, int maxdeg, int N,
+                    const double* __restrict__ coef, int n_pts, const int32_t* __restrict__ nodes,
+                    int Ns, const double* __restrict__ theta, float thr,
+                    unsigned long long* __restrict__ cnt, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* As = tc_smem;                           // A' tile
+    unsigned char* Bs0 = tc_smem + kTcTileBytes;           // B' chunk buffers
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(tc_smem + 3 * kTcTileBytes);  // 8 barriers
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 8);
+    int* bsm = reinterpret_cast<int*>(tmem_slot + 4);     // clamped multi-indices [T][M]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bsm + kTcTP * kTcMaxM);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile0 = blockIdx.x * kTcRows;
+    // this CTA's slice of the samples, whole chunks
+    const int nchunk_all = (Ns + kTcCols - 1) / kTcCols;
+    const int per = (nchunk_all + gridDim.y - 1) / gridDim.y;
+    const int c0 = blockIdx.y * per;
+    const int nchunk = max(0, min(nchunk_all, c0 + per) - c0);
+    // full[b], empty[b]: B' buffer b written / read by the MMAs;
+    // tfull[b], tempty[b]: accumulator b written by the MMAs / read out
+    const unsigned full0 = smem_u32(bars + 0), empty0 = smem_u32(bars + 2);
+    const unsigned tfull0 = smem_u32(bars + 4), tempty0 = smem_u32(bars + 6);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(full0 + 8 * b, 128);
+            mbar_init(empty0 + 8 * b, 1);
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 128);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = threadIdx.x; e < T * M; e += blockDim.x)
+        bsm[e] = min(max((int)beta[e], 0), maxdeg);
+    // A' = [C_hi | C_hi | C_lo], rows past n_pts and terms past T zero
+    for (int e = threadIdx.x; e < kTcRows * kTcKp; e += blockDim.x) {
+        const int row = e / kTcKp, k = e - row * kTcKp;
+        const int part = k / kTcTP, t = k - part * kTcTP;
+        float v = 0.f;
+        const int kk = tile0 + row;
+        if (part < 3 && t < T && kk < n_pts) {
+            const int n = nodes ? nodes[kk] : kk;
+            float hi, lo;
+            tf32_split((float)coef[(size_t)t * N + n], hi, lo);
+            v = part < 2 ? hi : lo;
+        }
+        *reinterpret_cast<float*>(As + tc_off(row, k)) = v;
+    }
+    fence_async_shared();
+    if (warp == 0) {  // two accumulators of 128 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                         smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+    if (warp < 4) {
+        // ---- counting: thread <-> node row 32 warp + lane ----
+        unsigned count = 0;
+        const int row = 32 * warp + lane;
+        for (int i = 0; i < nchunk; ++i) {
+            const int b = i & 1;
+            if (!mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, abort_flag)) break;
+            tc_fence_after();
+            const int valid = min(kTcCols, Ns - (c0 + i) * kTcCols);
+            const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(b * kTcCols);
+#pragma unroll
+            for (int h = 0; h < kTcCols; h += 64) {
+                float v0[32], v1[32];
+                tc_ld32(ta + h, v0);
+                tc_ld32(ta + h + 32, v1);
+                tc_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    count += (h + q < valid && v0[q] > thr) ? 1u : 0u;
+                    count += (h + 32 + q < valid && v1[q] > thr) ? 1u : 0u;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty0 + 8 * b);
+        }
+        const int kk = tile0 + row;
+        if (kk < n_pts && count) atomicAdd(cnt + kk, (unsigned long long)count);
+    } else if (warp < 8) {
+        // ---- B' chunks: thread <-> sample column ----
+        const int col = threadIdx.x - 128;
+        for (int i = 0; i < nchunk; ++i) {
+            const int b = i & 1;
+            unsigned char* Bs = Bs0 + b * kTcTileBytes;
+            if (i >= 2 && !mbar_wait(empty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
+            const int j = (c0 + i) * kTcCols + col;
+            float P[kTcMaxM][kTcMaxDeg + 1];
+            const bool ok = j < Ns;
+#pragma unroll
+            for (int m = 0; m < kTcMaxM; ++m) {
+                const float x = (ok && m < M) ? (float)theta[(size_t)j * M + m] : 0.f;
+                P[m][0] = 1.f;
+                P[m][1] = x;
+#pragma unroll
+                for (int k = 1; k < kTcMaxDeg; ++k)
+                    P[m][k + 1] = ((2 * k + 1) * x * P[m][k] - k * P[m][k - 1]) / (k + 1);
+            }
+            for (int t = 0; t < kTcTP; ++t) {
+                float v = 0.f;
+                if (ok && t < T) {
+                    v = 1.f;
+#pragma unroll
+                    for (int m = 0; m < kTcMaxM; ++m) {
+                        if (m < M) {
+                            const int d = bsm[t * M + m];
+                            float pv = P[m][0];
+#pragma unroll
+                            for (int k = 1; k <= kTcMaxDeg; ++k) pv = (k == d) ? P[m][k] : pv;
+                            v *= pv;
+                        }
+                    }
+                }
+                float hi, lo;
+                tf32_split(v, hi, lo);
+                *reinterpret_cast<float*>(Bs + tc_off(col, t)) = hi;
+                *reinterpret_cast<float*>(Bs + tc_off(col, kTcTP + t)) = lo;
+                *reinterpret_cast<float*>(Bs + tc_off(col, 2 * kTcTP + t)) = hi;
+            }
+            for (int k = 3 * kTcTP; k < kTcKp; ++k) *reinterpret_cast<float*>(Bs + tc_off(col, k)) = 0.f;
+            fence_async_shared();
+            mbar_arrive(full0 + 8 * b);
+        }
+    } else if (lane == 0) {
+        // ---- MMA issue ----
+        const unsigned a_base = smem_u32(As);
+        constexpr unsigned kLbo = 128, kSbo = (kTcKp / 4) * 128;
+        for (int i = 0; i < nchunk; ++i) {
+            const int b = i & 1;
+            if (!mbar_wait(full0 + 8 * b, (i >> 1) & 1, err, abort_flag)) break;
+            if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
+            tc_fence_after();
+            const unsigned b_base = smem_u32(Bs0 + b * kTcTileBytes);
+            const unsigned d = tmem + (unsigned)(b * kTcCols);
+#pragma unroll
+            for (int ks = 0; ks < kTcKp / 8; ++ks)
+                tc_mma(d, tc_desc(a_base + ks * 256, kLbo, kSbo), tc_desc(b_base + ks * 256, kLbo, kSbo),
+                       ks > 0 ? 1u : 0u);
+            tc_commit(empty0 + 8 * b);
+            tc_commit(tfull0 + 8 * b);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+}
+
+// Set by a tensor-core count whose bounded wait gave up (one flag per
+// device, cleared by each call before its kernel).
+__device__ int g_gpc_tc_err;
+
+__global__ void k_gpc_counts_to_fraction(int n_pts, int Ns, double* p, const int* err)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_pts) return;
     unsigned long long c;
     memcpy(&c, p + k, sizeof(c));
-    p[k] = (double)c / (double)Ns;
+    p[k] = (err && *err) ? __longlong_as_double(0x7FF8000000000000ll) : (double)c / (double)Ns;
 }
 
 int round_tp(int T) { return T <= 8 ? 8 : T <= 16 ? 16 : T <= 24 ? 24 : T <= 32 ? 32 : T <= 40 ? 40 : T <= 48 ? 48 : T <= 56 ? 56 : 64; }
@@ -335,16 +661,24 @@ int elder_gpc_project(int M, int T, const int32_t* beta, int maxdeg, int Nq, con
     return ELDER_OK;
 }
 
-int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const double* coef,
-                     int n_pts, const int32_t* nodes, int Ns, const double* theta,
-                     double threshold, double* p_exceed, void* stream)
+int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int maxdeg, int N,
+                            const double* coef, int n_pts, const int32_t* nodes, int Ns,
+                            const double* theta, double threshold, double* p_exceed,
+                            void* stream)
 {
     if (M < 1 || M > kGpcMaxM || T < 1 || T > 64 || maxdeg < 0 || maxdeg > kGpcMaxDeg ||
         N < 1 || n_pts < 1 || (!nodes && n_pts > N) || Ns < 1 || !beta || !coef || !theta ||
-        !p_exceed) {
+        !p_exceed || engine < 0 || engine > 2) {
         set_static_error("elder_gpc_exceed: bad argument");
         return ELDER_EINVAL;
     }
+    const bool tc_ok = M <= kTcMaxM && maxdeg <= kTcMaxDeg && T <= kTcTP;
+    if (engine == 2 && !tc_ok) {
+        set_static_error("elder_gpc_exceed: the tensor-core count needs M <= 4, maxdeg <= 8, "
+                         "T <= 36");
+        return ELDER_EINVAL;
+    }
+    const bool use_tc = engine == 2 || (engine == 0 && tc_ok);
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(p_exceed);
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * n_pts, st);
@@ -355,18 +689,43 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int TP = (T + 3) / 4 * 4;       // terms padded to a multiple of 4
-    const int NPT = TP <= 36 ? 4 : 2;     // listed nodes per thread
-    const int gx = (n_pts + NPT * kGpcBS - 1) / (NPT * kGpcBS);
-    // enough sample slices to give every SM several blocks, at least one
-    // chunk per slice
-    int gy = std::max(1, (8 * sms + gx - 1) / gx);
-    gy = std::min(gy, std::max(1, (Ns + kGpcChunk - 1) / kGpcChunk));
-    gy = std::min(gy, 65535);
-    dim3 grid(gx, gy);
     const float thr = (float)threshold;
-    const size_t smem = sizeof(float) * ((size_t)kGpcChunk * TP + (size_t)kGpcChunk * M * (maxdeg + 1)) +
-                        sizeof(int) * (size_t)T * M;
+    int* err = nullptr;
+    if (use_tc) {
+        void* ep = nullptr;
+        e = cudaGetSymbolAddress(&ep, g_gpc_tc_err);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ep, 0, sizeof(int), st);
+        if (e != cudaSuccess) {
+            set_static_error(cudaGetErrorString(e));
+            return ELDER_ECUDA;
+        }
+        err = static_cast<int*>(ep);
+        const int gx = (n_pts + kTcRows - 1) / kTcRows;
+        const int nchunk = (Ns + kTcCols - 1) / kTcCols;
+        // several CTAs per SM over the whole grid (one CTA fits an SM)
+        int gy = std::max(1, (8 * sms + gx - 1) / gx);
+        gy = std::min(std::min(gy, nchunk), 65535);
+        const size_t smem = 3 * (size_t)kTcTileBytes + 8 * sizeof(unsigned long long) +
+                            4 * sizeof(unsigned) + sizeof(int) * (kTcTP * kTcMaxM + 4);
+        e = cudaFuncSetAttribute(k_gpc_exceed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess) {
+            k_gpc_exceed_tc<<<dim3(gx, gy), 288, smem, st>>>(M, T, beta, maxdeg, N, coef, n_pts,
+                                                             nodes, Ns, theta, thr, cnt, err);
+            count_launch(1);
+        }
+    } else {
+        const int TP = (T + 3) / 4 * 4;       // terms padded to a multiple of 4
+        const int NPT = TP <= 36 ? 4 : 2;     // listed nodes per thread
+        const int gx = (n_pts + NPT * kGpcBS - 1) / (NPT * kGpcBS);
+        // enough sample slices to give every SM several blocks, at least one
+        // chunk per slice
+        int gy = std::max(1, (8 * sms + gx - 1) / gx);
+        gy = std::min(gy, std::max(1, (Ns + kGpcChunk - 1) / kGpcChunk));
+        gy = std::min(gy, 65535);
+        dim3 grid(gx, gy);
+        const size_t smem = sizeof(float) * ((size_t)kGpcChunk * TP + (size_t)kGpcChunk * M * (maxdeg + 1)) +
+                            sizeof(int) * (size_t)T * M;
 #define ELDER_GPC_EXC(TPV, NPTV)                                                                   \
     do {                                                                                           \
         cudaFuncSetAttribute(k_gpc_exceed<TPV, NPTV, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -374,33 +733,43 @@ int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const
         k_gpc_exceed<TPV, NPTV, 4><<<grid, kGpcBS, smem, st>>>(M, T, beta, N, coef, n_pts, nodes, Ns, \
                                                             theta, thr, maxdeg, cnt);              \
     } while (0)
-    switch (TP) {
-        case 4: ELDER_GPC_EXC(4, 4); break;
-        case 8: ELDER_GPC_EXC(8, 4); break;
-        case 12: ELDER_GPC_EXC(12, 4); break;
-        case 16: ELDER_GPC_EXC(16, 4); break;
-        case 20: ELDER_GPC_EXC(20, 4); break;
-        case 24: ELDER_GPC_EXC(24, 4); break;
-        case 28: ELDER_GPC_EXC(28, 4); break;
-        case 32: ELDER_GPC_EXC(32, 4); break;
-        case 36: ELDER_GPC_EXC(36, 4); break;
-        case 40: ELDER_GPC_EXC(40, 2); break;
-        case 44: ELDER_GPC_EXC(44, 2); break;
-        case 48: ELDER_GPC_EXC(48, 2); break;
-        case 52: ELDER_GPC_EXC(52, 2); break;
-        case 56: ELDER_GPC_EXC(56, 2); break;
-        case 60: ELDER_GPC_EXC(60, 2); break;
-        default: ELDER_GPC_EXC(64, 2); break;
-    }
+        switch (TP) {
+            case 4: ELDER_GPC_EXC(4, 4); break;
+            case 8: ELDER_GPC_EXC(8, 4); break;
+            case 12: ELDER_GPC_EXC(12, 4); break;
+            case 16: ELDER_GPC_EXC(16, 4); break;
+            case 20: ELDER_GPC_EXC(20, 4); break;
+            case 24: ELDER_GPC_EXC(24, 4); break;
+            case 28: ELDER_GPC_EXC(28, 4); break;
+            case 32: ELDER_GPC_EXC(32, 4); break;
+            case 36: ELDER_GPC_EXC(36, 4); break;
+            case 40: ELDER_GPC_EXC(40, 2); break;
+            case 44: ELDER_GPC_EXC(44, 2); break;
+            case 48: ELDER_GPC_EXC(48, 2); break;
+            case 52: ELDER_GPC_EXC(52, 2); break;
+            case 56: ELDER_GPC_EXC(56, 2); break;
+            case 60: ELDER_GPC_EXC(60, 2); break;
+            default: ELDER_GPC_EXC(64, 2); break;
+        }
 #undef ELDER_GPC_EXC
-    k_gpc_counts_to_fraction<<<(n_pts + 255) / 256, 256, 0, st>>>(n_pts, Ns, p_exceed);
-    count_launch(2);
-    e = cudaGetLastError();
+        count_launch(1);
+    }
+    k_gpc_counts_to_fraction<<<(n_pts + 255) / 256, 256, 0, st>>>(n_pts, Ns, p_exceed, err);
+    count_launch(1);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_static_error(cudaGetErrorString(e));
         return ELDER_ECUDA;
     }
     return ELDER_OK;
+}
+
+int elder_gpc_exceed(int M, int T, const int32_t* beta, int maxdeg, int N, const double* coef,
+                     int n_pts, const int32_t* nodes, int Ns, const double* theta,
+                     double threshold, double* p_exceed, void* stream)
+{
+    return elder_gpc_exceed_engine(0, M, T, beta, maxdeg, N, coef, n_pts, nodes, Ns, theta,
+                                   threshold, p_exceed, stream);
 }
 
 }  // extern "C"

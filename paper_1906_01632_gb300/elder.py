@@ -111,6 +111,8 @@ def _load():
     lib.elder_gpc_project.argtypes = [ip, ip, vp, ip, ip, vp, vp, ip, vp, vp, vp, vp, vp]
     lib.elder_gpc_exceed.argtypes = [ip, ip, vp, ip, ip, vp, ip, vp, ip, vp, ctypes.c_double,
                                      vp, vp]
+    lib.elder_gpc_exceed_engine.argtypes = [ip, ip, ip, vp, ip, ip, vp, ip, vp, ip, vp,
+                                            ctypes.c_double, vp, vp]
     del dp
     return lib
 
@@ -427,20 +429,30 @@ def elder_gpc_project(beta: torch.Tensor, theta: torch.Tensor, w: torch.Tensor, 
     return coef, mean, var
 
 
+GPC_ENGINES = {"auto": 0, "fp32": 1, "tensor": 2}
+
+
 def elder_gpc_exceed(beta: torch.Tensor, coef: torch.Tensor, theta: torch.Tensor,
-                     threshold: float, nodes: torch.Tensor | None = None, out=None, stream=None):
+                     threshold: float, nodes: torch.Tensor | None = None, out=None, stream=None,
+                     engine: str = "auto"):
     """P(u_hat > threshold) per node from the surrogate at the sample points
-    theta [Ns, M] (all N nodes, or the int32 node list)."""
+    theta [Ns, M] (all N nodes, or the int32 node list); engine "auto", "fp32"
+    (CUDA cores) or "tensor" (tcgen05 TF32 split product)."""
     T, M = beta.shape
     N = coef.shape[1]
     n_pts = N if nodes is None else nodes.numel()
     maxdeg = int(beta.max().item()) if beta.numel() else 0
     out = out if out is not None else torch.empty(n_pts, dtype=torch.float64, device=coef.device)
-    _static_check(_lib.elder_gpc_exceed(M, T, _iptr(beta, "beta"), maxdeg, N, _ptr(coef, "coef"),
-                                        n_pts, _iptr(nodes, "nodes"), theta.shape[0],
-                                        _ptr(theta, "theta"), float(threshold), _ptr(out, "out"),
-                                        _stream(stream)))
+    _static_check(_lib.elder_gpc_exceed_engine(GPC_ENGINES[engine], M, T, _iptr(beta, "beta"),
+                                               maxdeg, N, _ptr(coef, "coef"), n_pts,
+                                               _iptr(nodes, "nodes"), theta.shape[0],
+                                               _ptr(theta, "theta"), float(threshold),
+                                               _ptr(out, "out"), _stream(stream)))
     return out
+
+
+def elder_gpc_exceed_engine(engine: str, *a, **k):
+    return elder_gpc_exceed(*a, engine=engine, **k)
 
 
 def elder_initial_state(ctx: Elder, *a, **k):

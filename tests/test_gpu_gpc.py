@@ -50,9 +50,9 @@ def test_projection_matches_oracle(E, M, p, q, N):
     assert np.abs(var.cpu().numpy() - v_ref).max() < 1e-14
 
 
-def _bracket_check(E, beta, coef, theta, thr, nodes=None):
+def _bracket_check(E, beta, coef, theta, thr, nodes=None, engine="auto"):
     cg = E.elder_gpc_exceed(Ti(beta), Td(coef), Td(theta), thr,
-                            None if nodes is None else Ti(nodes)).cpu().numpy()
+                            None if nodes is None else Ti(nodes), engine=engine).cpu().numpy()
     sel = coef if nodes is None else coef[:, nodes]
     Ns = theta.shape[0]
     delta = 16 * beta.shape[0] * 2.0**-24 * np.abs(sel).sum(0)
@@ -67,8 +67,10 @@ def _bracket_check(E, beta, coef, theta, thr, nodes=None):
 
 # (3, 4): 35 terms (the bench's surrogate, padded to 36, 4 nodes per thread);
 # (3, 3): 20 terms; (3, 5) and (5, 3): 56 terms (2 nodes per thread)
-@pytest.mark.parametrize("M,p", [(3, 4), (3, 3), (3, 5), (5, 3)])
-def test_exceedance_brackets_oracle(E, M, p):
+@pytest.mark.parametrize("M,p,engine", [(3, 4, "fp32"), (3, 3, "fp32"), (3, 5, "fp32"),
+                                        (5, 3, "fp32"), (3, 4, "tensor"), (3, 3, "tensor"),
+                                        (2, 6, "tensor"), (4, 2, "tensor"), (3, 5, "auto")])
+def test_exceedance_brackets_oracle(E, M, p, engine):
     beta = G.multi_indices(M, p)
     rng = np.random.default_rng(7 + 10 * M + p)
     N = 300
@@ -77,10 +79,13 @@ def test_exceedance_brackets_oracle(E, M, p):
     coef = rng.standard_normal((beta.shape[0], N)) * (0.3 ** deg)[:, None]
     coef[0] = rng.uniform(0.3, 0.7, N)
     theta = rng.uniform(-1, 1, (20011, M))  # ragged: not a multiple of the chunk
-    got, lo, hi = _bracket_check(E, beta, coef, theta, 0.5)
+    got, lo, hi = _bracket_check(E, beta, coef, theta, 0.5, engine=engine)
     assert (hi - lo).max() <= 24  # the FP32 band holds at most a few samples
     nodes = np.array([5, 0, 299, 17, 17, 123], dtype=np.int32)
-    _bracket_check(E, beta, coef, theta, 0.5, nodes)
+    _bracket_check(E, beta, coef, theta, 0.5, nodes, engine=engine)
+    if engine == "tensor":  # the two engines agree but for samples inside the band
+        cf = E.elder_gpc_exceed(Ti(beta), Td(coef), Td(theta), 0.5, engine="fp32").cpu().numpy()
+        assert np.abs(np.rint(cf * theta.shape[0]) - got).max() <= (hi - lo).max()
 
 
 def test_exceedance_closed_form(E):
@@ -95,8 +100,9 @@ def test_exceedance_closed_form(E):
     K = 100000
     g = -1 + (np.arange(K) + 0.5) * 2 / K
     theta = np.stack([g, np.zeros(K)], 1)
-    pe = E.elder_gpc_exceed(Ti(beta), Td(coef), Td(theta), 0.3).cpu().numpy()
-    assert pe[0] == 0.35 and pe[1] == 0.0 and pe[2] == 1.0
+    for engine in ("fp32", "tensor"):
+        pe = E.elder_gpc_exceed(Ti(beta), Td(coef), Td(theta), 0.3, engine=engine).cpu().numpy()
+        assert pe[0] == 0.35 and pe[1] == 0.0 and pe[2] == 1.0, engine
 
 
 def test_surrogate_workflow_matches_oracle_and_qmc(E):
@@ -143,3 +149,32 @@ def test_surrogate_workflow_matches_oracle_and_qmc(E):
         assert (st == 0).all()
     qmc_mean = cq.reshape(Sq, -1).mean(0).cpu().numpy()
     assert np.abs(mean.cpu().numpy() - qmc_mean).max() < 5e-3
+
+
+def test_tensor_engine_many_tiles_and_slices(E):
+    """The tensor-core count at a size with many node tiles (1,000 nodes: 8
+    tiles, the last ragged) and many sample chunks per CTA (300,017 points,
+    the last chunk ragged), against the FP32 engine and the oracle bracket at
+    sampled nodes; nodes listed in reverse order."""
+    beta = G.multi_indices(3, 4)
+    rng = np.random.default_rng(99)
+    N = 1000
+    deg = beta.sum(1)
+    coef = rng.standard_normal((beta.shape[0], N)) * (0.3 ** deg)[:, None]
+    coef[0] = rng.uniform(0.3, 0.7, N)
+    theta = rng.uniform(-1, 1, (300017, 3))
+    nodes = np.arange(N - 1, -1, -1).astype(np.int32)
+    tc = E.elder_gpc_exceed(Ti(beta), Td(coef), Td(theta), 0.5, Ti(nodes), engine="tensor")
+    f32 = E.elder_gpc_exceed(Ti(beta), Td(coef), Td(theta), 0.5, Ti(nodes), engine="fp32")
+    tc, f32 = tc.cpu().numpy(), f32.cpu().numpy()
+    assert np.isfinite(tc).all()
+    Ns = theta.shape[0]
+    assert np.abs(np.rint(tc * Ns) - np.rint(f32 * Ns)).max() <= 24
+    pick = np.array([0, 1, 127, 128, 500, 998, 999])
+    sub = coef[:, nodes[pick]]
+    vals = G.evaluate(sub, beta, theta)
+    delta = 16 * beta.shape[0] * 2.0**-24 * np.abs(sub).sum(0)
+    lo = (vals > 0.5 + delta).sum(0)
+    hi = (vals > 0.5 - delta).sum(0)
+    got = np.rint(tc[pick] * Ns)
+    assert ((got >= lo) & (got <= hi)).all()
