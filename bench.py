@@ -620,13 +620,27 @@ def gpc_timings(E, torch, cfield, stream, Ns=1_000_000, apk=None):
     gen = torch.Generator(device=dev).manual_seed(5)
     theta_s = (torch.rand(Ns, M, generator=gen, dtype=torch.float64, device=dev) * 2 - 1).contiguous()
     coef, mean, var = E.elder_gpc_project(beta, theta_q, wt, u)
-    out = E.elder_gpc_exceed(beta, coef, theta_s, 0.5)
+    out = E.elder_gpc_exceed(beta, coef, theta_s, 0.5, engine="tensor")
+    out32 = E.elder_gpc_exceed(beta, coef, theta_s, 0.5, engine="fp32")
     torch.cuda.synchronize()
+    # the two engines' counts differ only for samples inside the FP32 band
+    engines_max_count_diff = int(((out - out32).abs() * Ns).round().max().item())
+    # tensor-core rate: TF32 dense peak from the measured bf16 GEMM peak and
+    # the nominal TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s); the product runs
+    # over the stacked inner dimension 112 for 128-node tiles and 128-point
+    # chunks
+    peaks = measured_peaks()
+    tf32_peak = (peaks["bf16_tflops"] * 1e3 if peaks else 1.9e6) * 1.1 / 2.25
+    mma_flops = 2.0 * 112 * (-(-N // 128) * 128) * (-(-Ns // 128) * 128)
     res = {}
     for name, fn, flops, unit_peak in (
             ("project", lambda: E.elder_gpc_project(beta, theta_q, wt, u, coef, mean, var),
              2.0 * T * Nq * N, (apk["fp64"][1], apk["fp64"][0])),
-            ("exceed", lambda: E.elder_gpc_exceed(beta, coef, theta_s, 0.5, out=out),
+            ("exceed", lambda: E.elder_gpc_exceed(beta, coef, theta_s, 0.5, out=out,
+                                                  engine="tensor"),
+             mma_flops, ("TF32 dense tensor peak: measured bf16 GEMM x 1.1/2.25", tf32_peak)),
+            ("exceed_fp32", lambda: E.elder_gpc_exceed(beta, coef, theta_s, 0.5, out=out32,
+                                                       engine="fp32"),
              2.0 * T * Ns * N, (apk["fp32"][1], apk["fp32"][0]))):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -638,10 +652,16 @@ def gpc_timings(E, torch, cfield, stream, Ns=1_000_000, apk=None):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         gf = flops / 1e9 / (ms / 1e3)
-        res[name] = {"ms": ms, "GFLOP/s": gf, "bound": "alu", "peak_GFLOP/s": unit_peak[1],
-                     "peak_source": unit_peak[0], "frac": gf / unit_peak[1]}
+        res[name] = {"ms": ms, "GFLOP/s": gf, "bound": "tensor" if name == "exceed" else "alu",
+                     "peak_GFLOP/s": unit_peak[1], "peak_source": unit_peak[0],
+                     "frac": gf / unit_peak[1]}
+    res["exceed"]["fp32_equivalent_GFLOP/s"] = 2.0 * T * Ns * N / 1e9 / (res["exceed"]["ms"] / 1e3)
+    res["exceed"]["engines_max_count_diff"] = engines_max_count_diff
     res["config"] = {"M": M, "order": p, "terms": T, "quadrature_points": Nq, "nodes": N,
-                     "surrogate_samples": Ns}
+                     "surrogate_samples": Ns,
+                     "exceed": "tcgen05 TF32 split product (hi*hi + hi*lo + lo*hi), FLOPs of "
+                               "the stacked product (inner dimension 112); exceed_fp32: the "
+                               "CUDA-core FP32 engine, FLOPs 2 T per node and point"}
     return res
 
 
