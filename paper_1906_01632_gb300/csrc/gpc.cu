@@ -374,6 +374,8 @@ __global__ void __launch_bounds__(288, 1)
     unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 8);
     int* bsm = reinterpret_cast<int*>(tmem_slot + 4);     // clamped multi-indices [T][M]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bsm + kTcTP * kTcMaxM);
+    // Legendre values of a chunk, [m][k][sample]
+    float* ptab = reinterpret_cast<float*>(tc_smem + 3 * kTcTileBytes + 1024);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile0 = blockIdx.x * kTcRows;
     // this CTA's slice of the samples, whole chunks
@@ -411,6 +413,12 @@ __global__ void __launch_bounds__(288, 1)
         }
         *reinterpret_cast<float*>(As + tc_off(row, k)) = v;
     }
+    // the inner-dimension padding of both B' buffers stays zero
+    for (int e = threadIdx.x; e < 2 * kTcCols; e += blockDim.x) {
+        unsigned char* Bs = Bs0 + (e / kTcCols) * kTcTileBytes;
+        *reinterpret_cast<float4*>(Bs + tc_off(e % kTcCols, 3 * kTcTP)) =
+            make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     fence_async_shared();
     if (warp == 0) {  // two accumulators of 128 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
@@ -438,10 +446,15 @@ __global__ void __launch_bounds__(288, 1)
                 tc_ld32(ta + h, v0);
                 tc_ld32(ta + h + 32, v1);
                 tc_wait_ld();
+                if (valid == kTcCols) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    count += (h + q < valid && v0[q] > thr) ? 1u : 0u;
-                    count += (h + 32 + q < valid && v1[q] > thr) ? 1u : 0u;
+                    for (int q = 0; q < 32; ++q) count += (v0[q] > thr) + (v1[q] > thr);
+                } else {  // the last, ragged chunk
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        count += (h + q < valid && v0[q] > thr) ? 1u : 0u;
+                        count += (h + 32 + q < valid && v1[q] > thr) ? 1u : 0u;
+                    }
                 }
             }
             tc_fence_before();
@@ -451,45 +464,59 @@ __global__ void __launch_bounds__(288, 1)
         if (kk < n_pts && count) atomicAdd(cnt + kk, (unsigned long long)count);
     } else if (warp < 8) {
         // ---- B' chunks: thread <-> sample column ----
+        // Legendre values of the chunk's samples, Ptab[(m * 9 + k) * 128 + col]
+        // (consecutive threads, consecutive words), then per group of 4 terms
+        // the basis products, split and stored as one 16-byte row segment of
+        // a core matrix in each of the three parts
         const int col = threadIdx.x - 128;
         for (int i = 0; i < nchunk; ++i) {
             const int b = i & 1;
             unsigned char* Bs = Bs0 + b * kTcTileBytes;
             if (i >= 2 && !mbar_wait(empty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
             const int j = (c0 + i) * kTcCols + col;
-            float P[kTcMaxM][kTcMaxDeg + 1];
             const bool ok = j < Ns;
 #pragma unroll
             for (int m = 0; m < kTcMaxM; ++m) {
-                const float x = (ok && m < M) ? (float)theta[(size_t)j * M + m] : 0.f;
-                P[m][0] = 1.f;
-                P[m][1] = x;
+                if (m < M) {
+                    const float x = ok ? (float)theta[(size_t)j * M + m] : 0.f;
+                    float pm1 = 1.f, p0 = x;
+                    ptab[(m * (kTcMaxDeg + 1)) * kTcCols + col] = 1.f;
+                    if (maxdeg >= 1) ptab[(m * (kTcMaxDeg + 1) + 1) * kTcCols + col] = x;
+                    // (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} with the ratios
+                    // folded into constants
 #pragma unroll
-                for (int k = 1; k < kTcMaxDeg; ++k)
-                    P[m][k + 1] = ((2 * k + 1) * x * P[m][k] - k * P[m][k - 1]) / (k + 1);
-            }
-            for (int t = 0; t < kTcTP; ++t) {
-                float v = 0.f;
-                if (ok && t < T) {
-                    v = 1.f;
-#pragma unroll
-                    for (int m = 0; m < kTcMaxM; ++m) {
-                        if (m < M) {
-                            const int d = bsm[t * M + m];
-                            float pv = P[m][0];
-#pragma unroll
-                            for (int k = 1; k <= kTcMaxDeg; ++k) pv = (k == d) ? P[m][k] : pv;
-                            v *= pv;
+                    for (int k = 1; k < kTcMaxDeg; ++k) {
+                        if (k < maxdeg) {
+                            const float p1 = (float(2 * k + 1) / float(k + 1)) * x * p0 -
+                                             (float(k) / float(k + 1)) * pm1;
+                            ptab[(m * (kTcMaxDeg + 1) + k + 1) * kTcCols + col] = p1;
+                            pm1 = p0;
+                            p0 = p1;
                         }
                     }
                 }
-                float hi, lo;
-                tf32_split(v, hi, lo);
-                *reinterpret_cast<float*>(Bs + tc_off(col, t)) = hi;
-                *reinterpret_cast<float*>(Bs + tc_off(col, kTcTP + t)) = lo;
-                *reinterpret_cast<float*>(Bs + tc_off(col, 2 * kTcTP + t)) = hi;
             }
-            for (int k = 3 * kTcTP; k < kTcKp; ++k) *reinterpret_cast<float*>(Bs + tc_off(col, k)) = 0.f;
+            // (each thread reads back only its own column)
+            for (int t0 = 0; t0 < kTcTP; t0 += 4) {
+                float4 hi4, lo4;
+                float* hp = &hi4.x;
+                float* lp = &lo4.x;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + q;
+                    float v = 0.f;
+                    if (ok && t < T) {
+                        v = 1.f;
+#pragma unroll
+                        for (int m = 0; m < kTcMaxM; ++m)
+                            if (m < M) v *= ptab[(m * (kTcMaxDeg + 1) + bsm[t * M + m]) * kTcCols + col];
+                    }
+                    tf32_split(v, hp[q], lp[q]);
+                }
+                *reinterpret_cast<float4*>(Bs + tc_off(col, t0)) = hi4;
+                *reinterpret_cast<float4*>(Bs + tc_off(col, kTcTP + t0)) = lo4;
+                *reinterpret_cast<float4*>(Bs + tc_off(col, 2 * kTcTP + t0)) = hi4;
+            }
             fence_async_shared();
             mbar_arrive(full0 + 8 * b);
         }
@@ -705,8 +732,10 @@ int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int m
         // several CTAs per SM over the whole grid (one CTA fits an SM)
         int gy = std::max(1, (8 * sms + gx - 1) / gx);
         gy = std::min(std::min(gy, nchunk), 65535);
-        const size_t smem = 3 * (size_t)kTcTileBytes + 8 * sizeof(unsigned long long) +
-                            4 * sizeof(unsigned) + sizeof(int) * (kTcTP * kTcMaxM + 4);
+        // operands, then 1 KiB of barriers, TMEM slot, indices and flag,
+        // then the Legendre table [4][9][128]
+        const size_t smem = 3 * (size_t)kTcTileBytes + 1024 +
+                            sizeof(float) * kTcMaxM * (kTcMaxDeg + 1) * kTcCols;
         e = cudaFuncSetAttribute(k_gpc_exceed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess) {
