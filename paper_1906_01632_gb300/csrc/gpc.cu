@@ -360,6 +360,37 @@ __device__ __forceinline__ int tc_off(int row, int k)
     return ((row >> 3) * (kTcKp / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
 }
 
+__device__ __forceinline__ void tc_mma_ta(unsigned d_tmem, unsigned a_tmem, uint64_t b, unsigned acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(kTcIdesc), "r"(acc)
+        : "memory");
+}
+
+// 16 consecutive columns of this warp's 32 lanes from registers, one row per
+// thread.
+__device__ __forceinline__ void tc_st16(unsigned taddr, const float* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// Two node tiles per CTA: their A' operands live in tensor memory (written
+// once by the counting warps), so every basis chunk the producers build
+// feeds two products.  Tensor memory: accumulators of tiles 0 and 1 at
+// columns 0 and 128, A' of tiles 0 and 1 at columns 256 and 384 (112 used).
+constexpr int kTcTiles = 2;
+
 __global__ void __launch_bounds__(288, 1)
     k_gpc_exceed_tc(int M, int T, const int32_t* __restrict__ beta, int maxdeg, int N,
                     const double* __restrict__ coef, int n_pts, const int32_t* __restrict__ nodes,
@@ -367,24 +398,23 @@ __global__ void __launch_bounds__(288, 1)
                     unsigned long long* __restrict__ cnt, int* err)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char* As = tc_smem;                           // A' tile
-    unsigned char* Bs0 = tc_smem + kTcTileBytes;           // B' chunk buffers
+    unsigned char* Bs0 = tc_smem;                          // B' chunk buffers
     unsigned long long* bars =
-        reinterpret_cast<unsigned long long*>(tc_smem + 3 * kTcTileBytes);  // 8 barriers
+        reinterpret_cast<unsigned long long*>(tc_smem + 2 * kTcTileBytes);  // 8 barriers
     unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 8);
     int* bsm = reinterpret_cast<int*>(tmem_slot + 4);     // clamped multi-indices [T][M]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bsm + kTcTP * kTcMaxM);
     // Legendre values of a chunk, [m][k][sample]
-    float* ptab = reinterpret_cast<float*>(tc_smem + 3 * kTcTileBytes + 1024);
+    float* ptab = reinterpret_cast<float*>(tc_smem + 2 * kTcTileBytes + 1024);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile0 = blockIdx.x * kTcRows;
+    const int tile0 = blockIdx.x * kTcTiles * kTcRows;
     // this CTA's slice of the samples, whole chunks
     const int nchunk_all = (Ns + kTcCols - 1) / kTcCols;
     const int per = (nchunk_all + gridDim.y - 1) / gridDim.y;
     const int c0 = blockIdx.y * per;
     const int nchunk = max(0, min(nchunk_all, c0 + per) - c0);
     // full[b], empty[b]: B' buffer b written / read by the MMAs;
-    // tfull[b], tempty[b]: accumulator b written by the MMAs / read out
+    // tfull[q], tempty[q]: accumulator of tile q written by the MMAs / read out
     const unsigned full0 = smem_u32(bars + 0), empty0 = smem_u32(bars + 2);
     const unsigned tfull0 = smem_u32(bars + 4), tempty0 = smem_u32(bars + 6);
     if (threadIdx.x == 0) {
@@ -399,20 +429,6 @@ __global__ void __launch_bounds__(288, 1)
     }
     for (int e = threadIdx.x; e < T * M; e += blockDim.x)
         bsm[e] = min(max((int)beta[e], 0), maxdeg);
-    // A' = [C_hi | C_hi | C_lo], rows past n_pts and terms past T zero
-    for (int e = threadIdx.x; e < kTcRows * kTcKp; e += blockDim.x) {
-        const int row = e / kTcKp, k = e - row * kTcKp;
-        const int part = k / kTcTP, t = k - part * kTcTP;
-        float v = 0.f;
-        const int kk = tile0 + row;
-        if (part < 3 && t < T && kk < n_pts) {
-            const int n = nodes ? nodes[kk] : kk;
-            float hi, lo;
-            tf32_split((float)coef[(size_t)t * N + n], hi, lo);
-            v = part < 2 ? hi : lo;
-        }
-        *reinterpret_cast<float*>(As + tc_off(row, k)) = v;
-    }
     // the inner-dimension padding of both B' buffers stays zero
     for (int e = threadIdx.x; e < 2 * kTcCols; e += blockDim.x) {
         unsigned char* Bs = Bs0 + (e / kTcCols) * kTcTileBytes;
@@ -420,8 +436,8 @@ __global__ void __launch_bounds__(288, 1)
             make_float4(0.f, 0.f, 0.f, 0.f);
     }
     fence_async_shared();
-    if (warp == 0) {  // two accumulators of 128 columns
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+    if (warp == 0) {  // all 512 columns: 2 accumulators, 2 A' operands
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                          smem_u32(tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -431,37 +447,77 @@ __global__ void __launch_bounds__(288, 1)
     tc_fence_after();
     const unsigned tmem = *tmem_slot;
     if (warp < 4) {
-        // ---- counting: thread <-> node row 32 warp + lane ----
-        unsigned count = 0;
+        // A' = [C_hi | C_hi | C_lo] of both tiles into tensor memory: thread
+        // <-> row 32 warp + lane, rows past n_pts and terms past T zero
+        const int row = 32 * warp + lane;
+        for (int q = 0; q < kTcTiles; ++q) {
+            const int kk = tile0 + q * kTcRows + row;
+            const int n = kk < n_pts ? (nodes ? nodes[kk] : kk) : -1;
+            const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 256u + 128u * q;
+#pragma unroll 1
+            for (int k0 = 0; k0 < kTcKp; k0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int k = k0 + r, part = k / kTcTP, t = k - part * kTcTP;
+                    float x = 0.f;
+                    if (part < 3 && t < T && n >= 0) {
+                        float hi, lo;
+                        tf32_split((float)coef[(size_t)t * N + n], hi, lo);
+                        x = part < 2 ? hi : lo;
+                    }
+                    v[r] = x;
+                }
+                tc_st16(ta + k0, v);
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp < 4) {
+        // ---- counting: thread <-> node row 32 warp + lane of each tile ----
+        unsigned count[kTcTiles] = {0u, 0u};
         const int row = 32 * warp + lane;
         for (int i = 0; i < nchunk; ++i) {
-            const int b = i & 1;
-            if (!mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, abort_flag)) break;
-            tc_fence_after();
             const int valid = min(kTcCols, Ns - (c0 + i) * kTcCols);
-            const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(b * kTcCols);
+            bool stop = false;
+            for (int q = 0; q < kTcTiles && !stop; ++q) {
+                if (!mbar_wait(tfull0 + 8 * q, i & 1, err, abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(q * kTcCols);
+                unsigned c = 0;
 #pragma unroll
-            for (int h = 0; h < kTcCols; h += 64) {
-                float v0[32], v1[32];
-                tc_ld32(ta + h, v0);
-                tc_ld32(ta + h + 32, v1);
-                tc_wait_ld();
-                if (valid == kTcCols) {
+                for (int h = 0; h < kTcCols; h += 64) {
+                    float v0[32], v1[32];
+                    tc_ld32(ta + h, v0);
+                    tc_ld32(ta + h + 32, v1);
+                    tc_wait_ld();
+                    if (valid == kTcCols) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) count += (v0[q] > thr) + (v1[q] > thr);
-                } else {  // the last, ragged chunk
+                        for (int r = 0; r < 32; ++r) c += (v0[r] > thr) + (v1[r] > thr);
+                    } else {  // the last, ragged chunk
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        count += (h + q < valid && v0[q] > thr) ? 1u : 0u;
-                        count += (h + 32 + q < valid && v1[q] > thr) ? 1u : 0u;
+                        for (int r = 0; r < 32; ++r) {
+                            c += (h + r < valid && v0[r] > thr) ? 1u : 0u;
+                            c += (h + 32 + r < valid && v1[r] > thr) ? 1u : 0u;
+                        }
                     }
                 }
+                count[q] += c;
+                tc_fence_before();
+                mbar_arrive(tempty0 + 8 * q);
             }
-            tc_fence_before();
-            mbar_arrive(tempty0 + 8 * b);
+            if (stop) break;
         }
-        const int kk = tile0 + row;
-        if (kk < n_pts && count) atomicAdd(cnt + kk, (unsigned long long)count);
+        for (int q = 0; q < kTcTiles; ++q) {
+            const int kk = tile0 + q * kTcRows + row;
+            if (kk < n_pts && count[q]) atomicAdd(cnt + kk, (unsigned long long)count[q]);
+        }
     } else if (warp < 8) {
         // ---- B' chunks: thread <-> sample column ----
         // Legendre values of the chunk's samples, Ptab[(m * 9 + k) * 128 + col]
@@ -502,8 +558,8 @@ __global__ void __launch_bounds__(288, 1)
                 float* hp = &hi4.x;
                 float* lp = &lo4.x;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = t0 + q;
+                for (int r = 0; r < 4; ++r) {
+                    const int t = t0 + r;
                     float v = 0.f;
                     if (ok && t < T) {
                         v = 1.f;
@@ -511,7 +567,7 @@ __global__ void __launch_bounds__(288, 1)
                         for (int m = 0; m < kTcMaxM; ++m)
                             if (m < M) v *= ptab[(m * (kTcMaxDeg + 1) + bsm[t * M + m]) * kTcCols + col];
                     }
-                    tf32_split(v, hp[q], lp[q]);
+                    tf32_split(v, hp[r], lp[r]);
                 }
                 *reinterpret_cast<float4*>(Bs + tc_off(col, t0)) = hi4;
                 *reinterpret_cast<float4*>(Bs + tc_off(col, kTcTP + t0)) = lo4;
@@ -521,29 +577,35 @@ __global__ void __launch_bounds__(288, 1)
             mbar_arrive(full0 + 8 * b);
         }
     } else if (lane == 0) {
-        // ---- MMA issue ----
-        const unsigned a_base = smem_u32(As);
+        // ---- MMA issue: both tiles against each chunk ----
         constexpr unsigned kLbo = 128, kSbo = (kTcKp / 4) * 128;
         for (int i = 0; i < nchunk; ++i) {
             const int b = i & 1;
             if (!mbar_wait(full0 + 8 * b, (i >> 1) & 1, err, abort_flag)) break;
-            if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
-            tc_fence_after();
             const unsigned b_base = smem_u32(Bs0 + b * kTcTileBytes);
-            const unsigned d = tmem + (unsigned)(b * kTcCols);
+            bool stop = false;
+            for (int q = 0; q < kTcTiles; ++q) {
+                if (i >= 1 && !mbar_wait(tempty0 + 8 * q, (i - 1) & 1, err, abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned d = tmem + (unsigned)(q * kTcCols);
+                const unsigned a = tmem + 256u + 128u * q;
 #pragma unroll
-            for (int ks = 0; ks < kTcKp / 8; ++ks)
-                tc_mma(d, tc_desc(a_base + ks * 256, kLbo, kSbo), tc_desc(b_base + ks * 256, kLbo, kSbo),
-                       ks > 0 ? 1u : 0u);
+                for (int ks = 0; ks < kTcKp / 8; ++ks)
+                    tc_mma_ta(d, a + 8 * ks, tc_desc(b_base + ks * 256, kLbo, kSbo), ks > 0 ? 1u : 0u);
+                tc_commit(tfull0 + 8 * q);
+            }
+            if (stop) break;
             tc_commit(empty0 + 8 * b);
-            tc_commit(tfull0 + 8 * b);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -727,14 +789,14 @@ int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int m
             return ELDER_ECUDA;
         }
         err = static_cast<int*>(ep);
-        const int gx = (n_pts + kTcRows - 1) / kTcRows;
+        const int gx = (n_pts + kTcTiles * kTcRows - 1) / (kTcTiles * kTcRows);
         const int nchunk = (Ns + kTcCols - 1) / kTcCols;
         // several CTAs per SM over the whole grid (one CTA fits an SM)
         int gy = std::max(1, (8 * sms + gx - 1) / gx);
         gy = std::min(std::min(gy, nchunk), 65535);
         // operands, then 1 KiB of barriers, TMEM slot, indices and flag,
         // then the Legendre table [4][9][128]
-        const size_t smem = 3 * (size_t)kTcTileBytes + 1024 +
+        const size_t smem = 2 * (size_t)kTcTileBytes + 1024 +
                             sizeof(float) * kTcMaxM * (kTcMaxDeg + 1) * kTcCols;
         e = cudaFuncSetAttribute(k_gpc_exceed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
