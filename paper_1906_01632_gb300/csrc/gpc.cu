@@ -391,7 +391,10 @@ __device__ __forceinline__ void tc_st16(unsigned taddr, const float* v)
 // columns 0 and 128, A' of tiles 0 and 1 at columns 256 and 384 (112 used).
 constexpr int kTcTiles = 2;
 
-__global__ void __launch_bounds__(288, 1)
+constexpr int kTcCountWarps = 8;   // 2 per TMEM lane quarter, half the columns each
+constexpr int kTcThreads = 32 * (kTcCountWarps + 4 + 1);
+
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_gpc_exceed_tc(int M, int T, const int32_t* __restrict__ beta, int maxdeg, int N,
                     const double* __restrict__ coef, int n_pts, const int32_t* __restrict__ nodes,
                     int Ns, const double* __restrict__ theta, float thr,
@@ -402,8 +405,9 @@ __global__ void __launch_bounds__(288, 1)
     unsigned long long* bars =
         reinterpret_cast<unsigned long long*>(tc_smem + 2 * kTcTileBytes);  // 8 barriers
     unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 8);
-    int* bsm = reinterpret_cast<int*>(tmem_slot + 4);     // clamped multi-indices [T][M]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bsm + kTcTP * kTcMaxM);
+    // per term and dimension, the offset of P_{beta_tm}(theta_m) in ptab
+    int* boff = reinterpret_cast<int*>(tmem_slot + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(boff + kTcTP * kTcMaxM);
     // Legendre values of a chunk, [m][k][sample]
     float* ptab = reinterpret_cast<float*>(tc_smem + 2 * kTcTileBytes + 1024);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -422,13 +426,15 @@ __global__ void __launch_bounds__(288, 1)
             mbar_init(full0 + 8 * b, 128);
             mbar_init(empty0 + 8 * b, 1);
             mbar_init(tfull0 + 8 * b, 1);
-            mbar_init(tempty0 + 8 * b, 128);
+            mbar_init(tempty0 + 8 * b, 32 * kTcCountWarps);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int e = threadIdx.x; e < T * M; e += blockDim.x)
-        bsm[e] = min(max((int)beta[e], 0), maxdeg);
+    for (int e = threadIdx.x; e < T * M; e += blockDim.x) {
+        const int m = e % M;
+        boff[e] = (m * (kTcMaxDeg + 1) + min(max((int)beta[e], 0), maxdeg)) * kTcCols;
+    }
     // the inner-dimension padding of both B' buffers stays zero
     for (int e = threadIdx.x; e < 2 * kTcCols; e += blockDim.x) {
         unsigned char* Bs = Bs0 + (e / kTcCols) * kTcTileBytes;
@@ -476,10 +482,12 @@ __global__ void __launch_bounds__(288, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp < 4) {
-        // ---- counting: thread <-> node row 32 warp + lane of each tile ----
+    if (warp < kTcCountWarps) {
+        // ---- counting: thread <-> node row 32 (warp % 4) + lane of each
+        // tile, columns [64 h, 64 h + 64) with h = warp / 4 ----
         unsigned count[kTcTiles] = {0u, 0u};
-        const int row = 32 * warp + lane;
+        const int quarter = warp & 3, h = (warp >> 2) * 64;
+        const int row = 32 * quarter + lane;
         for (int i = 0; i < nchunk; ++i) {
             const int valid = min(kTcCols, Ns - (c0 + i) * kTcCols);
             bool stop = false;
@@ -489,23 +497,21 @@ __global__ void __launch_bounds__(288, 1)
                     break;
                 }
                 tc_fence_after();
-                const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)(q * kTcCols);
+                const unsigned ta =
+                    tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(q * kTcCols + h);
                 unsigned c = 0;
+                float v0[32], v1[32];
+                tc_ld32(ta, v0);
+                tc_ld32(ta + 32, v1);
+                tc_wait_ld();
+                if (valid == kTcCols) {
 #pragma unroll
-                for (int h = 0; h < kTcCols; h += 64) {
-                    float v0[32], v1[32];
-                    tc_ld32(ta + h, v0);
-                    tc_ld32(ta + h + 32, v1);
-                    tc_wait_ld();
-                    if (valid == kTcCols) {
+                    for (int r = 0; r < 32; ++r) c += (v0[r] > thr) + (v1[r] > thr);
+                } else {  // the last, ragged chunk
 #pragma unroll
-                        for (int r = 0; r < 32; ++r) c += (v0[r] > thr) + (v1[r] > thr);
-                    } else {  // the last, ragged chunk
-#pragma unroll
-                        for (int r = 0; r < 32; ++r) {
-                            c += (h + r < valid && v0[r] > thr) ? 1u : 0u;
-                            c += (h + 32 + r < valid && v1[r] > thr) ? 1u : 0u;
-                        }
+                    for (int r = 0; r < 32; ++r) {
+                        c += (h + r < valid && v0[r] > thr) ? 1u : 0u;
+                        c += (h + 32 + r < valid && v1[r] > thr) ? 1u : 0u;
                     }
                 }
                 count[q] += c;
@@ -518,13 +524,13 @@ __global__ void __launch_bounds__(288, 1)
             const int kk = tile0 + q * kTcRows + row;
             if (kk < n_pts && count[q]) atomicAdd(cnt + kk, (unsigned long long)count[q]);
         }
-    } else if (warp < 8) {
+    } else if (warp < kTcCountWarps + 4) {
         // ---- B' chunks: thread <-> sample column ----
         // Legendre values of the chunk's samples, Ptab[(m * 9 + k) * 128 + col]
         // (consecutive threads, consecutive words), then per group of 4 terms
         // the basis products, split and stored as one 16-byte row segment of
         // a core matrix in each of the three parts
-        const int col = threadIdx.x - 128;
+        const int col = threadIdx.x - 32 * kTcCountWarps;
         for (int i = 0; i < nchunk; ++i) {
             const int b = i & 1;
             unsigned char* Bs = Bs0 + b * kTcTileBytes;
@@ -565,7 +571,7 @@ __global__ void __launch_bounds__(288, 1)
                         v = 1.f;
 #pragma unroll
                         for (int m = 0; m < kTcMaxM; ++m)
-                            if (m < M) v *= ptab[(m * (kTcMaxDeg + 1) + bsm[t * M + m]) * kTcCols + col];
+                            if (m < M) v *= ptab[boff[t * M + m] + col];
                     }
                     tf32_split(v, hp[r], lp[r]);
                 }
@@ -801,7 +807,7 @@ int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int m
         e = cudaFuncSetAttribute(k_gpc_exceed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess) {
-            k_gpc_exceed_tc<<<dim3(gx, gy), 288, smem, st>>>(M, T, beta, maxdeg, N, coef, n_pts,
+            k_gpc_exceed_tc<<<dim3(gx, gy), kTcThreads, smem, st>>>(M, T, beta, maxdeg, N, coef, n_pts,
                                                              nodes, Ns, theta, thr, cnt, err);
             count_launch(1);
         }
