@@ -531,16 +531,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // the basis products, split and stored as one 16-byte row segment of
         // a core matrix in each of the three parts
         const int col = threadIdx.x - 32 * kTcCountWarps;
+        // the next chunk's sample coordinates are loaded one chunk ahead
+        float xn[kTcMaxM];
+        auto load_theta = [&](int i) {
+            const int j = (c0 + i) * kTcCols + col;
+#pragma unroll
+            for (int m = 0; m < kTcMaxM; ++m)
+                xn[m] = (i < nchunk && j < Ns && m < M) ? (float)theta[(size_t)j * M + m] : 0.f;
+        };
+        load_theta(0);
         for (int i = 0; i < nchunk; ++i) {
             const int b = i & 1;
             unsigned char* Bs = Bs0 + b * kTcTileBytes;
+            float xc[kTcMaxM];
+#pragma unroll
+            for (int m = 0; m < kTcMaxM; ++m) xc[m] = xn[m];
+            load_theta(i + 1);
             if (i >= 2 && !mbar_wait(empty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
             const int j = (c0 + i) * kTcCols + col;
             const bool ok = j < Ns;
 #pragma unroll
             for (int m = 0; m < kTcMaxM; ++m) {
                 if (m < M) {
-                    const float x = ok ? (float)theta[(size_t)j * M + m] : 0.f;
+                    const float x = xc[m];
                     float pm1 = 1.f, p0 = x;
                     ptab[(m * (kTcMaxDeg + 1)) * kTcCols + col] = 1.f;
                     if (maxdeg >= 1) ptab[(m * (kTcMaxDeg + 1) + 1) * kTcCols + col] = x;

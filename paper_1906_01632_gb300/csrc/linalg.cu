@@ -569,8 +569,10 @@ void launch_zline_apply(const Grid& G, const B4<M>* J, const B4<T>* zMi, const B
                                                       mstride);
 }
 
+// (at most 32 registers: every warp slot of an SM can then hold a warp,
+// which this latency-bound stencil needs; at 34 a quarter stayed empty)
 template <class T, class M, bool TRANS>
-__global__ void __launch_bounds__(kMaxBS)
+__global__ void __launch_bounds__(kMaxBS, 2048 / kMaxBS)
     k_mg_residual(Grid G, const B4<M>* __restrict__ J, const uint8_t* __restrict__ bc,
                   const V2<T>* __restrict__ b, const V2<T>* __restrict__ x,
                   V2<T>* __restrict__ r, const int* mask, int mstride)
