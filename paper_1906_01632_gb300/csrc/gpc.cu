@@ -391,8 +391,9 @@ __device__ __forceinline__ void tc_st16(unsigned taddr, const float* v)
 // columns 0 and 128, A' of tiles 0 and 1 at columns 256 and 384 (112 used).
 constexpr int kTcTiles = 2;
 
-constexpr int kTcCountWarps = 8;   // 2 per TMEM lane quarter, half the columns each
-constexpr int kTcThreads = 32 * (kTcCountWarps + 4 + 1);
+constexpr int kTcCountWarps = 4;   // one per TMEM lane quarter
+constexpr int kTcProdWarps = 8;    // basis builders: two per sample, half the terms each
+constexpr int kTcThreads = 32 * (kTcCountWarps + kTcProdWarps + 1);
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gpc_exceed_tc(int M, int T, const int32_t* __restrict__ beta, int maxdeg, int N,
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const unsigned tfull0 = smem_u32(bars + 4), tempty0 = smem_u32(bars + 6);
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
-            mbar_init(full0 + 8 * b, 128);
+            mbar_init(full0 + 8 * b, 32 * kTcProdWarps);
             mbar_init(empty0 + 8 * b, 1);
             mbar_init(tfull0 + 8 * b, 1);
             mbar_init(tempty0 + 8 * b, 32 * kTcCountWarps);
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int e = threadIdx.x; e < T * M; e += blockDim.x) {
         const int m = e % M;
-        boff[e] = (m * (kTcMaxDeg + 1) + min(max((int)beta[e], 0), maxdeg)) * kTcCols;
+        boff[e] = (m * (kTcMaxDeg + 1) + min(max((int)beta[e], 0), maxdeg)) * 2 * kTcCols;
     }
     // the inner-dimension padding of both B' buffers stays zero
     for (int e = threadIdx.x; e < 2 * kTcCols; e += blockDim.x) {
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ---- counting: thread <-> node row 32 (warp % 4) + lane of each
         // tile, columns [64 h, 64 h + 64) with h = warp / 4 ----
         unsigned count[kTcTiles] = {0u, 0u};
-        const int quarter = warp & 3, h = (warp >> 2) * 64;
+        const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
         for (int i = 0; i < nchunk; ++i) {
             const int valid = min(kTcCols, Ns - (c0 + i) * kTcCols);
@@ -498,20 +499,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 tc_fence_after();
                 const unsigned ta =
-                    tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(q * kTcCols + h);
+                    tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(q * kTcCols);
                 unsigned c = 0;
-                float v0[32], v1[32];
-                tc_ld32(ta, v0);
-                tc_ld32(ta + 32, v1);
-                tc_wait_ld();
-                if (valid == kTcCols) {
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) c += (v0[r] > thr) + (v1[r] > thr);
-                } else {  // the last, ragged chunk
+                for (int h = 0; h < kTcCols; h += 64) {
+                    float v0[32], v1[32];
+                    tc_ld32(ta + h, v0);
+                    tc_ld32(ta + h + 32, v1);
+                    tc_wait_ld();
+                    if (valid == kTcCols) {
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) {
-                        c += (h + r < valid && v0[r] > thr) ? 1u : 0u;
-                        c += (h + 32 + r < valid && v1[r] > thr) ? 1u : 0u;
+                        for (int r = 0; r < 32; ++r) c += (v0[r] > thr) + (v1[r] > thr);
+                    } else {  // the last, ragged chunk
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            c += (h + r < valid && v0[r] > thr) ? 1u : 0u;
+                            c += (h + 32 + r < valid && v1[r] > thr) ? 1u : 0u;
+                        }
                     }
                 }
                 count[q] += c;
@@ -524,13 +528,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int kk = tile0 + q * kTcRows + row;
             if (kk < n_pts && count[q]) atomicAdd(cnt + kk, (unsigned long long)count[q]);
         }
-    } else if (warp < kTcCountWarps + 4) {
-        // ---- B' chunks: thread <-> sample column ----
-        // Legendre values of the chunk's samples, Ptab[(m * 9 + k) * 128 + col]
-        // (consecutive threads, consecutive words), then per group of 4 terms
-        // the basis products, split and stored as one 16-byte row segment of
-        // a core matrix in each of the three parts
-        const int col = threadIdx.x - 32 * kTcCountWarps;
+    } else if (warp < kTcCountWarps + kTcProdWarps) {
+        // ---- B' chunks: two threads per sample column, terms [0, 20) and
+        // [20, 36) ----
+        // Each thread forms its sample's Legendre values in its own column of
+        // ptab, [(m * 9 + k) * 256 + p] (consecutive threads, consecutive
+        // words), then per group of 4 terms the basis products, split and
+        // stored as one 16-byte row segment of a core matrix in each of the
+        // three parts
+        const int pt = threadIdx.x - 32 * kTcCountWarps;
+        const int col = pt & (kTcCols - 1), half = pt / kTcCols;
+        const int tbeg = half ? 20 : 0, tend = half ? kTcTP : 20;
         // the next chunk's sample coordinates are loaded one chunk ahead
         float xn[kTcMaxM];
         auto load_theta = [&](int i) {
@@ -555,8 +563,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (m < M) {
                     const float x = xc[m];
                     float pm1 = 1.f, p0 = x;
-                    ptab[(m * (kTcMaxDeg + 1)) * kTcCols + col] = 1.f;
-                    if (maxdeg >= 1) ptab[(m * (kTcMaxDeg + 1) + 1) * kTcCols + col] = x;
+                    ptab[(m * (kTcMaxDeg + 1)) * 2 * kTcCols + pt] = 1.f;
+                    if (maxdeg >= 1) ptab[(m * (kTcMaxDeg + 1) + 1) * 2 * kTcCols + pt] = x;
                     // (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} with the ratios
                     // folded into constants
 #pragma unroll
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         if (k < maxdeg) {
                             const float p1 = (float(2 * k + 1) / float(k + 1)) * x * p0 -
                                              (float(k) / float(k + 1)) * pm1;
-                            ptab[(m * (kTcMaxDeg + 1) + k + 1) * kTcCols + col] = p1;
+                            ptab[(m * (kTcMaxDeg + 1) + k + 1) * 2 * kTcCols + pt] = p1;
                             pm1 = p0;
                             p0 = p1;
                         }
@@ -572,7 +580,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
             // (each thread reads back only its own column)
-            for (int t0 = 0; t0 < kTcTP; t0 += 4) {
+            for (int t0 = tbeg; t0 < tend; t0 += 4) {
                 float4 hi4, lo4;
                 float* hp = &hi4.x;
                 float* lp = &lo4.x;
@@ -584,7 +592,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         v = 1.f;
 #pragma unroll
                         for (int m = 0; m < kTcMaxM; ++m)
-                            if (m < M) v *= ptab[boff[t * M + m] + col];
+                            if (m < M) v *= ptab[boff[t * M + m] + pt];
                     }
                     tf32_split(v, hp[r], lp[r]);
                 }
@@ -814,9 +822,9 @@ int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int m
         int gy = std::max(1, (8 * sms + gx - 1) / gx);
         gy = std::min(std::min(gy, nchunk), 65535);
         // operands, then 1 KiB of barriers, TMEM slot, indices and flag,
-        // then the Legendre table [4][9][128]
+        // then the Legendre table [4][9][256]
         const size_t smem = 2 * (size_t)kTcTileBytes + 1024 +
-                            sizeof(float) * kTcMaxM * (kTcMaxDeg + 1) * kTcCols;
+                            sizeof(float) * kTcMaxM * (kTcMaxDeg + 1) * 2 * kTcCols;
         e = cudaFuncSetAttribute(k_gpc_exceed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess) {
