@@ -392,7 +392,9 @@ __device__ __forceinline__ void tc_st16(unsigned taddr, const float* v)
 constexpr int kTcTiles = 2;
 
 constexpr int kTcCountWarps = 4;   // one per TMEM lane quarter
-constexpr int kTcProdWarps = 8;    // basis builders: two per sample, half the terms each
+constexpr int kTcSplit = 3;        // basis builders per sample (12 of the 36 terms each)
+constexpr int kTcProdWarps = 4 * kTcSplit;
+static_assert(kTcTP % (4 * kTcSplit) == 0, "whole 4-term groups per basis builder");
 constexpr int kTcThreads = 32 * (kTcCountWarps + kTcProdWarps + 1);
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int e = threadIdx.x; e < T * M; e += blockDim.x) {
         const int m = e % M;
-        boff[e] = (m * (kTcMaxDeg + 1) + min(max((int)beta[e], 0), maxdeg)) * 2 * kTcCols;
+        boff[e] = (m * (kTcMaxDeg + 1) + min(max((int)beta[e], 0), maxdeg)) * kTcSplit * kTcCols;
     }
     // the inner-dimension padding of both B' buffers stays zero
     for (int e = threadIdx.x; e < 2 * kTcCols; e += blockDim.x) {
@@ -529,16 +531,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (kk < n_pts && count[q]) atomicAdd(cnt + kk, (unsigned long long)count[q]);
         }
     } else if (warp < kTcCountWarps + kTcProdWarps) {
-        // ---- B' chunks: two threads per sample column, terms [0, 20) and
-        // [20, 36) ----
+        // ---- B' chunks: kTcSplit threads per sample column, 12 terms each ----
         // Each thread forms its sample's Legendre values in its own column of
-        // ptab, [(m * 9 + k) * 256 + p] (consecutive threads, consecutive
-        // words), then per group of 4 terms the basis products, split and
-        // stored as one 16-byte row segment of a core matrix in each of the
-        // three parts
+        // ptab, [(m * 9 + k) * kTcSplit * 128 + p] (consecutive threads,
+        // consecutive words), then per group of 4 terms the basis products,
+        // split and stored as one 16-byte row segment of a core matrix in
+        // each of the three parts
         const int pt = threadIdx.x - 32 * kTcCountWarps;
-        const int col = pt & (kTcCols - 1), half = pt / kTcCols;
-        const int tbeg = half ? 20 : 0, tend = half ? kTcTP : 20;
+        const int col = pt & (kTcCols - 1), part = pt / kTcCols;
+        const int tbeg = part * (kTcTP / kTcSplit), tend = tbeg + kTcTP / kTcSplit;
         // the next chunk's sample coordinates are loaded one chunk ahead
         float xn[kTcMaxM];
         auto load_theta = [&](int i) {
@@ -563,8 +564,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (m < M) {
                     const float x = xc[m];
                     float pm1 = 1.f, p0 = x;
-                    ptab[(m * (kTcMaxDeg + 1)) * 2 * kTcCols + pt] = 1.f;
-                    if (maxdeg >= 1) ptab[(m * (kTcMaxDeg + 1) + 1) * 2 * kTcCols + pt] = x;
+                    ptab[(m * (kTcMaxDeg + 1)) * kTcSplit * kTcCols + pt] = 1.f;
+                    if (maxdeg >= 1) ptab[(m * (kTcMaxDeg + 1) + 1) * kTcSplit * kTcCols + pt] = x;
                     // (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} with the ratios
                     // folded into constants
 #pragma unroll
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         if (k < maxdeg) {
                             const float p1 = (float(2 * k + 1) / float(k + 1)) * x * p0 -
                                              (float(k) / float(k + 1)) * pm1;
-                            ptab[(m * (kTcMaxDeg + 1) + k + 1) * 2 * kTcCols + pt] = p1;
+                            ptab[(m * (kTcMaxDeg + 1) + k + 1) * kTcSplit * kTcCols + pt] = p1;
                             pm1 = p0;
                             p0 = p1;
                         }
@@ -822,9 +823,9 @@ int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int m
         int gy = std::max(1, (8 * sms + gx - 1) / gx);
         gy = std::min(std::min(gy, nchunk), 65535);
         // operands, then 1 KiB of barriers, TMEM slot, indices and flag,
-        // then the Legendre table [4][9][256]
+        // then the Legendre table [4][9][kTcSplit * 128]
         const size_t smem = 2 * (size_t)kTcTileBytes + 1024 +
-                            sizeof(float) * kTcMaxM * (kTcMaxDeg + 1) * 2 * kTcCols;
+                            sizeof(float) * kTcMaxM * (kTcMaxDeg + 1) * kTcSplit * kTcCols;
         e = cudaFuncSetAttribute(k_gpc_exceed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess) {
