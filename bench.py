@@ -582,6 +582,11 @@ def run_ours(a):
                                "krylov_per_step": float(np.mean(krylov)), "failed_samples": fails,
                                "fp64_retries": retries},
                 "profiled_pass": {"steps": a.profile_steps, "ms_per_step": prof_step_ms},
+                "autotune": {"threads_per_block": ctx.autotune_result()["threads_per_block"],
+                             "mg_residual (threads, samples per CTA, ms of candidates)":
+                                 ctx.autotune_choice(E.K_MGRES),
+                             "zline_sweep (threads, samples per CTA, ms of candidates)":
+                                 ctx.autotune_choice(E.K_SMOOTH0)},
                 "timing": "value: CUDA events on the launching stream around the K timed steps "
                           "(graphs replayed, no per-launch events); kernel_classes and roofline: "
                           "CUDA events around every launch of each class in a profiled pass of "

@@ -113,8 +113,12 @@ typedef struct {
                                  configured settings, outside profiling, and
                                  cached for the 4 most recent argument sets
                                  (array pointers, S, dt, Newton start)      */
-    int autotune;             /* time threads-per-block candidates of the
-                                 stencil kernels on the first step          */
+    int autotune;             /* 1 (default): time the candidates (threads
+                                 per block; for the multigrid residual and
+                                 the z-line sweep also 1 or 2 samples per
+                                 CTA) of the stencil kernels on the first
+                                 step; 0: defaults (one sample per CTA);
+                                 2: two samples per CTA without timing     */
     int newton_estimate;      /* also accept when the linear-convergence
                                  error estimate theta/(1-theta)|d| is within
                                  the Newton tolerances                      */
@@ -338,6 +342,19 @@ int elder_profile_read(const elder_ctx* ctx, int kernel_class,
  * replays count every kernel node, the loop bodies of a device-controlled
  * step as often as they ran).  Host output. */
 int elder_launch_count(int64_t* launches);
+
+/* The autotuner's choice for one kernel class (ELDER_K_*): threads per
+ * block and samples per CTA (1, or 2: each thread works on its node or line
+ * in two samples, whose loads and recursions are independent).  For
+ * ELDER_K_MGRES (the multigrid residual; candidates 128, 256, 512 threads)
+ * and ELDER_K_SMOOTH0 (the z-line sweep from x = 0; candidates 64, 128, 256
+ * threads) ms receives the measured milliseconds per launch of the 6
+ * candidates [samples per CTA 1, 2][threads ascending], 0 when not tuned;
+ * for the other classes 0.  Timed on the first step of a context (3
+ * launches after a warm-up, CUDA events) on its level-0 operator with all
+ * samples active.  Host outputs; any may be NULL. */
+int elder_autotune_choice(const elder_ctx* ctx, int kernel_class, int* threads_per_block,
+                          int* samples_per_cta, float* ms);
 
 /* Device-controlled steps of ctx (use_graphs = 2): *cached receives the
  * number of captured step graphs held, *replays the steps run through them

@@ -233,7 +233,12 @@ struct elder_ctx {
     std::unique_ptr<Solver<float>> s32;
     int nblk0 = 0;
     // threads per block of the autotuned kernel classes (indexed by ELDER_K_*)
-    int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, kBS};
+    int bs[ELDER_K_CLASSES] = {kBS, kBS, kBS, kBS, kBS, 128};
+    // samples per CTA of the multigrid residual and the z-line sweep
+    int spc[ELDER_K_CLASSES] = {1, 1, 1, 1, 1, 1};
+    // the (threads per block, samples per CTA) candidates' ms per launch of
+    // the multigrid residual [0] and the z-line sweep [1]
+    float tune2_ms[2][6] = {};
     int smoother_now = ELDER_SMOOTH_JACOBI;  // smoother of the solve in progress
     double omega_now = 0.5;                  // its damping
     int nu2_now = 1;                         // its post-smoothing sweeps
@@ -556,6 +561,9 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     using M = typename Solver<T>::M;
     const int na = ctx->n_active_k;
     const int bs_sm = ctx->bs[ELDER_K_SMOOTH], bs_mr = ctx->bs[ELDER_K_MGRES];
+    const int bs_zl = ctx->bs[ELDER_K_SMOOTH0], spc_zl = ctx->spc[ELDER_K_SMOOTH0];
+    // (the transposed residual keeps one sample per CTA: two spill registers)
+    const int spc_mr = trans ? 1 : ctx->spc[ELDER_K_MGRES];
     const bool line = ctx->smoother_now == ELDER_SMOOTH_ZLINE && G.nz + 1 <= kMaxLine;
     // the non-transposed z-line sweep substitutes with the line factors of
     // the assembly; the transposed one (adjoint solves) factors as it goes
@@ -563,12 +571,12 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     auto sweep = [&](const V2<T>* xin, V2<T>* xout) {
         if (fact && xin == nullptr) {
             launch_zline_apply<T, M>(G, sv.Jm[l], sv.zMi[l], sv.zC[l], ctx->bc[l], b, nullptr,
-                                     xout, ctx->omega_now, mask, KSTRIDE, S, st, 1);
+                                     xout, ctx->omega_now, mask, KSTRIDE, S, st, 1, bs_zl, spc_zl);
         } else if (fact) {
             launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, xin, sv.mr[l], trans, mask,
-                                     KSTRIDE, S, st, bs_mr);
+                                     KSTRIDE, S, st, bs_mr, spc_mr);
             launch_zline_apply<T, M>(G, sv.Jm[l], sv.zMi[l], sv.zC[l], ctx->bc[l], sv.mr[l], xin,
-                                     xout, ctx->omega_now, mask, KSTRIDE, S, st, 2);
+                                     xout, ctx->omega_now, mask, KSTRIDE, S, st, 2, bs_zl, spc_zl);
         } else if (line && xin == nullptr) {
             launch_smooth_zline<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], b, xin, xout,
                                       ctx->omega_now, trans, mask, KSTRIDE, S, st, 1);
@@ -594,7 +602,7 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     }
     pi = prof_begin(ctx, st);
     launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, cur, sv.mr[l], trans, mask, KSTRIDE, S,
-                             st, bs_mr);
+                             st, bs_mr, spc_mr);
     prof_end(ctx, pi, ELDER_K_MGRES, G, sizeof(T), sizeof(M), na, st);
     launch_restrict<T>(G, ctx->grids[l + 1], ctx->bc[l + 1], sv.mr[l], sv.mb[l + 1], mask,
                        KSTRIDE, S, st);
@@ -620,6 +628,11 @@ void autotune(elder_ctx* ctx, Solver<T>& sv, int S, cudaStream_t st)
 {
     const int idx = std::is_same<T, float>::value ? 1 : 0;
     if (ctx->tuned[idx] || !ctx->cfg.autotune) return;
+    if (ctx->cfg.autotune == 2) {  // fixed: two samples per CTA, default blocks
+        ctx->spc[ELDER_K_MGRES] = ctx->spc[ELDER_K_SMOOTH0] = 2;
+        ctx->tuned[idx] = true;
+        return;
+    }
     using M = typename Solver<T>::M;
     const Grid& G = ctx->grids[0];
     const size_t nv = (size_t)S * G.N;
@@ -655,6 +668,42 @@ void autotune(elder_ctx* ctx, Solver<T>& sv, int S, cudaStream_t st)
             if (ms < best) {
                 best = ms;
                 ctx->bs[cls[c]] = cand[q];
+            }
+        }
+    }
+    // (threads per block, samples per CTA) of the multigrid residual and of
+    // the factored z-line sweep from x = 0 (the default V(1,0) cycle's only
+    // sweep); two samples per CTA give a thread two independent stencil rows
+    // or line recursions
+    if (sv.zMi[0] && G.nz + 1 <= kMaxLine) {
+        const int bsm[3] = {kMinBS, kBS, kMaxBS}, bsz[3] = {64, 128, 256};
+        for (int c = 0; c < 2; ++c) {
+            float best = 1e30f;
+            for (int q = 0; q < 6; ++q) {
+                const int bsq = c == 0 ? bsm[q % 3] : bsz[q % 3], spq = 1 + q / 3;
+                auto run = [&]() {
+                    if (c == 0)
+                        launch_mg_residual<T, M>(G, sv.Jm[0], ctx->bc[0], sv.mb[0], sv.mx[0],
+                                                 sv.mx2[0], 0, nullptr, 0, S, st, bsq, spq);
+                    else
+                        launch_zline_apply<T, M>(G, sv.Jm[0], sv.zMi[0], sv.zC[0], ctx->bc[0],
+                                                 sv.mb[0], nullptr, sv.mx2[0], 1.0, nullptr, 0, S,
+                                                 st, 1, bsq, spq);
+                };
+                run();
+                CK(cudaEventRecord(e0, st));
+                for (int r = 0; r < 3; ++r) run();
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                ctx->tune2_ms[c][q] = ms / 3.f;
+                if (ms < best) {
+                    best = ms;
+                    const int cl = c == 0 ? ELDER_K_MGRES : ELDER_K_SMOOTH0;
+                    ctx->bs[cl] = bsq;
+                    ctx->spc[cl] = spq;
+                }
             }
         }
     }
@@ -1568,6 +1617,7 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
     if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.max_samples < 1 || !(c.Lx > 0) ||
         !(c.Ly > 0) || !(c.Lz > 0) || !(c.mu > 0) || c.bc_mode < 0 || c.bc_mode > 3 ||
         (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
+        c.autotune < 0 || c.autotune > 2 ||
         c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0 ||
         (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE) ||
         !(c.omega > 0) || !(c.omega_line > 0) || c.mixed_newton_maxit < 0 ||
@@ -1921,6 +1971,19 @@ int elder_measure_peak(int kind, double* gflops, void* stream)
     } catch (const Fail& f) {
         g_create_error = f.msg;
         return f.code;
+    }
+    return ELDER_OK;
+}
+
+int elder_autotune_choice(const elder_ctx* ctx, int kernel_class, int* threads_per_block,
+                          int* samples_per_cta, float* ms)
+{
+    if (!ctx || kernel_class < 0 || kernel_class >= ELDER_K_CLASSES) return ELDER_EINVAL;
+    if (threads_per_block) *threads_per_block = ctx->bs[kernel_class];
+    if (samples_per_cta) *samples_per_cta = ctx->spc[kernel_class];
+    if (ms) {
+        const int row = kernel_class == ELDER_K_MGRES ? 0 : kernel_class == ELDER_K_SMOOTH0 ? 1 : -1;
+        for (int q = 0; q < 6; ++q) ms[q] = row >= 0 ? ctx->tune2_ms[row][q] : 0.f;
     }
     return ELDER_OK;
 }

@@ -141,11 +141,13 @@ void launch_smooth(const Grid& G, const B4<M>* J, const B4<T>* Dinv,
                    const uint8_t* bc, const V2<T>* b, const V2<T>* x,
                    V2<T>* xo, double omega, int trans, const int* mask,
                    int mask_stride, int S, cudaStream_t st, int bs = kBS);
+// spc: samples per CTA (1 or 2), each thread forming its node's residual in
+// spc samples
 template <class T, class M>
 void launch_mg_residual(const Grid& G, const B4<M>* J, const uint8_t* bc,
                         const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
                         const int* mask, int mask_stride, int S,
-                        cudaStream_t st, int bs = kBS);
+                        cudaStream_t st, int bs = kBS, int spc = 1);
 template <class T>
 void launch_restrict(const Grid& Gf, const Grid& Gc, const uint8_t* bcc,
                      const V2<T>* rf, V2<T>* bc_out, const int* mask,
@@ -218,11 +220,12 @@ template <class T, class M>
 void launch_zline_factor(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
                          B4<T>* zMi, B4<T>* zC, const int* mask, int mstride, int S,
                          cudaStream_t st);
+// bs threads per block; spc lines of different samples per thread (1 or 2)
 template <class T, class M>
 void launch_zline_apply(const Grid& G, const B4<M>* J, const B4<T>* zMi, const B4<T>* zC,
                         const uint8_t* bc, const V2<T>* r, const V2<T>* x, V2<T>* xo,
                         double omega, const int* mask, int mstride, int S, cudaStream_t st,
-                        int mode);
+                        int mode, int bs = 128, int spc = 1);
 
 // Keeps the iterate of smallest residual: copies x into xbest for the
 // samples whose last iteration improved it (keep == 1), or x <- xbest for

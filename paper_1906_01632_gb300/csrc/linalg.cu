@@ -493,63 +493,82 @@ void launch_zline_factor(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const
 // non-transposed operator): forward substitution g_k = zMi_k (r_k - L_k
 // g_{k-1}), g kept in x_out, then back substitution d_k = g_k - zC_k d_{k+1}
 // and x_out = x + omega d (x = 0 in MODE 1; in MODE 2 r is the masked
-// residual b - A x).  One thread per line; the loads of a node do not depend
-// on the recursion, so unrolled iterations keep several nodes in flight.
-template <class T, class M, int MODE>
+// residual b - A x).  One thread per line of SPC samples: the SPC
+// recursions are independent, so their steps overlap (the autotuner picks
+// SPC with the block size); the loads of a node do not depend on the
+// recursion, so unrolled iterations keep several nodes in flight.  An
+// inactive sample's line is read as sample s0's and not written.
+template <class T, class M, int MODE, int SPC>
 __global__ void __launch_bounds__(kBS)
     k_zline_apply(Grid G, const B4<M>* __restrict__ J, const B4<T>* __restrict__ zMi,
                   const B4<T>* __restrict__ zC, const uint8_t* __restrict__ bc,
                   const V2<T>* __restrict__ r, const V2<T>* __restrict__ x, V2<T>* xo, T omega,
-                  const int* mask, int mstride)
+                  const int* mask, int mstride, int S)
 {
-    const int s = blockIdx.y;
-    if (!on(mask, mstride, s)) return;
+    const int s0 = blockIdx.y * SPC;
+    bool act[SPC];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) {
+        act[q] = s0 + q < S && on(mask, mstride, s0 + q);
+        any = any || act[q];
+    }
+    if (!any) return;
     const int sz = (G.nx + 1) * (G.ny + 1);
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= sz) return;
-    const size_t on_ = (size_t)s * G.N;
-    const B4<M>* Jl = J + (size_t)s * 27 * G.N + (size_t)slot27(0, 0, -1) * G.N;
-    r += on_;
-    zMi += on_;
-    zC += on_;
-    xo += on_;
-    V2<T> gp{T(0), T(0)};
+    size_t on_[SPC];
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) on_[q] = (size_t)(act[q] ? s0 + q : s0) * G.N;
+    const size_t jl = (size_t)slot27(0, 0, -1) * G.N;
+    V2<T> gp[SPC];
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) gp[q] = V2<T>{T(0), T(0)};
     uint8_t bc_prev = 0;
 #pragma unroll 4
     for (int k = 0; k <= G.nz; ++k) {
         const int n = col + k * sz;
         const uint8_t mk = bc[n];
-        const V2<T> bv = r[n];
-        const B4<M> qL = Jl[k > 0 ? n : col];
-        const B4<T> Mi = zMi[n];
-        T rp = (mk & BC_P) ? T(0) : bv.p;
-        T rc = (mk & BC_C) ? T(0) : bv.c;
-        if (k > 0) {
-            const B4<T> L = mask_block(raw_line_block<T, M, false>(qL), mk, bc_prev);
-            rp -= L.pp * gp.p + L.pc * gp.c;
-            rc -= L.cp * gp.p + L.cc * gp.c;
+#pragma unroll
+        for (int q = 0; q < SPC; ++q) {
+            const V2<T> bv = r[on_[q] + n];
+            const B4<M> qL = J[on_[q] * 27 + jl + (k > 0 ? n : col)];
+            const B4<T> Mi = zMi[on_[q] + n];
+            T rp = (mk & BC_P) ? T(0) : bv.p;
+            T rc = (mk & BC_C) ? T(0) : bv.c;
+            if (k > 0) {
+                const B4<T> L = mask_block(raw_line_block<T, M, false>(qL), mk, bc_prev);
+                rp -= L.pp * gp[q].p + L.pc * gp[q].c;
+                rc -= L.cp * gp[q].p + L.cc * gp[q].c;
+            }
+            gp[q] = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
+            if (act[q]) xo[on_[q] + n] = gp[q];
         }
-        gp = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
-        xo[n] = gp;
         bc_prev = mk;
     }
-    V2<T> d = gp;
-    const V2<T>* xs = (MODE == 1) ? nullptr : x + on_;
+    V2<T> d[SPC];
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) d[q] = gp[q];
 #pragma unroll 4
     for (int k = G.nz; k >= 0; --k) {
         const int n = col + k * sz;
-        if (k < G.nz) {
-            const B4<T> C = zC[n];
-            const V2<T> g = xo[n];
-            d = V2<T>{g.p - (C.pp * d.p + C.pc * d.c), g.c - (C.cp * d.p + C.cc * d.c)};
-        }
-        V2<T> xn{T(0), T(0)};
-        if (MODE != 1) xn = xs[n];
-        T op = xn.p + omega * d.p, oc = xn.c + omega * d.c;
         const uint8_t m = bc[n];
-        if (m & BC_P) op = T(0);
-        if (m & BC_C) oc = T(0);
-        xo[n] = V2<T>{op, oc};
+#pragma unroll
+        for (int q = 0; q < SPC; ++q) {
+            if (!act[q]) continue;
+            if (k < G.nz) {
+                const B4<T> C = zC[on_[q] + n];
+                const V2<T> g = xo[on_[q] + n];
+                d[q] = V2<T>{g.p - (C.pp * d[q].p + C.pc * d[q].c),
+                             g.c - (C.cp * d[q].p + C.cc * d[q].c)};
+            }
+            V2<T> xn{T(0), T(0)};
+            if (MODE != 1) xn = x[on_[q] + n];
+            T op = xn.p + omega * d[q].p, oc = xn.c + omega * d[q].c;
+            if (m & BC_P) op = T(0);
+            if (m & BC_C) oc = T(0);
+            xo[on_[q] + n] = V2<T>{op, oc};
+        }
     }
 }
 
@@ -557,52 +576,85 @@ template <class T, class M>
 void launch_zline_apply(const Grid& G, const B4<M>* J, const B4<T>* zMi, const B4<T>* zC,
                         const uint8_t* bc, const V2<T>* r, const V2<T>* x, V2<T>* xo,
                         double omega, const int* mask, int mstride, int S, cudaStream_t st,
-                        int mode)
+                        int mode, int bs, int spc)
 {
     count_launch(1);
-    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), 128), S);
-    if (mode == 1)
-        k_zline_apply<T, M, 1><<<grid, 128, 0, st>>>(G, J, zMi, zC, bc, r, x, xo, T(omega), mask,
-                                                      mstride);
-    else
-        k_zline_apply<T, M, 2><<<grid, 128, 0, st>>>(G, J, zMi, zC, bc, r, x, xo, T(omega), mask,
-                                                      mstride);
+    dim3 grid(nblocks((G.nx + 1) * (G.ny + 1), bs), (S + spc - 1) / spc);
+#define ELDER_ZLA(MO, SP)                                                                      \
+    k_zline_apply<T, M, MO, SP><<<grid, bs, 0, st>>>(G, J, zMi, zC, bc, r, x, xo, T(omega),   \
+                                                     mask, mstride, S)
+    if (mode == 1) {
+        if (spc == 2) ELDER_ZLA(1, 2);
+        else ELDER_ZLA(1, 1);
+    } else {
+        if (spc == 2) ELDER_ZLA(2, 2);
+        else ELDER_ZLA(2, 1);
+    }
+#undef ELDER_ZLA
 }
 
-// (at most 32 registers: every warp slot of an SM can then hold a warp,
-// which this latency-bound stencil needs; at 34 a quarter stayed empty)
-template <class T, class M, bool TRANS>
-__global__ void __launch_bounds__(kMaxBS, 2048 / kMaxBS)
+// SPC samples per CTA: a thread forms the residual of its node in SPC
+// samples, whose loads are independent (more loads in flight per thread at
+// the price of registers); the autotuner picks SPC with the block size.  The
+// loads of an inactive sample read sample s0's rows and its result is not
+// stored.  At SPC = 1, at most 32 registers: every warp slot of an SM can
+// then hold a warp, which this latency-bound stencil needs (at 34 a quarter
+// stayed empty).
+template <class T, class M, bool TRANS, int SPC>
+__global__ void __launch_bounds__(kMaxBS, (2048 / kMaxBS) / SPC)
     k_mg_residual(Grid G, const B4<M>* __restrict__ J, const uint8_t* __restrict__ bc,
                   const V2<T>* __restrict__ b, const V2<T>* __restrict__ x,
-                  V2<T>* __restrict__ r, const int* mask, int mstride)
+                  V2<T>* __restrict__ r, const int* mask, int mstride, int S)
 {
-    const int s = blockIdx.y;
-    if (!on(mask, mstride, s)) return;
+    const int s0 = blockIdx.y * SPC;
+    bool act[SPC];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) {
+        act[q] = s0 + q < S && on(mask, mstride, s0 + q);
+        any = any || act[q];
+    }
+    if (!any) return;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.N) return;
-    const size_t on_ = (size_t)s * G.N;
     int i, j, k;
     node_ijk(G, n, i, j, k);
-    T yp, yc;
-    stencil_apply<T, TRANS, M>(G, J + (size_t)s * 27 * G.N, x + on_, n, i, j, k, yp, yc);
-    const V2<T> bv = b[on_ + n];
-    T rp = bv.p - yp, rc = bv.c - yc;
+    T yp[SPC], yc[SPC];
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) {
+        const size_t s = act[q] ? s0 + q : s0;
+        stencil_apply<T, TRANS, M>(G, J + s * 27 * G.N, x + s * G.N, n, i, j, k, yp[q], yc[q]);
+    }
     const uint8_t m = bc[n];
-    if (m & BC_P) rp = T(0);
-    if (m & BC_C) rc = T(0);
-    r[on_ + n] = V2<T>{rp, rc};
+#pragma unroll
+    for (int q = 0; q < SPC; ++q) {
+        if (!act[q]) continue;
+        const size_t on_ = (size_t)(s0 + q) * G.N;
+        const V2<T> bv = b[on_ + n];
+        T rp = bv.p - yp[q], rc = bv.c - yc[q];
+        if (m & BC_P) rp = T(0);
+        if (m & BC_C) rc = T(0);
+        r[on_ + n] = V2<T>{rp, rc};
+    }
 }
 
 template <class T, class M>
 void launch_mg_residual(const Grid& G, const B4<M>* J, const uint8_t* bc,
                         const V2<T>* b, const V2<T>* x, V2<T>* r, int trans,
-                        const int* mask, int mstride, int S, cudaStream_t st, int bs)
+                        const int* mask, int mstride, int S, cudaStream_t st, int bs, int spc)
 {
     count_launch(1);
-    dim3 grid(nblocks(G.N, bs), S);
-    if (trans) k_mg_residual<T, M, true><<<grid, bs, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
-    else k_mg_residual<T, M, false><<<grid, bs, 0, st>>>(G, J, bc, b, x, r, mask, mstride);
+    dim3 grid(nblocks(G.N, bs), (S + spc - 1) / spc);
+#define ELDER_MGR(TR, SP) \
+    k_mg_residual<T, M, TR, SP><<<grid, bs, 0, st>>>(G, J, bc, b, x, r, mask, mstride, S)
+    if (spc == 2) {
+        if (trans) ELDER_MGR(true, 2);
+        else ELDER_MGR(false, 2);
+    } else {
+        if (trans) ELDER_MGR(true, 1);
+        else ELDER_MGR(false, 1);
+    }
+#undef ELDER_MGR
 }
 
 // Full weighting = transpose of trilinear interpolation on the vertex-centred
@@ -1475,7 +1527,7 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
         cudaStream_t, int);                                                              \
     template void launch_mg_residual<T, MgType<T>::type>(                                \
         const Grid&, const B4<MgType<T>::type>*, const uint8_t*, const V2<T>*,           \
-        const V2<T>*, V2<T>*, int, const int*, int, int, cudaStream_t, int);             \
+        const V2<T>*, V2<T>*, int, const int*, int, int, cudaStream_t, int, int);        \
     template void launch_restrict<T>(const Grid&, const Grid&, const uint8_t*,           \
                                      const V2<T>*, V2<T>*, const int*, int, int,         \
                                      cudaStream_t);                                      \
@@ -1514,7 +1566,7 @@ void launch_convert(const V2<Ts>* x, V2<Td>* y, size_t n, cudaStream_t st)
     template void launch_zline_apply<T, typename MgType<T>::type>(                       \
         const Grid&, const B4<typename MgType<T>::type>*, const B4<T>*, const B4<T>*,    \
         const uint8_t*, const V2<T>*, const V2<T>*, V2<T>*, double, const int*, int, int,\
-        cudaStream_t, int);
+        cudaStream_t, int, int, int);
 ELDER_INST(double)
 ELDER_INST(float)
 #undef ELDER_INST

@@ -96,6 +96,9 @@ def _load():
     lib.elder_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
     lib.elder_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     lib.elder_measure_peak.argtypes = [ip, dp, vp]
+    lib.elder_autotune_choice.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_float)]
     lib.elder_graph_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_char_p)]
@@ -218,6 +221,14 @@ class Elder:
         return {"threads_per_block": dict(zip(names, (x.value for x in b))),
                 "ms_per_launch": {n: dict(zip(cand, [round(ms[3 * i + q], 4) for q in range(3)]))
                                   for i, n in enumerate(names)}}
+
+    def autotune_choice(self, kernel_class: int):
+        """(threads per block, samples per CTA, ms of the 6 candidates) of one class."""
+        bs, spc = ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * 6)()
+        self._check(_lib.elder_autotune_choice(self._h, kernel_class, ctypes.byref(bs),
+                                               ctypes.byref(spc), ms))
+        return bs.value, spc.value, [round(float(v), 4) for v in ms]
 
     def graph_status(self):
         """Device-controlled steps: (cached step graphs, replays, fallback note)."""
@@ -517,6 +528,10 @@ def elder_jacobian(ctx: Elder, *a, **k):
 
 def elder_graph_status(ctx: Elder):
     return ctx.graph_status()
+
+
+def elder_autotune_choice(ctx: Elder, kernel_class: int):
+    return ctx.autotune_choice(kernel_class)
 
 
 class ElderRollout(torch.autograd.Function):

@@ -523,3 +523,30 @@ def test_device_controlled_step_matches_host_driven_step(E, precision):
         p, c, oi = O.newton_step(P, phi[0], K[0], p, c, dt)
         tol = 1e-10 if precision == 0 else 1e-6
         assert np.abs(out[2][n][1].reshape(S, -1)[0] - c).max() <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_samples_per_cta_variants_are_bitwise_equal(E, precision):
+    """Two samples per CTA in the multigrid residual and the z-line sweep
+    (autotune = 2) only regroup the same per-node arithmetic: the states and
+    iteration counts of 3 steps equal those with one sample per CTA
+    (autotune = 0) bit for bit; S = 5 leaves the last CTA half empty."""
+    P = O.Problem(16, 16, 4)
+    S = 5
+    phi, K = _fields(P, S, 61)
+    p0, c0 = O.initial_state(P)
+    out = {}
+    for at in (0, 2):
+        ctx = _ctx(E, 16, 16, 4, S, precision=precision, autotune=at)
+        pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+        hp, hc = pt.repeat(2), ct.repeat(2)
+        traj = []
+        for _ in range(3):
+            st, info = ctx.step_predicted(S, T(phi), T(K), 2, hp, hc, pt, ct, YEAR / 12)
+            assert (st == 0).all()
+            traj.append((H(pt).copy(), H(ct).copy(), [i["krylov_iters"] for i in info]))
+        assert ctx.autotune_choice(E.K_MGRES)[1] == (2 if at == 2 else 1)
+        out[at] = traj
+        ctx.destroy()
+    for a, b in zip(out[0], out[2]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
