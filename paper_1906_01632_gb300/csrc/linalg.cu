@@ -42,12 +42,14 @@ __device__ __forceinline__ void stencil_term(const Grid& G, const B4<M>* __restr
     if (raw) *raw = b;
     const T pp = ok ? mg_load<T>(b.pp) : T(0), pc = ok ? mg_load<T>(b.pc) : T(0);
     const T cp = ok ? mg_load<T>(b.cp) : T(0), cc = ok ? mg_load<T>(b.cc) : T(0);
+    // explicit fused multiply-adds: every instantiation (one or two samples
+    // per CTA) rounds the same way
     if (!TRANS) {
-        yp += pp * xv.p + pc * xv.c;
-        yc += cp * xv.p + cc * xv.c;
+        yp = fma(pp, xv.p, fma(pc, xv.c, yp));
+        yc = fma(cp, xv.p, fma(cc, xv.c, yc));
     } else {
-        yp += pp * xv.p + cp * xv.c;
-        yc += pc * xv.p + cc * xv.c;
+        yp = fma(pp, xv.p, fma(cp, xv.c, yp));
+        yc = fma(pc, xv.p, fma(cc, xv.c, yc));
     }
 }
 
@@ -538,10 +540,10 @@ __global__ void __launch_bounds__(kBS)
             T rc = (mk & BC_C) ? T(0) : bv.c;
             if (k > 0) {
                 const B4<T> L = mask_block(raw_line_block<T, M, false>(qL), mk, bc_prev);
-                rp -= L.pp * gp[q].p + L.pc * gp[q].c;
-                rc -= L.cp * gp[q].p + L.cc * gp[q].c;
+                rp = fma(-L.pp, gp[q].p, fma(-L.pc, gp[q].c, rp));
+                rc = fma(-L.cp, gp[q].p, fma(-L.cc, gp[q].c, rc));
             }
-            gp[q] = V2<T>{Mi.pp * rp + Mi.pc * rc, Mi.cp * rp + Mi.cc * rc};
+            gp[q] = V2<T>{fma(Mi.pp, rp, Mi.pc * rc), fma(Mi.cp, rp, Mi.cc * rc)};
             if (act[q]) xo[on_[q] + n] = gp[q];
         }
         bc_prev = mk;
@@ -559,12 +561,12 @@ __global__ void __launch_bounds__(kBS)
             if (k < G.nz) {
                 const B4<T> C = zC[on_[q] + n];
                 const V2<T> g = xo[on_[q] + n];
-                d[q] = V2<T>{g.p - (C.pp * d[q].p + C.pc * d[q].c),
-                             g.c - (C.cp * d[q].p + C.cc * d[q].c)};
+                d[q] = V2<T>{fma(-C.pp, d[q].p, fma(-C.pc, d[q].c, g.p)),
+                             fma(-C.cp, d[q].p, fma(-C.cc, d[q].c, g.c))};
             }
             V2<T> xn{T(0), T(0)};
             if (MODE != 1) xn = x[on_[q] + n];
-            T op = xn.p + omega * d[q].p, oc = xn.c + omega * d[q].c;
+            T op = fma(omega, d[q].p, xn.p), oc = fma(omega, d[q].c, xn.c);
             if (m & BC_P) op = T(0);
             if (m & BC_C) oc = T(0);
             xo[on_[q] + n] = V2<T>{op, oc};
