@@ -81,12 +81,24 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="the same as --graphs 0")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps of the profiled pass (per-kernel-class CUDA events)")
-    ap.add_argument("--workload", choices=["qmc", "uneven", "config2"], default="qmc",
+    ap.add_argument("--workload", choices=["qmc", "uneven", "config2", "fingers"], default="qmc",
                     help="qmc: the batched 64x64x16 ensemble (the headline); uneven: 48 samples "
                          "at 128x128x32 plus 16 at 256x256x64, dt = 1/24 yr, one context per grid "
                          "size, samples shared out longest-processing-time first across ranks; "
                          "config2: one sample at 128x128x32 for --run-steps steps with the FP64 "
-                         "and the mixed solver, their states compared along the run")
+                         "and the mixed solver, their states compared along the run; "
+                         "fingers: the paper's parallelepiped ensemble (3 random variables, "
+                         "Halton points, 128x128x32, dt = 0.005 yr, the paper's boundary sets) "
+                         "marched 1500 steps to 7.5 yr, with the plume lobes of the mean's 0.5 "
+                         "level set counted")
+    ap.add_argument("--fingers-samples", type=int, default=200)
+    ap.add_argument("--fingers-grid", type=int, nargs=3, default=[128, 128, 32])
+    ap.add_argument("--fingers-dt-yr", type=float, default=0.005)
+    ap.add_argument("--fingers-steps", type=int, default=1500)
+    ap.add_argument("--fingers-snap", type=int, default=300,
+                    help="steps between the moment snapshots of the fingers workload")
+    ap.add_argument("--fingers-out", default="",
+                    help="npz file for the fingers workload's mean and variance fields")
     ap.add_argument("--run-steps", type=int, default=60,
                     help="steps of the configuration's whole run from t = 0, timed beside the "
                          "K bench steps (0: skip)")
@@ -899,6 +911,146 @@ def run_config2(a):
     print(json.dumps(line), flush=True)
 
 
+def plume_lobes(mean, nx, ny, nz, Lx=600.0, Ly=600.0, Lz=150.0, level=0.5, min_nodes=4):
+    """Plume lobes of the level set {mean = level} of a node field
+    [nz+1][ny+1][nx+1] (x fastest, z up, the top plane k = nz).
+
+    Plane cuts: for every node plane below the top, the 8-connected
+    components of {mean > level} with at least min_nodes nodes.  The largest
+    such count and the first plane from the top that reaches it are reported
+    with the centroids [m] of its lobes, each labelled with the nearest of
+    the source square's four corners and its centre.  Column depths: per node
+    column the depth below the top of the lowest node above the level; the
+    components of {depth >= depth_max / 2} are counted the same way."""
+    import numpy as np
+    from scipy import ndimage
+
+    m = np.asarray(mean, dtype=np.float64).reshape(nz + 1, ny + 1, nx + 1)
+    hx, hy, hz = Lx / nx, Ly / ny, Lz / nz
+    conn = np.ones((3, 3), dtype=bool)
+    refs = {"corner(-,-)": (Lx / 4, Ly / 4), "corner(+,-)": (3 * Lx / 4, Ly / 4),
+            "corner(-,+)": (Lx / 4, 3 * Ly / 4), "corner(+,+)": (3 * Lx / 4, 3 * Ly / 4),
+            "centre": (Lx / 2, Ly / 2)}
+
+    def lobes(mask):
+        lab, n = ndimage.label(mask, structure=conn)
+        if n == 0:
+            return lab, []
+        sizes = np.bincount(lab.ravel(), minlength=n + 1)
+        return lab, [i for i in range(1, n + 1) if sizes[i] >= min_nodes]
+
+    counts, best = [], {"count": 0, "z_m": None, "lobes": []}
+    for k in range(nz - 1, -1, -1):
+        lab, keep = lobes(m[k] > level)
+        counts.append(len(keep))
+        if len(keep) > best["count"]:
+            out = []
+            for i in keep:
+                cy, cx = ndimage.center_of_mass(lab == i)
+                x, y = cx * hx, cy * hy
+                near = min(refs, key=lambda r: (refs[r][0] - x) ** 2 + (refs[r][1] - y) ** 2)
+                out.append({"x_m": round(x, 1), "y_m": round(y, 1), "nearest": near,
+                            "nodes": int((lab == i).sum())})
+            best = {"count": len(keep), "z_m": round(k * hz, 3), "lobes": out}
+    above = m > level
+    low = np.where(above.any(0), above.argmax(0), nz + 1)
+    depth = np.where(low <= nz, (nz - low) * hz, 0.0)
+    dmax = float(depth.max())
+    _, ckeep = lobes(depth >= 0.5 * dmax) if dmax > 0 else (None, [])
+    return {"plane_counts_top_down": counts, "max_plane_count": best["count"],
+            "plane": best, "column_depth_max_m": round(dmax, 3),
+            "column_lobes_half_depth": len(ckeep)}
+
+
+def run_fingers(a):
+    """The paper's parallelepiped workload with three random variables
+    (Section 5.3, eq. poro-paral3RVS): the porosity field at Halton points,
+    Kozeny-Carman K, 128x128x32 cells, dt = 0.005 yr, the paper's boundary
+    sets (Section 2.1: c = 1 on the top square, c = 0 on the rest of the top
+    and on the bottom, p = 0 on the four top edges), mixed precision, Newton
+    from the quadratic extrapolation, marched --fingers-steps steps (1500 =
+    7.5 yr) from t = 0 and timed with CUDA events per step.  Every
+    --fingers-snap steps the ensemble mean, variance and P(c > 0.5) are
+    formed (elder_moments) and the plume lobes of the mean's 0.5 level set
+    counted (plume_lobes); Section 5.3 reports five fingers at 7.5 yr, four at
+    the corners and one at the centre."""
+    import numpy as np
+    import torch
+
+    from paper_1906_01632_gb300 import build as B
+    B.build()
+    from paper_1906_01632_gb300 import elder as E
+    from paper_1906_01632_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nx, ny, nz = a.fingers_grid
+    S, steps, snap = a.fingers_samples, a.fingers_steps, max(1, a.fingers_snap)
+    dt = YEAR * a.fingers_dt_yr
+    stream = torch.cuda.current_stream()
+    ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S,
+                                                precision=E.ELDER_MIXED, bc_mode=1))
+    N = ctx.N
+    xi_np = I.halton_xi(S)
+    xi = torch.tensor(xi_np.ravel(), dtype=torch.float64, device=dev)
+    phi, K = ctx.fields(S, 2, xi)
+    p0, c0 = ctx.initial_state(S, device=dev)
+    warm = [p0.clone(), c0.clone(), p0.repeat(2), c0.repeat(2)]
+    for _ in range(max(a.warmup, 2)):  # tuning and graph capture on a discarded copy
+        ctx.step_predicted(S, phi, K, 2, warm[2], warm[3], warm[0], warm[1], dt)
+    del warm
+    p, c, ph, ch = p0.clone(), c0.clone(), p0.repeat(2), c0.repeat(2)
+    torch.cuda.synchronize()
+    ms, newton, krylov, failed, retries = 0.0, 0, 0, 0, 0
+    snaps, lob, fields = {}, {}, {}
+    t_wall = time.time()
+    for n in range(1, steps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = ctx.step_predicted(S, phi, K, 2, ph, ch, p, c, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        newton += sum(i["newton_iters"] for i in info)
+        krylov += sum(i["krylov_iters"] for i in info)
+        failed += int((st != 0).sum())
+        retries += sum(1 for i in info if i["fp64_retry"])
+        if n % snap == 0 or n == steps:
+            mean, var, pexc = ctx.moments(S, c)
+            mh = mean.cpu().numpy()
+            lob[str(n)] = plume_lobes(mh, nx, ny, nz)
+            snaps[f"mean_{n}"] = mh.astype(np.float32)
+            if n == steps:
+                fields = {"var": var.cpu().numpy().astype(np.float32),
+                          "pexc": pexc.cpu().numpy().astype(np.float32)}
+            print(f"fingers: step {n} ({n * a.fingers_dt_yr:.2f} yr), "
+                  f"{S * n / (ms / 1000.0):.1f} sample-timesteps/s so far, lobes "
+                  f"{lob[str(n)]['max_plane_count']} at z = {lob[str(n)]['plane']['z_m']} m, "
+                  f"wall {time.time() - t_wall:.0f} s", file=sys.stderr, flush=True)
+    if a.fingers_out:
+        np.savez_compressed(a.fingers_out, xi=xi_np, grid=np.array([nx, ny, nz]),
+                            dt_yr=np.array(a.fingers_dt_yr), **snaps, **fields)
+    ctx.destroy()
+    line = {"metric": f"sample-timesteps/s, the paper's parallelepiped ensemble (3 random "
+                      f"variables) at {nx}x{ny}x{nz}",
+            "value": S * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": max(a.warmup, 2), "higher_is_better": True, "dtype": "f64+f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": f"elder3d-box-{nx}x{ny}x{nz}-paper3rv-halton{S}",
+                       "dt_yr": a.fingers_dt_yr, "bc": "paper variant (bc_mode 1)",
+                       "fields": "Halton points (bases 2,3,5, first point skipped) -> the "
+                                 "paper's parallelepiped porosity field, Kozeny-Carman K",
+                       "newton_start": "3u^n - 3u^(n-1) + u^(n-2)",
+                       "timed_steps": f"1-{steps} from t = 0"},
+            "iterations": {"newton_per_step": newton / (S * steps),
+                           "krylov_per_step": krylov / (S * steps),
+                           "failed_sample_steps": failed, "fp64_retries": retries},
+            "lobes": lob,
+            "timing": "CUDA events around each step on the launching stream"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -907,6 +1059,8 @@ def main():
         run_uneven(a)
     elif a.workload == "config2":
         run_config2(a)
+    elif a.workload == "fingers":
+        run_fingers(a)
     else:
         run_ours(a)
 

@@ -43,7 +43,7 @@ def test_byte_model_matches_the_stored_formats():
 
 
 def test_traffic_lines_of_the_committed_profiles():
-    assert bench.ncu_traffic("spmv", "mixed") == pytest.approx(436.3)
+    assert bench.ncu_traffic("spmv", "mixed") == pytest.approx(428.0)
     assert bench.ncu_traffic("mg_residual", "mixed") == pytest.approx(229.8)
     assert bench.ncu_traffic("residual", "fp64") == pytest.approx(302.0)
     assert bench.ncu_traffic("no_such_class", "mixed") is None
@@ -65,3 +65,54 @@ def test_uneven_plan_covers_the_ensemble_once():
     assert sorted(seen) == list(range(64))
     total = 48 * nodes[(128, 128, 32)] + 16 * nodes[(256, 256, 64)]
     assert max(loads) <= 4 / 3 * total / 4
+
+
+def _lobe_field(nx, ny, nz, centres, sigma=30.0, depth=93.75):
+    """A node field [nz+1][ny+1][nx+1]: 1 on the top square, and below it
+    Gaussian columns around the given (x, y) centres reaching `depth` m
+    below the top."""
+    import numpy as np
+    x = np.linspace(0, 600, nx + 1)
+    y = np.linspace(0, 600, ny + 1)
+    z = np.linspace(0, 150, nz + 1)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    m = np.zeros_like(X)
+    for xc, yc in centres:
+        m = np.maximum(m, np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / (2 * sigma ** 2)) *
+                       (Z >= 150 - depth))
+    top = (X >= 150) & (X <= 450) & (Y >= 150) & (Y <= 450)
+    m[-1] = np.where(top[-1], 1.0, 0.0)
+    return m.ravel()
+
+
+def test_plume_lobes_counts_five_fingers_at_the_corners_and_centre():
+    pytest.importorskip("scipy")
+    cen = [(150, 150), (450, 150), (150, 450), (450, 450), (300, 300)]
+    r = bench.plume_lobes(_lobe_field(32, 32, 8, cen), 32, 32, 8)
+    assert r["max_plane_count"] == 5
+    assert sorted(l["nearest"] for l in r["plane"]["lobes"]) == sorted(
+        ["corner(-,-)", "corner(+,-)", "corner(-,+)", "corner(+,+)", "centre"])
+    for l in r["plane"]["lobes"]:
+        assert min(abs(l["x_m"] - 150), abs(l["x_m"] - 300), abs(l["x_m"] - 450)) < 1e-6
+    # planes deeper than the columns hold no lobe; the column-depth map sees
+    # the five columns reaching 93.75 m, five cells (the top plane's square
+    # does not count)
+    assert r["plane_counts_top_down"][-1] == 0
+    assert r["column_depth_max_m"] == pytest.approx(93.75)
+    assert r["column_lobes_half_depth"] == 5
+
+
+def test_plume_lobes_single_sheet_and_empty():
+    pytest.importorskip("scipy")
+    import numpy as np
+    one = bench.plume_lobes(_lobe_field(32, 32, 8, [(300, 300)], sigma=120.0), 32, 32, 8)
+    assert one["max_plane_count"] == 1 and one["plane"]["lobes"][0]["nearest"] == "centre"
+    none = bench.plume_lobes(np.zeros(33 * 33 * 9), 32, 32, 8)
+    assert none["max_plane_count"] == 0 and none["column_depth_max_m"] == 0.0
+    assert none["column_lobes_half_depth"] == 0
+
+
+def test_fingers_workload_defaults(monkeypatch):
+    a = _args(monkeypatch, "--workload", "fingers")
+    assert (a.fingers_samples, a.fingers_steps, a.fingers_grid, a.fingers_dt_yr) == \
+        (200, 1500, [128, 128, 32], 0.005)
