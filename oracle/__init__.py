@@ -64,7 +64,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("maxit", ctypes.c_int), ("tol_c", ctypes.c_double),
                 ("tol_p", ctypes.c_double), ("lin_rtol", ctypes.c_double),
                 ("lin_maxit", ctypes.c_int), ("ls_max", ctypes.c_int),
-                ("dense_max", ctypes.c_int), ("smoother", ctypes.c_int)]
+                ("dense_max", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("ilu_beta", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -112,11 +113,15 @@ class NewtonOpts:
     lin_maxit: int = 2000
     ls_max: int = 6
     dense_max: int = 1200
-    smoother: int = 0  # 0 point block Jacobi, 1 vertical-line block Jacobi
+    # 0 point block Jacobi, 1 vertical-line block Jacobi, 2 multicolour
+    # block ILU_beta(0) with beta = ilu_beta
+    smoother: int = 0
+    ilu_beta: float = 0.0
 
     def _c(self) -> _Opts:
         return _Opts(self.maxit, self.tol_c, self.tol_p, self.lin_rtol,
-                     self.lin_maxit, self.ls_max, self.dense_max, self.smoother)
+                     self.lin_maxit, self.ls_max, self.dense_max, self.smoother,
+                     self.ilu_beta)
 
 
 def lib():
@@ -241,6 +246,57 @@ def linear_solve(rowptr, col, val, b, opts: NewtonOpts | None = None, transpose=
     rc = lib().orc_linear_solve(ctypes.c_int(n), _ip(rowptr), _ip(col), _dp(_f64(val)),
                                 _dp(b), _dp(x), ctypes.byref(opts._c()), ctypes.byref(it))
     return x, rc
+
+
+def mc_rank(P: Problem) -> np.ndarray:
+    """Position of every node in the multicolour order (colour = (i&1) +
+    2(j&1) + 4(k&1) ascending, node index order within a colour)."""
+    rank = np.zeros(P.N, np.int32)
+    lib().orc_mc_rank(ctypes.byref(P._c()), _ip(rank))
+    return rank
+
+
+def csr_to_blocks(P: Problem, rowptr, col, val) -> np.ndarray:
+    """Block form [N][27][4] of a CSR matrix with the 27-point block pattern:
+    [n][s] = block (n, n+d), s = (dx+1) + 3(dy+1) + 9(dz+1), (pp, pc, cp, cc)."""
+    B = np.zeros((P.N, 27, 4))
+    lib().orc_csr_to_blocks(ctypes.byref(P._c()), _ip(np.ascontiguousarray(rowptr, np.int32)),
+                            _ip(np.ascontiguousarray(col, np.int32)), _dp(_f64(val)), _dp(B))
+    return B
+
+
+def mcilu_factor(P: Problem, B, beta=0.0) -> np.ndarray:
+    """Multicolour block ILU_beta(0) factors of the block matrix B [N][27][4]
+    (slots of earlier-ranked neighbours: L; the others: U, pivots in slot 13)."""
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    F = np.zeros_like(B)
+    rc = lib().orc_mcilu_factor(ctypes.byref(P._c()), _dp(B), ctypes.c_double(beta), _dp(F))
+    if rc != 0:
+        raise np.linalg.LinAlgError("singular pivot block")
+    return F
+
+
+def mcilu_solve(P: Problem, F, r, transpose=False) -> np.ndarray:
+    """z = (L U)^{-1} r, or (L U)^{-T} r, with the factors of mcilu_factor."""
+    z = np.zeros(2 * P.N)
+    lib().orc_mcilu_solve(ctypes.byref(P._c()), _dp(np.ascontiguousarray(F, dtype=np.float64)),
+                          ctypes.c_int(1 if transpose else 0), _dp(_f64(r)), _dp(z))
+    return z
+
+
+def smoother_apply(P: Problem, phi, K, p, c, dt, kind, r, beta=0.0, transpose=False):
+    """z = P^{-1} r (or P^{-T} r) for the finest level's smoother at (p, c):
+    kind 0 block diagonal, 1 vertical-line block tridiagonal, 2 L U of the
+    multicolour block ILU_beta(0); interior unknowns only (Dirichlet
+    components of r ignored, of z zero)."""
+    z = np.zeros(2 * P.N)
+    rc = lib().orc_smoother_apply(ctypes.byref(P._c()), _dp(_f64(phi)), _dp(_f64(K)),
+                                  _dp(_f64(p)), _dp(_f64(c)), ctypes.c_double(dt),
+                                  ctypes.c_int(kind), ctypes.c_double(beta),
+                                  ctypes.c_int(1 if transpose else 0), _dp(_f64(r)), _dp(z))
+    if rc != 0:
+        raise RuntimeError("orc_smoother_apply failed (singular pivot or coarse grid too large)")
+    return z
 
 
 def newton_step(P: Problem, phi, K, p, c, dt, opts: NewtonOpts | None = None):

@@ -719,9 +719,10 @@ int orc_linear_solve(int n, const int* rowptr, const int* col,
  * with cell-averaged phi and K.  Each level matrix is taken on the interior
  * unknowns: Dirichlet rows and columns are replaced by the identity and the
  * Dirichlet components of every multigrid vector are kept at zero.
- * Smoother: damped 2x2-block Jacobi (the paper's ILU_beta smoother is not
- * specified further); transfers: trilinear interpolation and its
- * transpose; coarsest level: dense LU. */
+ * Smoothers: damped 2x2-block Jacobi, damped block Jacobi over vertical
+ * grid lines, or the multicolour block ILU_beta(0) (the paper's ILU_beta
+ * smoother is not specified further); transfers: trilinear interpolation
+ * and its transpose; coarsest level: dense LU. */
 
 #define ORC_MAXLEV 16
 
@@ -739,6 +740,10 @@ typedef struct {
     int nu1, nu2;
     double omega;
     int line;                     /* vertical-line smoother (else point)      */
+    int ilu;                      /* multicolour block ILU_beta(0) smoother   */
+    int ilu_trans;                /* its factors are the untransposed level
+                                     matrix's: sweeps apply (L U)^{-T}        */
+    double* F[ORC_MAXLEV];        /* [N][27][4] ILU factors                   */
     double* Lb[ORC_MAXLEV];       /* [N][4] line blocks A(n, n-below)         */
     double* Db[ORC_MAXLEV];       /* [N][4] diagonal blocks A(n, n)           */
     double* Ub[ORC_MAXLEV];       /* [N][4] line blocks A(n, n-above)         */
@@ -758,7 +763,7 @@ static void mg_free(orc_mg* mg)
     for (int l = 0; l < mg->nlev; ++l) {
         free(mg->rp[l]); free(mg->ci[l]); free(mg->A[l]); free(mg->Dinv[l]);
         free(mg->dm[l]); free(mg->b[l]); free(mg->x[l]); free(mg->r[l]);
-        free(mg->Lb[l]); free(mg->Db[l]); free(mg->Ub[l]);
+        free(mg->Lb[l]); free(mg->Db[l]); free(mg->Ub[l]); free(mg->F[l]);
     }
     free(mg->LU);
     free(mg->piv);
@@ -784,8 +789,9 @@ static void csr_block(const int* rp, const int* ci, const double* A, int r, int 
 
 static int mg_setup(orc_mg* mg, const orc_problem* P0, const double* phi0,
                     const double* K0, const double* p0, const double* c0,
-                    double dt, int transpose, int line)
+                    double dt, int transpose, int smoother, double beta)
 {
+    int line = smoother == 1;
     memset(mg, 0, sizeof(*mg));
     /* point smoother, damping 0.5: at dt = 1/12 yr the pressure/salt
      * coupling next to the salt source makes block Jacobi with damping 0.7
@@ -796,7 +802,10 @@ static int mg_setup(orc_mg* mg, const orc_problem* P0, const double* phi0,
     mg->nu1 = 1;
     mg->nu2 = 1;
     mg->line = line;
-    mg->omega = line ? 0.7 : 0.5;
+    mg->ilu = smoother == 2;
+    mg->ilu_trans = mg->ilu && transpose;
+    /* ILU sweeps are undamped */
+    mg->omega = mg->ilu ? 1.0 : (line ? 0.7 : 0.5);
     orc_problem P = *P0;
     double *phi = (double*)phi0, *K = (double*)K0, *p = (double*)p0,
            *c = (double*)c0;
@@ -827,6 +836,21 @@ static int mg_setup(orc_mg* mg, const orc_problem* P0, const double* phi0,
                 if (dm[r]) A[q] = (ci[q] == r) ? 1.0 : 0.0;
                 else if (dm[ci[q]]) A[q] = 0.0;
             }
+        if (mg->ilu) {
+            /* the factors of the untransposed level matrix: the transposed
+             * solve's sweeps use their transpose */
+            double* B = (double*)malloc(sizeof(double) * 108 * (size_t)N);
+            mg->F[l] = (double*)malloc(sizeof(double) * 108 * (size_t)N);
+            orc_csr_to_blocks(&P, rp, ci, A, B);
+            int bad = orc_mcilu_factor(&P, B, beta, mg->F[l]);
+            free(B);
+            if (bad) {
+                mg->rp[l] = rp; mg->ci[l] = ci; mg->A[l] = A; mg->dm[l] = dm;
+                mg->nlev = l + 1;
+                if (owned) { free(phi); free(K); free(p); free(c); }
+                return 1;
+            }
+        }
         if (transpose) {
             int* trp = malloc(sizeof(int) * ((size_t)n2 + 1));
             int* tci = malloc(sizeof(int) * (size_t)nnz);
@@ -1019,6 +1043,228 @@ static void mg_smooth_line(const orc_mg* mg, int l, const double* b, double* x,
     mg_zero_dirichlet(mg, l, x);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Multicolour block ILU_beta(0) (Section 5.1)                              */
+/* ------------------------------------------------------------------------ */
+/* The paper's multigrid smoother is ILU_beta, not specified further.
+ * Reading: the incomplete LU factorisation with 2x2 blocks for scalars,
+ * restricted to the block pattern of the level matrix (the 27-point
+ * stencil), in the multicolour order of the nodes: colour = (i&1) + 2(j&1)
+ * + 4(k&1), colours ascending, node index order within a colour.  Two nodes
+ * of one colour never share a cell, so each colour class is an independent
+ * set of the stencil.  The factorisation is Gaussian elimination in its IKJ
+ * form with every update of an entry outside the pattern dropped (Saad,
+ * Iterative Methods for Sparse Linear Systems, 2nd ed., Alg. 10.4); beta
+ * times the dropped block is subtracted from the row's diagonal block
+ * instead (beta = 0: block ILU(0); beta = 1: block modified ILU, whose L U
+ * keeps every block row sum of A). */
+
+static void node_ijk(const orc_problem* P, int n, int* i, int* j, int* k)
+{
+    int sx = P->nx + 1, sy = P->ny + 1;
+    *i = n % sx;
+    *j = (n / sx) % sy;
+    *k = n / (sx * sy);
+}
+
+void orc_mc_rank(const orc_problem* P, int* rank)
+{
+    int N = orc_num_nodes(P), q = 0;
+    for (int colour = 0; colour < 8; ++colour)
+        for (int n = 0; n < N; ++n) {
+            int i, j, k;
+            node_ijk(P, n, &i, &j, &k);
+            if (((i & 1) | ((j & 1) << 1) | ((k & 1) << 2)) == colour) rank[n] = q++;
+        }
+}
+
+/* the neighbour of node n in slot s, or -1 outside the grid */
+static int slot_node(const orc_problem* P, int n, int s)
+{
+    int i, j, k;
+    node_ijk(P, n, &i, &j, &k);
+    i += s % 3 - 1;
+    j += (s / 3) % 3 - 1;
+    k += s / 9 - 1;
+    if (i < 0 || i > P->nx || j < 0 || j > P->ny || k < 0 || k > P->nz) return -1;
+    return node_id(P, i, j, k);
+}
+
+/* the slot of node m in the row of node n, or -1 when they are not
+ * neighbours */
+static int node_slot(const orc_problem* P, int n, int m)
+{
+    int i, j, k, a, b, c;
+    node_ijk(P, n, &i, &j, &k);
+    node_ijk(P, m, &a, &b, &c);
+    int dx = a - i, dy = b - j, dz = c - k;
+    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return -1;
+    return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+}
+
+void orc_csr_to_blocks(const orc_problem* P, const int* rowptr, const int* col,
+                       const double* val, double* B)
+{
+    int N = orc_num_nodes(P);
+    memset(B, 0, sizeof(double) * 108 * (size_t)N);
+    for (int n = 0; n < N; ++n)
+        for (int v = 0; v < 2; ++v)
+            for (int q = rowptr[2 * n + v]; q < rowptr[2 * n + v + 1]; ++q) {
+                int m = col[q] / 2, w = col[q] % 2;
+                int s = node_slot(P, n, m);
+                if (s < 0) abort();  /* not the 27-point block pattern */
+                B[(size_t)n * 108 + 4 * s + 2 * v + w] += val[q];
+            }
+}
+
+static void mul2x2(const double* a, const double* b, double* c)
+{
+    c[0] = a[0] * b[0] + a[1] * b[2];
+    c[1] = a[0] * b[1] + a[1] * b[3];
+    c[2] = a[2] * b[0] + a[3] * b[2];
+    c[3] = a[2] * b[1] + a[3] * b[3];
+}
+
+int orc_mcilu_factor(const orc_problem* P, const double* A, double beta, double* F)
+{
+    int N = orc_num_nodes(P);
+    int* rank = (int*)malloc(sizeof(int) * (size_t)N);
+    int* order = (int*)malloc(sizeof(int) * (size_t)N);
+    orc_mc_rank(P, rank);
+    for (int n = 0; n < N; ++n) order[rank[n]] = n;
+    memcpy(F, A, sizeof(double) * 108 * (size_t)N);
+    int singular = 0;
+    for (int q = 0; q < N; ++q) {
+        int i = order[q];
+        double* Fi = F + (size_t)i * 108;
+        /* the slots of the row's earlier neighbours, by ascending rank */
+        int ks[27], nk = 0;
+        for (int s = 0; s < 27; ++s) {
+            int k = slot_node(P, i, s);
+            if (k < 0 || rank[k] >= rank[i]) continue;
+            int t = nk++;
+            while (t > 0 && rank[slot_node(P, i, ks[t - 1])] > rank[k]) {
+                ks[t] = ks[t - 1];
+                --t;
+            }
+            ks[t] = s;
+        }
+        for (int a = 0; a < nk; ++a) {
+            int k = slot_node(P, i, ks[a]);
+            const double* Fk = F + (size_t)k * 108;
+            double Ui[4], l[4];
+            inv2x2(Fk + 4 * 13, Ui);
+            mul2x2(Fi + 4 * ks[a], Ui, l);            /* L_ik = A_ik U_kk^{-1} */
+            memcpy(Fi + 4 * ks[a], l, sizeof l);
+            for (int e = 0; e < 27; ++e) {            /* row k's U part */
+                int j = slot_node(P, k, e);
+                if (j < 0 || rank[j] <= rank[k]) continue;
+                double lu[4];
+                mul2x2(l, Fk + 4 * e, lu);
+                int t = node_slot(P, i, j);
+                for (int r = 0; r < 4; ++r) {
+                    if (t >= 0) Fi[4 * t + r] -= lu[r];
+                    else Fi[4 * 13 + r] -= beta * lu[r];
+                }
+            }
+        }
+        const double* D = Fi + 4 * 13;
+        if (D[0] * D[3] - D[1] * D[2] == 0.0) singular = 1;
+    }
+    free(rank);
+    free(order);
+    return singular;
+}
+
+void orc_mcilu_solve(const orc_problem* P, const double* F, int transpose,
+                     const double* r, double* z)
+{
+    int N = orc_num_nodes(P);
+    int* rank = (int*)malloc(sizeof(int) * (size_t)N);
+    int* order = (int*)malloc(sizeof(int) * (size_t)N);
+    orc_mc_rank(P, rank);
+    for (int n = 0; n < N; ++n) order[rank[n]] = n;
+    /* z holds y of the first sweep, then the result */
+    if (!transpose) {
+        for (int q = 0; q < N; ++q) {                 /* L y = r */
+            int i = order[q];
+            double y0 = r[2 * i], y1 = r[2 * i + 1];
+            for (int s = 0; s < 27; ++s) {
+                int k = slot_node(P, i, s);
+                if (k < 0 || rank[k] >= rank[i]) continue;
+                const double* Lb = F + (size_t)i * 108 + 4 * s;
+                y0 -= Lb[0] * z[2 * k] + Lb[1] * z[2 * k + 1];
+                y1 -= Lb[2] * z[2 * k] + Lb[3] * z[2 * k + 1];
+            }
+            z[2 * i] = y0;
+            z[2 * i + 1] = y1;
+        }
+        for (int q = N - 1; q >= 0; --q) {            /* U z = y */
+            int i = order[q];
+            double t0 = z[2 * i], t1 = z[2 * i + 1], Di[4];
+            for (int s = 0; s < 27; ++s) {
+                int j = slot_node(P, i, s);
+                if (j < 0 || rank[j] <= rank[i]) continue;
+                const double* Ub = F + (size_t)i * 108 + 4 * s;
+                t0 -= Ub[0] * z[2 * j] + Ub[1] * z[2 * j + 1];
+                t1 -= Ub[2] * z[2 * j] + Ub[3] * z[2 * j + 1];
+            }
+            inv2x2(F + (size_t)i * 108 + 4 * 13, Di);
+            z[2 * i] = Di[0] * t0 + Di[1] * t1;
+            z[2 * i + 1] = Di[2] * t0 + Di[3] * t1;
+        }
+    } else {
+        /* (L U)^T = U^T L^T; U^T is lower block triangular in the order, with
+         * the transposed pivots on its diagonal, L^T upper with unit blocks */
+        for (int q = 0; q < N; ++q) {                 /* U^T y = r */
+            int i = order[q];
+            double t0 = r[2 * i], t1 = r[2 * i + 1], Di[4];
+            for (int s = 0; s < 27; ++s) {
+                int j = slot_node(P, i, s);
+                if (j < 0 || rank[j] >= rank[i]) continue;
+                const double* Ub = F + (size_t)j * 108 + 4 * node_slot(P, j, i);
+                t0 -= Ub[0] * z[2 * j] + Ub[2] * z[2 * j + 1];
+                t1 -= Ub[1] * z[2 * j] + Ub[3] * z[2 * j + 1];
+            }
+            inv2x2(F + (size_t)i * 108 + 4 * 13, Di);
+            z[2 * i] = Di[0] * t0 + Di[2] * t1;
+            z[2 * i + 1] = Di[1] * t0 + Di[3] * t1;
+        }
+        for (int q = N - 1; q >= 0; --q) {            /* L^T z = y */
+            int i = order[q];
+            double t0 = z[2 * i], t1 = z[2 * i + 1];
+            for (int s = 0; s < 27; ++s) {
+                int j = slot_node(P, i, s);
+                if (j < 0 || rank[j] <= rank[i]) continue;
+                const double* Lb = F + (size_t)j * 108 + 4 * node_slot(P, j, i);
+                t0 -= Lb[0] * z[2 * j] + Lb[2] * z[2 * j + 1];
+                t1 -= Lb[1] * z[2 * j] + Lb[3] * z[2 * j + 1];
+            }
+            z[2 * i] = t0;
+            z[2 * i + 1] = t1;
+        }
+    }
+    free(rank);
+    free(order);
+}
+
+/* one ILU sweep: x += omega (L U)^{-1} (b - A x), or (L U)^{-T} for the
+ * transposed level matrix (the factors of the untransposed one) */
+static void mg_smooth_ilu(const orc_mg* mg, int l, const double* b, double* x,
+                          double* tmp)
+{
+    int n = mg->n[l];
+    csr_matvec(n, mg->rp[l], mg->ci[l], mg->A[l], x, tmp);
+    double* r = (double*)calloc((size_t)n, sizeof(double));
+    double* z = (double*)calloc((size_t)n, sizeof(double));
+    for (int i = 0; i < n; ++i) r[i] = mg->dm[l][i] ? 0.0 : b[i] - tmp[i];
+    orc_mcilu_solve(&mg->P[l], mg->F[l], mg->ilu_trans, r, z);
+    for (int i = 0; i < n; ++i) x[i] += mg->omega * z[i];
+    free(r);
+    free(z);
+    mg_zero_dirichlet(mg, l, x);
+}
+
 /* one damped block-Jacobi sweep: x += omega D^{-1} (b - A x) */
 static void mg_smooth(const orc_mg* mg, int l, const double* b, double* x,
                       double* tmp)
@@ -1026,6 +1272,10 @@ static void mg_smooth(const orc_mg* mg, int l, const double* b, double* x,
     int n = mg->n[l];
     if (mg->line) {
         mg_smooth_line(mg, l, b, x, tmp);
+        return;
+    }
+    if (mg->ilu) {
+        mg_smooth_ilu(mg, l, b, x, tmp);
         return;
     }
     csr_matvec(n, mg->rp[l], mg->ci[l], mg->A[l], x, tmp);
@@ -1107,6 +1357,21 @@ static void mg_precond(void* vctx, const double* r, double* z)
         if (mg->dm[0][i]) z[i] = r[i];
 }
 
+int orc_smoother_apply(const orc_problem* P, const double* phi, const double* K,
+                       const double* p, const double* c, double dt, int kind,
+                       double beta, int transpose, const double* r, double* z)
+{
+    orc_mg mg;
+    int rc = mg_setup(&mg, P, phi, K, p, c, dt, transpose, kind, beta);
+    if (rc == 0) {
+        for (int i = 0; i < mg.n[0]; ++i) z[i] = 0.0;
+        mg.omega = 1.0;   /* one undamped sweep from 0: z = P^{-1} r */
+        mg_smooth(&mg, 0, r, z, mg.r[0]);
+    }
+    mg_free(&mg);
+    return rc;
+}
+
 /* Solve J x = b (or J^T x = b) at state (p, c); (rowptr, col, val) hold the
  * full J (or J^T).  Dense LU for small systems, else BiCGStab + V-cycle. */
 static int solve_at_state(const orc_problem* P, const double* phi,
@@ -1118,7 +1383,7 @@ static int solve_at_state(const orc_problem* P, const double* phi,
     int n = 2 * orc_num_nodes(P);
     if (n <= o->dense_max) return orc_linear_solve(n, rowptr, col, val, b, x, o, iters);
     orc_mg mg;
-    int rc = mg_setup(&mg, P, phi, K, p, c, dt, transpose, o->smoother == 1);
+    int rc = mg_setup(&mg, P, phi, K, p, c, dt, transpose, o->smoother, o->ilu_beta);
     if (rc == 0) {
         for (int i = 0; i < n; ++i) x[i] = 0.0;
         double rr;

@@ -52,8 +52,10 @@ typedef struct {
     int smoother;       /* multigrid smoother of the iterative solve:
                            0 damped 2x2-block Jacobi, 1 damped block Jacobi
                            over vertical grid lines (block-tridiagonal
-                           solve per line); the converged step does not
-                           depend on it                                    */
+                           solve per line), 2 multicolour block
+                           ILU_beta(0) (orc_mcilu_factor, undamped); the
+                           converged step does not depend on it            */
+    double ilu_beta;    /* beta of smoother 2                              */
 } orc_newton_opts;
 
 typedef struct {
@@ -116,6 +118,41 @@ int orc_bicgstab_ilu0(int n, const int* rowptr, const int* col,
 int orc_linear_solve(int n, const int* rowptr, const int* col,
                      const double* val, const double* b, double* x,
                      const orc_newton_opts* o, int* iters);
+
+/* Multicolour block ILU_beta(0) (Section 5.1 names the multigrid smoother
+ * ILU_beta without defining it).  Block matrices on the node grid are held
+ * as [N][27][4]: entry [n][s] is the 2x2 block (n, n+d) of the neighbour at
+ * offset d = (dx,dy,dz), s = (dx+1) + 3(dy+1) + 9(dz+1), entries (pp, pc,
+ * cp, cc); blocks of neighbours outside the grid are 0.
+ *
+ * orc_mc_rank: rank[n] = position of node n in the multicolour order
+ * (colour = (i&1) + 2(j&1) + 4(k&1), colours ascending, node index order
+ * within a colour).
+ * orc_csr_to_blocks: the block form B of a CSR matrix with the 27-point
+ * block pattern (orc_jac_pattern, or its transpose).
+ * orc_mcilu_factor: the factors F of A in that order, in A's block form:
+ * slots whose neighbour has a smaller rank hold L (unit block diagonal
+ * implied), the others U with the pivot blocks in slot 13.  Returns 0, or 1
+ * when a pivot block is singular.
+ * orc_mcilu_solve: z = (L U)^{-1} r, or (L U)^{-T} r when transpose = 1;
+ * r, z: [N][2] (z may not alias r).
+ * orc_smoother_apply: one application of a multigrid smoother's
+ * preconditioner on the finest grid, linearised at (p, c) with time step dt:
+ * z = P^{-1} r (transpose = 0) or P^{-T} r on the interior unknowns of the
+ * Jacobian (Dirichlet rows and columns replaced by the identity; Dirichlet
+ * components of r ignored, those of z set to 0), with P the 2x2 block
+ * diagonal (kind 0), the block-tridiagonal part along vertical grid lines
+ * (kind 1) or L U of the multicolour block ILU_beta(0) factors (kind 2).
+ * Returns 0, or 1 on a singular pivot. */
+void orc_mc_rank(const orc_problem* P, int* rank);
+void orc_csr_to_blocks(const orc_problem* P, const int* rowptr, const int* col,
+                       const double* val, double* B);
+int orc_mcilu_factor(const orc_problem* P, const double* A, double beta, double* F);
+void orc_mcilu_solve(const orc_problem* P, const double* F, int transpose,
+                     const double* r, double* z);
+int orc_smoother_apply(const orc_problem* P, const double* phi, const double* K,
+                       const double* p, const double* c, double dt, int kind,
+                       double beta, int transpose, const double* r, double* z);
 
 /* One implicit Euler step by Newton with line search.  p, c: in u^n, out
  * u^{n+1}.  Returns info->status. */
