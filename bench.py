@@ -68,7 +68,9 @@ def parse():
                     help="time only the gPC surrogate kernels (projection, exceedance) and exit")
     ap.add_argument("--gpc-samples", type=int, default=1_000_000,
                     help="surrogate sample points per node of the exceedance timing")
-    ap.add_argument("--smoother", choices=["jacobi", "zline"], default="zline")
+    ap.add_argument("--smoother", choices=["jacobi", "zline", "ilu"], default="zline",
+                    help="multigrid smoother: point block Jacobi, z-line block Jacobi, or the "
+                         "multicolour block ILU(0)")
     ap.add_argument("--predictor", type=int, choices=[0, 1, 2], default=2,
                     help="Newton's starting point: 0 u^n (elder_step), 1 2u^n - u^{n-1}, "
                          "2 3u^n - 3u^{n-1} + u^{n-2} (elder_step_predicted)")
@@ -126,7 +128,8 @@ def workload_config(a):
         "precision": a.precision,
         "smoother": a.smoother,
         "solver": "inexact Newton (Krylov rtol 1e-2), BiCGStab + V(1,0) multigrid, " +
-                  ("z-line damping 0.95" if a.smoother == "zline" else "point block Jacobi damping 0.5"),
+                  {"zline": "z-line damping 0.95", "jacobi": "point block Jacobi damping 0.5",
+                   "ilu": "multicolour block ILU(0), undamped"}[a.smoother],
         "newton_start": ["u^n", "2u^n - u^(n-1)", "3u^n - 3u^(n-1) + u^(n-2)"][a.predictor],
         "fields": fields,
         "l2": "no flush: per-step working set (Jacobians of all levels, vectors) ~10 GB >> 129 MB L2",
@@ -327,7 +330,8 @@ def run_ours(a):
     S = a.samples
     dt = YEAR * a.dt_yr
     prec = E.ELDER_MIXED if a.precision == "mixed" else E.ELDER_FP64
-    smoother = E.ELDER_SMOOTH_ZLINE if a.smoother == "zline" else E.ELDER_SMOOTH_JACOBI
+    smoother = {"zline": E.ELDER_SMOOTH_ZLINE, "jacobi": E.ELDER_SMOOTH_JACOBI,
+                "ilu": E.ELDER_SMOOTH_ILU}[a.smoother]
     ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S, precision=prec,
                                                 smoother=smoother,
                                                 use_graphs=a.graphs))
@@ -457,7 +461,9 @@ def run_ours(a):
                 "frac": achieved / peak if achieved else None,
                 "peak_source": src,
                 "traffic": (tr * bytes_per_launch /
-                            max(1e-30, E_model_bytes(top, tsize, nx, ny, nz, a.smoother == "zline"))
+                            max(1e-30, E_model_bytes(top, tsize, nx, ny, nz,
+                                                     a.smoother != "jacobi",
+                                                     ilu=a.smoother == "ilu"))
                             if tr is not None else None),
                 "algorithmic_flops_per_launch": pk["flops"] / max(pk["launches"], 1),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": per_launch_ms,
@@ -682,21 +688,29 @@ def gpc_timings(E, torch, cfield, stream, Ns=1_000_000, apk=None):
     return res
 
 
-def E_model_bytes(cls, tsize, nx, ny, nz, line=True):
+def E_model_bytes(cls, tsize, nx, ny, nz, line=True, ilu=False):
     """Algorithmic bytes per node of one launch (mirrors the library's model);
     the mixed path stores the multigrid matrices in bfloat16.  With the z-line
     smoother the sweep from x = 0 reads the assembly's line factors (zMi, zC),
     the lower line block, b and writes x; the assembly also forms those
-    factors (reading Dinv and both line blocks)."""
+    factors (reading Dinv and both line blocks).  With the ILU smoother
+    (ilu=True) the sweep from x = 0 reads the 26 factor blocks, the inverse
+    pivot, b and bc twice, writes, reads and rewrites its scratch vector and
+    writes x; the assembly also forms the factors (J, Dinv, bc read; 26
+    factor blocks and the inverse pivot written)."""
     N = (nx + 1) * (ny + 1) * (nz + 1)
     cpn = nx * ny * nz / N
     mz = 2 if tsize == 4 else 8
+    smooth0 = (12 * tsize + 4 * mz + 1) if line else 8 * tsize + 1
+    if ilu:
+        smooth0 = 104 * mz + 14 * tsize + 2
     return {"smooth": 108 * mz + 10 * tsize + 1,
-            "smooth0": (12 * tsize + 4 * mz + 1) if line else 8 * tsize + 1,
+            "smooth0": smooth0,
             "spmv": 108 * tsize + 6 * tsize + 1, "mg_residual": 108 * mz + 6 * tsize + 1,
             "residual": 49 + 16 * cpn,
             "jacobian": 108 * tsize + 108 * mz + 4 * tsize + 17 + 16 * cpn +
-                        ((12 * tsize + 8 * mz + 1) if line else 0)}[cls]
+                        ((12 * tsize + 8 * mz + 1) if line else 0) +
+                        ((212 * mz + 8 * tsize + 1) if ilu else 0)}[cls]
 
 
 # --------------------------------------------------------------------------

@@ -61,7 +61,7 @@ enum {
 enum { ELDER_FP64 = 0, ELDER_MIXED = 1 };
 
 /* multigrid smoothers (Section 5.1) */
-enum { ELDER_SMOOTH_JACOBI = 0, ELDER_SMOOTH_ZLINE = 1 };
+enum { ELDER_SMOOTH_JACOBI = 0, ELDER_SMOOTH_ZLINE = 1, ELDER_SMOOTH_ILU = 2 };
 
 /* Boundary-condition sets (Section 2.1 and the caption of Fig. 1):
  *  0 benchmark: c=1 on the closed top square [Lx/4,3Lx/4]x[Ly/4,3Ly/4],
@@ -126,7 +126,16 @@ typedef struct {
                                  Jacobi; ELDER_SMOOTH_ZLINE: damped block
                                  Jacobi over vertical grid lines (block
                                  tridiagonal solve per line, nz <= 128;
-                                 the default).  The robust re-solve of
+                                 the default); ELDER_SMOOTH_ILU: the
+                                 multicolour block ILU_beta(0) of the
+                                 paper's smoother ILU_beta (factors of each
+                                 level's interior operator in the 8-colour
+                                 node order, colour (i&1)+2(j&1)+4(k&1);
+                                 fill outside the 27-point block pattern
+                                 dropped, beta times it subtracted from the
+                                 row's diagonal block; a sweep is x += omega
+                                 (L U)^{-1}(b - A x), and (L U)^{-T} in the
+                                 transposed solves).  The robust re-solve of
                                  failed samples always uses the z-line
                                  smoother (damping 0.5).                    */
     double omega_line;        /* damping of the z-line smoother (default
@@ -136,6 +145,11 @@ typedef struct {
                                  reaches it is solved again in FP64 with
                                  newton_maxit; a cap of 1 forces that FP64
                                  re-solve from the host (failure-tier test) */
+    double ilu_beta;          /* beta of ELDER_SMOOTH_ILU (default 0: block
+                                 ILU(0); 1: modified ILU, whose pivots are
+                                 nearly singular on this system because the
+                                 pressure rows sum to about 0)              */
+    double omega_ilu;         /* damping of the ILU sweep (default 1)       */
 } elder_config;
 
 /* Per-sample statistics of one elder_step call (host struct). */
@@ -273,6 +287,24 @@ int elder_solve(elder_ctx* ctx, int S, const double* phi, const double* K,
                 const double* p, const double* c, double dt, int transpose,
                 const double* rhs, double* x, double rtol, int32_t* status,
                 void* stream);
+
+/* One application of a multigrid smoother's preconditioner on the finest
+ * level (Section 5.1), linearised at (p, c) with time step dt: z = P^{-1} r
+ * (transpose = 0) or P^{-T} r (transpose = 1) on the interior unknowns of
+ * the Jacobian (Dirichlet rows and columns replaced by the identity), with
+ * P the 2x2 block diagonal (kind ELDER_SMOOTH_JACOBI), the block-tridiagonal
+ * part along vertical grid lines (kind ELDER_SMOOTH_ZLINE, nz <= 128) or
+ * L U of the multicolour block ILU_beta(0) factors with beta = cfg ilu_beta
+ * (kind ELDER_SMOOTH_ILU; the transposed application uses the factors of
+ * the untransposed operator).  Every kind needs no configuration: the
+ * factors are formed for the call.  Computed in the context's multigrid
+ * precision: FP64, or in ELDER_MIXED bfloat16 matrices and factors with
+ * FP32 arithmetic and vectors.  r, z: [S][N][2] device (p, c interleaved);
+ * Dirichlet components of r are ignored, those of z are 0.  Used by the
+ * parity tests of the smoothers. */
+int elder_smoother_apply(elder_ctx* ctx, int S, const double* phi, const double* K,
+                         const double* p, const double* c, double dt, int kind,
+                         int transpose, const double* r, double* z, void* stream);
 
 /* Sample statistics over S fields c[S][N] (Section 3, eqs. pdestat and
  * numer_var, and the exceedance estimate of Section 3.3):

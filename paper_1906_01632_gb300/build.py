@@ -1,6 +1,6 @@
 """Builds libelder.so (the C-ABI library of include/elder.h) in-tree with nvcc.
 
-Four translation units compiled in parallel for sm_103a only, then linked
+Five translation units compiled in parallel for sm_103a only, then linked
 as one shared library.  Output: paper_1906_01632_gb300/_build/libelder.so.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libelder.so")
-UNITS = ["assembly.cu", "linalg.cu", "elder_api.cu", "gpc.cu"]
+UNITS = ["assembly.cu", "linalg.cu", "elder_api.cu", "gpc.cu", "ilu.cu"]
 HEADERS = ["common.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

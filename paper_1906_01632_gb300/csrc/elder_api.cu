@@ -147,6 +147,8 @@ template <class T> struct Solver : SolverBase {
     std::vector<B4<M>*> Jm;        // multigrid matrices per level (M)
     std::vector<B4<T>*> Dinv;      // inverse interior diagonal blocks per level
     std::vector<B4<T>*> zMi, zC;   // block-LU factors of the vertical lines per level
+    std::vector<B4<M>*> F;         // multicolour ILU factors per level (ILU smoother)
+    std::vector<B4<T>*> Fd;        // their inverse pivot blocks
     std::vector<V2<T>*> mb, mx, mx2, mr;  // multigrid vectors per level
     V2<T> *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr,
           *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr, *b = nullptr,
@@ -288,6 +290,7 @@ Phys make_phys(const elder_config& c, double dt)
 // Damping of the configured smoother.
 double configured_omega(const elder_config& cf)
 {
+    if (cf.smoother == ELDER_SMOOTH_ILU) return cf.omega_ilu;
     return cf.smoother == ELDER_SMOOTH_ZLINE ? cf.omega_line : cf.omega;
 }
 
@@ -298,12 +301,17 @@ double model_bytes(int cls, int T, int Mz, const Grid& G, int line)
     // or 0 when the level has none).  line (SMOOTH0): 1 the z-line sweep that
     // factors as it goes, reading the two vertical line blocks of J besides
     // Dinv; 2 the sweep with the assembly's line factors (zMi, zC and the
-    // lower line block).  line (JACOBIAN): 1 with the line factorisation.
+    // lower line block); 3 the multicolour ILU sweep from x = 0 (both
+    // triangular solves: the 26 factor blocks, the inverse pivot, b, the
+    // scratch vector written, read and written again, x_out, bc twice).
+    // line (JACOBIAN): bit 0 with the line factorisation, bit 1 with the ILU
+    // factorisation (J, Dinv and bc read, the factors written).
     const double cells_per_node = (double)G.C / G.N;
     const int Td = T ? T : Mz;
     switch (cls) {
     case ELDER_K_SMOOTH: return 108 * Mz + (4 + 2 + 2 + 2) * T + 1;  // J, Dinv, b, x, xo, bc
     case ELDER_K_SMOOTH0:
+        if (line == 3) return 104 * Mz + (4 + 2 + 2 + 2 + 2 + 2) * T + 2;
         if (line == 2) return (4 + 4 + 2 + 2) * T + 4 * Mz + 1;    // zMi, zC, b, xo, L, bc
         return (4 + 2 + 2) * T + 1 + (line ? 8 * Mz : 0);          // Dinv, b, xo, bc (+ L, U)
     case ELDER_K_SPMV: return 108 * Mz + (2 + 2 + 2) * T + 1;        // J, x, y, a, bc
@@ -313,7 +321,8 @@ double model_bytes(int cls, int T, int Mz, const Grid& G, int line)
     case ELDER_K_JACOBIAN:  // J written (Krylov + multigrid copies), Dinv; p, c, bc, phi, K;
                             // line factors: Dinv, L, U, bc read, zMi, zC written
         return 108 * T + 108 * Mz + 4 * Td + 16 + 1 + 16 * cells_per_node +
-               (line ? 12 * Td + 8 * Mz + 1 : 0);
+               ((line & 1) ? 12 * Td + 8 * Mz + 1 : 0) +
+               ((line & 2) ? 108 * Mz + 104 * Mz + 8 * Td + 1 : 0);
     }
     return 0.0;
 }
@@ -455,6 +464,17 @@ template <class T> void solver_alloc(elder_ctx* ctx, Solver<T>& sv, int cap)
             sv.zMi.push_back(nullptr);
             sv.zC.push_back(nullptr);
         }
+        // the ILU smoother's factors on every smoothed level (the coarsest
+        // is solved by its dense inverse)
+        if (ctx->cfg.smoother == ELDER_SMOOTH_ILU && l < L - 1) {
+            sv.F.push_back(dalloc<B4<typename Solver<T>::M>>(nN * 27));
+            sv.mem.add(sv.F.back());
+            sv.Fd.push_back(dalloc<B4<T>>(nN));
+            sv.mem.add(sv.Fd.back());
+        } else {
+            sv.F.push_back(nullptr);
+            sv.Fd.push_back(nullptr);
+        }
         for (auto* vec : {&sv.mb, &sv.mx, &sv.mx2, &sv.mr}) {
             vec->push_back(dalloc<V2<T>>(nN));
             sv.mem.add(vec->back());
@@ -510,8 +530,12 @@ void assemble(elder_ctx* ctx, Solver<T>& sv, int S, const double* phi0,
         if (sv.zMi[l])
             launch_zline_factor<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], sv.zMi[l], sv.zC[l],
                                       mask, mstride, S, st);
+        // the multicolour ILU factors for the ILU sweeps
+        if (sv.F[l])
+            launch_ilu_factor<T, M>(G, sv.Jm[l], sv.Dinv[l], ctx->bc[l], sv.F[l], sv.Fd[l],
+                                    ctx->cfg.ilu_beta, mask, mstride, S, st);
         prof_end(ctx, pi, ELDER_K_JACOBIAN, G, JT ? (int)sizeof(T) : 0, (int)sizeof(M), n_active,
-                 st, sv.zMi[l] ? 1 : 0);
+                 st, (sv.zMi[l] ? 1 : 0) | (sv.F[l] ? 2 : 0));
     }
     launch_coarse_inverse<typename Solver<T>::M>(ctx->grids.back(), ctx->bc.back(), sv.Jm.back(),
                                                  sv.work,
@@ -568,8 +592,19 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     // the non-transposed z-line sweep substitutes with the line factors of
     // the assembly; the transposed one (adjoint solves) factors as it goes
     const bool fact = line && !trans && sv.zMi[l];
+    // the ILU sweeps keep their triangular solves in the level's residual
+    // vector (free until the restriction's residual is formed)
+    const bool ilu = ctx->smoother_now == ELDER_SMOOTH_ILU && sv.F[l];
     auto sweep = [&](const V2<T>* xin, V2<T>* xout) {
-        if (fact && xin == nullptr) {
+        if (ilu && xin == nullptr) {
+            launch_ilu_apply<T, M>(G, sv.F[l], sv.Fd[l], ctx->bc[l], b, sv.mr[l], nullptr, xout,
+                                   ctx->omega_now, trans, 1, mask, KSTRIDE, S, st);
+        } else if (ilu) {
+            launch_mg_residual<T, M>(G, sv.Jm[l], ctx->bc[l], b, xin, sv.mr[l], trans, mask,
+                                     KSTRIDE, S, st, bs_mr, spc_mr);
+            launch_ilu_apply<T, M>(G, sv.F[l], sv.Fd[l], ctx->bc[l], sv.mr[l], sv.mr[l], xin,
+                                   xout, ctx->omega_now, trans, 2, mask, KSTRIDE, S, st);
+        } else if (fact && xin == nullptr) {
             launch_zline_apply<T, M>(G, sv.Jm[l], sv.zMi[l], sv.zC[l], ctx->bc[l], b, nullptr,
                                      xout, ctx->omega_now, mask, KSTRIDE, S, st, 1, bs_zl, spc_zl);
         } else if (fact) {
@@ -593,7 +628,8 @@ void vcycle(elder_ctx* ctx, Solver<T>& sv, int l, const V2<T>* b, V2<T>* out,
     };
     int pi = prof_begin(ctx, st);
     sweep(nullptr, cur);
-    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), sizeof(M), na, st, fact ? 2 : -1);
+    prof_end(ctx, pi, ELDER_K_SMOOTH0, G, sizeof(T), sizeof(M), na, st,
+             ilu ? 3 : (fact ? 2 : -1));
     for (int q = 1; q < nu1; ++q) {
         pi = prof_begin(ctx, st);
         sweep(cur, oth);
@@ -1490,6 +1526,57 @@ int solve_impl(elder_ctx* ctx, int S, const double* phi, const double* K, const 
     return rc;
 }
 
+// elder_smoother_apply in the multigrid precision of T's solver.
+template <class T>
+void smoother_apply_impl(elder_ctx* ctx, int S, const double* phi, const double* K,
+                         const double* p, const double* c, double dt, int kind, int trans,
+                         const double* r, double* z, cudaStream_t st)
+{
+    using M = typename Solver<T>::M;
+    Solver<T>& sv = solver_reserve<T>(ctx, S);
+    const Grid& G = ctx->grids[0];
+    const size_t nN = (size_t)S * G.N;
+    average_coefficients<T>(ctx, S, phi, K, st);
+    assemble<T>(ctx, sv, S, phi, K, p, c, make_phys(ctx->cfg, dt), nullptr, 0, S, st);
+    V2<T>* bT = sv.b;
+    if (std::is_same<T, double>::value)
+        CK(cudaMemcpyAsync(bT, r, sizeof(double) * 2 * nN, cudaMemcpyDeviceToDevice, st));
+    else
+        launch_convert<double, T>(reinterpret_cast<const V2<double>*>(r), bT, nN, st);
+    DevFree tmp;
+    if (kind == ELDER_SMOOTH_JACOBI) {
+        launch_smooth<T, M>(G, sv.Jm[0], sv.Dinv[0], ctx->bc[0], bT, nullptr, sv.x, 1.0, trans,
+                            nullptr, 0, S, st, kBS);
+    } else if (kind == ELDER_SMOOTH_ZLINE) {
+        if (!trans && sv.zMi[0])
+            launch_zline_apply<T, M>(G, sv.Jm[0], sv.zMi[0], sv.zC[0], ctx->bc[0], bT, nullptr,
+                                     sv.x, 1.0, nullptr, 0, S, st, 1);
+        else
+            launch_smooth_zline<T, M>(G, sv.Jm[0], sv.Dinv[0], ctx->bc[0], bT, nullptr, sv.x,
+                                      1.0, trans, nullptr, 0, S, st, 1);
+    } else {
+        B4<M>* F = sv.F[0];
+        B4<T>* Fd = sv.Fd[0];
+        if (!F) {  // not configured: factors for this call
+            F = dalloc<B4<M>>(nN * 27);
+            tmp.add(F);
+            Fd = dalloc<B4<T>>(nN);
+            tmp.add(Fd);
+            launch_ilu_factor<T, M>(G, sv.Jm[0], sv.Dinv[0], ctx->bc[0], F, Fd,
+                                    ctx->cfg.ilu_beta, nullptr, 0, S, st);
+        }
+        launch_ilu_apply<T, M>(G, F, Fd, ctx->bc[0], bT, sv.mr[0], nullptr, sv.x, 1.0, trans, 1,
+                               nullptr, 0, S, st);
+    }
+    if (std::is_same<T, double>::value)
+        CK(cudaMemcpyAsync(z, sv.x, sizeof(double) * 2 * nN, cudaMemcpyDeviceToDevice, st));
+    else
+        launch_convert<T, double>(sv.x, reinterpret_cast<V2<double>*>(z), nN, st);
+    CKL();
+    CK(cudaStreamSynchronize(st));  // before the temporary factors are freed
+}
+
+
 int set_error(elder_ctx* ctx, const Fail& f)
 {
     if (ctx) ctx->err = f.msg;
@@ -1597,6 +1684,8 @@ int elder_config_default(elder_config* cfg, int nx, int ny, int nz)
     cfg->newton_estimate = 1;
     cfg->smoother = ELDER_SMOOTH_ZLINE;
     cfg->mixed_newton_maxit = 0;
+    cfg->ilu_beta = 0.0;
+    cfg->omega_ilu = 1.0;
     return ELDER_OK;
 }
 
@@ -1619,8 +1708,10 @@ int elder_create(const elder_config* cfg, elder_ctx** out)
         (c.precision != ELDER_FP64 && c.precision != ELDER_MIXED) || c.newton_maxit < 1 ||
         c.autotune < 0 || c.autotune > 2 ||
         c.lin_maxit < 1 || c.nu1 < 1 || c.nu2 < 0 || c.ls_max < 0 ||
-        (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE) ||
-        !(c.omega > 0) || !(c.omega_line > 0) || c.mixed_newton_maxit < 0 ||
+        (c.smoother != ELDER_SMOOTH_JACOBI && c.smoother != ELDER_SMOOTH_ZLINE &&
+         c.smoother != ELDER_SMOOTH_ILU) ||
+        !(c.omega > 0) || !(c.omega_line > 0) || !(c.omega_ilu > 0) ||
+        !std::isfinite(c.ilu_beta) || c.mixed_newton_maxit < 0 ||
         c.use_graphs < 0 || c.use_graphs > 2) {
         g_create_error = "invalid elder_config";
         return ELDER_EINVAL;
@@ -1895,6 +1986,34 @@ int elder_solve(elder_ctx* ctx, int S, const double* phi, const double* K, const
     } catch (const Fail& f) {
         return set_error(ctx, f);
     }
+}
+
+int elder_smoother_apply(elder_ctx* ctx, int S, const double* phi, const double* K,
+                         const double* p, const double* c, double dt, int kind, int transpose,
+                         const double* r, double* z, void* stream)
+{
+    if (!ctx) return ELDER_EINVAL;
+    if (bad_S(ctx, S)) return ELDER_EINVAL;
+    if (!phi || !K || !p || !c || !r || !z || !(dt > 0) || kind < ELDER_SMOOTH_JACOBI ||
+        kind > ELDER_SMOOTH_ILU || (transpose != 0 && transpose != 1)) {
+        ctx->err = "elder_smoother_apply: bad argument";
+        return ELDER_EINVAL;
+    }
+    if (kind == ELDER_SMOOTH_ZLINE && ctx->grids[0].nz + 1 > kMaxLine) {
+        ctx->err = "elder_smoother_apply: the z-line smoother needs nz <= 128";
+        return ELDER_EINVAL;
+    }
+    try {
+        if (ctx->cfg.precision == ELDER_MIXED)
+            smoother_apply_impl<float>(ctx, S, phi, K, p, c, dt, kind, transpose, r, z,
+                                       (cudaStream_t)stream);
+        else
+            smoother_apply_impl<double>(ctx, S, phi, K, p, c, dt, kind, transpose, r, z,
+                                        (cudaStream_t)stream);
+    } catch (const Fail& f) {
+        return set_error(ctx, f);
+    }
+    return ELDER_OK;
 }
 
 int elder_initial_state(elder_ctx* ctx, int S, double* p, double* c, void* stream)

@@ -227,6 +227,33 @@ void launch_zline_apply(const Grid& G, const B4<M>* J, const B4<T>* zMi, const B
                         double omega, const int* mask, int mstride, int S, cudaStream_t st,
                         int mode, int bs = 128, int spc = 1);
 
+// Multicolour block ILU_beta(0) smoother.  Colour c = (i&1) + 2(j&1) +
+// 4(k&1); the factors are stored with the node axis in colour-blocked order:
+// colour c at positions off[c] .. off[c+1]-1, its nodes in natural order;
+// cnt_x[p] / cnt_y[p] count the nodes of index parity p along x / y.
+struct IluLayout {
+    int off[9];
+    int cnt_x[2], cnt_y[2];
+};
+IluLayout ilu_layout(const Grid& G);
+// Factors of a level's interior operator: F [S][27][N] (storage type M,
+// colour-blocked node axis: L in the slots of smaller-colour neighbours, U
+// in the others) and Fd [S][N] (inverse pivot blocks).  8 launches.
+template <class T, class M>
+void launch_ilu_factor(const Grid& G, const B4<M>* J, const B4<T>* Dinv, const uint8_t* bc,
+                       B4<M>* F, B4<T>* Fd, double beta, const int* mask, int mstride, int S,
+                       cudaStream_t st);
+// One ILU sweep: x_out = x + omega (L U)^{-1} r (mode 2, r the masked
+// residual of x) or x_out = omega (L U)^{-1} r (mode 1, x = 0, r = b); the
+// transposed sweep applies (L U)^{-T}.  t: [S][N] scratch holding both
+// triangular solves' results (t may be r).  16 launches, one per colour and
+// solve.
+template <class T, class M>
+void launch_ilu_apply(const Grid& G, const B4<M>* F, const B4<T>* Fd, const uint8_t* bc,
+                      const V2<T>* r, V2<T>* t, const V2<T>* x, V2<T>* xo, double omega,
+                      int trans, int mode, const int* mask, int mstride, int S, cudaStream_t st,
+                      int bs = kBS);
+
 // Keeps the iterate of smallest residual: copies x into xbest for the
 // samples whose last iteration improved it (keep == 1), or x <- xbest for
 // the samples that did not converge (keep == 2).

@@ -25,7 +25,7 @@ SECONDS_PER_YEAR = 365.25 * 86400.0
 
 ELDER_OK, ELDER_EINVAL, ELDER_ENOMEM, ELDER_ECUDA, ELDER_ENOTCONV, ELDER_ETIMEOUT = range(6)
 ELDER_FP64, ELDER_MIXED = 0, 1
-ELDER_SMOOTH_JACOBI, ELDER_SMOOTH_ZLINE = 0, 1
+ELDER_SMOOTH_JACOBI, ELDER_SMOOTH_ZLINE, ELDER_SMOOTH_ILU = 0, 1, 2
 SAMPLE_STATUS = {0: "ok", 1: "newton_maxit", 2: "krylov_maxit", 3: "breakdown", 4: "nonfinite",
                  5: "linesearch"}
 
@@ -44,7 +44,8 @@ class elder_config(ctypes.Structure):
                 ("coarse_K_harmonic", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("newton_estimate", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("omega_line", ctypes.c_double),
-                ("mixed_newton_maxit", ctypes.c_int)]
+                ("mixed_newton_maxit", ctypes.c_int), ("ilu_beta", ctypes.c_double),
+                ("omega_ilu", ctypes.c_double)]
 
 
 class elder_stats(ctypes.Structure):
@@ -89,6 +90,8 @@ def _load():
                                          ctypes.POINTER(elder_stats), vp]
     lib.elder_solve.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, vp, vp,
                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int32), vp]
+    lib.elder_smoother_apply.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, ip, vp,
+                                         vp, vp]
     lib.elder_moments.argtypes = [vp, ip, vp, vp, ctypes.c_double, vp, vp, vp, vp]
     lib.elder_grad.argtypes = [vp, ip, vp, vp, vp, vp, ctypes.c_double, ip, dp, vp, vp, vp]
     lib.elder_initial_state.argtypes = [vp, ip, vp, vp, vp]
@@ -322,6 +325,17 @@ class Elder:
         self._check(rc, allow_notconv=True)
         return x, np.frombuffer(status, dtype=np.int32).copy()
 
+    def smoother_apply(self, S, phi, K, p, c, dt, kind, r, transpose=False, z=None,
+                       stream=None):
+        """z = P^{-1} r (or P^{-T} r) of the finest level's smoother `kind`
+        (ELDER_SMOOTH_*) linearised at (p, c); r, z: [S][N][2] FP64."""
+        z = z if z is not None else torch.empty_like(r)
+        self._check(_lib.elder_smoother_apply(self._h, S, _ptr(phi, "phi"), _ptr(K, "K"),
+                                              _ptr(p, "p"), _ptr(c, "c"), dt, kind,
+                                              1 if transpose else 0, _ptr(r, "r"), _ptr(z, "z"),
+                                              _stream(stream)))
+        return z
+
     def moments(self, S, c, w=None, threshold=0.5, stream=None):
         dev = c.device
         mean = torch.empty(self.N, dtype=torch.float64, device=dev)
@@ -508,6 +522,10 @@ def elder_solve(ctx: Elder, *a, **k):
 
 def elder_moments(ctx: Elder, *a, **k):
     return ctx.moments(*a, **k)
+
+
+def elder_smoother_apply(ctx: Elder, *a, **k):
+    return ctx.smoother_apply(*a, **k)
 
 
 def elder_grad(ctx: Elder, *a, **k):

@@ -64,6 +64,7 @@ def test_config_default_without_gpu():
     assert (cfg.nx, cfg.ny, cfg.nz) == (32, 32, 8)
     assert cfg.Lx == 600.0 and cfg.Lz == 150.0 and cfg.rho1 == 1200.0
     assert cfg.Dm == 3.565e-6
+    assert (cfg.smoother, cfg.ilu_beta, cfg.omega_ilu) == (E.ELDER_SMOOTH_ZLINE, 0.0, 1.0)
     with pytest.raises(AttributeError):
         E.elder_config_default(4, 4, 2, no_such_field=1)
 
@@ -73,6 +74,7 @@ def test_config_default_without_gpu():
     dict(nz=129),                     # z-line smoother: lines of at most 129 nodes
     dict(smoother=7), dict(precision=5), dict(omega_line=0.0), dict(omega=-1.0),
     dict(max_samples=0), dict(nu1=0), dict(bc_mode=9), dict(mu=0.0),
+    dict(smoother=2, omega_ilu=0.0), dict(smoother=2, ilu_beta=float("nan")),
 ])
 def test_create_rejects_invalid_config_before_touching_a_device(bad):
     """elder_create validates the configuration on the host and returns
