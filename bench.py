@@ -1040,11 +1040,11 @@ def run_fingers(a):
                           "pexc": pexc.cpu().numpy().astype(np.float32)}
             print(f"fingers: step {n} ({n * a.fingers_dt_yr:.2f} yr), "
                   f"{S * n / (ms / 1000.0):.1f} sample-timesteps/s so far, lobes "
-                  f"{lob[str(n)]['max_plane_count']} at z = {lob[str(n)]['plane']['z_m']} m, "
-                  f"wall {time.time() - t_wall:.0f} s", file=sys.stderr, flush=True)
-    if a.fingers_out:
-        np.savez_compressed(a.fingers_out, xi=xi_np, grid=np.array([nx, ny, nz]),
-                            dt_yr=np.array(a.fingers_dt_yr), **snaps, **fields)
+                  f"{json.dumps(lob[str(n)]['plane'])}, wall {time.time() - t_wall:.0f} s",
+                  file=sys.stderr, flush=True)
+            if a.fingers_out:  # written at every snapshot, so a cut-off run keeps its fields
+                np.savez_compressed(a.fingers_out, xi=xi_np, grid=np.array([nx, ny, nz]),
+                                    dt_yr=np.array(a.fingers_dt_yr), **snaps, **fields)
     ctx.destroy()
     line = {"metric": f"sample-timesteps/s, the paper's parallelepiped ensemble (3 random "
                       f"variables) at {nx}x{ny}x{nz}",

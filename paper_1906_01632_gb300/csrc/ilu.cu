@@ -136,15 +136,21 @@ __global__ void __launch_bounds__(128)
             w[q] = B4<T>{T(0), T(0), T(0), T(0)};
         }
     }
+    const int pn = Lo.off[C] + t;
+    // Every load is issued unconditionally, so that the compiler can start
+    // them ahead of the dependent arithmetic: a neighbour outside the grid
+    // reads the row's own (not yet written) slots, and its terms are
+    // selected away, never multiplied by 0 (the slots may hold any bits).
 #pragma unroll
     for (int cc = 0; cc < C; ++cc) {
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
             if (d == 13 || slot_axes(d) != (C ^ cc)) continue;
             const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-            if (!inside(G, i + dx, j + dy, k + dz)) continue;
-            const int pk = colour_pos(Lo, i + dx, j + dy, k + dz);
-            const B4<T> l = mul2_(w[d], Fds[pk]);
+            const bool okk = inside(G, i + dx, j + dy, k + dz);
+            const int pk = okk ? colour_pos(Lo, i + dx, j + dy, k + dz) : pn;
+            const B4<T> dk = Fds[pk];
+            const B4<T> l = okk ? mul2_(w[d], dk) : B4<T>{T(0), T(0), T(0), T(0)};
             w[d] = l;
 #pragma unroll
             for (int e = 0; e < 27; ++e) {
@@ -153,20 +159,25 @@ __global__ void __launch_bounds__(128)
                 const int fx = dx + ex, fy = dy + ey, fz = dz + ez;
                 const bool inpat = fx >= -1 && fx <= 1 && fy >= -1 && fy <= 1 &&
                                    fz >= -1 && fz <= 1;
-                if (!inpat && beta == T(0)) continue;
-                if (!inside(G, i + fx, j + fy, k + fz)) continue;
-                const B4<T> u = load_blk<T, M>(Fs[(size_t)e * G.N + pk]);
-                const B4<T> lu = mul2_(l, u);
-                const int f = inpat ? (fx + 1) + 3 * (fy + 1) + 9 * (fz + 1) : 13;
-                const T sc = inpat ? T(1) : beta;
-                w[f].pp = fma(-sc, lu.pp, w[f].pp);
-                w[f].pc = fma(-sc, lu.pc, w[f].pc);
-                w[f].cp = fma(-sc, lu.cp, w[f].cp);
-                w[f].cc = fma(-sc, lu.cc, w[f].cc);
+                if (inpat) {
+                    const bool ok = okk && inside(G, i + fx, j + fy, k + fz);
+                    const B4<T> lu = mul2_(l, load_blk<T, M>(Fs[(size_t)e * G.N + pk]));
+                    const int f = (fx + 1) + 3 * (fy + 1) + 9 * (fz + 1);
+                    w[f].pp = ok ? w[f].pp - lu.pp : w[f].pp;
+                    w[f].pc = ok ? w[f].pc - lu.pc : w[f].pc;
+                    w[f].cp = ok ? w[f].cp - lu.cp : w[f].cp;
+                    w[f].cc = ok ? w[f].cc - lu.cc : w[f].cc;
+                } else if (beta != T(0) && okk && inside(G, i + fx, j + fy, k + fz)) {
+                    // fill outside the pattern: beta times it onto the pivot
+                    const B4<T> lu = mul2_(l, load_blk<T, M>(Fs[(size_t)e * G.N + pk]));
+                    w[13].pp = fma(-beta, lu.pp, w[13].pp);
+                    w[13].pc = fma(-beta, lu.pc, w[13].pc);
+                    w[13].cp = fma(-beta, lu.cp, w[13].cp);
+                    w[13].cc = fma(-beta, lu.cc, w[13].cc);
+                }
             }
         }
     }
-    const int pn = Lo.off[C] + t;
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
         if (q == 13) continue;
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(128)
     Fds[pn] = inv2_(w[13]);
 }
 
-// One colour of a triangular solve with the factors (the vector t holds the
+// One colour C of a triangular solve with the factors (the vector t holds the
 // first solve's result for the processed rows, the second's after it):
 //  PASS 0 (colours ascending): non-transposed L y = r, y_i = r_i - sum_lower
 //    L_ik y_k; transposed U^T y = r, y_i = U_ii^{-T} (r_i - sum_lower U_ki^T
@@ -186,24 +197,25 @@ __global__ void __launch_bounds__(128)
 //  PASS 1 (colours descending): non-transposed U z = y, z_i = U_ii^{-1} (y_i
 //    - sum_upper U_ij z_j); transposed L^T z = y, z_i = y_i - sum_upper
 //    L_ji^T z_j; then x_out = x + omega z (MODE 2) or omega z (MODE 1).
-// "lower" / "upper": neighbours of smaller / larger colour.
-template <class T, class M, bool TRANS, int PASS, int MODE>
+// "lower" / "upper": neighbours of smaller / larger colour, fixed at compile
+// time by C.  The loads are unconditional (a neighbour outside the grid reads
+// the node's own entries, and its term is selected away).
+template <class T, class M, bool TRANS, int PASS, int MODE, int C>
 __global__ void __launch_bounds__(kBS)
     k_ilu_pass(Grid G, IluLayout Lo, const B4<M>* __restrict__ F,
                const B4<T>* __restrict__ Fd, const uint8_t* __restrict__ bc, const V2<T>* src,
-               V2<T>* tv, const V2<T>* x, V2<T>* xo, T omega, int c, const int* mask,
-               int mstride)
+               V2<T>* tv, const V2<T>* x, V2<T>* xo, T omega, const int* mask, int mstride)
 {
     const int s = blockIdx.y;
     if (!on_(mask, mstride, s)) return;
     int i, j, k;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!colour_node(G, Lo, c, t, i, j, k)) return;
+    if (!colour_node(G, Lo, C, t, i, j, k)) return;
     const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
     const int n = i + sy * j + sz * k;
     const size_t on = (size_t)s * G.N;
     const B4<M>* Fs = F + (size_t)s * 27 * G.N;
-    const int pn = Lo.off[c] + t;
+    const int pn = Lo.off[C] + t;
     const uint8_t bn = bc[n];
     T ap, ac;
     if (PASS == 0) {
@@ -218,23 +230,25 @@ __global__ void __launch_bounds__(kBS)
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
         if (d == 13) continue;
-        const int cd = c ^ slot_axes(d);
-        if (PASS == 0 ? cd > c : cd < c) continue;
+        const int cd = C ^ slot_axes(d);
+        if (PASS == 0 ? cd > C : cd < C) continue;
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        if (!inside(G, i + dx, j + dy, k + dz)) continue;
-        const int m = n + dx + dy * sy + dz * sz;
-        const V2<T> v = tv[on + m];
+        const bool ok = inside(G, i + dx, j + dy, k + dz);
+        const V2<T> v = tv[on + (ok ? n + dx + dy * sy + dz * sz : n)];
+        T np, nc;
         if (!TRANS) {
             const B4<T> b = load_blk<T, M>(Fs[(size_t)d * G.N + pn]);
-            ap = fma(-b.pp, v.p, fma(-b.pc, v.c, ap));
-            ac = fma(-b.cp, v.p, fma(-b.cc, v.c, ac));
+            np = fma(-b.pp, v.p, fma(-b.pc, v.c, ap));
+            nc = fma(-b.cp, v.p, fma(-b.cc, v.c, ac));
         } else {
             // row m's block of offset -d, transposed
-            const int pm = colour_pos(Lo, i + dx, j + dy, k + dz);
+            const int pm = ok ? colour_pos(Lo, i + dx, j + dy, k + dz) : pn;
             const B4<T> b = load_blk<T, M>(Fs[(size_t)(26 - d) * G.N + pm]);
-            ap = fma(-b.pp, v.p, fma(-b.cp, v.c, ap));
-            ac = fma(-b.pc, v.p, fma(-b.cc, v.c, ac));
+            np = fma(-b.pp, v.p, fma(-b.cp, v.c, ap));
+            nc = fma(-b.pc, v.p, fma(-b.cc, v.c, ac));
         }
+        ap = ok ? np : ap;
+        ac = ok ? nc : ac;
     }
     const bool pivot = (PASS == 0) == TRANS;
     if (pivot) {
@@ -307,19 +321,28 @@ void launch_ilu_apply(const Grid& G, const B4<M>* F, const B4<T>* Fd, const uint
         count_launch(1);
         dim3 grid(nblocks(Lo.off[c + 1] - Lo.off[c], bs), S);
         const V2<T>* src = pass == 0 ? r : nullptr;
-#define ELDER_ILUP(TR, PA, MO)                                                            \
-    k_ilu_pass<T, M, TR, PA, MO><<<grid, bs, 0, st>>>(G, Lo, F, Fd, bc, src, t, x, xo, w, c, \
-                                                      mask, mstride)
+#define ELDER_ILUP(TR, PA, MO, CC)                                                            \
+    case CC:                                                                                  \
+        k_ilu_pass<T, M, TR, PA, MO, CC><<<grid, bs, 0, st>>>(G, Lo, F, Fd, bc, src, t, x, xo, w, \
+                                                              mask, mstride);                 \
+        break;
+#define ELDER_ILUP_C(TR, PA, MO)                                                              \
+    switch (c) {                                                                              \
+        ELDER_ILUP(TR, PA, MO, 0) ELDER_ILUP(TR, PA, MO, 1) ELDER_ILUP(TR, PA, MO, 2)         \
+        ELDER_ILUP(TR, PA, MO, 3) ELDER_ILUP(TR, PA, MO, 4) ELDER_ILUP(TR, PA, MO, 5)         \
+        ELDER_ILUP(TR, PA, MO, 6) ELDER_ILUP(TR, PA, MO, 7)                                   \
+    }
         if (pass == 0) {
-            if (trans) ELDER_ILUP(true, 0, 1);
-            else ELDER_ILUP(false, 0, 1);
+            if (trans) { ELDER_ILUP_C(true, 0, 1) }
+            else { ELDER_ILUP_C(false, 0, 1) }
         } else if (mode == 1) {
-            if (trans) ELDER_ILUP(true, 1, 1);
-            else ELDER_ILUP(false, 1, 1);
+            if (trans) { ELDER_ILUP_C(true, 1, 1) }
+            else { ELDER_ILUP_C(false, 1, 1) }
         } else {
-            if (trans) ELDER_ILUP(true, 1, 2);
-            else ELDER_ILUP(false, 1, 2);
+            if (trans) { ELDER_ILUP_C(true, 1, 2) }
+            else { ELDER_ILUP_C(false, 1, 2) }
         }
+#undef ELDER_ILUP_C
 #undef ELDER_ILUP
     }
 }
