@@ -590,8 +590,9 @@ def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, 
     (order + 1)).  The history levels and fields of step n+1 do not depend on
     step n's result, so a side stream copies them into the second of two
     device buffer sets while step n runs; the state u^n comes in on the
-    launching stream right before its step.  Returns the elapsed seconds and
-    the final state (host)."""
+    launching stream right before its step.  Two untimed steps first capture
+    the step graphs of both buffer sets.  Returns the elapsed seconds and the
+    final state (host)."""
     R = max(order, 0) + 1
     f64 = torch.float64
     hp = [torch.empty(S * N, dtype=f64, pin_memory=True) for _ in range(R)]
@@ -633,31 +634,42 @@ def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, 
             sets[X]["K"].copy_(hK, non_blocking=True)
             ready[X].record(side)
 
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    prefetch(0, 0)
-    for n in range(steps):
-        X = n % 2
-        main.wait_event(ready[X])
-        dp_.copy_(hp[n % R], non_blocking=True)
-        dc_.copy_(hc[n % R], non_blocking=True)
-        if n + 1 < steps:
-            prefetch(n + 1, 1 - X)
-        st_ = sets[X]
-        if order == 0:
-            ctx.step(S, st_["phi"], st_["K"], dp_, dc_, dt)
-        else:
-            ctx.step_predicted(S, st_["phi"], st_["K"], order, st_["ph"], st_["ch"], dp_, dc_, dt)
-        free[X].record(main)
-        m, v, pe = ctx.moments(S, dc_, stream=main)
-        hp[(n + 1) % R].copy_(dp_, non_blocking=True)
-        hc[(n + 1) % R].copy_(dc_, non_blocking=True)
-        hmom[:N].copy_(m, non_blocking=True)
-        hmom[N:2 * N].copy_(v, non_blocking=True)
-        hmom[2 * N:].copy_(pe, non_blocking=True)
-        landed.record(main)
-    torch.cuda.synchronize()
-    return time.perf_counter() - t0, hp[steps % R], hc[steps % R]
+    def run(nsteps):
+        for q in range(R):
+            hp[q].copy_(p_init)
+            hc[q].copy_(c_init)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prefetch(0, 0)
+        for n in range(nsteps):
+            X = n % 2
+            main.wait_event(ready[X])
+            dp_.copy_(hp[n % R], non_blocking=True)
+            dc_.copy_(hc[n % R], non_blocking=True)
+            if n + 1 < nsteps:
+                prefetch(n + 1, 1 - X)
+            st_ = sets[X]
+            if order == 0:
+                ctx.step(S, st_["phi"], st_["K"], dp_, dc_, dt)
+            else:
+                ctx.step_predicted(S, st_["phi"], st_["K"], order, st_["ph"], st_["ch"], dp_,
+                                   dc_, dt)
+            free[X].record(main)
+            m, v, pe = ctx.moments(S, dc_, stream=main)
+            hp[(n + 1) % R].copy_(dp_, non_blocking=True)
+            hc[(n + 1) % R].copy_(dc_, non_blocking=True)
+            hmom[:N].copy_(m, non_blocking=True)
+            hmom[N:2 * N].copy_(v, non_blocking=True)
+            hmom[2 * N:].copy_(pe, non_blocking=True)
+            landed.record(main)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    # untimed: two steps from t = 0, so that the step graphs of both buffer
+    # sets are captured before the timed steps (as in the device-timed run)
+    run(min(2, steps))
+    el = run(steps)
+    return el, hp[steps % R], hc[steps % R]
 
 
 def gpc_timings(E, torch, cfield, stream, Ns=1_000_000, apk=None):

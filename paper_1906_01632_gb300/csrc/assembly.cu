@@ -272,12 +272,12 @@ __global__ void __launch_bounds__(kBS)
         const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
         p8[L] = __ldg(p + on + base + off);
         c8[L] = __ldg(c + on + base + off);
-        pf[L] = (float)p8[L];
-        cf[L] = (float)c8[L];
+        pf[L] = d2f_trunc(p8[L]);
+        cf[L] = d2f_trunc(c8[L]);
     }
     const double phie = __ldg(phi + oc + e);
     const double Ke = __ldg(K + oc + e);
-    const float phif = (float)phie, Kf = (float)Ke;
+    const float phif = d2f_trunc(phie), Kf = d2f_trunc(Ke);
     QF* out = qf + (size_t)s * 12 * G.C + e;
     const size_t qs = (size_t)G.C;
     cell_dir_faces<0>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(kBS)
                     const double* __restrict__ p, const double* __restrict__ c,
                     const double* __restrict__ c_old, const QF* __restrict__ qf,
                     V2<double>* __restrict__ R, double* __restrict__ partial,
-                    double* __restrict__ act, const int* mask, int mstride)
+                    double* __restrict__ act, const int* mask, int mstride, float drhof,
+                    float rho0f)
 {
     __shared__ double red[32];
     const int s = blockIdx.y;
@@ -354,9 +355,9 @@ __global__ void __launch_bounds__(kBS)
         const double rn = fma(ph.drho, cn, ph.rho0), ro = fma(ph.drho, co, ph.rho0);
         Rp += vdt * (rn - ro);
         Rc += vdt * (rn * cn - ro * co);
-        const float vdtf = (float)vdt, cnf = (float)cn, cof = (float)co;
-        const float rnf = fmaf((float)ph.drho, cnf, (float)ph.rho0);
-        const float rof = fmaf((float)ph.drho, cof, (float)ph.rho0);
+        const float vdtf = d2f_trunc(vdt), cnf = d2f_trunc(cn), cof = d2f_trunc(co);
+        const float rnf = fmaf(drhof, cnf, rho0f);
+        const float rof = fmaf(drhof, cof, rho0f);
         Ap = fmaf(vdtf, fabsf(rnf) + fabsf(rof), Ap);
         Ac = fmaf(vdtf, fabsf(rnf * cnf) + fabsf(rof * cof), Ac);
         const uint8_t b = bc[n];
@@ -391,7 +392,8 @@ void launch_residual(const Grid& G, const Phys& ph, const uint8_t* bc,
     dim3 grid(nblocks(G.N), S);
     const double vsc = G.hx * G.hy * G.hz / (8.0 * ph.dt);
     k_cell_residual<<<grid, kBS, 0, st>>>(G, ph, vsc, bc, cval, phi, p, c, c_old, qf, R,
-                                          partial, act, mask, mstride);
+                                          partial, act, mask, mstride, (float)ph.drho,
+                                          (float)ph.rho0);
 }
 
 // ---------------------------------------------------------------------------

@@ -95,6 +95,21 @@ template <> __device__ __forceinline__ __nv_bfloat16 mg_store<__nv_bfloat16>(dou
     return __float2bfloat16_rn(float(v));
 }
 
+// FP32 value of an FP64 number formed with integer operations only (on
+// GB300 an FP64-to-FP32 conversion issues on the slow FP64 pipe): the FP64
+// exponent rebiased, the top 23 mantissa bits kept (truncated, not rounded);
+// magnitudes below 2^-126 become 0, those from 2^128 up (and NaN) infinity.
+// For the residual's round-off scale, a magnitude needed to a few digits.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const unsigned sign = hi & 0x80000000u;
+    unsigned bits = sign | ((unsigned)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    bits = e <= 896 ? sign : (e >= 1151 ? (sign | 0x7F800000u) : bits);
+    return __uint_as_float(bits);
+}
+
 __host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
 {
     return i + (G.nx + 1) * (j + (G.ny + 1) * k);
