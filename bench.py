@@ -589,7 +589,8 @@ def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, 
     keeps the states in a ring of order + 1 pinned buffers (u^m in slot m mod
     (order + 1)).  The history levels and fields of step n+1 do not depend on
     step n's result, so a side stream copies them into the second of two
-    device buffer sets while step n runs; the state u^n comes in on the
+    device buffer sets while step n runs (after step n's own state copy,
+    with which it would share the host link); the state u^n comes in on the
     launching stream right before its step.  Two untimed steps first capture
     the step graphs of both buffer sets.  Returns the elapsed seconds and the
     final state (host)."""
@@ -617,14 +618,19 @@ def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, 
     ready = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
     landed = torch.cuda.Event()
+    state_in = torch.cuda.Event()
     for e in free:
         e.record(main)
     landed.record(main)
+    state_in.record(main)
 
     def prefetch(n, X):
         with torch.cuda.stream(side):
             side.wait_event(free[X])      # the step that used set X is done
             side.wait_event(landed)       # u^n is in its host slot
+            # after the current step's state copies: both directions share the
+            # host link, so a concurrent prefetch would only delay the step
+            side.wait_event(state_in)
             for q in range(order):        # level q holds u^{n-1-q}
                 sets[X]["ph"][q * S * N:(q + 1) * S * N].copy_(hp[(n - 1 - q) % R],
                                                                non_blocking=True)
@@ -646,6 +652,7 @@ def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, 
             main.wait_event(ready[X])
             dp_.copy_(hp[n % R], non_blocking=True)
             dc_.copy_(hc[n % R], non_blocking=True)
+            state_in.record(main)
             if n + 1 < nsteps:
                 prefetch(n + 1, 1 - X)
             st_ = sets[X]
