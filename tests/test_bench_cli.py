@@ -45,7 +45,7 @@ def test_byte_model_matches_the_stored_formats():
 def test_traffic_lines_of_the_committed_profiles():
     assert bench.ncu_traffic("spmv", "mixed") == pytest.approx(428.0)
     assert bench.ncu_traffic("mg_residual", "mixed") == pytest.approx(229.8)
-    assert bench.ncu_traffic("residual", "fp64") == pytest.approx(302.0)
+    assert bench.ncu_traffic("residual", "fp64") == pytest.approx(582.0)
     assert bench.ncu_traffic("no_such_class", "mixed") is None
 
 
