@@ -675,11 +675,6 @@ __global__ void __launch_bounds__(kBS)
     node_ijk_fast(Gc, n, I, J, K);
     rf += (size_t)s * Gf.N;
     T sp = T(0), sc = T(0);
-    // unconditional loads (a fine node outside the grid reads the centre
-    // node, and its term is selected away), so that all 27 are in flight
-    // before the first use; the sum runs in the same order as before
-    const int sxf = Gf.nx + 1, szf = (Gf.nx + 1) * (Gf.ny + 1);
-    const int f0 = 2 * I + sxf * 2 * J + szf * 2 * K;
 #pragma unroll
     for (int c = -1; c <= 1; ++c)
 #pragma unroll
@@ -687,12 +682,12 @@ __global__ void __launch_bounds__(kBS)
 #pragma unroll
             for (int a = -1; a <= 1; ++a) {
                 const int fi = 2 * I + a, fj = 2 * J + b, fk = 2 * K + c;
-                const bool ok =
-                    fi >= 0 && fi <= Gf.nx && fj >= 0 && fj <= Gf.ny && fk >= 0 && fk <= Gf.nz;
+                if (fi < 0 || fi > Gf.nx || fj < 0 || fj > Gf.ny || fk < 0 || fk > Gf.nz)
+                    continue;
                 const T w = T((a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5) * (c == 0 ? 1.0 : 0.5));
-                const V2<T> v = rf[ok ? f0 + a + sxf * b + szf * c : f0];
-                sp = ok ? sp + w * v.p : sp;
-                sc = ok ? sc + w * v.c : sc;
+                const V2<T> v = rf[node_id(Gf, fi, fj, fk)];
+                sp += w * v.p;
+                sc += w * v.c;
             }
     const uint8_t m = bcc[n];
     if (m & BC_P) sp = T(0);
