@@ -329,6 +329,50 @@ def test_paper_parallelepiped_workload_steps_match_oracle(E):
             assert np.abs(traj[n][0][s] - ref[n][0]).max() <= 1e-9 * P.rho0 * P.g * P.Lz, (s, n)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+def test_fingers_launch_configuration_matches_oracle(E, precision, tol):
+    """The launch configuration of the paper's ensemble run (bench.py
+    --workload fingers, Section 5.3) on a 16x16x4 grid: the parallelepiped
+    field at Halton points, the paper's boundary sets (bc_mode 1: c = 0 on
+    the top outside the square, p = 0 on the top edges), dt = 0.005 yr, Newton
+    from the quadratic extrapolation (elder_step_predicted, order 2), 8
+    steps, against the oracle's states; then the ensemble mean's 0.5 level
+    set counted by the bench's plume_lobes on both means."""
+    import bench
+    from paper_1906_01632_gb300 import inputs as I
+    P = O.Problem(16, 16, 4, bc_mode=1)
+    S = 4
+    xi = I.halton_xi(S)
+    ctx = _ctx(E, 16, 16, 4, S=S, bc_mode=1, precision=precision)
+    phi_t, K_t = ctx.fields(S, 2, T(xi))
+    phi, K = H(phi_t).reshape(S, -1), H(K_t).reshape(S, -1)
+    p0, c0 = O.initial_state(P)
+    dt = 0.005 * YEAR
+    steps = 8
+    pt, ct = T(np.tile(p0, (S, 1))), T(np.tile(c0, (S, 1)))
+    ph, ch = pt.repeat(2), ct.repeat(2)
+    traj = []
+    for _ in range(steps):
+        st, info = ctx.step_predicted(S, phi_t, K_t, 2, ph, ch, pt, ct, dt)
+        assert (st == 0).all(), info
+        traj.append((H(pt).reshape(S, -1).copy(), H(ct).reshape(S, -1).copy()))
+    mean_gpu = H(ctx.moments(S, ct)[0])
+    ctx.destroy()
+    pscale = P.rho0 * P.g * P.Lz
+    c_end = []
+    for s in range(S):
+        ref = _oracle_traj(P, phi[s], K[s], p0, c0, steps, dt)
+        for n in range(steps):
+            assert np.abs(traj[n][1][s] - ref[n][1]).max() <= tol, (s, n)
+            assert np.abs(traj[n][0][s] - ref[n][0]).max() <= max(tol, 1e-9) * pscale, (s, n)
+        c_end.append(ref[-1][1])
+    mean_orc = np.mean(c_end, axis=0)
+    assert np.abs(mean_gpu - mean_orc).max() <= tol
+    a = bench.plume_lobes(mean_gpu, 16, 16, 4)
+    b = bench.plume_lobes(mean_orc, 16, 16, 4)
+    assert a["plane_counts_top_down"] == b["plane_counts_top_down"]
+
+
 def test_step_argument_errors(E):
     """S outside [1, max_samples] and a non-positive dt are rejected with
     ELDER_EINVAL before anything is launched; the state is left untouched."""
