@@ -11,7 +11,9 @@ oracle fixes it: a node's P may differ by at most (the number of samples
 whose oracle c lies within 1e-6 of the threshold) / S, plus 1e-3.
 
 The expected moments are stored in tests/golden/longrun_moments_*.npz, written
-by tests/golden/make_longrun_moments.py, which calls only the oracle.  The
+by tests/golden/make_longrun_moments.py, which calls only the oracle.  A third
+case runs the paper's own parallelepiped ensemble (Section 5.3) for 300
+steps of 0.005 yr with the paper's boundary sets.  The
 CUDA path runs the samples batched in mixed precision with the bench's
 Newton start (elder_step_predicted, order 2); the 64x64x16 case runs inside
 the bench's 256-sample batch and compares its first 16 samples.
@@ -39,18 +41,18 @@ def E():
     return elder
 
 
-def _march(E, grid, xi, steps, S_batch=None):
+def _march(E, grid, xi, steps, S_batch=None, kind=0, bc_mode=0, dt=YEAR / 12):
     """The batched mixed-precision run from t = 0; returns c [S_batch][N]."""
     nx, ny, nz = grid
     S = S_batch or xi.shape[0]
     ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S,
-                                                precision=E.ELDER_MIXED))
+                                                precision=E.ELDER_MIXED, bc_mode=bc_mode))
     xt = torch.tensor(np.ascontiguousarray(xi[:S]).ravel(), dtype=torch.float64, device=DEV)
-    phi, K = ctx.fields(S, 0, xt)
+    phi, K = ctx.fields(S, kind, xt)
     p, c = ctx.initial_state(S, device=DEV)
     ph, ch = p.repeat(2), c.repeat(2)
     for n in range(steps):
-        st, info = ctx.step_predicted(S, phi, K, 2, ph, ch, p, c, YEAR / 12)
+        st, info = ctx.step_predicted(S, phi, K, 2, ph, ch, p, c, dt)
         assert (st == 0).all(), (n, [i for i in info if i["status"]][:3])
     torch.cuda.synchronize()
     return ctx, c.view(S, -1)
@@ -98,5 +100,19 @@ def test_moments_after_60_steps_64x64x16_in_the_256_sample_batch(E):
     xi = I.sobol_xi(256, seed=0)
     assert np.array_equal(xi[:S], g["xi"])
     ctx, c = _march(E, (64, 64, 16), xi, int(g["steps"]), S_batch=256)
+    _compare(E, ctx, c, g, S)
+    ctx.destroy()
+
+
+def test_moments_after_300_steps_of_the_paper_ensemble_32x32x8(E):
+    """The paper's own ensemble (Section 5.3) at 32x32x8: the parallelepiped
+    field of eq. poro-paral3RVS at the first 16 Halton points, the paper's
+    boundary sets (bc_mode 1), 300 steps of dt = 0.005 yr (1.5 yr), as in the
+    128x128x32 run of bench.py --workload fingers."""
+    g = _golden("longrun_moments_paper3rv_32x32x8.npz")
+    xi = g["xi"]
+    S = xi.shape[0]
+    ctx, c = _march(E, (32, 32, 8), xi, int(g["steps"]), kind=2, bc_mode=int(g["bc_mode"]),
+                    dt=float(g["dt_yr"]) * YEAR)
     _compare(E, ctx, c, g, S)
     ctx.destroy()
