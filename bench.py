@@ -94,6 +94,10 @@ def parse():
                          "marched 1500 steps to 7.5 yr, with the plume lobes of the mean's 0.5 "
                          "level set counted")
     ap.add_argument("--fingers-samples", type=int, default=200)
+    ap.add_argument("--fingers-method", choices=["qmc", "gpc"], default="qmc",
+                    help="qmc: the Halton ensemble's sample moments; gpc: the 125 points of "
+                         "the 5^3 Gauss-Legendre rule, the moments of the order-4 gPC "
+                         "surrogate projected from them (Section 3, Section 5.3)")
     ap.add_argument("--fingers-grid", type=int, nargs=3, default=[128, 128, 32])
     ap.add_argument("--fingers-dt-yr", type=float, default=0.005)
     ap.add_argument("--fingers-steps", type=int, default=1500)
@@ -1047,7 +1051,11 @@ def run_fingers(a):
     --fingers-snap steps the ensemble mean, variance and P(c > 0.5) are
     formed (elder_moments) and the plume lobes of the mean's 0.5 level set
     counted (plume_lobes); Section 5.3 reports five fingers at 7.5 yr, four at
-    the corners and one at the centre."""
+    the corners and one at the centre.  With --fingers-method gpc the samples
+    are the 125 points of the 5^3 Gauss-Legendre rule and the moments are the
+    order-4 gPC surrogate's (elder_gpc_project; P(c > 0.5) from 10^5 uniform
+    points, elder_gpc_exceed), the paper's second method for the same
+    figure."""
     import numpy as np
     import torch
 
@@ -1060,12 +1068,24 @@ def run_fingers(a):
     dev = torch.device("cuda", 0)
     nx, ny, nz = a.fingers_grid
     S, steps, snap = a.fingers_samples, a.fingers_steps, max(1, a.fingers_snap)
+    gpc = a.fingers_method == "gpc"
+    if gpc:  # the 5^3 tensor Gauss-Legendre rule, total degree <= 4 (35 terms)
+        xg, wg = E.elder_gauss_legendre(5)
+        theta = np.stack(np.meshgrid(xg, xg, xg, indexing="ij"), -1).reshape(-1, 3)[:, ::-1]
+        wq = np.prod(np.stack(np.meshgrid(wg, wg, wg, indexing="ij"), -1).reshape(-1, 3), 1)
+        S = theta.shape[0]
+        beta = torch.tensor(E.elder_gpc_indices(3, 4), device=dev)
+        theta_t = torch.tensor(np.ascontiguousarray(theta), dtype=torch.float64, device=dev)
+        wq_t = torch.tensor(wq, dtype=torch.float64, device=dev)
+        gen = torch.Generator(device=dev).manual_seed(5)
+        theta_s = (torch.rand(100_000, 3, generator=gen, dtype=torch.float64, device=dev) * 2
+                   - 1).contiguous()
     dt = YEAR * a.fingers_dt_yr
     stream = torch.cuda.current_stream()
     ctx = E.elder_create(E.elder_config_default(nx, ny, nz, max_samples=S,
                                                 precision=E.ELDER_MIXED, bc_mode=1))
     N = ctx.N
-    xi_np = I.halton_xi(S)
+    xi_np = np.ascontiguousarray(theta) if gpc else I.halton_xi(S)
     xi = torch.tensor(xi_np.ravel(), dtype=torch.float64, device=dev)
     phi, K = ctx.fields(S, 2, xi)
     p0, c0 = ctx.initial_state(S, device=dev)
@@ -1091,7 +1111,11 @@ def run_fingers(a):
         failed += int((st != 0).sum())
         retries += sum(1 for i in info if i["fp64_retry"])
         if n % snap == 0 or n == steps:
-            mean, var, pexc = ctx.moments(S, c)
+            if gpc:  # moments of the surrogate (eqs. PCEcoef, var), P from 10^5 points
+                coef, mean, var = E.elder_gpc_project(beta, theta_t, wq_t, c.view(S, N))
+                pexc = E.elder_gpc_exceed(beta, coef, theta_s, 0.5)
+            else:
+                mean, var, pexc = ctx.moments(S, c)
             mh = mean.cpu().numpy()
             lob[str(n)] = plume_lobes(mh, nx, ny, nz)
             snaps[f"mean_{n}"] = mh.astype(np.float32)
@@ -1111,10 +1135,13 @@ def run_fingers(a):
             "value": S * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": max(a.warmup, 2), "higher_is_better": True, "dtype": "f64+f32+bf16",
             "data": "synthetic",
-            "config": {"workload": f"elder3d-box-{nx}x{ny}x{nz}-paper3rv-halton{S}",
+            "config": {"workload": (f"elder3d-box-{nx}x{ny}x{nz}-paper3rv-"
+                                    + (f"gauss-legendre{S}-gpc4" if gpc else f"halton{S}")),
                        "dt_yr": a.fingers_dt_yr, "bc": "paper variant (bc_mode 1)",
-                       "fields": "Halton points (bases 2,3,5, first point skipped) -> the "
-                                 "paper's parallelepiped porosity field, Kozeny-Carman K",
+                       "fields": ("5^3 Gauss-Legendre points; mean, variance and P(c > 0.5) "
+                                  "of the order-4 gPC surrogate" if gpc else
+                                  "Halton points (bases 2,3,5, first point skipped)") +
+                                 " -> the paper's parallelepiped porosity field, Kozeny-Carman K",
                        "newton_start": "3u^n - 3u^(n-1) + u^(n-2)",
                        "timed_steps": f"1-{steps} from t = 0"},
             "iterations": {"newton_per_step": newton / (S * steps),
