@@ -103,6 +103,10 @@ def parse():
     ap.add_argument("--fingers-steps", type=int, default=1500)
     ap.add_argument("--fingers-snap", type=int, default=300,
                     help="steps between the moment snapshots of the fingers workload")
+    ap.add_argument("--fingers-compare", nargs=2, metavar=("A.npz", "B.npz"), default=None,
+                    help="compare the fields of two --fingers-out files (e.g. QMC against gPC) "
+                         "and exit: mean differences per snapshot, lobe counts, variance level "
+                         "sets at 0.05")
     ap.add_argument("--fingers-out", default="",
                     help="npz file for the fingers workload's mean and variance fields")
     ap.add_argument("--run-steps", type=int, default=60,
@@ -1040,6 +1044,37 @@ def plume_lobes(mean, nx, ny, nz, Lx=600.0, Ly=600.0, Lz=150.0, level=0.5, min_n
             "column_lobes_half_depth": len(ckeep)}
 
 
+def compare_fingers(path_a, path_b, var_level=0.05):
+    """Compares two --fingers-out files of the same grid (Section 5.3 compares
+    the QMC and the gPC moments): per common snapshot the largest and mean
+    |mean_a - mean_b| and the number of nodes where the decision mean > 0.5
+    differs; at the last snapshot the per-plane lobe counts of both means
+    (plume_lobes) and the variance level sets {var > var_level}."""
+    import numpy as np
+    A, B = np.load(path_a), np.load(path_b)
+    nx, ny, nz = (int(v) for v in A["grid"])
+    assert [int(v) for v in B["grid"]] == [nx, ny, nz]
+    snaps = sorted(int(k[5:]) for k in A.files if k.startswith("mean_") and k in B.files)
+    out = {"snapshots": {}}
+    for t in snaps:
+        ma, mb = A[f"mean_{t}"].astype(np.float64), B[f"mean_{t}"].astype(np.float64)
+        out["snapshots"][str(t)] = {"max_abs_dmean": float(np.abs(ma - mb).max()),
+                                    "mean_abs_dmean": float(np.abs(ma - mb).mean()),
+                                    "decision_differs": int(((ma > 0.5) != (mb > 0.5)).sum())}
+    t = snaps[-1]
+    la = plume_lobes(A[f"mean_{t}"], nx, ny, nz)
+    lb = plume_lobes(B[f"mean_{t}"], nx, ny, nz)
+    out["plane_counts_top_down"] = {"a": la["plane_counts_top_down"],
+                                    "b": lb["plane_counts_top_down"]}
+    out["column_depth_max_m"] = {"a": la["column_depth_max_m"], "b": lb["column_depth_max_m"]}
+    if "var" in A.files and "var" in B.files:
+        va, vb = A["var"] > var_level, B["var"] > var_level
+        out["var_level_set"] = {"level": var_level, "a": int(va.sum()), "b": int(vb.sum()),
+                                "both": int((va & vb).sum())}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def run_fingers(a):
     """The paper's parallelepiped workload with three random variables
     (Section 5.3, eq. poro-paral3RVS): the porosity field at Halton points,
@@ -1160,6 +1195,8 @@ def main():
         run_uneven(a)
     elif a.workload == "config2":
         run_config2(a)
+    elif a.fingers_compare:
+        compare_fingers(*a.fingers_compare)
     elif a.workload == "fingers":
         run_fingers(a)
     else:

@@ -116,3 +116,28 @@ def test_fingers_workload_defaults(monkeypatch):
     a = _args(monkeypatch, "--workload", "fingers")
     assert (a.fingers_samples, a.fingers_steps, a.fingers_grid, a.fingers_dt_yr) == \
         (200, 1500, [128, 128, 32], 0.005)
+
+
+def test_compare_fingers_on_synthetic_fields(tmp_path):
+    """Two field files of the same grid: one shifted by 0.01 at a quarter of
+    the nodes; the comparison reports that difference, the lobe counts of
+    both means and the variance level sets."""
+    pytest.importorskip("scipy")
+    import numpy as np
+    nx, ny, nz = 32, 32, 8
+    cen = [(150, 150), (450, 150), (150, 450), (450, 450), (300, 300)]
+    m = _lobe_field(nx, ny, nz, cen).astype(np.float32)
+    m2 = m.copy()
+    m2[::4] += 0.01
+    var = np.zeros_like(m)
+    var[:100] = 0.06
+    var2 = np.zeros_like(m)
+    var2[:40] = 0.06
+    a, b = tmp_path / "a.npz", tmp_path / "b.npz"
+    np.savez(a, grid=np.array([nx, ny, nz]), mean_10=m, var=var)
+    np.savez(b, grid=np.array([nx, ny, nz]), mean_10=m2, var=var2)
+    out = bench.compare_fingers(str(a), str(b))
+    assert out["snapshots"]["10"]["max_abs_dmean"] == pytest.approx(0.01, rel=1e-3)
+    assert out["plane_counts_top_down"]["a"] == out["plane_counts_top_down"]["b"]
+    assert max(out["plane_counts_top_down"]["a"]) == 5
+    assert out["var_level_set"] == {"level": 0.05, "a": 100, "b": 40, "both": 40}
