@@ -589,7 +589,8 @@ def run_ours(a):
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x FMA x max SM clock (GHz)
 
 
-def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, dev):
+def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, dev,
+                 arena=True):
     """Steps 1..steps from t = 0 through host buffers, timed on the host wall
     clock: every step copies its inputs (state u^n, the history levels
     u^{n-1}[, u^{n-2}] of the Newton start, phi and K) from pinned host memory
@@ -604,16 +605,19 @@ def e2e_pipeline(torch, ctx, S, N, C, order, dt, steps, p_init, c_init, phi, K, 
     final state (host)."""
     R = max(order, 0) + 1
     f64 = torch.float64
-    hp = [torch.empty(S * N, dtype=f64, pin_memory=True) for _ in range(R)]
-    hc = [torch.empty(S * N, dtype=f64, pin_memory=True) for _ in range(R)]
+    sizes = [S * N] * (2 * R) + [S * C, S * C, 3 * N]
+    if arena:  # all host buffers as views of one pinned allocation
+        pool = torch.empty(sum(sizes), dtype=f64, pin_memory=True)
+        bufs = list(torch.split(pool, sizes))
+    else:
+        bufs = [torch.empty(n, dtype=f64, pin_memory=True) for n in sizes]
+    hp, hc = bufs[:R], bufs[R:2 * R]
+    hphi, hK, hmom = bufs[2 * R:]
     for q in range(R):
         hp[q].copy_(p_init)
         hc[q].copy_(c_init)
-    hphi = torch.empty(S * C, dtype=f64, pin_memory=True)
-    hK = torch.empty(S * C, dtype=f64, pin_memory=True)
     hphi.copy_(phi)
     hK.copy_(K)
-    hmom = torch.empty(3 * N, dtype=f64, pin_memory=True)
     dp_ = torch.empty(S * N, dtype=f64, device=dev)
     dc_ = torch.empty_like(dp_)
     lv = max(order, 1)
