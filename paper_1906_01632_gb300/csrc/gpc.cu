@@ -819,9 +819,19 @@ int elder_gpc_exceed_engine(int engine, int M, int T, const int32_t* beta, int m
         err = static_cast<int*>(ep);
         const int gx = (n_pts + kTcTiles * kTcRows - 1) / (kTcTiles * kTcRows);
         const int nchunk = (Ns + kTcCols - 1) / kTcCols;
-        // several CTAs per SM over the whole grid (one CTA fits an SM)
-        int gy = std::max(1, (8 * sms + gx - 1) / gx);
-        gy = std::min(std::min(gy, nchunk), 65535);
+        // one CTA fits an SM: split the chunks into gy slices so that the
+        // waves of gx * gy CTAs times the chunks per slice is least (the last
+        // wave otherwise runs part-empty), with at least 16 chunks per slice
+        // so that each CTA's set-up (TMEM, coefficients) stays amortised
+        // (the fewest slices within 0.5 % of the least cost)
+        const int gy_max = std::min(65535, std::max(1, nchunk / 16));
+        auto slice_cost = [&](int g) {
+            return (((long long)gx * g + sms - 1) / sms) * ((nchunk + g - 1) / g);
+        };
+        long long best = slice_cost(1);
+        for (int g = 2; g <= gy_max; ++g) best = std::min(best, slice_cost(g));
+        int gy = 1;
+        while (gy < gy_max && slice_cost(gy) * 200 > best * 201) ++gy;
         // operands, then 1 KiB of barriers, TMEM slot, indices and flag,
         // then the Legendre table [4][9][kTcSplit * 128]
         const size_t smem = 2 * (size_t)kTcTileBytes + 1024 +
