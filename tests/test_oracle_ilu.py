@@ -24,12 +24,16 @@ import oracle as O
 DT = O.SECONDS_PER_YEAR / 12
 
 
-@pytest.fixture(scope="module")
-def case():
-    """An 8x8x4 box after one implicit step (a physical, nonsymmetric
-    Jacobian with upwinding and Dirichlet rows)."""
+@pytest.fixture(scope="module", params=[(8, 8, 4, 0), (6, 10, 3, 2)],
+                ids=["8x8x4-benchmark", "6x10x3-column"])
+def case(request):
+    """A box after one implicit step (a physical, nonsymmetric Jacobian with
+    upwinding and Dirichlet rows): 8x8x4 with the benchmark boundary sets,
+    and 6x10x3 (odd node counts in y and z, colour classes of unequal
+    sizes) with the diffusion-column set."""
     O.build()
-    P = O.Problem(8, 8, 4)
+    nx, ny, nz, bc = request.param
+    P = O.Problem(nx, ny, nz, bc_mode=bc)
     rng = np.random.default_rng(5)
     phi = 0.1 * (1 + 0.2 * rng.uniform(-1, 1, P.C))
     K = 4.845e-13 * (phi / 0.1) ** 3 * (0.9 / (1 - phi)) ** 2
