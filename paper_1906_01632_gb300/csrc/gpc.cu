@@ -394,6 +394,7 @@ constexpr int kTcTiles = 2;
 constexpr int kTcCountWarps = 4;   // one per TMEM lane quarter
 constexpr int kTcSplit = 3;        // basis builders per sample (12 of the 36 terms each)
 constexpr int kTcProdWarps = 4 * kTcSplit;
+constexpr int kTcPartTerms = kTcTP / kTcSplit;  // terms per basis builder
 static_assert(kTcTP % (4 * kTcSplit) == 0, "whole 4-term groups per basis builder");
 constexpr int kTcThreads = 32 * (kTcCountWarps + kTcProdWarps + 1);
 
@@ -539,7 +540,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // each of the three parts
         const int pt = threadIdx.x - 32 * kTcCountWarps;
         const int col = pt & (kTcCols - 1), part = pt / kTcCols;
-        const int tbeg = part * (kTcTP / kTcSplit), tend = tbeg + kTcTP / kTcSplit;
+        const int tbeg = part * kTcPartTerms;
+        int bo[kTcPartTerms][kTcMaxM];
+#pragma unroll
+        for (int r = 0; r < kTcPartTerms; ++r)
+#pragma unroll
+            for (int m = 0; m < kTcMaxM; ++m)
+                bo[r][m] = (tbeg + r < T && m < M) ? boff[(tbeg + r) * M + m] : 0;
         // the next chunk's sample coordinates are loaded one chunk ahead
         float xn[kTcMaxM];
         auto load_theta = [&](int i) {
@@ -580,8 +587,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                 }
             }
-            // (each thread reads back only its own column)
-            for (int t0 = tbeg; t0 < tend; t0 += 4) {
+            // (each thread reads back only its own column; the table
+            // offsets of its terms sit in registers, bo)
+#pragma unroll
+            for (int g = 0; g < kTcPartTerms; g += 4) {
+                const int t0 = tbeg + g;
                 float4 hi4, lo4;
                 float* hp = &hi4.x;
                 float* lp = &lo4.x;
@@ -593,7 +603,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         v = 1.f;
 #pragma unroll
                         for (int m = 0; m < kTcMaxM; ++m)
-                            if (m < M) v *= ptab[boff[t * M + m] + pt];
+                            if (m < M) v *= ptab[bo[g + r][m] + pt];
                     }
                     tf32_split(v, hp[r], lp[r]);
                 }
