@@ -141,3 +141,23 @@ def test_compare_fingers_on_synthetic_fields(tmp_path):
     assert out["plane_counts_top_down"]["a"] == out["plane_counts_top_down"]["b"]
     assert max(out["plane_counts_top_down"]["a"]) == 5
     assert out["var_level_set"] == {"level": 0.05, "a": 100, "b": 40, "both": 40}
+
+
+def test_reference_arm_line_on_a_tiny_grid():
+    """bench.py --impl reference on a 4x4x2 grid with 2 worker processes: one
+    JSON line with the reference keys (impl, cpu_baseline with its cores and
+    sample, an e2e object with zero copy bytes) and a positive rate."""
+    import json
+    import os
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--grid", "4", "4", "2",
+                          "--steps", "3", "--warmup", "1", "--cpu-workers", "2"],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == 2 and line["cpu_baseline"]["kind"] == "oracle"
+    assert "4 sample-steps" in line["cpu_baseline"]["sample"]   # 3 steps -> 2 whole rounds of 2
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["higher_is_better"] is True and line["unit"] == bench.UNIT
