@@ -511,8 +511,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc_ld32(ta + h + 32, v1);
                     tc_wait_ld();
                     if (valid == kTcCols) {
+                        // four independent partial counts: no serial chain of
+                        // dependent adds
+                        unsigned cq[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                        for (int r = 0; r < 32; ++r) c += (v0[r] > thr) + (v1[r] > thr);
+                        for (int r = 0; r < 32; ++r)
+                            cq[r & 3] += (unsigned)(v0[r] > thr) + (unsigned)(v1[r] > thr);
+                        c += (cq[0] + cq[1]) + (cq[2] + cq[3]);
                     } else {  // the last, ragged chunk
 #pragma unroll
                         for (int r = 0; r < 32; ++r) {
