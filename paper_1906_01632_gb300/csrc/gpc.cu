@@ -392,11 +392,63 @@ __device__ __forceinline__ void tc_st16(unsigned taddr, const float* v)
 constexpr int kTcTiles = 2;
 
 constexpr int kTcCountWarps = 4;   // one per TMEM lane quarter
+// Degree of variable m in term t of the total-degree-4 basis in 3 variables,
+// in the order elder_gpc_indices gives it (total degree ascending, then the
+// degree vector lexicographically ascending); -1 past its 35 terms.
+__host__ __device__ constexpr int canon_deg(int t, int m)
+{
+    int q = 0;
+    for (int s = 0; s <= 4; ++s)
+        for (int a = 0; a <= s; ++a)
+            for (int b = 0; b <= s - a; ++b) {
+                if (q == t) return m == 0 ? a : (m == 1 ? b : s - a - b);
+                ++q;
+            }
+    return -1;
+}
+constexpr int kCanonT = 35;
+
+// One step of the Legendre recurrence, (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1},
+// with the ratios as constants (the same arithmetic in both basis builders).
+__device__ __forceinline__ float leg_next(int k, float x, float p0, float pm1)
+{
+    return fmaf((float(2 * k + 1) / float(k + 1)) * x, p0, -(float(k) / float(k + 1)) * pm1);
+}
+
 constexpr int kTcSplit = 3;        // basis builders per sample (12 of the 36 terms each)
 constexpr int kTcProdWarps = 4 * kTcSplit;
 constexpr int kTcPartTerms = kTcTP / kTcSplit;  // terms per basis builder
 static_assert(kTcTP % (4 * kTcSplit) == 0, "whole 4-term groups per basis builder");
 constexpr int kTcThreads = 32 * (kTcCountWarps + kTcProdWarps + 1);
+
+// The basis builder's terms for the total-degree-4 basis in 3 variables in
+// canonical order: part PART holds terms 12 PART .. 12 PART + 11, whose
+// degrees are compile-time constants, so that each basis value is a product
+// of the sample's Legendre values in registers, P[m][k] = P_k(theta_m),
+// formed in the same order as the general builder, (P_a P_b) P_c.
+template <int PART>
+__device__ __forceinline__ void canon_build(const float (&P)[3][5], bool ok, unsigned char* Bs,
+                                            int col)
+{
+#pragma unroll
+    for (int g = 0; g < kTcPartTerms; g += 4) {
+        const int t0 = PART * kTcPartTerms + g;
+        float4 hi4, lo4;
+        float* hp = &hi4.x;
+        float* lp = &lo4.x;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int t = t0 + r;
+            float v = 0.f;
+            if (t < kCanonT && ok)
+                v = (P[0][canon_deg(t, 0)] * P[1][canon_deg(t, 1)]) * P[2][canon_deg(t, 2)];
+            tf32_split(v, hp[r], lp[r]);
+        }
+        *reinterpret_cast<float4*>(Bs + tc_off(col, t0)) = hi4;
+        *reinterpret_cast<float4*>(Bs + tc_off(col, kTcTP + t0)) = lo4;
+        *reinterpret_cast<float4*>(Bs + tc_off(col, 2 * kTcTP + t0)) = hi4;
+    }
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gpc_exceed_tc(int M, int T, const int32_t* __restrict__ beta, int maxdeg, int N,
@@ -552,6 +604,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int m = 0; m < kTcMaxM; ++m)
                 bo[r][m] = (tbeg + r < T && m < M) ? boff[(tbeg + r) * M + m] : 0;
+        // the total-degree-4 basis in 3 variables in canonical order takes
+        // the register builder (canon_build); any other basis the table
+        bool canon = M == 3 && T == kCanonT && maxdeg == 4;
+        for (int e = 0; canon && e < kCanonT * 3; ++e)
+            canon = beta[e] == canon_deg(e / 3, e % 3);
         // the next chunk's sample coordinates are loaded one chunk ahead
         float xn[kTcMaxM];
         auto load_theta = [&](int i) {
@@ -571,6 +628,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (i >= 2 && !mbar_wait(empty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
             const int j = (c0 + i) * kTcCols + col;
             const bool ok = j < Ns;
+            if (canon) {
+                float P[3][5];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float x = xc[m];
+                    float pm1 = 1.f, p0 = x;
+                    P[m][0] = 1.f;
+                    P[m][1] = x;
+#pragma unroll
+                    for (int k = 1; k < 4; ++k) {
+                        const float p1 = leg_next(k, x, p0, pm1);
+                        P[m][k + 1] = p1;
+                        pm1 = p0;
+                        p0 = p1;
+                    }
+                }
+                if (part == 0) canon_build<0>(P, ok, Bs, col);
+                else if (part == 1) canon_build<1>(P, ok, Bs, col);
+                else canon_build<2>(P, ok, Bs, col);
+                fence_async_shared();
+                mbar_arrive(full0 + 8 * b);
+                continue;
+            }
 #pragma unroll
             for (int m = 0; m < kTcMaxM; ++m) {
                 if (m < M) {
@@ -583,8 +663,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int k = 1; k < kTcMaxDeg; ++k) {
                         if (k < maxdeg) {
-                            const float p1 = (float(2 * k + 1) / float(k + 1)) * x * p0 -
-                                             (float(k) / float(k + 1)) * pm1;
+                            const float p1 = leg_next(k, x, p0, pm1);
                             ptab[(m * (kTcMaxDeg + 1) + k + 1) * kTcSplit * kTcCols + pt] = p1;
                             pm1 = p0;
                             p0 = p1;

@@ -88,6 +88,24 @@ def test_exceedance_brackets_oracle(E, M, p, engine):
         assert np.abs(np.rint(cf * theta.shape[0]) - got).max() <= (hi - lo).max()
 
 
+def test_tensor_engine_basis_in_other_order(E):
+    """The total-degree-4 basis in 3 variables with its terms permuted (the
+    kernel builds the canonical order from registers and any other order from
+    the Legendre table): the count still lies in the oracle bracket, and
+    agrees with the canonical order but for samples inside the band."""
+    beta = G.multi_indices(3, 4)
+    rng = np.random.default_rng(31)
+    N = 300
+    deg = beta.sum(1)
+    coef = rng.standard_normal((beta.shape[0], N)) * (0.3 ** deg)[:, None]
+    coef[0] = rng.uniform(0.3, 0.7, N)
+    theta = rng.uniform(-1, 1, (20011, 3))
+    perm = rng.permutation(beta.shape[0])
+    got, lo, hi = _bracket_check(E, beta[perm], coef[perm], theta, 0.5, engine="tensor")
+    canon, _, _ = _bracket_check(E, beta, coef, theta, 0.5, engine="tensor")
+    assert np.abs(got - canon).max() <= (hi - lo).max()
+
+
 def test_exceedance_closed_form(E):
     """u_hat = theta_1 on a midpoint grid: exactly 35% exceed 0.3 (the FP32
     band is empty there: no grid point within 1e-6 of 0.3)."""
