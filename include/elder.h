@@ -363,7 +363,7 @@ int elder_profile(elder_ctx* ctx, int on);
  *   RESIDUAL 49 + 16 C/N         JACOBIAN 108 T + 108 Mz + 4 T + 17 + 16 C/N
  * (the Jacobian writes the Krylov and the multigrid copies of J and the
  * inverse diagonal blocks; the residual reads p, c, c_old, phi, K and writes
- * R).  Flops: the FP64 residual counts 326 C/N + 75 of its factored face
+ * R).  Flops: the FP64 residual counts 266 C/N + 75 of its factored face
  * form, the stencil products 216 + their vector terms.  Any output pointer
  * may be NULL.  Host outputs. */
 int elder_profile_read(const elder_ctx* ctx, int kernel_class,

@@ -151,12 +151,18 @@ __host__ __device__ inline CellGeom make_geom(const Grid& G)
 //   m = -(rho K kA_d) (g16_d + [d=z] g16h rho),  F = c_up m - rho phi dA_d gc16_d,
 //   rho = rho0 + drho32 sc16,
 // with g16, gc16, sc16 the 16x-weighted sums of the edge differences of p and
-// c and of the edge sums of c.
+// c and of the edge sums of c.  For c the three passes of (3,1) sums over the
+// cell's 2x2x2 values, Z = (W x W x W) c with W = [[3,1],[1,3]], give every
+// direction's sums at once: across a direction-d edge pair (A, B) the (3,1)
+// sum along d turns into Z_B - Z_A = 2 gc16 and Z_B + Z_A = 4 sc16, and the
+// powers of two sit in the constants (dA2 = dA / 2, drho128 = drho32 / 4,
+// exact scalings).  p keeps its per-direction differences, which are exact
+// (Sterbenz) for neighbouring values of the hydrostatic pressure.
 struct FluxConst {
-    double kA[3];   // A_d / (16 h_d mu)
-    double dA[3];   // Dm A_d / (16 h_d)
-    double g16h;    // 16 h_z g
-    double drho32;  // drho / 32 (sc16 = 32 c_ip)
+    double kA[3];    // A_d / (16 h_d mu)
+    double dA2[3];   // Dm A_d / (32 h_d)
+    double g16h;     // 16 h_z g
+    double drho128;  // drho / 128 (4 sc16 = 128 c_ip)
     // FP32 copies for the round-off scale (a magnitude)
     float kAf[3], dAf[3], g16hf, drho32f, rho0f;
 };
@@ -168,14 +174,15 @@ static FluxConst make_flux_const(const Grid& G, const Phys& ph)
     FluxConst f;
     for (int d = 0; d < 3; ++d) {
         f.kA[d] = cg.area[d] / (16.0 * h[d] * ph.mu);
-        f.dA[d] = ph.Dm * cg.area[d] / (16.0 * h[d]);
+        const double dA = ph.Dm * cg.area[d] / (16.0 * h[d]);
+        f.dA2[d] = 0.5 * dA;
         f.kAf[d] = (float)f.kA[d];
-        f.dAf[d] = (float)f.dA[d];
+        f.dAf[d] = (float)dA;
     }
     f.g16h = 16.0 * G.hz * ph.g;
-    f.drho32 = ph.drho / 32.0;
+    f.drho128 = ph.drho / 128.0;
     f.g16hf = (float)f.g16h;
-    f.drho32f = (float)f.drho32;
+    f.drho32f = (float)(ph.drho / 32.0);
     f.rho0f = (float)ph.rho0;
     return f;
 }
@@ -218,30 +225,64 @@ __device__ __forceinline__ void dir_sums(const R (&p8)[8], const R (&c8)[8], R (
     kron31(cs, sc);
 }
 
+// the 16x-weighted sums of the direction-D edge differences of p
+template <int D>
+__device__ __forceinline__ void dir_grad(const double (&p8)[8], double (&gp)[2][2])
+{
+    double dp[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+            dp[u][v] = p8[corner_of(D, u, v, 1)] - p8[corner_of(D, u, v, 0)];
+    kron31(dp, gp);
+}
+
+// Z = (W x W x W) x over the cell's corners L = x + 2 y + 4 z: a (3,1) pass
+// along each axis, (a, b) -> (2 a + (a + b), 2 b + (a + b))
+__device__ __forceinline__ void cube31(const double (&x)[8], double (&Z)[8])
+{
+#pragma unroll
+    for (int L = 0; L < 8; ++L) Z[L] = x[L];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int L = 0; L < 8; ++L)
+            if (!((L >> d) & 1)) {
+                const int H = L | (1 << d);
+                const double a = Z[L] + Z[H];
+                Z[L] = fma(2.0, Z[L], a);
+                Z[H] = fma(2.0, Z[H], a);
+            }
+}
+
 template <int D>
 __device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const double (&c8)[8],
-                                               const float (&pf)[8], const float (&cf)[8],
-                                               const Phys& ph, const FluxConst& fc, double Ke,
-                                               double phie, float Kf, float phif,
-                                               QF* __restrict__ out, size_t qs)
+                                               const double (&Zc)[8], const float (&pf)[8],
+                                               const float (&cf)[8], const Phys& ph,
+                                               const FluxConst& fc, double Ke, double phie,
+                                               float Kf, float phif, QF* __restrict__ out,
+                                               size_t qs)
 {
-    double gp[2][2], gc[2][2], sc[2][2];
-    dir_sums<double, D>(p8, c8, gp, gc, sc);
+    double gp[2][2];
+    dir_grad<D>(p8, gp);
     float gpf[2][2], gcf[2][2], scf[2][2];
     dir_sums<float, D>(pf, cf, gpf, gcf, scf);
-    const double kmuA = Ke * fc.kA[D], dA = phie * fc.dA[D];
+    const double kmuA = Ke * fc.kA[D], dA2 = phie * fc.dA2[D];
     const float kmuAf = Kf * fc.kAf[D], dAf = phif * fc.dAf[D];
 #pragma unroll
     for (int S_ = 0; S_ < 2; ++S_)
 #pragma unroll
         for (int T_ = 0; T_ < 2; ++T_) {
-            const double rho = fma(fc.drho32, sc[S_][T_], ph.rho0);
+            const double zA = Zc[corner_of(D, S_, T_, 0)], zB = Zc[corner_of(D, S_, T_, 1)];
+            // rho = rho0 + drho32 sc16 with 4 sc16 = zA + zB; dA gc16 = dA2 (zB - zA)
+            const double rho = fma(fc.drho128, zA + zB, ph.rho0);
             const double G = (D == 2) ? fma(fc.g16h, rho, gp[S_][T_]) : gp[S_][T_];
             const double m = -(rho * kmuA) * G;
             // upwind end from the sign bit (an integer test)
             const bool upA = __double2hiint(m) >= 0;
             const double cup = upA ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
-            const double F = fma(cup, m, -(rho * dA) * gc[S_][T_]);
+            const double F = fma(cup, m, -(rho * dA2) * (zB - zA));
             // rounding scale in FP32: the Darcy flux cancels grad p against rho g
             const float rhof = fmaf(fc.drho32f, scf[S_][T_], fc.rho0f);
             const float mm = rhof * kmuAf *
@@ -280,9 +321,11 @@ __global__ void __launch_bounds__(kBS)
     const float phif = d2f_trunc(phie), Kf = d2f_trunc(Ke);
     QF* out = qf + (size_t)s * 12 * G.C + e;
     const size_t qs = (size_t)G.C;
-    cell_dir_faces<0>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
-    cell_dir_faces<1>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
-    cell_dir_faces<2>(p8, c8, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
+    double Zc[8];
+    cube31(c8, Zc);
+    cell_dir_faces<0>(p8, c8, Zc, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
+    cell_dir_faces<1>(p8, c8, Zc, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
+    cell_dir_faces<2>(p8, c8, Zc, pf, cf, ph, fc, Ke, phie, Kf, phif, out, qs);
 }
 
 // Sum of the up to 4 quarter faces of the direction-D edge whose lower node

@@ -336,13 +336,15 @@ double model_flops(int cls, const Grid& G)
     case ELDER_K_SPMV: return 216 + 8;
     case ELDER_K_MGRES: return 216 + 2;
     case ELDER_K_RESIDUAL:
-        // FP64 flops (FMA = 2) of the quarter-face form.  Per cell and
-        // direction: 12 edge differences and sums, three (3,1) weight passes
-        // of 20, and per quarter face 8 (+2 on vertical edges) for rho, m, F;
-        // plus 6 per cell for the coefficients: 326.  Per node: 36 edge sums,
-        // 10 edge accumulations, 8 porosity sums and 21 for storage and the
-        // squared norm: 75.
-        return 326 * cells_per_node + 75;
+        // FP64 flops (FMA = 2) of the quarter-face form.  Per cell: for p
+        // and each direction 4 edge differences and one (3,1) weight pass of
+        // 20 (72); for c the three (3,1) passes over the cell's 8 values
+        // (60); per quarter face the sum and difference of the two weighted
+        // c values and 8 (+2 on vertical edges) for rho, m, F (128); 6 for
+        // the coefficients: 266.  Per node: 36 edge sums, 10 edge
+        // accumulations, 8 porosity sums and 21 for storage and the squared
+        // norm: 75.
+        return 266 * cells_per_node + 75;
     case ELDER_K_JACOBIAN: return 24 * (54 + 66) + 10;
     }
     return 0.0;
