@@ -609,13 +609,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bool canon = M == 3 && T == kCanonT && maxdeg == 4;
         for (int e = 0; canon && e < kCanonT * 3; ++e)
             canon = beta[e] == canon_deg(e / 3, e % 3);
-        // the next chunk's sample coordinates are loaded one chunk ahead
-        float xn[kTcMaxM];
+        // the next chunk's sample coordinates are loaded one chunk ahead and
+        // held in FP64 until that chunk: the FP32 conversion is their first
+        // use, so the load's latency hides behind a chunk of work
+        double xn[kTcMaxM];
         auto load_theta = [&](int i) {
             const int j = (c0 + i) * kTcCols + col;
 #pragma unroll
             for (int m = 0; m < kTcMaxM; ++m)
-                xn[m] = (i < nchunk && j < Ns && m < M) ? (float)theta[(size_t)j * M + m] : 0.f;
+                xn[m] = (i < nchunk && j < Ns && m < M) ? theta[(size_t)j * M + m] : 0.0;
         };
         load_theta(0);
         for (int i = 0; i < nchunk; ++i) {
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             unsigned char* Bs = Bs0 + b * kTcTileBytes;
             float xc[kTcMaxM];
 #pragma unroll
-            for (int m = 0; m < kTcMaxM; ++m) xc[m] = xn[m];
+            for (int m = 0; m < kTcMaxM; ++m) xc[m] = (float)xn[m];
             load_theta(i + 1);
             if (i >= 2 && !mbar_wait(empty0 + 8 * b, ((i >> 1) - 1) & 1, err, abort_flag)) break;
             const int j = (c0 + i) * kTcCols + col;
