@@ -256,6 +256,29 @@ __device__ __forceinline__ void cube31(const double (&x)[8], double (&Z)[8])
             }
 }
 
+// Mass flux m and salt flux F of the direction-D quarter face at transverse
+// position (S_, T_), from its edge's lower corner A = corner_of(D, S_, T_, 0)
+// to B; upA: c is upwinded from A.  gp: the direction's 16x-weighted p
+// differences; Zc: the cell's c cube transform; kmuA = K kA_d, dA2 =
+// phi dA2_d.
+template <int D>
+__device__ __forceinline__ void quarter_face(int S_, int T_, const double (&gp)[2][2],
+                                             const double (&c8)[8], const double (&Zc)[8],
+                                             const Phys& ph, const FluxConst& fc, double kmuA,
+                                             double dA2, double& m, double& F, bool& upA)
+{
+    const int A = corner_of(D, S_, T_, 0), B = corner_of(D, S_, T_, 1);
+    const double zA = Zc[A], zB = Zc[B];
+    // rho = rho0 + drho32 sc16 with 4 sc16 = zA + zB; dA gc16 = dA2 (zB - zA)
+    const double rho = fma(fc.drho128, zA + zB, ph.rho0);
+    const double G = (D == 2) ? fma(fc.g16h, rho, gp[S_][T_]) : gp[S_][T_];
+    m = -(rho * kmuA) * G;
+    // upwind end from the sign bit (an integer test)
+    upA = __double2hiint(m) >= 0;
+    const double cup = upA ? c8[A] : c8[B];
+    F = fma(cup, m, -(rho * dA2) * (zB - zA));
+}
+
 template <int D>
 __device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const double (&c8)[8],
                                                const double (&Zc)[8], const float (&pf)[8],
@@ -274,15 +297,9 @@ __device__ __forceinline__ void cell_dir_faces(const double (&p8)[8], const doub
     for (int S_ = 0; S_ < 2; ++S_)
 #pragma unroll
         for (int T_ = 0; T_ < 2; ++T_) {
-            const double zA = Zc[corner_of(D, S_, T_, 0)], zB = Zc[corner_of(D, S_, T_, 1)];
-            // rho = rho0 + drho32 sc16 with 4 sc16 = zA + zB; dA gc16 = dA2 (zB - zA)
-            const double rho = fma(fc.drho128, zA + zB, ph.rho0);
-            const double G = (D == 2) ? fma(fc.g16h, rho, gp[S_][T_]) : gp[S_][T_];
-            const double m = -(rho * kmuA) * G;
-            // upwind end from the sign bit (an integer test)
-            const bool upA = __double2hiint(m) >= 0;
-            const double cup = upA ? c8[corner_of(D, S_, T_, 0)] : c8[corner_of(D, S_, T_, 1)];
-            const double F = fma(cup, m, -(rho * dA2) * (zB - zA));
+            double m, F;
+            bool upA;
+            quarter_face<D>(S_, T_, gp, c8, Zc, ph, fc, kmuA, dA2, m, F, upA);
             // rounding scale in FP32: the Darcy flux cancels grad p against rho g
             const float rhof = fmaf(fc.drho32f, scf[S_][T_], fc.rho0f);
             const float mm = rhof * kmuAf *
@@ -1456,8 +1473,50 @@ namespace elder {
 // interior salt residuals.  partial: [S][3][nblk].
 // ---------------------------------------------------------------------------
 
+// Salt flux out of node (i, j, k) through the 3 quarter faces of cell
+// (i + OX, j + OY, k + OZ) on the boundary of the node's sub-control volume,
+// with the face arithmetic of k_cell_flux (quarter_face)
+template <int OX, int OY, int OZ>
+__device__ __forceinline__ double corner_salt_out(const Grid& G, const Phys& ph,
+                                                  const FluxConst& fc, int i, int j, int k,
+                                                  const double* __restrict__ phi,
+                                                  const double* __restrict__ K,
+                                                  const double* __restrict__ p,
+                                                  const double* __restrict__ c)
+{
+    const int ci = i + OX, cj = j + OY, ck = k + OZ;
+    if (ci < 0 || ci >= G.nx || cj < 0 || cj >= G.ny || ck < 0 || ck >= G.nz) return 0.0;
+    const int e = ci + G.nx * (cj + G.ny * ck);
+    const int sy = G.nx + 1, sz = (G.nx + 1) * (G.ny + 1);
+    const int base = ci + sy * cj + sz * ck;
+    double p8[8], c8[8];
+#pragma unroll
+    for (int L = 0; L < 8; ++L) {
+        const int off = (L & 1) + ((L >> 1) & 1) * sy + (L >> 2) * sz;
+        p8[L] = __ldg(p + base + off);
+        c8[L] = __ldg(c + base + off);
+    }
+    const double phie = __ldg(phi + e), Ke = __ldg(K + e);
+    double Zc[8];
+    cube31(c8, Zc);
+    constexpr int lx = -OX, ly = -OY, lz = -OZ;  // the node's corner of the cell
+    double out = 0.0, m, F, gp[2][2];
+    bool up;
+    // the node is the lower end of the face's edge along D (+F) or the upper (-F)
+    dir_grad<0>(p8, gp);
+    quarter_face<0>(ly, lz, gp, c8, Zc, ph, fc, Ke * fc.kA[0], phie * fc.dA2[0], m, F, up);
+    out += lx == 0 ? F : -F;
+    dir_grad<1>(p8, gp);
+    quarter_face<1>(lx, lz, gp, c8, Zc, ph, fc, Ke * fc.kA[1], phie * fc.dA2[1], m, F, up);
+    out += ly == 0 ? F : -F;
+    dir_grad<2>(p8, gp);
+    quarter_face<2>(lx, ly, gp, c8, Zc, ph, fc, Ke * fc.kA[2], phie * fc.dA2[2], m, F, up);
+    out += lz == 0 ? F : -F;
+    return out;
+}
+
 __global__ void __launch_bounds__(kBS)
-    k_mass_balance(Grid G, Phys ph, CellGeom cg, const uint8_t* __restrict__ bc,
+    k_mass_balance(Grid G, Phys ph, FluxConst fc, const uint8_t* __restrict__ bc,
                    const double* __restrict__ phi, const double* __restrict__ K,
                    const double* __restrict__ p, const double* __restrict__ c,
                    const double* __restrict__ c_old, double* __restrict__ partial)
@@ -1482,17 +1541,15 @@ __global__ void __launch_bounds__(kBS)
         m1 = phis * vscv * fma(ph.drho, cn, ph.rho0) * cn;
         m0 = phis * vscv * fma(ph.drho, co, ph.rho0) * co;
         if (bc[n] & BC_C) {
-            double Rp = 0.0, Rc = 0.0, ps = 0.0, Ap = 0.0, Ac = 0.0;
-            residual_cell<-1, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<0, -1, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<-1, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<0, 0, -1>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<-1, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<0, -1, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<-1, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
-            residual_cell<0, 0, 0>(G, ph, cg, i, j, k, phi, K, p, c, Rp, Rc, ps, Ap, Ac);
+            double Rc = corner_salt_out<-1, -1, -1>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<0, -1, -1>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<-1, 0, -1>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<0, 0, -1>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<-1, -1, 0>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<0, -1, 0>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<-1, 0, 0>(G, ph, fc, i, j, k, phi, K, p, c);
+            Rc += corner_salt_out<0, 0, 0>(G, ph, fc, i, j, k, phi, K, p, c);
             in = ph.dt * Rc;  // net salt flux out of this Dirichlet node
-
         }
     }
     const double t0 = block_sum(m0, red);
@@ -1511,8 +1568,8 @@ void launch_mass_balance(const Grid& G, const Phys& ph, const uint8_t* bc, const
 {
     count_launch(1);
     dim3 grid(nblocks(G.N), S);
-    k_mass_balance<<<grid, kBS, 0, st>>>(G, ph, make_geom(G), bc, phi, K, p, c, c_old,
-                                         partial);
+    k_mass_balance<<<grid, kBS, 0, st>>>(G, ph, make_flux_const(G, ph), bc, phi, K, p, c,
+                                         c_old, partial);
 }
 
 }  // namespace elder

@@ -110,6 +110,29 @@ __device__ __forceinline__ float d2f_trunc(double x)
     return __uint_as_float(bits);
 }
 
+// FP32 -> FP64 widening with integer operations (exact, like the
+// conversion instruction, which issues on the slow FP64 pipe on this part):
+// exponent rebiased by 1023 - 127, mantissa shifted up by 29 bits; signed
+// zeros in the integer path, subnormals, infinities and NaN by the
+// conversion instruction.
+__device__ __forceinline__ double f2d_exact(float x)
+{
+    const unsigned u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (a == 0u) return __longlong_as_double((long long)sign);
+    if (a < 0x00800000u || a >= 0x7F800000u) return (double)x;
+    return __longlong_as_double(
+        (long long)(sign | (((unsigned long long)a + (896ull << 23)) << 29)));
+}
+
+// |x| as its bit pattern, which orders like the magnitude; NaN maps to the
+// pattern of +inf
+__device__ __forceinline__ unsigned mag_bits(float x)
+{
+    const unsigned a = __float_as_uint(x) & 0x7FFFFFFFu;
+    return a > 0x7F800000u ? 0x7F800000u : a;
+}
+
 __host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
 {
     return i + (G.nx + 1) * (j + (G.ny + 1) * k);
@@ -182,6 +205,24 @@ __device__ __forceinline__ double block_sum(double v, double* smem32)
     if (threadIdx.x == 0) smem32[0] = t;
     __syncthreads();
     double r = smem32[0];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide maximum of unsigned values (integer pipe)
+__device__ __forceinline__ unsigned block_max(unsigned v, unsigned* smem32)
+{
+    v = __reduce_max_sync(0xffffffffu, v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem32[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    unsigned t = (threadIdx.x < nw) ? smem32[threadIdx.x] : 0u;
+    if (w == 0) t = __reduce_max_sync(0xffffffffu, t);
+    if (threadIdx.x == 0) smem32[0] = t;
+    __syncthreads();
+    unsigned r = smem32[0];
     __syncthreads();
     return r;
 }

@@ -12,6 +12,7 @@
 //
 // Solver vectors hold the unknowns of the interior system: Dirichlet
 // components are kept at 0 by masking every kernel's output.
+#include <type_traits>
 #include <cuda_pipeline.h>
 
 #include "kernels.h"
@@ -1136,6 +1137,35 @@ __global__ void __launch_bounds__(kBS)
     if (!ns[s].ls_active) return;
     const double lam = ns[s].lambda;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 correction: lambda is a power of two (1 halved by the line
+        // search), so lambda d is exact in FP32 (above 2^-126 in magnitude;
+        // below, it rounds to FP32's subnormals, far under the rounding of p
+        // and c) and its widening exact; the maxima of the magnitudes are
+        // integer maxima of their bit patterns.  Neither touches the FP64
+        // pipe, and the values equal the FP64 form's, lambda (double) d.
+        const float lamf = d2f_trunc(lam);
+        unsigned up = 0u, uc = 0u;
+        if (n < N) {
+            const size_t q = (size_t)s * N + n;
+            const V2<T> d = dx[q];
+            const float dpf = lamf * d.p, dcf = lamf * d.c;
+            pt[q] = p[q] + f2d_exact(dpf);
+            ct[q] = c[q] + f2d_exact(dcf);
+            // a non-finite correction must never meet the Newton stop: NaN
+            // enters the maxima as +inf
+            up = mag_bits(dpf);
+            uc = mag_bits(dcf);
+        }
+        unsigned* ured = reinterpret_cast<unsigned*>(red);
+        const unsigned t0 = block_max(up, ured);
+        const unsigned t1 = block_max(uc, ured);
+        if (threadIdx.x == 0) {
+            partial[((size_t)s * 2 + 0) * gridDim.x + blockIdx.x] = f2d_exact(__uint_as_float(t0));
+            partial[((size_t)s * 2 + 1) * gridDim.x + blockIdx.x] = f2d_exact(__uint_as_float(t1));
+        }
+        return;
+    }
     double mp = 0.0, mc = 0.0;
     if (n < N) {
         const size_t q = (size_t)s * N + n;
