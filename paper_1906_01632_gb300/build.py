@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libelder.so")
 UNITS = ["assembly.cu", "linalg.cu", "elder_api.cu", "gpc.cu", "ilu.cu"]
-HEADERS = ["common.cuh", "kernels.h"]
+HEADERS = ["bits.cuh", "common.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bits.cuh"
+
 namespace elder {
 
 // Division of a 32-bit unsigned dividend by a fixed divisor d through a
@@ -93,44 +95,6 @@ template <class M> __device__ __forceinline__ M mg_store(double v) { return M(v)
 template <> __device__ __forceinline__ __nv_bfloat16 mg_store<__nv_bfloat16>(double v)
 {
     return __float2bfloat16_rn(float(v));
-}
-
-// FP32 value of an FP64 number formed with integer operations only (on
-// GB300 an FP64-to-FP32 conversion issues on the slow FP64 pipe): the FP64
-// exponent rebiased, the top 23 mantissa bits kept (truncated, not rounded);
-// magnitudes below 2^-126 become 0, those from 2^128 up (and NaN) infinity.
-// For the residual's round-off scale, a magnitude needed to a few digits.
-__device__ __forceinline__ float d2f_trunc(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    const unsigned sign = hi & 0x80000000u;
-    unsigned bits = sign | ((unsigned)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    bits = e <= 896 ? sign : (e >= 1151 ? (sign | 0x7F800000u) : bits);
-    return __uint_as_float(bits);
-}
-
-// FP32 -> FP64 widening with integer operations (exact, like the
-// conversion instruction, which issues on the slow FP64 pipe on this part):
-// exponent rebiased by 1023 - 127, mantissa shifted up by 29 bits; signed
-// zeros in the integer path, subnormals, infinities and NaN by the
-// conversion instruction.
-__device__ __forceinline__ double f2d_exact(float x)
-{
-    const unsigned u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if (a == 0u) return __longlong_as_double((long long)sign);
-    if (a < 0x00800000u || a >= 0x7F800000u) return (double)x;
-    return __longlong_as_double(
-        (long long)(sign | (((unsigned long long)a + (896ull << 23)) << 29)));
-}
-
-// |x| as its bit pattern, which orders like the magnitude; NaN maps to the
-// pattern of +inf
-__device__ __forceinline__ unsigned mag_bits(float x)
-{
-    const unsigned a = __float_as_uint(x) & 0x7FFFFFFFu;
-    return a > 0x7F800000u ? 0x7F800000u : a;
 }
 
 __host__ __device__ inline int node_id(const Grid& G, int i, int j, int k)
