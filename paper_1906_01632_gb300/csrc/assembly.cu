@@ -131,9 +131,10 @@ __host__ __device__ inline CellGeom make_geom(const Grid& G)
 //
 // k_cell_flux: one thread per cell computes the 12 quarter faces of its
 // sub-control-volume boundary (one per cell edge): the 4 edge differences of
-// p and c and the 4 edge sums of c per direction are formed once and shared
-// by the 4 quarter faces of that direction, which only differ in their Q1
-// weights (9,3,3,1)/16.  Output: [S][12][C] records (mass flux m and salt
+// p per direction, and for c one cube transform of the cell's 8 values that
+// holds every direction's weighted edge differences and sums, are formed once
+// and shared by the quarter faces, which only differ in their Q1 weights
+// (9,3,3,1)/16.  Output: [S][12][C] records (mass flux m and salt
 // flux F from the edge's lower end A to its upper end B, and the magnitudes
 // of their terms, the round-off scale).
 // k_cell_residual: node n sums, for each direction, the 4 quarter faces of
