@@ -26,6 +26,18 @@ def test_multi_indices_match_oracle(E, rule, M, p):
     assert np.array_equal(E.elder_gpc_indices(M, p, rule), G.multi_indices(M, p, rule))
 
 
+def test_total_degree_4_basis_in_3_variables_is_in_canonical_order(E):
+    """The tensor-core count builds the total-degree-4 basis in 3 variables
+    from Legendre values in registers when the index set comes in this order
+    (total degree, then the first variable's degree, then the second's);
+    any other order takes the shared-memory table.  The library's index set
+    for (3, 4) must keep this order, so that the bench's surrogate takes the
+    register builder."""
+    want = [(a, b, s - a - b) for s in range(5) for a in range(s + 1) for b in range(s - a + 1)]
+    got = [tuple(int(v) for v in row) for row in E.elder_gpc_indices(3, 4)]
+    assert got == want
+
+
 def test_gpc_argument_errors(E):
     with pytest.raises(E.ElderError):
         E.elder_gauss_legendre(0)
